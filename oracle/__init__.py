@@ -1,0 +1,220 @@
+"""FP64 CPU oracle of the DOLINC stage (arXiv 2404.08952) — test infrastructure.
+
+Only tests, the smoke check and the benchmark's CPU-baseline leg use this package.
+It compiles `dolinc_oracle.c` with the host C compiler into `oracle/_build/` and
+calls it through ctypes.  It imports nothing from the CUDA library's package.
+"""
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SRC = [os.path.join(_HERE, "dolinc_oracle.c"), os.path.join(_HERE, "indicator_oracle.c")]
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+FLUX = {"upwind": 0, "burgers": 1, "rusanov": 2}
+
+
+def build(force=False):
+    """Compile the oracle shared library (plain C, -O2, no machine-specific flags)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = [s for s in _SRC if os.path.exists(s)]
+    stale = force or not os.path.exists(_LIB) or any(
+        os.path.getmtime(s) > os.path.getmtime(_LIB) for s in srcs)
+    if stale:
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            _declare(_lib)
+    return _lib
+
+
+class _Mesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_nodes", C.c_long), ("n_cells", C.c_long), ("n_faces", C.c_long),
+                ("nodes", C.c_void_p), ("face_node_off", C.c_void_p), ("face_nodes", C.c_void_p),
+                ("owner", C.c_void_p), ("neigh", C.c_void_p), ("shift", C.c_void_p)]
+
+
+class _Geom(C.Structure):
+    _fields_ = [("V", C.c_void_p), ("xc", C.c_void_p), ("S", C.c_void_p), ("xf", C.c_void_p),
+                ("w", C.c_void_p), ("d", C.c_void_p)]
+
+
+class _Scheme(C.Structure):
+    _fields_ = [("nv", C.c_int), ("k", C.c_int), ("r", C.c_int), ("n_diff", C.c_int), ("flux", C.c_int),
+                ("gamma", C.c_double), ("adv", C.c_double * 3), ("eno", C.c_int), ("troubled", C.c_void_p)]
+
+
+def _declare(L):
+    P = C.c_void_p
+    L.or_geometry.argtypes = [P, P]
+    L.or_differentials.argtypes = [P, P, C.c_int, C.c_int, P, P]
+    L.or_coeff.argtypes = [C.c_int, C.c_int, C.c_double, P]
+    L.or_phantoms.argtypes = [C.c_int, C.c_double, P, P, P]
+    L.or_face_values.argtypes = [P, P, P, P, P, P, P, P]
+    L.or_residual_T.argtypes = [P, P, P, P, P]
+    L.or_residual.argtypes = [P, P, P, P, P]
+    L.or_rk3_step.argtypes = [P, P, P, C.c_double, P]
+    L.or_rk3_stage.argtypes = [P, P, P, C.c_double, C.c_int, P, P, P]
+    if hasattr(L, "or_indicator_features"):
+        L.or_criterion.argtypes = [P, P, P, P, C.c_double, C.c_double, P]
+        L.or_indicator_features.argtypes = [P, P, P, P, C.c_double, P]
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def coeff(k, r, g):
+    """Eq coeff weights c_rj (j = 0..k-1) on cells growing by g."""
+    c = np.zeros(k)
+    if lib().or_coeff(k, r, float(g), _ptr(c)) != 0:
+        raise ValueError("bad stencil")
+    return c
+
+
+def phantoms(N, g, phi0, phi1):
+    """phi_n^(0), n = -N..N+1, from the two face cells' differentials (Eq diffDLC)."""
+    phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
+    phi1 = np.ascontiguousarray(phi1, dtype=np.float64)
+    out = np.zeros(2 * N + 2)
+    if lib().or_phantoms(N, float(g), _ptr(phi0), _ptr(phi1), _ptr(out)) != 0:
+        raise ValueError("bad order")
+    return out
+
+
+class Scheme:
+    """Scheme parameters.  Stencil (k, r): k cells starting at i-r.
+    n_diff: differential orders computed (>= what the stencil needs)."""
+
+    def __init__(self, k=3, r=1, n_diff=None, flux="upwind", nv=1, gamma=1.4, adv=(1.0, 1.0, 0.0), eno=0,
+                 troubled=None):
+        need = max(r, k - r - 2)
+        if eno:
+            need = max(need, 2)
+        self.k, self.r = k, r
+        self.n_diff = need if n_diff is None else n_diff
+        if self.n_diff < need:
+            raise ValueError("stencil (k=%d, r=%d) needs differentials through order %d" % (k, r, need))
+        self.flux, self.nv, self.gamma = flux, nv, gamma
+        self.adv = tuple(float(a) for a in adv) + (0.0,) * (3 - len(adv))
+        self.eno = eno
+        self.troubled = None if troubled is None else np.ascontiguousarray(troubled, dtype=np.uint8)
+
+    def _c(self):
+        s = _Scheme()
+        s.nv, s.k, s.r, s.n_diff, s.flux = self.nv, self.k, self.r, self.n_diff, FLUX[self.flux]
+        s.gamma = self.gamma
+        for i in range(3):
+            s.adv[i] = self.adv[i]
+        s.eno = self.eno
+        s.troubled = _ptr(self.troubled) if self.troubled is not None else None
+        return s
+
+
+class Oracle:
+    """Geometry plus the stage operators of one mesh (dict from `synth`)."""
+
+    def __init__(self, mesh):
+        self.dim = int(mesh["dim"])
+        self._keep = {}
+        for key, dt in (("nodes", np.float64), ("face_node_offsets", np.int64), ("face_nodes", np.int64),
+                        ("face_owner", np.int64), ("face_neighbour", np.int64),
+                        ("face_periodic_shift", np.float64)):
+            self._keep[key] = np.ascontiguousarray(mesh[key], dtype=dt)
+        k = self._keep
+        self.n_cells = int(mesh["cell_face_offsets"].shape[0] - 1)
+        self.n_faces = int(k["face_owner"].shape[0])
+        m = _Mesh()
+        m.dim = self.dim
+        m.n_nodes, m.n_cells, m.n_faces = k["nodes"].shape[0], self.n_cells, self.n_faces
+        m.nodes, m.face_node_off, m.face_nodes = _ptr(k["nodes"]), _ptr(k["face_node_offsets"]), _ptr(k["face_nodes"])
+        m.owner, m.neigh, m.shift = _ptr(k["face_owner"]), _ptr(k["face_neighbour"]), _ptr(k["face_periodic_shift"])
+        self._m = m
+        nc, nf = self.n_cells, self.n_faces
+        self.V = np.zeros(nc)
+        self.xc = np.zeros((nc, 3))
+        self.S = np.zeros((nf, 3))
+        self.xf = np.zeros((nf, 3))
+        self.w = np.zeros(nf)
+        self.d = np.zeros((nf, 3))
+        g = _Geom()
+        g.V, g.xc, g.S, g.xf, g.w, g.d = (_ptr(a) for a in (self.V, self.xc, self.S, self.xf, self.w, self.d))
+        self._g = g
+        if lib().or_geometry(C.byref(m), C.byref(g)) != 0:
+            raise MemoryError("oracle geometry")
+        self.owner = k["face_owner"]
+        self.neigh = k["face_neighbour"]
+
+    # differentials: list of arrays, order m -> [nv, n_cells, dim**m]
+    def differentials(self, u, N, nv=None):
+        u = np.ascontiguousarray(np.atleast_2d(u), dtype=np.float64)
+        nv = u.shape[0]
+        D = self.dim
+        sizes = [nv * self.n_cells * D ** m for m in range(N + 1)]
+        T = np.zeros(sum(sizes))
+        lib().or_differentials(C.byref(self._m), C.byref(self._g), nv, N, _ptr(u), _ptr(T))
+        out, o = [], 0
+        for m in range(N + 1):
+            out.append(T[o:o + sizes[m]].reshape(nv, self.n_cells, D ** m))
+            o += sizes[m]
+        return out, T
+
+    def face_values(self, u, scheme):
+        """(phiL, phiR, rL, rR): [nv, n_faces] owner-upwind / neighbour-upwind states
+        and the ENO3 stencil offsets chosen (-1 on boundary faces)."""
+        _, T = self.differentials(u, scheme.n_diff)
+        nv = scheme.nv
+        L = np.zeros((nv, self.n_faces))
+        R = np.zeros((nv, self.n_faces))
+        rL = np.zeros((nv, self.n_faces), dtype=np.int32)
+        rR = np.zeros((nv, self.n_faces), dtype=np.int32)
+        s = scheme._c()
+        lib().or_face_values(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(T), _ptr(L), _ptr(R),
+                             _ptr(rL), _ptr(rR))
+        return L, R, rL, rR
+
+    def residual(self, u, scheme):
+        u = np.ascontiguousarray(np.atleast_2d(u), dtype=np.float64)
+        R = np.zeros_like(u)
+        s = scheme._c()
+        if lib().or_residual(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(u), _ptr(R)) != 0:
+            raise MemoryError
+        return R
+
+    def rk3_step(self, u, scheme, dt):
+        u = np.array(np.atleast_2d(u), dtype=np.float64, order="C")
+        s = scheme._c()
+        if lib().or_rk3_step(C.byref(self._m), C.byref(self._g), C.byref(s), float(dt), _ptr(u)) != 0:
+            raise MemoryError
+        return u
+
+    def rk3_stage(self, u0, us, scheme, dt, stage):
+        u0 = np.ascontiguousarray(np.atleast_2d(u0), dtype=np.float64)
+        us = np.ascontiguousarray(np.atleast_2d(us), dtype=np.float64)
+        out = np.zeros_like(us)
+        s = scheme._c()
+        if lib().or_rk3_stage(C.byref(self._m), C.byref(self._g), C.byref(s), float(dt), int(stage),
+                              _ptr(u0), _ptr(us), _ptr(out)) != 0:
+            raise MemoryError
+        return out
+
+    def run(self, u, scheme, dt, steps):
+        for _ in range(steps):
+            u = self.rk3_step(u, scheme, dt)
+        return u

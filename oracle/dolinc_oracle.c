@@ -1,0 +1,505 @@
+/*
+ * Plain FP64 CPU oracle of one DOLINC explicit Runge-Kutta stage on an
+ * unstructured finite-volume mesh (arXiv 2404.08952).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load this file's library.  It shares no code with the CUDA
+ * library: it computes its own geometry, keeps FULL (unsymmetrised) Gauss tensors
+ * of every differential order, obtains far-field values by the paper's recursion
+ * in the paper's order, and builds reconstruction weights from the Lagrange
+ * primitive formula itself.  Loops are face-centric scatters written for reading,
+ * not for speed.
+ *
+ * Paper passages followed (section / equation of the paper):
+ *   Sec 2.1            owner/neighbour face addressing
+ *   Sec 2.2 Eqs 1-4    growth rate g, centre distance d, weight omega, g = omega/(1-omega)
+ *   Sec 2.3            central-differencing (Gauss + linear interpolation) gradient,
+ *                      Eq recursion, DOLINC differential definition, Eq diffDLC,
+ *                      first/second-order inversion (Eqs lCoeffDLC1 .. rCoeffDLC2)
+ *   Sec 2.4 Eq coeff   k-th order reconstruction weights c_rj on non-uniform cells
+ *   Sec 2.4            ENO3-DOLINC smoothness indicators
+ *   Sec 2.6            boundary handling (zero-gradient auxiliary cell)
+ *   Sec 3              third-order TVD (SSP) Runge-Kutta; upwind, local Lax-Friedrichs
+ *                      (Rusanov) and Roe fluxes
+ *
+ * Readings taken where the paper is silent (each is listed with its reason in the
+ * design notes): Euclidean distances in Eq 3; cell averages (Eq 5 read with the
+ * 1/dx factor); multi-dimensional differentials are the cell's m-fold Gauss tensor
+ * contracted m times with the face's d; zero-gradient boundary faces take the
+ * cell value as face value for every order; one flux point per face.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXD 3
+#define OR_MAXN 4      /* highest differential order */
+#define OR_MAXK 10     /* widest stencil: k <= 2N+2 */
+#define OR_MAXV 5
+
+typedef struct {
+    int dim;
+    long n_nodes, n_cells, n_faces;
+    const double *nodes;            /* [n_nodes][dim] */
+    const long *face_node_off;      /* [n_faces+1] */
+    const long *face_nodes;
+    const long *owner, *neigh;      /* neigh < 0: boundary face */
+    const double *shift;            /* [n_faces][dim] neighbour translation, may be NULL */
+} or_mesh;
+
+typedef struct {
+    double *V;    /* [n_cells]           cell volume (area in 2D) */
+    double *xc;   /* [n_cells][3]        cell centroid */
+    double *S;    /* [n_faces][3]        face area vector, out of the owner */
+    double *xf;   /* [n_faces][3]        face centroid (owner side) */
+    double *w;    /* [n_faces]           Eq 3 weight of the owner */
+    double *d;    /* [n_faces][3]        Eq 2 centre distance, owner -> neighbour */
+} or_geom;
+
+typedef struct {
+    int nv;           /* number of variables */
+    int k, r;         /* stencil: k cells starting at i-r (Eq coeff) */
+    int n_diff;       /* differential orders computed */
+    int flux;         /* 0 linear advection upwind, 1 Burgers Roe, 2 Euler Rusanov */
+    double gamma;     /* ratio of specific heats (Euler) */
+    double adv[3];    /* advection velocity (flux 0) */
+    int eno;          /* 0 fixed stencil, 1 ENO3 on every face, 2 ENO3 on faces touching a troubled cell */
+    const unsigned char *troubled;   /* [n_cells] for eno == 2 */
+} or_scheme;
+
+static int ipow(int b, int e) { int p = 1; while (e-- > 0) p *= b; return p; }
+
+static void vsub(const double *a, const double *b, double *o) { for (int k = 0; k < 3; ++k) o[k] = a[k] - b[k]; }
+static double vdot(const double *a, const double *b) { return a[0]*b[0] + a[1]*b[1] + a[2]*b[2]; }
+static double vnorm(const double *a) { return sqrt(vdot(a, a)); }
+static void vcross(const double *a, const double *b, double *o)
+{
+    o[0] = a[1]*b[2] - a[2]*b[1];
+    o[1] = a[2]*b[0] - a[0]*b[2];
+    o[2] = a[0]*b[1] - a[1]*b[0];
+}
+
+static void node3(const or_mesh *m, long n, double *x)
+{
+    x[0] = x[1] = x[2] = 0.0;
+    for (int k = 0; k < m->dim; ++k) x[k] = m->nodes[n * m->dim + k];
+}
+
+static void shift3(const or_mesh *m, long f, double *s)
+{
+    s[0] = s[1] = s[2] = 0.0;
+    if (m->shift && m->neigh[f] >= 0)
+        for (int k = 0; k < m->dim; ++k) s[k] = m->shift[f * m->dim + k];
+}
+
+/* Sub-triangles of a face, as seen from its owner: area vectors St and centroids ct.
+ * 2D: the face is an edge a->b with area vector (b_y-a_y, -(b_x-a_x)).
+ * 3D: a triangle is itself; a polygon is split into the triangles joining each
+ * edge to the mean of its nodes.  Returns the number of pieces. */
+static int face_pieces(const or_mesh *m, long f, double St[][3], double ct[][3])
+{
+    long o = m->face_node_off[f], n = m->face_node_off[f + 1] - o;
+    if (m->dim == 2) {
+        double a[3], b[3];
+        node3(m, m->face_nodes[o], a);
+        node3(m, m->face_nodes[o + 1], b);
+        St[0][0] = b[1] - a[1]; St[0][1] = -(b[0] - a[0]); St[0][2] = 0.0;
+        for (int k = 0; k < 3; ++k) ct[0][k] = 0.5 * (a[k] + b[k]);
+        return 1;
+    }
+    if (n == 3) {
+        double a[3], b[3], c[3], ab[3], ac[3];
+        node3(m, m->face_nodes[o], a);
+        node3(m, m->face_nodes[o + 1], b);
+        node3(m, m->face_nodes[o + 2], c);
+        vsub(b, a, ab); vsub(c, a, ac);
+        vcross(ab, ac, St[0]);
+        for (int k = 0; k < 3; ++k) { St[0][k] *= 0.5; ct[0][k] = (a[k] + b[k] + c[k]) / 3.0; }
+        return 1;
+    }
+    double mc[3] = {0, 0, 0}, p[3];
+    for (long e = 0; e < n; ++e) { node3(m, m->face_nodes[o + e], p); for (int k = 0; k < 3; ++k) mc[k] += p[k] / (double)n; }
+    for (long e = 0; e < n; ++e) {
+        double a[3], b[3], am[3], bm[3];
+        node3(m, m->face_nodes[o + e], a);
+        node3(m, m->face_nodes[o + (e + 1) % n], b);
+        vsub(a, mc, am); vsub(b, mc, bm);
+        vcross(am, bm, St[e]);
+        for (int k = 0; k < 3; ++k) { St[e][k] *= 0.5; ct[e][k] = (mc[k] + a[k] + b[k]) / 3.0; }
+    }
+    return (int)n;
+}
+
+/* Geometry (Sec 2.2).  Cells are the polyhedra (polygons) bounded by the face
+ * pieces above; a periodic face's neighbour side is the owner side moved by -shift. */
+int or_geometry(const or_mesh *m, or_geom *g)
+{
+    const int D = m->dim;
+    double (*St)[3] = malloc(sizeof(double[64][3]));
+    double (*ct)[3] = malloc(sizeof(double[64][3]));
+    double *cnt = calloc((size_t)m->n_cells, sizeof(double));
+    double *apex = calloc((size_t)m->n_cells * 3, sizeof(double));
+    if (!St || !ct || !cnt || !apex) return -1;
+    memset(g->V, 0, sizeof(double) * (size_t)m->n_cells);
+    memset(g->xc, 0, sizeof(double) * 3 * (size_t)m->n_cells);
+    for (long f = 0; f < m->n_faces; ++f) {
+        int np = face_pieces(m, f, St, ct);
+        double S[3] = {0, 0, 0}, xf[3] = {0, 0, 0}, area = 0.0;
+        for (int t = 0; t < np; ++t) {
+            double a = vnorm(St[t]);
+            for (int k = 0; k < 3; ++k) { S[k] += St[t][k]; xf[k] += a * ct[t][k]; }
+            area += a;
+        }
+        for (int k = 0; k < 3; ++k) { g->S[3*f + k] = S[k]; g->xf[3*f + k] = xf[k] / area; }
+    }
+    /* apex of each cell: mean of its face centroids in its own frame */
+    for (long f = 0; f < m->n_faces; ++f) {
+        long P = m->owner[f], N = m->neigh[f];
+        double s[3];
+        shift3(m, f, s);
+        for (int k = 0; k < 3; ++k) apex[3*P + k] += g->xf[3*f + k];
+        cnt[P] += 1.0;
+        if (N >= 0) {
+            for (int k = 0; k < 3; ++k) apex[3*N + k] += g->xf[3*f + k] - s[k];
+            cnt[N] += 1.0;
+        }
+    }
+    for (long c = 0; c < m->n_cells; ++c) for (int k = 0; k < 3; ++k) apex[3*c + k] /= cnt[c];
+    /* volumes and centroids from pyramids (apex, face piece) */
+    for (long f = 0; f < m->n_faces; ++f) {
+        int np = face_pieces(m, f, St, ct);
+        long P = m->owner[f], N = m->neigh[f];
+        double s[3];
+        shift3(m, f, s);
+        for (int side = 0; side < (N >= 0 ? 2 : 1); ++side) {
+            long c = side == 0 ? P : N;
+            double sg = side == 0 ? 1.0 : -1.0;
+            for (int t = 0; t < np; ++t) {
+                double cc[3], rel[3], St_out[3];
+                for (int k = 0; k < 3; ++k) { cc[k] = ct[t][k] - (side ? s[k] : 0.0); St_out[k] = sg * St[t][k]; }
+                vsub(cc, &apex[3*c], rel);
+                double vol = vdot(St_out, rel) / (double)D;
+                g->V[c] += vol;
+                for (int k = 0; k < 3; ++k) g->xc[3*c + k] += vol * (apex[3*c + k] + D * cc[k]) / (double)(D + 1);
+            }
+        }
+    }
+    for (long c = 0; c < m->n_cells; ++c) for (int k = 0; k < 3; ++k) g->xc[3*c + k] /= g->V[c];
+    /* Eq 3 weight and Eq 2 distance, Euclidean, with the periodic translation */
+    for (long f = 0; f < m->n_faces; ++f) {
+        long P = m->owner[f], N = m->neigh[f];
+        const double *xf = &g->xf[3*f];
+        if (N < 0) {
+            g->w[f] = 1.0;
+            for (int k = 0; k < 3; ++k) g->d[3*f + k] = 2.0 * (xf[k] - g->xc[3*P + k]);
+            continue;
+        }
+        double s[3], xN[3], a[3], b[3];
+        shift3(m, f, s);
+        for (int k = 0; k < 3; ++k) xN[k] = g->xc[3*N + k] + s[k];
+        vsub(xN, xf, a);
+        vsub(&g->xc[3*P], xf, b);
+        g->w[f] = vnorm(a) / (vnorm(b) + vnorm(a));
+        for (int k = 0; k < 3; ++k) g->d[3*f + k] = xN[k] - g->xc[3*P + k];
+    }
+    free(St); free(ct); free(cnt); free(apex);
+    return 0;
+}
+
+/* offset of differential order mm in the concatenated full-tensor buffer */
+static long toff(int D, int nv, long nc, int mm)
+{
+    long o = 0;
+    for (int j = 0; j < mm; ++j) o += (long)ipow(D, j);
+    return o * nv * nc;
+}
+
+/* DOLINC differentials, Sec 2.3: T^(0) is the cell average; T^(m) is the
+ * central-differencing (Gauss, linearly interpolated) gradient of T^(m-1):
+ *   T^(m)_c = (1/V_c) sum_f S_{c,f} (x) [ w T^(m-1)_c + (1-w) T^(m-1)_nb ].
+ * The new gradient index is the leading one.  Zero-gradient boundary faces carry
+ * the cell value (Sec 2.6).  Buffer: order m at toff(m), laid out [v][c][D^m]. */
+int or_differentials(const or_mesh *m, const or_geom *g, int nv, int N, const double *u, double *T)
+{
+    const int D = m->dim;
+    const long nc = m->n_cells;
+    memcpy(T, u, sizeof(double) * (size_t)nv * (size_t)nc);
+    for (int mm = 1; mm <= N; ++mm) {
+        const int Ain = ipow(D, mm - 1), Aout = ipow(D, mm);
+        const double *Ti = T + toff(D, nv, nc, mm - 1);
+        double *To = T + toff(D, nv, nc, mm);
+        memset(To, 0, sizeof(double) * (size_t)nv * (size_t)nc * (size_t)Aout);
+        for (long f = 0; f < m->n_faces; ++f) {
+            long P = m->owner[f], Q = m->neigh[f];
+            const double *S = &g->S[3*f];
+            double w = g->w[f];
+            for (int v = 0; v < nv; ++v)
+                for (int a = 0; a < Ain; ++a) {
+                    double tP = Ti[((long)v * nc + P) * Ain + a];
+                    double tf = Q >= 0 ? w * tP + (1.0 - w) * Ti[((long)v * nc + Q) * Ain + a] : tP;
+                    for (int k = 0; k < D; ++k) {
+                        To[((long)v * nc + P) * Aout + k * Ain + a] += S[k] * tf / g->V[P];
+                        if (Q >= 0) To[((long)v * nc + Q) * Aout + k * Ain + a] -= S[k] * tf / g->V[Q];
+                    }
+                }
+        }
+    }
+    return 0;
+}
+
+/* DOLINC differential of a cell along d (Sec 2.3):
+ * varphi^(m) = 2^m T_{j1..jm} d_j1 ... d_jm, summed over every index tuple. */
+static double contract(int D, int mm, const double *Tm, const double *d)
+{
+    int A = ipow(D, mm);
+    double s = 0.0;
+    for (int a = 0; a < A; ++a) {
+        double p = Tm[a];
+        int t = a;
+        for (int j = 0; j < mm; ++j) { p *= d[t % D]; t /= D; }
+        s += p;
+    }
+    return ldexp(s, mm);
+}
+
+/* Eq coeff: k-th order reconstruction weights at x_{i+1/2} from the cell averages
+ * of cells i-r .. i-r+k-1, on cells that grow by the constant factor g (Eq 1).
+ * Cell i has unit width, cell i+n width g^n; x_{i+1/2} = 0. */
+static double face_pos(double g, int n)   /* right face of cell i+n */
+{
+    double x = 0.0;
+    if (n >= 0) { for (int j = 1; j <= n; ++j) x += pow(g, j); }
+    else        { for (int j = n + 1; j <= 0; ++j) x -= pow(g, j); }
+    return x;
+}
+
+int or_coeff(int k, int r, double g, double *c)
+{
+    double x[OR_MAXK + 1];
+    if (k < 1 || k > OR_MAXK || r < 0 || r >= k) return -1;
+    for (int q = 0; q <= k; ++q) x[q] = face_pos(g, -r + q - 1);   /* x_{i-r+q-1/2} */
+    const double xf = 0.0;                                          /* x_{i+1/2} */
+    for (int j = 0; j < k; ++j) {
+        double s = 0.0;
+        for (int mq = j + 1; mq <= k; ++mq) {
+            double num = 0.0, den = 1.0;
+            for (int l = 0; l <= k; ++l) {
+                if (l == mq) continue;
+                double p = 1.0;
+                for (int q = 0; q <= k; ++q) if (q != mq && q != l) p *= (xf - x[q]);
+                num += p;
+                den *= (x[mq] - x[l]);
+            }
+            s += num / den;
+        }
+        c[j] = s * (x[j + 1] - x[j]);                               /* times dx_{i-r+j} */
+    }
+    return 0;
+}
+
+/* Far-field values by Eq diffDLC,
+ *   phi_{n+1}^(m) - g phi_{n-1}^(m) = g^n phi_n^(m+1) + (1-g) phi_n^(m),
+ * applied outward from the two face cells (n = 0, 1) in the paper's order:
+ * forward for n >= 2 (Eq recursion form), backward for n <= -1.
+ * phi0[m], phi1[m] (m = 0..N) are the upwind and downwind cells' differentials.
+ * out[n + N] = phi_n^(0) for n = -N .. N+1 (2N+2 values). */
+int or_phantoms(int N, double g, const double *phi0, const double *phi1, double *out)
+{
+    double tab[2 * OR_MAXN + 2][OR_MAXN + 1];
+    if (N < 0 || N > OR_MAXN) return -1;
+    const int o = N;              /* tab[n + o][m] */
+    for (int mm = 0; mm <= N; ++mm) { tab[o][mm] = phi0[mm]; tab[o + 1][mm] = phi1[mm]; }
+    for (int n = 2; n <= N + 1; ++n)               /* centre n-1 */
+        for (int mm = 0; mm <= N - (n - 1); ++mm)
+            tab[n + o][mm] = g * tab[n - 2 + o][mm] + pow(g, n - 1) * tab[n - 1 + o][mm + 1]
+                           + (1.0 - g) * tab[n - 1 + o][mm];
+    for (int n = -1; n >= -N; --n)                 /* centre n+1 */
+        for (int mm = 0; mm <= N + n; ++mm)
+            tab[n + o][mm] = (tab[n + 2 + o][mm] - pow(g, n + 1) * tab[n + 1 + o][mm + 1]
+                              - (1.0 - g) * tab[n + 1 + o][mm]) / g;
+    for (int n = -N; n <= N + 1; ++n) out[n + N] = tab[n + o][0];
+    return 0;
+}
+
+/* ENO3-DOLINC (Sec 2.4): classical two-level stencil growth with the paper's
+ * non-uniform divided-difference indicators.  Ties: level 2 keeps the upwind
+ * side {i-1, i}; level 3 keeps the centred stencil {i-1, i, i+1}.
+ * ph[n+2] = phi_n for n = -2..2.  Returns the chosen r (0, 1 or 2). */
+static int eno3_choose(double g, const double *ph)
+{
+    const double p_2 = ph[0], p_1 = ph[1], p0 = ph[2], p1 = ph[3], p2 = ph[4];
+    double d2l = g * (p0 - p_1), d2r = p1 - p0;
+    double dL = g * g * (p0 - (1.0 + g) * p_1 + g * p_2);
+    double dC = p1 - (1.0 + g) * p0 + g * p_1;
+    double dR = (p2 - (1.0 + g) * p1 + g * p0) / (g * g);
+    if (fabs(d2l) <= fabs(d2r)) return fabs(dL) < fabs(dC) ? 2 : 1;
+    return fabs(dR) < fabs(dC) ? 0 : 1;
+}
+
+/* Face value of one variable for one orientation (upwind cell i, downwind i+1). */
+static double reconstruct(const or_scheme *s, int N, double g, const double *phi0, const double *phi1, int use_eno,
+                          int *r_used)
+{
+    double ph[2 * OR_MAXN + 2], c[OR_MAXK];
+    or_phantoms(N, g, phi0, phi1, ph);
+    int k = s->k, r = s->r;
+    if (use_eno) { k = 3; r = eno3_choose(g, &ph[N - 2]); }
+    if (r_used) *r_used = r;
+    or_coeff(k, r, g, c);
+    double v = 0.0;
+    for (int j = 0; j < k; ++j) v += c[j] * ph[N + j - r];
+    return v;
+}
+
+/* Both orientations of every variable at face f: L = owner upwind, R = neighbour upwind. */
+static void face_states(const or_mesh *m, const or_geom *g, const or_scheme *s, const double *T,
+                        long f, double *UL, double *UR, int *rL, int *rR)
+{
+    const int D = m->dim, nv = s->nv, N = s->n_diff;
+    const long nc = m->n_cells;
+    long P = m->owner[f], Q = m->neigh[f];
+    if (Q < 0) {
+        for (int v = 0; v < nv; ++v) { UL[v] = UR[v] = T[(long)v * nc + P]; if (rL) rL[v] = rR[v] = -1; }
+        return;
+    }
+    double sh[3], xQ[3], dL[3], dR[3], a[3], b[3];
+    const double *xf = &g->xf[3*f];
+    shift3(m, f, sh);
+    for (int k = 0; k < 3; ++k) xQ[k] = g->xc[3*Q + k] + sh[k];
+    vsub(xQ, &g->xc[3*P], dL);                  /* owner upwind: d = x_{i+1} - x_i */
+    vsub(&g->xc[3*P], xQ, dR);                  /* neighbour upwind */
+    vsub(xQ, xf, a); vsub(xf, &g->xc[3*P], b);
+    double gL = vnorm(a) / vnorm(b);            /* Eq 4 from the owner */
+    double gR = vnorm(b) / vnorm(a);            /* Eq 4 from the neighbour */
+    int eno = s->eno == 1 || (s->eno == 2 && s->troubled && (s->troubled[P] || s->troubled[Q]));
+    for (int v = 0; v < nv; ++v) {
+        double pP[OR_MAXN + 1], pQ[OR_MAXN + 1], qP[OR_MAXN + 1], qQ[OR_MAXN + 1];
+        for (int mm = 0; mm <= N; ++mm) {
+            const double *Tm = T + toff(D, nv, nc, mm);
+            long A = ipow(D, mm);
+            pP[mm] = contract(D, mm, &Tm[((long)v * nc + P) * A], dL);
+            pQ[mm] = contract(D, mm, &Tm[((long)v * nc + Q) * A], dL);
+            qQ[mm] = contract(D, mm, &Tm[((long)v * nc + Q) * A], dR);
+            qP[mm] = contract(D, mm, &Tm[((long)v * nc + P) * A], dR);
+        }
+        UL[v] = reconstruct(s, N, gL, pP, pQ, eno, rL ? &rL[v] : NULL);
+        UR[v] = reconstruct(s, N, gR, qQ, qP, eno, rR ? &rR[v] : NULL);
+    }
+}
+
+static void euler_phys(int D, double gam, const double *U, const double *S, double *F, double *un, double *c)
+{
+    double rho = U[0], ke = 0.0, vn = 0.0, Sn = 0.0;
+    for (int k = 0; k < D; ++k) { double vk = U[1 + k] / rho; ke += vk * U[1 + k]; vn += vk * S[k]; Sn += S[k] * S[k]; }
+    double E = U[D + 1];
+    double p = (gam - 1.0) * (E - 0.5 * ke);
+    F[0] = rho * vn;
+    for (int k = 0; k < D; ++k) F[1 + k] = U[1 + k] * vn + p * S[k];
+    F[D + 1] = (E + p) * vn;
+    *un = vn / sqrt(Sn);
+    *c = sqrt(gam * p / rho);
+}
+
+/* Numerical flux through S (owner -> neighbour) from the two reconstructed states. */
+static void num_flux(int D, const or_scheme *s, const double *UL, const double *UR, const double *S, double *F)
+{
+    if (s->flux == 0) {
+        double an = 0.0;
+        for (int k = 0; k < D; ++k) an += s->adv[k] * S[k];
+        F[0] = an * (an >= 0.0 ? UL[0] : UR[0]);
+    } else if (s->flux == 1) {
+        double sg = 0.0;
+        for (int k = 0; k < D; ++k) sg += S[k];
+        double lam = 0.5 * (UL[0] + UR[0]) * sg;      /* Roe speed of f(u) = u^2/2 (1,..,1) */
+        double uu = lam >= 0.0 ? UL[0] : UR[0];
+        F[0] = 0.5 * uu * uu * sg;
+    } else {
+        double FL[OR_MAXV], FR[OR_MAXV], unL, unR, cL, cR;
+        euler_phys(D, s->gamma, UL, S, FL, &unL, &cL);
+        euler_phys(D, s->gamma, UR, S, FR, &unR, &cR);
+        double a = fmax(fabs(unL) + cL, fabs(unR) + cR);
+        double Sn = sqrt(vdot(S, S));
+        for (int v = 0; v < D + 2; ++v) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * a * Sn * (UR[v] - UL[v]);
+    }
+}
+
+/* Reconstructed face states of every face: [v][f] for L (owner upwind) and R. */
+int or_face_values(const or_mesh *m, const or_geom *g, const or_scheme *s, const double *T,
+                   double *phiL, double *phiR, int *rL, int *rR)
+{
+    const int nv = s->nv;
+    for (long f = 0; f < m->n_faces; ++f) {
+        double UL[OR_MAXV], UR[OR_MAXV];
+        int a[OR_MAXV], b[OR_MAXV];
+        face_states(m, g, s, T, f, UL, UR, a, b);
+        for (int v = 0; v < nv; ++v) {
+            phiL[(long)v * m->n_faces + f] = UL[v];
+            phiR[(long)v * m->n_faces + f] = UR[v];
+            if (rL) { rL[(long)v * m->n_faces + f] = a[v]; rR[(long)v * m->n_faces + f] = b[v]; }
+        }
+    }
+    return 0;
+}
+
+/* Residual R_c = -(1/V_c) sum_f (+-) F_f from differentials T (Sec 3). */
+int or_residual_T(const or_mesh *m, const or_geom *g, const or_scheme *s, const double *T, double *R)
+{
+    const int D = m->dim, nv = s->nv;
+    const long nc = m->n_cells;
+    memset(R, 0, sizeof(double) * (size_t)nv * (size_t)nc);
+    for (long f = 0; f < m->n_faces; ++f) {
+        long P = m->owner[f], Q = m->neigh[f];
+        double UL[OR_MAXV], UR[OR_MAXV], F[OR_MAXV];
+        face_states(m, g, s, T, f, UL, UR, NULL, NULL);
+        num_flux(D, s, UL, UR, &g->S[3*f], F);
+        for (int v = 0; v < nv; ++v) {
+            R[(long)v * nc + P] -= F[v] / g->V[P];
+            if (Q >= 0) R[(long)v * nc + Q] += F[v] / g->V[Q];
+        }
+    }
+    return 0;
+}
+
+static long tsize(int D, int nv, long nc, int N) { return toff(D, nv, nc, N + 1); }
+
+int or_residual(const or_mesh *m, const or_geom *g, const or_scheme *s, const double *u, double *R)
+{
+    double *T = malloc(sizeof(double) * (size_t)tsize(m->dim, s->nv, m->n_cells, s->n_diff));
+    if (!T) return -1;
+    or_differentials(m, g, s->nv, s->n_diff, u, T);
+    or_residual_T(m, g, s, T, R);
+    free(T);
+    return 0;
+}
+
+/* One step of the third-order TVD (SSP) Runge-Kutta scheme (Sec 3):
+ *   u1 = u + dt R(u);  u2 = 3/4 u + 1/4 (u1 + dt R(u1));  u' = 1/3 u + 2/3 (u2 + dt R(u2)). */
+int or_rk3_step(const or_mesh *m, const or_geom *g, const or_scheme *s, double dt, double *u)
+{
+    const long n = (long)s->nv * m->n_cells;
+    double *u1 = malloc(sizeof(double) * (size_t)n), *R = malloc(sizeof(double) * (size_t)n);
+    if (!u1 || !R) return -1;
+    or_residual(m, g, s, u, R);
+    for (long i = 0; i < n; ++i) u1[i] = u[i] + dt * R[i];
+    or_residual(m, g, s, u1, R);
+    for (long i = 0; i < n; ++i) u1[i] = 0.75 * u[i] + 0.25 * (u1[i] + dt * R[i]);
+    or_residual(m, g, s, u1, R);
+    for (long i = 0; i < n; ++i) u[i] = u[i] / 3.0 + 2.0 / 3.0 * (u1[i] + dt * R[i]);
+    free(u1); free(R);
+    return 0;
+}
+
+/* One stage as the fused GPU stage computes it: given the step's start u0 and the
+ * stage input us, return  a*u0 + b*(us + dt R(us))  with (a, b) = (0,1), (3/4,1/4), (1/3,2/3). */
+int or_rk3_stage(const or_mesh *m, const or_geom *g, const or_scheme *s, double dt, int stage,
+                 const double *u0, const double *us, double *out)
+{
+    static const double A[3] = {0.0, 0.75, 1.0 / 3.0}, B[3] = {1.0, 0.25, 2.0 / 3.0};
+    const long n = (long)s->nv * m->n_cells;
+    double *R = malloc(sizeof(double) * (size_t)n);
+    if (!R || stage < 0 || stage > 2) { free(R); return -1; }
+    or_residual(m, g, s, us, R);
+    for (long i = 0; i < n; ++i) out[i] = A[stage] * u0[i] + B[stage] * (us[i] + dt * R[i]);
+    free(R);
+    return 0;
+}
