@@ -1,0 +1,342 @@
+"""Benchmark of the DOLINC SSP-RK3 stage on one GB300 (or N replicas under torchrun).
+
+Workload (default): euler3d_tet64 — 64^3 hexes x 5 tetrahedra (1,310,720 cells),
++-15% node jitter, periodic, isentropic vortex, Rusanov flux, scheme order 4
+(stencil (4,1), differentials through order 3), FP32 differentials/reconstruction/
+flux with FP64 geometry master and FP64 state update.  A step is one SSP-RK3 time
+step (3 stages, each: differential passes + fused reconstruct/flux/residual/update).
+
+Metric: cell-updates per second per RK stage = cells * 3 * steps / time.
+The line also carries the FP64 GPU run of the same steps, the mixed-vs-FP64
+difference and the full-size error of one GPU stage against the FP64 oracle.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dolinc|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per RK stage; % HBM roofline; mixed vs FP64 GPU at stated L2 error"
+UNIT = "cell-updates/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _ncoef(dim, m):
+    return m + 1 if dim == 2 else (m + 1) * (m + 2) // 2
+
+
+def alg_bytes(kind, M, sch):
+    """Algorithmic bytes of one launch: every array the kernel needs read or written
+    once (neighbour re-reads served on chip), at the stored element widths and
+    without record padding.  kind: 'pack', 'diff<m>', 'stage'."""
+    nc, nf, ns, dim, nv = M.n_cells, M.n_faces, M.n_slots, M.dim, sch.nv
+    sg = 8 if sch.precision == "fp64" else 4
+
+    def sb(m):
+        return 8 if sch.precision == "fp64" else (2 if sch.precision == "fp32_bf16" and m >= 2 else 4)
+    if kind == "pack":
+        return nc * nv * (8 + sb(0))
+    if kind.startswith("diff"):
+        m = int(kind[4:])
+        data = nc * nv * (_ncoef(dim, m - 1) * sb(m - 1) + _ncoef(dim, m) * sb(m))
+        geo = nc * (4 * sg + 4) + ns * 4 * sg
+        return data + geo
+    NS = max(sch.r, sch.k - sch.r - 2, 1)
+    data = nc * nv * sum(_ncoef(dim, m) * sb(m) for m in range(NS + 1))
+    state = nc * nv * 8 * (5.0 / 3.0 + 1.0) + nc * nv * sb(0) * (2.0 / 3.0)   # u0/us reads, out write, next record
+    geo = nc * (4 + 4 * sg) + ns * 8 + nf * 8 * sg
+    return data + state + geo
+
+
+KINDS = ["pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces"]
+
+
+def run_dolinc(args):
+    import torch
+    import paper_2404_08952_gb300 as dg
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = synth.workload(args.workload, order=args.order, q=args.quad)
+    m, u0, dt = w["mesh"], w["u0"], w["dt"]
+    M = dg.Mesh(m, renumber="morton")
+    stream = torch.cuda.current_stream()
+    results = {}
+    launches_per_step = None
+    for prec in (args.precision, "fp64"):
+        sch = dg.Scheme(precision=prec, **w["scheme"])
+        ws = dg.workspace(M, sch)
+        u = torch.from_numpy(M.to_lib(u0)).cuda()
+        for _ in range(args.warmup):
+            dg.dolinc_rk_step(M, sch, dt, u, ws)
+        dg.dolinc_sync_status(M, ws)
+        dg.dolinc_profile_enable(M, True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with Clocks(local) as ck:
+            e0.record(stream)
+            for _ in range(args.steps):
+                dg.dolinc_rk_step(M, sch, dt, u, ws)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        kms, kn = dg.profile_read(M)
+        dg.dolinc_profile_enable(M, False)
+        dg.dolinc_sync_status(M, ws)
+        results[prec] = dict(ms=ms, state=u, kms=kms, kn=kn, clocks=ck.summary(), sch=sch, ws=ws)
+        if prec == args.precision:
+            launches_per_step = int(sum(kn)) / args.steps
+        if prec == args.precision and args.precision == "fp64":
+            break
+    main = results[args.precision]
+    cells = M.n_cells
+    total_cells = cells * world
+    ms_step = main["ms"] / args.steps
+    value = total_cells * 3 * args.steps / (main["ms"] / 1e3)
+    # dominant kernel and its roofline
+    kms, kn = main["kms"], main["kn"]
+    top = int(np.argmax(kms))
+    peak, peak_src = _peaks()
+    per_launch_ms = kms[top] / max(kn[top], 1)
+    bytes_alg = alg_bytes(KINDS[top], M, main["sch"])
+    achieved = bytes_alg / (per_launch_ms / 1e3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            tj = json.load(open(tfile))
+            key = "%s/%s/%s/order%d" % (args.workload, args.precision, KINDS[top], w["info"].get("order", 0))
+            traffic = tj.get(key)
+        except Exception:
+            traffic = None
+    kernels = {KINDS[i]: {"ms_per_launch": round(kms[i] / kn[i], 5), "launches": int(kn[i]),
+                          "share": round(kms[i] / sum(kms), 4),
+                          "alg_bytes": int(alg_bytes(KINDS[i], M, main["sch"])),
+                          "alg_GBs": round(alg_bytes(KINDS[i], M, main["sch"]) / (kms[i] / kn[i] / 1e3) / 1e9, 1)}
+               for i in range(len(KINDS)) if kn[i] > 0}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "cells": cells, "faces": M.n_faces,
+                   "scheme_order": w["info"].get("order"), "stencil_k_r": [w["scheme"]["k"], w["scheme"]["r"]],
+                   "n_diff": w["scheme"]["n_diff"], "precision": args.precision,
+                   "flux": w["scheme"]["flux"], "stages_per_step": 3,
+                   "l2_policy": "inputs larger than L2 (working set %.0f MB > 129 MB L2)" % (
+                       main["ws"].numel() / 2 ** 20),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": KINDS[top], "achieved": round(achieved, 1), "peak": peak,
+                     "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic, "alg_bytes_per_launch": int(bytes_alg),
+                     "ms_per_launch": round(per_launch_ms, 5)},
+        "kernels": kernels,
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "clocks": main["clocks"],
+    }
+    if "fp64" in results and args.precision != "fp64":
+        f = results["fp64"]
+        v64 = total_cells * 3 * args.steps / (f["ms"] / 1e3)
+        a = main["state"].double().cpu().numpy()
+        b = f["state"].cpu().numpy()
+        l2 = float(np.sqrt(((a - b) ** 2).sum(axis=1) / (b ** 2).sum(axis=1)).max())
+        line["fp64_gpu"] = {"value": v64, "ms_per_step": f["ms"] / args.steps,
+                            "speedup_mixed_vs_fp64": value / v64,
+                            "l2_rel_mixed_vs_fp64_after_steps": l2, "steps_compared": args.steps + args.warmup}
+    # e2e: the public call with host buffers, copies inside the timed region
+    sch = main["sch"]
+    ws = main["ws"]
+    uh = torch.from_numpy(M.to_lib(u0)).pin_memory()
+    ud = torch.empty_like(uh, device="cuda")
+    for _ in range(2):
+        ud.copy_(uh, non_blocking=True)
+        dg.dolinc_rk_step(M, sch, dt, ud, ws)
+        uh.copy_(ud, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ud.copy_(uh, non_blocking=True)
+        dg.dolinc_rk_step(M, sch, dt, ud, ws)
+        uh.copy_(ud, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ems = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ems], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ems = float(t.item())
+    nbytes = uh.numel() * 8
+    line["e2e"] = {"value": total_cells * 3 * args.steps / (ems / 1e3), "unit": UNIT,
+                   "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                   "ms_per_step": ems / args.steps}
+    # full-size accuracy of one stage against the FP64 oracle, and the CPU baseline
+    if rank == 0 and not args.no_oracle:
+        import oracle
+        O = oracle.Oracle(m)
+        osch = oracle.Scheme(**w["scheme"])
+        t0 = time.perf_counter()
+        ref = O.rk3_stage(u0, u0, osch, dt, 0)
+        tcpu = time.perf_counter() - t0
+        acc = {}
+        for prec, r in results.items():
+            out = torch.zeros_like(torch.from_numpy(u0)).cuda()
+            ud.copy_(torch.from_numpy(M.to_lib(u0)))
+            dg.dolinc_rk_stage(M, r["sch"], dt, 0, ud, ud, out, r["ws"])
+            got = M.from_lib(out.cpu().numpy())
+            inc, inc_ref = got - u0, ref - u0
+            acc[prec] = {"l2_rel_stage_increment": float(np.sqrt(((inc - inc_ref) ** 2).sum() / (inc_ref ** 2).sum())),
+                         "linf_rel_stage_increment": float(np.abs(inc - inc_ref).max() / np.abs(inc_ref).max())}
+        line["accuracy_vs_oracle"] = acc
+        line["cpu_baseline"] = {"value": cells / tcpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "one SSP-RK3 stage (stage 0) of the full %s workload (%d cells), "
+                                          "FP64 C oracle, single thread" % (args.workload, cells),
+                                "seconds": tcpu}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The oracle as the reference arm: host cores, a bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    w = synth.workload(args.workload, order=args.order, size=args.ref_size, q=args.quad)
+    O = oracle.Oracle(w["mesh"])
+    osch = oracle.Scheme(**w["scheme"])
+    u = w["u0"]
+    for _ in range(args.warmup):
+        O.rk3_stage(u, u, osch, w["dt"], 0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.rk3_stage(u, u, osch, w["dt"], 0)
+    t = time.perf_counter() - t0
+    cells = int(w["u0"].shape[1])
+    value = cells * args.steps / t
+    sample = ("one SSP-RK3 stage per step on the %s family at %d^3 hexes x 5 (%d cells), "
+              "FP64 C oracle, single thread" % (args.workload, args.ref_size, cells))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "cells": cells, "scheme_order": w["info"].get("order"),
+                   "precision": "fp64"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dolinc", choices=["dolinc", "reference"])
+    ap.add_argument("--workload", default="euler3d_tet64")
+    ap.add_argument("--order", type=int, default=4)
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp32_bf16"])
+    ap.add_argument("--quad", type=int, default=2, help="quadrature points per direction for initial averages")
+    ap.add_argument("--ref-size", type=int, default=20)
+    ap.add_argument("--no-oracle", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_dolinc(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * dolinc.h — C ABI of the GB300 DOLINC stage library (libdolinc.so).
+ *
+ * DOLINC (arXiv 2404.08952) lifts the far-field cells a high-order finite-volume
+ * reconstruction needs into "order-lifted" differentials stored in each cell, and
+ * inverts them exactly at every face.  One explicit Runge-Kutta stage here is:
+ *
+ *   1. differentials   T^(m)_c = (1/V_c) sum_f S_{c,f} (x) [w T^(m-1)_c + (1-w) T^(m-1)_nb],
+ *                      m = 1..n_diff, T^(0) = cell average            (Sec 2.3)
+ *   2. inversion       far-field averages phi_{-r}..phi_{k-r-1} from the two face cells'
+ *                      differentials phi^(m) = 2^m T^(m) : d^m by Eq diffDLC
+ *                      (first/second order: Eqs lCoeffDLC1 .. rCoeffDLC2)  (Sec 2.3)
+ *   3. reconstruction  phi_{i+1/2} = sum_j c_rj(g) phi_{i-r+j}, c_rj from Eq coeff (Sec 2.4)
+ *   4. flux            upwind (linear advection), Roe (Burgers), local Lax-Friedrichs /
+ *                      Rusanov (Euler)                                     (Sec 3)
+ *   5. residual and    R_c = -(1/V_c) sum_f (+-)F_f, third-order TVD (SSP) Runge-Kutta
+ *      update                                                              (Sec 3)
+ *
+ * Conventions shared by every entry point
+ *   - Status codes only; no exception crosses the ABI.  dolinc_last_error() gives the
+ *     calling thread's last message.
+ *   - Device buffers belong to the caller.  The library never frees them.  Arguments
+ *     named *_dev are device pointers on the current CUDA device; everything else is
+ *     host memory.  Calls are asynchronous on the given stream, except where noted.
+ *   - Cell fields are FP64, variables first: u[v * n_cells + c], in the LIBRARY's cell
+ *     order (see dolinc_mesh_permutation; renumber = 0 keeps the caller's order).
+ *   - Face fields are FP64 [v * n_faces + f] in the CALLER's face order and orientation.
+ *   - A mesh handle may be used by one stream at a time.
+ *   - Workspace: every compute entry point takes a caller-owned device buffer
+ *     (ws_dev, ws_bytes) at least dolinc_workspace_size() bytes, 256-byte aligned.
+ *     It is scratch: its contents between calls mean nothing, except that the
+ *     first 256 bytes hold the device status word read by dolinc_sync_status.
+ */
+#ifndef DOLINC_H
+#define DOLINC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *dolinc_stream;   /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    DOLINC_OK = 0,
+    DOLINC_ERR_INVALID_ARG = 1,     /* bad pointer, size, or scheme parameter */
+    DOLINC_ERR_MESH = 2,            /* mesh descriptor fails validation */
+    DOLINC_ERR_UNSUPPORTED = 3,     /* valid request this build does not implement */
+    DOLINC_ERR_CUDA = 4,            /* a CUDA runtime call failed (message has the CUDA error) */
+    DOLINC_ERR_DEVICE_TIMEOUT = 5,  /* a bounded device-side wait gave up */
+    DOLINC_ERR_NONFINITE = 6,       /* a stage produced NaN or Inf */
+    DOLINC_ERR_OOM = 7              /* device or host allocation failed */
+} dolinc_status;
+
+enum { DOLINC_FLUX_UPWIND = 0, DOLINC_FLUX_BURGERS = 1, DOLINC_FLUX_RUSANOV = 2 };
+enum { DOLINC_FP64 = 0, DOLINC_FP32 = 1, DOLINC_FP32_BF16 = 2 };
+enum { DOLINC_LIMIT_NONE = 0, DOLINC_LIMIT_ENO3_ALL = 1, DOLINC_LIMIT_ENO3_FLAGGED = 2 };
+enum { DOLINC_RENUMBER_NONE = 0, DOLINC_RENUMBER_MORTON = 1 };
+
+/* Mesh in owner/neighbour face form (Sec 2.1: a cell knows its neighbours only
+ * through faces).  All arrays are host memory; dolinc_mesh_create copies them.
+ *   nodes                [n_nodes][dim] coordinates
+ *   face_node_offsets    [n_faces+1] CSR into face_nodes
+ *   face_nodes           node ids, ordered so that the area vector points out of the
+ *                        owner: 2D edge a->b has area vector (b_y-a_y, -(b_x-a_x));
+ *                        3D polygon nodes are counter-clockwise seen from outside the
+ *                        owner.  A polygon with more than 3 nodes is the union of the
+ *                        triangles joining each edge to the mean of its nodes.
+ *   face_owner           [n_faces] owner cell
+ *   face_neighbour       [n_faces] neighbour cell, or -1 on a boundary face
+ *   face_periodic_shift  [n_faces][dim] translation carrying the neighbour cell next to
+ *                        the owner across a periodic face (0 elsewhere); NULL = none
+ *   boundary_kind        [n_faces] 0 interior/periodic, 1 zero-gradient (transmissive);
+ *                        NULL = all boundary faces zero-gradient
+ *   cell_face_offsets,   optional CSR cell -> faces (NULL to skip); when given, every
+ *   cell_faces           face must appear in its owner's and neighbour's lists
+ *   renumber             DOLINC_RENUMBER_NONE keeps the caller's cell order;
+ *                        DOLINC_RENUMBER_MORTON orders cells along a Morton curve of
+ *                        their centroids (better cache reuse of neighbour gathers)     */
+typedef struct {
+    int dim;                                   /* 2 or 3 */
+    int64_t n_nodes;
+    const double *nodes;
+    int64_t n_cells;
+    const int64_t *cell_face_offsets;
+    const int64_t *cell_faces;
+    int64_t n_faces;
+    const int64_t *face_node_offsets;
+    const int64_t *face_nodes;
+    const int64_t *face_owner;
+    const int64_t *face_neighbour;
+    const double *face_periodic_shift;
+    const int32_t *boundary_kind;
+    int renumber;
+} dolinc_mesh_desc;
+
+/* Scheme of one stage.
+ *   k, r        reconstruction stencil: k cells i-r .. i-r+k-1 (Eq coeff).  USR3 = (3,1),
+ *               CSR4 = (4,1), USR5 = (5,2), CSR6 = (6,2), second-order upwind = (2,1).
+ *               Needs differentials through order max(r, k-r-2) (Sec 2.3: r far cells
+ *               upwind need order r, k-r-1 cells downwind need order k-r-2).
+ *   n_diff      differential orders computed each stage (1..4), >= what (k, r) needs
+ *               (and >= 2 with an ENO3 limiter).  Orders above the need are computed
+ *               and stored but do not change the face values.
+ *   flux        DOLINC_FLUX_*; nv = 1 for UPWIND and BURGERS, nv = dim+2 for RUSANOV
+ *               (conserved rho, rho u.., rho E, reconstructed component-wise)
+ *   precision   DOLINC_FP64: all FP64.  DOLINC_FP32: differentials, reconstruction and
+ *               flux in FP32, geometry master and state update FP64.
+ *               DOLINC_FP32_BF16: as FP32 with differential orders >= 2 stored in BF16.
+ *   limiter     DOLINC_LIMIT_*: ENO3-DOLINC (Sec 2.4) on every face, or on faces touching
+ *               a cell flagged with dolinc_set_flags / dolinc_indicator_infer
+ *   gamma       ratio of specific heats (RUSANOV)
+ *   adv         advection velocity (UPWIND); Burgers flux is u^2/2 (1,..,1)          */
+typedef struct {
+    int k, r;
+    int n_diff;
+    int flux;
+    int nv;
+    int precision;
+    int limiter;
+    double gamma;
+    double adv[3];
+} dolinc_scheme;
+
+typedef struct dolinc_mesh dolinc_mesh;
+
+typedef struct {
+    int dim;
+    int64_t n_cells, n_faces, n_boundary_faces, n_slots;
+    double g_min, g_max;                       /* Eq 4 growth rates over interior faces */
+    double volume;                             /* sum of cell volumes */
+    double h_min;                              /* min over cells of V_c / max_f |S_f| */
+} dolinc_mesh_info;
+
+/* Validate and copy a mesh, compute its FP64 geometry (Sec 2.2 Eqs 1-4: volumes,
+ * centroids, area vectors, Euclidean weights w, growth rates g = w/(1-w), centre
+ * distances d), renumber, build the cell -> face slots and copy everything to the
+ * current device.  Synchronous.  *out is NULL on failure. */
+dolinc_status dolinc_mesh_create(const dolinc_mesh_desc *desc, dolinc_mesh **out);
+void dolinc_mesh_destroy(dolinc_mesh *mesh);
+dolinc_status dolinc_mesh_get_info(const dolinc_mesh *mesh, dolinc_mesh_info *info);
+/* new_of_old[caller cell] = library cell (host array of n_cells). */
+dolinc_status dolinc_mesh_permutation(const dolinc_mesh *mesh, int64_t *new_of_old);
+/* Host copies of the library's FP64 geometry, in library cell order and caller face
+ * order/orientation; any pointer may be NULL.  V [n_cells], xc [n_cells][3],
+ * S [n_faces][3], w [n_faces] (weight of the caller's owner), d [n_faces][3]. */
+dolinc_status dolinc_mesh_geometry(const dolinc_mesh *mesh, double *V, double *xc, double *S, double *w,
+                                   double *d);
+
+/* Bytes of workspace the compute entry points need for this scheme. */
+dolinc_status dolinc_workspace_size(const dolinc_mesh *mesh, const dolinc_scheme *scheme, size_t *bytes);
+
+/* Clears the device status word at the start of a new workspace (ws_dev, at least
+ * 256 bytes, 256-byte aligned).  Call once after allocating a workspace, before the
+ * first compute call that uses it; dolinc_sync_status clears it again after reading. */
+dolinc_status dolinc_workspace_init(void *ws_dev, size_t ws_bytes, dolinc_stream stream);
+
+/* Layout of the differential buffer of dolinc_differentials.  Order m (1..order)
+ * starts at element offset[m-1]; the record of cell c is `stride[m-1]` elements of
+ * `elem_bytes[m-1]` bytes (8 FP64, 4 FP32, 2 BF16) at offset + c*stride; inside it
+ * variable v's coefficients start at v*C_m, C_m = m+1 (2D) or (m+1)(m+2)/2 (3D).
+ * Coefficient q of order m multiplies the monomial d_x^a d_y^b d_z^c (a+b+c = m) with
+ * t = b+c, q = t(t+1)/2 + c (3D) or q = b (2D), so that
+ *   T^(m) : d^m = sum_q coef[q] * monomial_q(d),  phi^(m) = 2^m T^(m) : d^m.
+ * total_elems: size of the buffer in elements of the widest type (FP64 or FP32). */
+dolinc_status dolinc_diff_layout(const dolinc_mesh *mesh, const dolinc_scheme *scheme, int order,
+                                 int64_t *offset, int *stride, int *elem_bytes, int64_t *total_bytes);
+
+/* Differentials of orders 1..order (Sec 2.3) of the FP64 cell averages u_dev, in the
+ * scheme's precision, written to diff_dev with the dolinc_diff_layout layout. */
+dolinc_status dolinc_differentials(dolinc_mesh *mesh, const dolinc_scheme *scheme, const double *u_dev,
+                                   int order, void *diff_dev, void *ws_dev, size_t ws_bytes,
+                                   dolinc_stream stream);
+
+/* Left/right face states (Sec 2.3-2.4): face_L_dev[v*n_faces+f] is the reconstruction
+ * with the caller's owner as upwind cell i, face_R_dev with the neighbour upwind.
+ * Differentials are recomputed from u_dev.  Boundary faces return the cell value. */
+dolinc_status dolinc_reconstruct_faces(dolinc_mesh *mesh, const dolinc_scheme *scheme, const double *u_dev,
+                                       double *face_L_dev, double *face_R_dev, void *ws_dev, size_t ws_bytes,
+                                       dolinc_stream stream);
+
+/* Residual R_c = -(1/V_c) sum_f (+-) F_f of the FP64 cell averages u_dev. */
+dolinc_status dolinc_residual(dolinc_mesh *mesh, const dolinc_scheme *scheme, const double *u_dev,
+                              double *R_dev, void *ws_dev, size_t ws_bytes, dolinc_stream stream);
+
+/* One SSP-RK3 stage (Sec 3): out = a*u0 + b*(us + dt R(us)) with
+ * (a, b) = (0, 1), (3/4, 1/4), (1/3, 2/3) for stage 0, 1, 2.  out may alias us. */
+dolinc_status dolinc_rk_stage(dolinc_mesh *mesh, const dolinc_scheme *scheme, double dt, int stage,
+                              const double *u0_dev, const double *us_dev, double *out_dev, void *ws_dev,
+                              size_t ws_bytes, dolinc_stream stream);
+
+/* One full SSP-RK3 step of u_dev in place (three stages, each: n_diff differential
+ * passes + one fused reconstruction/flux/residual/update pass). */
+dolinc_status dolinc_rk_step(dolinc_mesh *mesh, const dolinc_scheme *scheme, double dt, double *u_dev,
+                             void *ws_dev, size_t ws_bytes, dolinc_stream stream);
+
+/* Cell flags for DOLINC_LIMIT_ENO3_FLAGGED: flags_dev [n_cells] uint8 (library order),
+ * non-zero = troubled.  The pointer is kept by the mesh until replaced or NULL. */
+dolinc_status dolinc_set_flags(dolinc_mesh *mesh, const uint8_t *flags_dev);
+
+/* Synchronises `stream`, reads and clears the device status word in ws_dev:
+ * DOLINC_ERR_NONFINITE if a stage wrote NaN/Inf since the last call,
+ * DOLINC_ERR_DEVICE_TIMEOUT if a bounded wait gave up, else DOLINC_OK. */
+dolinc_status dolinc_sync_status(dolinc_mesh *mesh, void *ws_dev, dolinc_stream stream);
+
+/* Per-kernel timing.  While enabled, every compute call on this mesh records CUDA
+ * events around each of its kernel launches, on the call's stream.  Kernel kinds:
+ * DOLINC_KERNEL_PACK (FP64 field -> order-0 record), DOLINC_KERNEL_DIFF1..DIFF4 (the
+ * differential pass producing order m), DOLINC_KERNEL_STAGE (reconstruction + flux +
+ * residual + update), DOLINC_KERNEL_FACES (dolinc_reconstruct_faces).
+ * dolinc_profile_enable resets the counters.  dolinc_profile_read waits for the
+ * recorded events and fills ms[DOLINC_KERNEL_COUNT] (summed device time) and
+ * launches[DOLINC_KERNEL_COUNT]; either pointer may be NULL. */
+enum { DOLINC_KERNEL_PACK = 0, DOLINC_KERNEL_DIFF1 = 1, DOLINC_KERNEL_DIFF2 = 2, DOLINC_KERNEL_DIFF3 = 3,
+       DOLINC_KERNEL_DIFF4 = 4, DOLINC_KERNEL_STAGE = 5, DOLINC_KERNEL_FACES = 6, DOLINC_KERNEL_COUNT = 7 };
+dolinc_status dolinc_profile_enable(dolinc_mesh *mesh, int enable);
+dolinc_status dolinc_profile_read(dolinc_mesh *mesh, double *ms, int64_t *launches);
+
+/* Message of the calling thread's last failing call ("" if none). */
+const char *dolinc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DOLINC_H */

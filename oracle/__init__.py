@@ -71,6 +71,7 @@ def _declare(L):
     L.or_residual.argtypes = [P, P, P, P, P]
     L.or_rk3_step.argtypes = [P, P, P, C.c_double, P]
     L.or_rk3_stage.argtypes = [P, P, P, C.c_double, C.c_int, P, P, P]
+    L.or_face_weights.argtypes = [P, P, P, P, P]
     if hasattr(L, "or_indicator_features"):
         L.or_criterion.argtypes = [P, P, P, P, C.c_double, C.c_double, P]
         L.or_indicator_features.argtypes = [P, P, P, P, C.c_double, P]
@@ -188,6 +189,16 @@ class Oracle:
         lib().or_face_values(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(T), _ptr(L), _ptr(R),
                              _ptr(rL), _ptr(rR))
         return L, R, rL, rR
+
+    def face_weights(self, scheme):
+        """DOLINC representation weights per face: (WL, WR) each [n_faces, 2, n_diff+1]
+        (upwind cell's W0[m], downwind cell's W1[m])."""
+        nw = 2 * (scheme.n_diff + 1)
+        WL = np.zeros((self.n_faces, nw))
+        WR = np.zeros((self.n_faces, nw))
+        s = scheme._c()
+        lib().or_face_weights(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(WL), _ptr(WR))
+        return WL.reshape(self.n_faces, 2, -1), WR.reshape(self.n_faces, 2, -1)
 
     def residual(self, u, scheme):
         u = np.ascontiguousarray(np.atleast_2d(u), dtype=np.float64)

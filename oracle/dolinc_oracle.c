@@ -503,3 +503,41 @@ int or_rk3_stage(const or_mesh *m, const or_geom *g, const or_scheme *s, double 
     free(R);
     return 0;
 }
+
+/* Conditioning of each face value: the weights W0[m], W1[m] (m = 0..N) of the DOLINC
+ * representation  phi_f = sum_m W0[m] phi_0^(m) + W1[m] phi_1^(m)  (Sec 2.4, Eq USR3
+ * generalised), obtained by running the oracle's own recursion (or_phantoms) on unit
+ * data and weighting with or_coeff.  Used by the tests to scale parity tolerances by
+ * sum |W| (large growth rates amplify rounding like g^N).  Output per face:
+ * WL[f][2(N+1)] for the owner-upwind orientation, WR for the neighbour-upwind one,
+ * W0 first then W1.  Boundary faces get W0[0] = 1. */
+int or_face_weights(const or_mesh *m, const or_geom *g, const or_scheme *s, double *WL, double *WR)
+{
+    const int N = s->n_diff, nw = 2 * (N + 1);
+    double c[OR_MAXK], e0[OR_MAXN + 1], e1[OR_MAXN + 1], ph[2 * OR_MAXN + 2];
+    for (long f = 0; f < m->n_faces; ++f) {
+        long P = m->owner[f], Q = m->neigh[f];
+        for (int o = 0; o < 2; ++o) {
+            double *W = (o == 0 ? WL : WR) + f * nw;
+            for (int i = 0; i < nw; ++i) W[i] = 0.0;
+            if (Q < 0) { W[0] = 1.0; continue; }
+            double sh[3], xQ[3], a[3], b[3];
+            const double *xf = &g->xf[3*f];
+            shift3(m, f, sh);
+            for (int k = 0; k < 3; ++k) xQ[k] = g->xc[3*Q + k] + sh[k];
+            vsub(xQ, xf, a); vsub(xf, &g->xc[3*P], b);
+            double gg = o == 0 ? vnorm(a) / vnorm(b) : vnorm(b) / vnorm(a);
+            or_coeff(s->k, s->r, gg, c);
+            for (int side = 0; side < 2; ++side)
+                for (int mm = 0; mm <= N; ++mm) {
+                    for (int q = 0; q <= N; ++q) { e0[q] = 0.0; e1[q] = 0.0; }
+                    if (side == 0) e0[mm] = 1.0; else e1[mm] = 1.0;
+                    or_phantoms(N, gg, e0, e1, ph);
+                    double w = 0.0;
+                    for (int j = 0; j < s->k; ++j) w += c[j] * ph[N + j - s->r];
+                    W[side * (N + 1) + mm] = w;
+                }
+        }
+    }
+    return 0;
+}

@@ -1,0 +1,300 @@
+"""Python binding of libdolinc (the GB300 DOLINC stage library, include/dolinc.h).
+
+Argument marshalling only: every step of the stage runs in the library's CUDA
+kernels.  Functions keep the C names (dolinc_mesh_create, dolinc_rk_step, ...);
+device buffers are torch CUDA tensors, streams are torch CUDA streams.  If the
+library is not built the import still works, but every call raises: there is no
+CPU fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdolinc.so")
+
+FLUX = {"upwind": 0, "burgers": 1, "rusanov": 2}
+PRECISION = {"fp64": 0, "fp32": 1, "fp32_bf16": 2}
+LIMITER = {"none": 0, "eno3_all": 1, "eno3_flagged": 2}
+RENUMBER = {"none": 0, "morton": 1}
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "MESH", 3: "UNSUPPORTED", 4: "CUDA", 5: "DEVICE_TIMEOUT",
+          6: "NONFINITE", 7: "OOM"}
+
+# every entry point declared in include/dolinc.h
+ABI_SYMBOLS = (
+    "dolinc_mesh_create", "dolinc_mesh_destroy", "dolinc_mesh_get_info", "dolinc_mesh_permutation",
+    "dolinc_mesh_geometry", "dolinc_workspace_size", "dolinc_workspace_init", "dolinc_diff_layout",
+    "dolinc_differentials", "dolinc_reconstruct_faces", "dolinc_residual", "dolinc_rk_stage",
+    "dolinc_rk_step", "dolinc_set_flags", "dolinc_sync_status", "dolinc_profile_enable",
+    "dolinc_profile_read", "dolinc_last_error",
+)
+KERNEL_KINDS = ("pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces")
+
+
+class DolincError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("dolinc %s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class _Desc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_nodes", C.c_int64), ("nodes", C.c_void_p), ("n_cells", C.c_int64),
+                ("cell_face_offsets", C.c_void_p), ("cell_faces", C.c_void_p), ("n_faces", C.c_int64),
+                ("face_node_offsets", C.c_void_p), ("face_nodes", C.c_void_p), ("face_owner", C.c_void_p),
+                ("face_neighbour", C.c_void_p), ("face_periodic_shift", C.c_void_p),
+                ("boundary_kind", C.c_void_p), ("renumber", C.c_int)]
+
+
+class _Scheme(C.Structure):
+    _fields_ = [("k", C.c_int), ("r", C.c_int), ("n_diff", C.c_int), ("flux", C.c_int), ("nv", C.c_int),
+                ("precision", C.c_int), ("limiter", C.c_int), ("gamma", C.c_double), ("adv", C.c_double * 3)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_cells", C.c_int64), ("n_faces", C.c_int64),
+                ("n_boundary_faces", C.c_int64), ("n_slots", C.c_int64), ("g_min", C.c_double),
+                ("g_max", C.c_double), ("volume", C.c_double), ("h_min", C.c_double)]
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libdolinc.so; raises if it has not been built (see __graft_entry__.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("libdolinc.so is not built (%s): run __graft_entry__.build()" % path)
+        L = C.CDLL(path)
+        P, S, I, D = C.c_void_p, C.c_size_t, C.c_int, C.c_double
+        sig = {
+            "dolinc_mesh_create": [P, P], "dolinc_mesh_destroy": [P], "dolinc_mesh_get_info": [P, P],
+            "dolinc_mesh_permutation": [P, P], "dolinc_mesh_geometry": [P, P, P, P, P, P],
+            "dolinc_workspace_size": [P, P, P], "dolinc_workspace_init": [P, S, P],
+            "dolinc_diff_layout": [P, P, I, P, P, P, P],
+            "dolinc_differentials": [P, P, P, I, P, P, S, P],
+            "dolinc_reconstruct_faces": [P, P, P, P, P, P, S, P],
+            "dolinc_residual": [P, P, P, P, P, S, P],
+            "dolinc_rk_stage": [P, P, D, I, P, P, P, P, S, P],
+            "dolinc_rk_step": [P, P, D, P, P, S, P],
+            "dolinc_set_flags": [P, P], "dolinc_sync_status": [P, P, P], "dolinc_last_error": [],
+            "dolinc_profile_enable": [P, I], "dolinc_profile_read": [P, P, P],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_char_p if name == "dolinc_last_error" else (None if name == "dolinc_mesh_destroy"
+                                                                        else C.c_int)
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        raise DolincError(status, load().dolinc_last_error().decode())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(a.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Scheme:
+    """dolinc_scheme.  precision: 'fp64' | 'fp32' | 'fp32_bf16'; limiter: 'none' |
+    'eno3_all' | 'eno3_flagged'."""
+
+    def __init__(self, k=3, r=1, n_diff=None, flux="upwind", nv=1, precision="fp64", limiter="none",
+                 gamma=1.4, adv=(1.0, 1.0, 0.0)):
+        need = max(r, k - r - 2, 2 if limiter != "none" else 1)
+        self.k, self.r = k, r
+        self.n_diff = need if n_diff is None else n_diff
+        self.flux, self.nv, self.precision, self.limiter = flux, nv, precision, limiter
+        self.gamma = gamma
+        self.adv = tuple(float(a) for a in adv) + (0.0,) * (3 - len(adv))
+
+    def c(self):
+        s = _Scheme()
+        s.k, s.r, s.n_diff, s.flux, s.nv = self.k, self.r, self.n_diff, FLUX[self.flux], self.nv
+        s.precision, s.limiter, s.gamma = PRECISION[self.precision], LIMITER[self.limiter], self.gamma
+        for i in range(3):
+            s.adv[i] = self.adv[i]
+        return s
+
+
+class Mesh:
+    """A library mesh handle built from a mesh dict (see synth.meshes)."""
+
+    def __init__(self, m, renumber="morton"):
+        L = load()
+        self._arrays = {}
+        for key, dt in (("nodes", np.float64), ("cell_face_offsets", np.int64), ("cell_faces", np.int64),
+                        ("face_node_offsets", np.int64), ("face_nodes", np.int64), ("face_owner", np.int64),
+                        ("face_neighbour", np.int64), ("face_periodic_shift", np.float64),
+                        ("boundary_kind", np.int32)):
+            if key in m and m[key] is not None:
+                self._arrays[key] = np.ascontiguousarray(m[key], dtype=dt)
+        a = self._arrays
+        d = _Desc()
+        d.dim = int(m["dim"])
+        d.n_nodes = a["nodes"].shape[0]
+        d.nodes = _ptr(a["nodes"])
+        d.n_cells = a["cell_face_offsets"].shape[0] - 1
+        d.cell_face_offsets = _ptr(a.get("cell_face_offsets"))
+        d.cell_faces = _ptr(a.get("cell_faces"))
+        d.n_faces = a["face_owner"].shape[0]
+        d.face_node_offsets = _ptr(a["face_node_offsets"])
+        d.face_nodes = _ptr(a["face_nodes"])
+        d.face_owner = _ptr(a["face_owner"])
+        d.face_neighbour = _ptr(a["face_neighbour"])
+        d.face_periodic_shift = _ptr(a.get("face_periodic_shift"))
+        d.boundary_kind = _ptr(a.get("boundary_kind"))
+        d.renumber = RENUMBER[renumber] if isinstance(renumber, str) else int(renumber)
+        h = C.c_void_p()
+        _check(L.dolinc_mesh_create(C.byref(d), C.byref(h)))
+        self.handle = h
+        info = _Info()
+        _check(L.dolinc_mesh_get_info(h, C.byref(info)))
+        self.dim, self.n_cells, self.n_faces = info.dim, info.n_cells, info.n_faces
+        self.n_boundary_faces, self.n_slots = info.n_boundary_faces, info.n_slots
+        self.g_min, self.g_max, self.volume, self.h_min = info.g_min, info.g_max, info.volume, info.h_min
+        perm = np.zeros(self.n_cells, dtype=np.int64)
+        _check(L.dolinc_mesh_permutation(h, _ptr(perm)))
+        self.perm = perm                              # library index of each caller cell
+        self._arrays = None                           # the library copied what it needs
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.dolinc_mesh_destroy(h)
+            self.handle = None
+
+    def to_lib(self, u):
+        """caller cell order -> library order (last axis)."""
+        out = np.empty_like(u)
+        out[..., self.perm] = u
+        return out
+
+    def from_lib(self, u):
+        return u[..., self.perm]
+
+    def geometry(self):
+        V = np.zeros(self.n_cells)
+        xc = np.zeros((self.n_cells, 3))
+        S = np.zeros((self.n_faces, 3))
+        w = np.zeros(self.n_faces)
+        d = np.zeros((self.n_faces, 3))
+        _check(load().dolinc_mesh_geometry(self.handle, _ptr(V), _ptr(xc), _ptr(S), _ptr(w), _ptr(d)))
+        return dict(V=V, xc=xc, S=S, w=w, d=d)
+
+
+def dolinc_workspace_size(mesh, scheme):
+    n = C.c_size_t()
+    s = scheme.c()
+    _check(load().dolinc_workspace_size(mesh.handle, C.byref(s), C.byref(n)))
+    return n.value
+
+
+def workspace(mesh, scheme, device="cuda", stream=None):
+    """A zero-status workspace tensor (uint8, 256-byte aligned) for this mesh and scheme."""
+    import torch
+    n = dolinc_workspace_size(mesh, scheme)
+    ws = torch.empty(n + 256, dtype=torch.uint8, device=device)
+    off = (-ws.data_ptr()) % 256
+    ws = ws[off:off + n]
+    _check(load().dolinc_workspace_init(_ptr(ws), n, _stream(stream)))
+    return ws
+
+
+def dolinc_diff_layout(mesh, scheme, order):
+    off = np.zeros(order, dtype=np.int64)
+    stride = np.zeros(order, dtype=np.int32)
+    eb = np.zeros(order, dtype=np.int32)
+    tot = C.c_int64()
+    s = scheme.c()
+    _check(load().dolinc_diff_layout(mesh.handle, C.byref(s), order, _ptr(off), _ptr(stride), _ptr(eb),
+                                     C.byref(tot)))
+    return off, stride, eb, tot.value
+
+
+def dolinc_differentials(mesh, scheme, u, order, diff, ws, stream=None):
+    s = scheme.c()
+    _check(load().dolinc_differentials(mesh.handle, C.byref(s), _ptr(u), int(order), _ptr(diff), _ptr(ws),
+                                       ws.numel(), _stream(stream)))
+
+
+def dolinc_reconstruct_faces(mesh, scheme, u, face_L, face_R, ws, stream=None):
+    s = scheme.c()
+    _check(load().dolinc_reconstruct_faces(mesh.handle, C.byref(s), _ptr(u), _ptr(face_L), _ptr(face_R),
+                                           _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def dolinc_residual(mesh, scheme, u, R, ws, stream=None):
+    s = scheme.c()
+    _check(load().dolinc_residual(mesh.handle, C.byref(s), _ptr(u), _ptr(R), _ptr(ws), ws.numel(),
+                                  _stream(stream)))
+
+
+def dolinc_rk_stage(mesh, scheme, dt, stage, u0, us, out, ws, stream=None):
+    s = scheme.c()
+    _check(load().dolinc_rk_stage(mesh.handle, C.byref(s), float(dt), int(stage), _ptr(u0), _ptr(us), _ptr(out),
+                                  _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def dolinc_rk_step(mesh, scheme, dt, u, ws, stream=None):
+    s = scheme.c()
+    _check(load().dolinc_rk_step(mesh.handle, C.byref(s), float(dt), _ptr(u), _ptr(ws), ws.numel(),
+                                 _stream(stream)))
+
+
+def dolinc_set_flags(mesh, flags):
+    _check(load().dolinc_set_flags(mesh.handle, _ptr(flags)))
+
+
+def dolinc_sync_status(mesh, ws, stream=None):
+    """Raises DolincError on a non-finite stage or a device timeout."""
+    _check(load().dolinc_sync_status(mesh.handle, _ptr(ws), _stream(stream)))
+
+
+def dolinc_profile_enable(mesh, enable=True):
+    _check(load().dolinc_profile_enable(mesh.handle, 1 if enable else 0))
+
+
+def dolinc_profile_read(mesh):
+    """(ms, launches) per kernel kind (KERNEL_KINDS order), waiting for recorded events."""
+    ms = np.zeros(len(KERNEL_KINDS))
+    n = np.zeros(len(KERNEL_KINDS), dtype=np.int64)
+    _check(load().dolinc_profile_read(mesh.handle, _ptr(ms), _ptr(n)))
+    return ms, n
+
+
+profile_read = dolinc_profile_read
+
+
+def diff_to_numpy(mesh, scheme, diff, order):
+    """Unpack a dolinc_differentials buffer into a list over m = 1..order of
+    arrays [nv, n_cells, C_m] (library cell order) of polynomial coefficients."""
+    import torch
+    off, stride, eb, _ = dolinc_diff_layout(mesh, scheme, order)
+    raw = diff.detach()
+    out = []
+    for m in range(1, order + 1):
+        Cm = m + 1 if mesh.dim == 2 else (m + 1) * (m + 2) // 2
+        b = int(eb[m - 1])
+        dt = {8: torch.float64, 4: torch.float32, 2: torch.bfloat16}[b]
+        start = int(off[m - 1]) * b
+        n = mesh.n_cells * int(stride[m - 1])
+        blk = raw[start:start + n * b].view(dt).reshape(mesh.n_cells, int(stride[m - 1]))
+        blk = blk[:, :scheme.nv * Cm].to(torch.float64).cpu().numpy()
+        out.append(blk.reshape(mesh.n_cells, scheme.nv, Cm).transpose(1, 0, 2).copy())
+    return out

@@ -1,0 +1,23 @@
+// Device-resident mesh tables read by the stage kernels (all owned by the library).
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+namespace dol {
+
+struct DevMesh {
+    int dim, n_cells, n_faces, n_slots;
+    const int32_t *off;          // [n_cells+1] slot ranges
+    const int2 *slot2;           // [n_slots] (neighbour cell, slot word)
+    const double *slotk64;       // [n_slots][4] ((1-w_c) S_{c,f} / V_c, neighbour id bits)
+    const float *slotk32;
+    const double *cellk64;       // [n_cells][4] (sum_f w_c S_{c,f} / V_c, 1/V_c)
+    const float *cellk32;
+    const double *face64;        // [n_faces][8] (d, g, S, |S|), internal orientation
+    const float *face32;
+    const int32_t *fo, *fn;      // [n_faces] internal owner / neighbour (-1 boundary)
+    const int32_t *face_ext;     // [n_faces] caller face id
+    const int8_t *face_flip;     // [n_faces] 1 if the caller orientation is reversed
+};
+
+}  // namespace dol

@@ -1,0 +1,369 @@
+// DOLINC stage kernels for sm_103a.  One thread per cell; each cell gathers over its
+// own face slots, so no kernel uses atomics on field data.
+//
+//   k_pack   FP64 cell averages [v][c]  ->  order-0 record (bulk precision, per cell)
+//   k_diff   order m-1 -> order m differential (Sec 2.3), the Gauss step on the
+//            polynomial coefficients:  p_m = w_c (S.d) p_{m-1,c} + sum_f k_f (S.d) p_{m-1,nb}
+//   k_stage  per face: contract both cells' differentials with d, invert + reconstruct
+//            both orientations (Secs 2.3-2.4), numerical flux (Sec 3), residual,
+//            then the SSP-RK3 combination in FP64 and the next order-0 record.
+//            A face is evaluated identically from its two cells (canonical
+//            owner -> neighbour orientation, same operands, same order), so the two
+//            contributions cancel exactly in the sum over cells.
+//   k_faces  face states written in the caller's face order (diagnostic entry point)
+#pragma once
+#include "common.cuh"
+#include "device_mesh.hpp"
+
+namespace dol {
+
+enum { PREC_F64 = 0, PREC_F32 = 1, PREC_BF16 = 2 };
+
+template <int PREC> struct PrecT;
+template <> struct PrecT<PREC_F64> { using R = double; using T0 = double; using TH = double; };
+template <> struct PrecT<PREC_F32> { using R = float; using T0 = float; using TH = float; };
+template <> struct PrecT<PREC_BF16> { using R = float; using T0 = float; using TH = __nv_bfloat16; };
+
+// storage type of order m
+template <int PREC, int M> struct OrdT { using T = typename std::conditional<(M >= 2), typename PrecT<PREC>::TH, typename PrecT<PREC>::T0>::type; };
+
+template <int DIM, int NV, int M, int PREC>
+DOL_HD constexpr int ord_stride() { return rec_stride(NV * ncoef(DIM, M), (int)sizeof(typename OrdT<PREC, M>::T)); }
+
+template <class R> struct Geo;
+template <> struct Geo<double> {
+    static __device__ __forceinline__ const double *slotk(const DevMesh &m) { return m.slotk64; }
+    static __device__ __forceinline__ const double *cellk(const DevMesh &m) { return m.cellk64; }
+    static __device__ __forceinline__ const double *face(const DevMesh &m) { return m.face64; }
+    static __device__ __forceinline__ int nb_of(double w) { return (int)__double_as_longlong(w); }
+};
+template <> struct Geo<float> {
+    static __device__ __forceinline__ const float *slotk(const DevMesh &m) { return m.slotk32; }
+    static __device__ __forceinline__ const float *cellk(const DevMesh &m) { return m.cellk32; }
+    static __device__ __forceinline__ const float *face(const DevMesh &m) { return m.face32; }
+    static __device__ __forceinline__ int nb_of(float w) { return __float_as_int(w); }
+};
+
+template <class R> __device__ __forceinline__ void ld4(const R *p, R &a, R &b, R &c, R &d)
+{
+    if constexpr (sizeof(R) == 4) {
+        float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+        a = v.x, b = v.y, c = v.z, d = v.w;
+    } else {
+        double2 v0 = __ldg(reinterpret_cast<const double2 *>(p));
+        double2 v1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+        a = v0.x, b = v0.y, c = v1.x, d = v1.y;
+    }
+}
+
+// ------------------------------------------------------------------ pack
+template <int NV, int PREC>
+__global__ void __launch_bounds__(256) k_pack(int n, const double *__restrict__ u, typename PrecT<PREC>::T0 *o0)
+{
+    using R = typename PrecT<PREC>::R;
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    R v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = (R)u[(long long)i * n + c];
+    store_rec<typename PrecT<PREC>::T0, NV, rec_stride(NV, (int)sizeof(typename PrecT<PREC>::T0))>(o0, c, v);
+}
+
+// ------------------------------------------------------------------ differential pass
+template <int DIM, int NV, int M, int PREC>
+__global__ void __launch_bounds__(256) k_diff(DevMesh mesh, const void *__restrict__ in_v, void *__restrict__ out_v)
+{
+    using R = typename PrecT<PREC>::R;
+    using TI = typename OrdT<PREC, M - 1>::T;
+    using TO = typename OrdT<PREC, M>::T;
+    constexpr int CI = ncoef(DIM, M - 1), CO = ncoef(DIM, M);
+    constexpr int SI = ord_stride<DIM, NV, M - 1, PREC>(), SO = ord_stride<DIM, NV, M, PREC>();
+    const TI *in = static_cast<const TI *>(in_v);
+    TO *out = static_cast<TO *>(out_v);
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= mesh.n_cells) return;
+    R acc[NV * CO];
+#pragma unroll
+    for (int i = 0; i < NV * CO; ++i) acc[i] = (R)0;
+    R x[NV * CI];
+    R wx, wy, wz, iv;
+    ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, wx, wy, wz, iv);
+    load_rec<TI, NV * CI, SI, R>(in, c, x);
+    poly_mul_acc<DIM, NV, M, R>(acc, x, wx, wy, wz);
+    const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+    for (int s = s0; s < s1; ++s) {
+        R kx, ky, kz, kb;
+        ld4<R>(Geo<R>::slotk(mesh) + 4ll * s, kx, ky, kz, kb);
+        int nb = Geo<R>::nb_of(kb);
+        load_rec<TI, NV * CI, SI, R>(in, nb, x);
+        poly_mul_acc<DIM, NV, M, R>(acc, x, kx, ky, kz);
+    }
+    store_rec<TO, NV * CO, SO, R>(out, c, acc);
+}
+
+// ------------------------------------------------------------------ stage
+struct StageArgs {
+    const void *ord[MAXN + 1];   // order records 0..NS (order 0 = bulk copy of the stage input)
+    void *o0_next;               // order-0 record of the stage output (may be null)
+    const double *u0, *us;       // FP64 step start and stage input [v][c]
+    double *out;                 // FP64 output [v][c]: residual (mode 0) or stage value (mode 1)
+    double A, B, dt;             // out = A u0 + B (us + dt R)
+    unsigned *status;            // bit 0: non-finite output
+    int k, r, mode, flux;
+    double gamma, adv[3];
+    const uint8_t *flags;        // ENO3 on faces touching a flagged cell (null: none)
+    int eno_all;
+};
+
+// phi^(m) of every variable of cell X along the monomials of d (m = 0..NS)
+template <int DIM, int NV, int NS, int PREC, int M>
+__device__ __forceinline__ void contract_order(const StageArgs &a, int X, const typename PrecT<PREC>::R *mono,
+                                               typename PrecT<PREC>::R (*ph)[NS + 1])
+{
+    using R = typename PrecT<PREC>::R;
+    using T = typename OrdT<PREC, M>::T;
+    constexpr int C = ncoef(DIM, M);
+    R rec[NV * C];
+    load_rec<T, NV * C, ord_stride<DIM, NV, M, PREC>(), R>(static_cast<const T *>(a.ord[M]), X, rec);
+    constexpr int mo = ncum(DIM, M - 1);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        R s = (R)0;
+#pragma unroll
+        for (int q = 0; q < C; ++q) s = fma(rec[v * C + q], mono[mo + q], s);
+        ph[v][M] = s * (R)(1 << M);
+    }
+}
+
+template <int DIM, int NV, int NS, int PREC>
+__device__ __forceinline__ void contract_cell(const StageArgs &a, int X, const typename PrecT<PREC>::R *mono,
+                                              typename PrecT<PREC>::R (*ph)[NS + 1])
+{
+    using R = typename PrecT<PREC>::R;
+    {
+        R rec[NV];
+        load_rec<typename PrecT<PREC>::T0, NV, ord_stride<DIM, NV, 0, PREC>(), R>(
+            static_cast<const typename PrecT<PREC>::T0 *>(a.ord[0]), X, rec);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) ph[v][0] = rec[v];
+    }
+    if constexpr (NS >= 1) contract_order<DIM, NV, NS, PREC, 1>(a, X, mono, ph);
+    if constexpr (NS >= 2) contract_order<DIM, NV, NS, PREC, 2>(a, X, mono, ph);
+    if constexpr (NS >= 3) contract_order<DIM, NV, NS, PREC, 3>(a, X, mono, ph);
+    if constexpr (NS >= 4) contract_order<DIM, NV, NS, PREC, 4>(a, X, mono, ph);
+}
+
+// ENO3-DOLINC value of one variable (Sec 2.4): far values n = -2..2 by Eq diffDLC, the
+// paper's non-uniform indicators, then the k = 3 weights of the chosen stencil.
+template <int NS, class R>
+__device__ __forceinline__ R eno3_value(R g, const R *p0, const R *p1)
+{
+    static_assert(NS >= 2, "ENO3 needs second-order differentials");
+    // phi_{-1}^(m) (m = 0, 1), phi_{-2}, phi_2
+    R gi = (R)1 / g;
+    R m1_0 = gi * (p1[0] - p0[1] - ((R)1 - g) * p0[0]);
+    R m1_1 = gi * (p1[1] - p0[2] - ((R)1 - g) * p0[1]);
+    R m2 = gi * (p0[0] - gi * m1_1 - ((R)1 - g) * m1_0);
+    R p2 = g * p0[0] + g * p1[1] + ((R)1 - g) * p1[0];
+    R d2l = g * (p0[0] - m1_0), d2r = p1[0] - p0[0];
+    R dL = g * g * (p0[0] - ((R)1 + g) * m1_0 + g * m2);
+    R dC = p1[0] - ((R)1 + g) * p0[0] + g * m1_0;
+    R dR = (p2 - ((R)1 + g) * p1[0] + g * p0[0]) * gi * gi;
+    int r = (fabs(d2l) <= fabs(d2r)) ? (fabs(dL) < fabs(dC) ? 2 : 1) : (fabs(dR) < fabs(dC) ? 0 : 1);
+    // k = 3 weights on the geometric cells (closed forms of Eq coeff)
+    R g2 = g * g, G2 = (R)1 + g, G3 = (R)1 + g + g2;
+    if (r == 1) return (-g2 * g * m1_0 + g * ((R)1 + (R)2 * g + (R)2 * g2) * p0[0]) / (G2 * G3) + p1[0] / G3;
+    if (r == 0) return (g2 * p0[0]) / G3 + ((g2 + (R)2 * g + (R)2) * p1[0] - p2) / (G2 * G3);
+    return (g2 * g * m2) / G3 + (-g * (g2 * g + (R)3 * g2 + (R)2 * g + (R)1) * m1_0 +
+                                 ((R)3 * g2 * g + (R)4 * g2 + (R)3 * g + (R)1) * p0[0]) / (G2 * G3);
+}
+
+// Both face states (or the upwind one only for linear advection) of face record fr.
+template <int DIM, int NV, int NS, int PREC, bool UPWIND_ONLY>
+__device__ __forceinline__ void face_states(const StageArgs &a, const typename PrecT<PREC>::R *fr, int P, int N,
+                                            bool eno, typename PrecT<PREC>::R *UL, typename PrecT<PREC>::R *UR,
+                                            bool want_left)
+{
+    using R = typename PrecT<PREC>::R;
+    constexpr int NM = ncum(DIM, NS);
+    R mono[NM];
+    monomials<DIM, NS, R>(fr[0], fr[1], fr[2], mono);
+    R phP[NV][NS + 1], phN[NV][NS + 1];
+    contract_cell<DIM, NV, NS, PREC>(a, P, mono, phP);
+    contract_cell<DIM, NV, NS, PREC>(a, N, mono, phN);
+    const R g = fr[3];
+    if constexpr (NS >= 2) {
+        if (eno) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                R q0[3], q1[3];
+#pragma unroll
+                for (int m = 0; m < 3; ++m) { q0[m] = (m & 1) ? -phN[v][m] : phN[v][m]; q1[m] = (m & 1) ? -phP[v][m] : phP[v][m]; }
+                if (!UPWIND_ONLY || want_left) UL[v] = eno3_value<NS, R>(g, phP[v], phN[v]);
+                if (!UPWIND_ONLY || !want_left) UR[v] = eno3_value<NS, R>((R)1 / g, q0, q1);
+            }
+            return;
+        }
+    }
+    R W0[NS + 1], W1[NS + 1];
+    if (!UPWIND_ONLY || want_left) {
+        dolinc_weights<NS, R>(a.k, a.r, g, W0, W1);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            R s = (R)0;
+#pragma unroll
+            for (int m = 0; m <= NS; ++m) s = fma(W0[m], phP[v][m], fma(W1[m], phN[v][m], s));
+            UL[v] = s;
+        }
+    }
+    if (!UPWIND_ONLY || !want_left) {
+        // neighbour upwind: d -> -d, g -> 1/g, phi^(m) -> (-1)^m phi^(m)
+        dolinc_weights<NS, R>(a.k, a.r, (R)1 / g, W0, W1);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            R s = (R)0;
+#pragma unroll
+            for (int m = 0; m <= NS; ++m) {
+                R t = fma(W0[m], phN[v][m], W1[m] * phP[v][m]);
+                s = (m & 1) ? s - t : s + t;
+            }
+            UR[v] = s;
+        }
+    }
+}
+
+template <int DIM, int NV, class R>
+__device__ __forceinline__ void phys_flux(const StageArgs &a, const R *U, const R *fr, R *F)
+{
+    if constexpr (NV == 1) {
+        if (a.flux == 0) {
+            R an = (R)a.adv[0] * fr[4] + (R)a.adv[1] * fr[5] + (DIM == 3 ? (R)a.adv[2] * fr[6] : (R)0);
+            F[0] = an * U[0];
+        } else {
+            R sg = fr[4] + fr[5] + (DIM == 3 ? fr[6] : (R)0);
+            F[0] = (R)0.5 * U[0] * U[0] * sg;
+        }
+    } else {
+        R un, c2;
+        euler_phys<DIM, R>((R)a.gamma, U, fr[4], fr[5], fr[6], F, un, c2);
+    }
+}
+
+template <int DIM, int NV, int NS, int PREC>
+__global__ void __launch_bounds__(128) k_stage(DevMesh mesh, StageArgs a)
+{
+    using R = typename PrecT<PREC>::R;
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= mesh.n_cells) return;
+    R res[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) res[v] = (R)0;
+    const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+    const bool own_flag = a.flags && a.flags[c];
+    for (int s = s0; s < s1; ++s) {
+        const int2 sw = __ldg(mesh.slot2 + s);
+        const int nb = sw.x;
+        const unsigned word = (unsigned)sw.y;
+        const int f = (int)(word >> 2);
+        const int side = word & 1;
+        R fr[8];
+        {
+            const R *p = Geo<R>::face(mesh) + 8ll * f;
+            ld4<R>(p, fr[0], fr[1], fr[2], fr[3]);
+            ld4<R>(p + 4, fr[4], fr[5], fr[6], fr[7]);
+        }
+        R F[NV];
+        if (word & 2) {
+            // zero-gradient boundary (Sec 2.6): the auxiliary cell mirrors the cell value
+            R U[NV];
+            load_rec<typename PrecT<PREC>::T0, NV, ord_stride<DIM, NV, 0, PREC>(), R>(
+                static_cast<const typename PrecT<PREC>::T0 *>(a.ord[0]), c, U);
+            phys_flux<DIM, NV, R>(a, U, fr, F);
+        } else {
+            const int P = side ? nb : c, N = side ? c : nb;
+            const bool eno = a.eno_all || (a.flags && (own_flag || a.flags[nb]));
+            R UL[NV], UR[NV];
+            if constexpr (NV == 1) {
+                if (a.flux == 0) {
+                    R an = (R)a.adv[0] * fr[4] + (R)a.adv[1] * fr[5] + (DIM == 3 ? (R)a.adv[2] * fr[6] : (R)0);
+                    bool left = an >= (R)0;
+                    face_states<DIM, NV, NS, PREC, true>(a, fr, P, N, eno, UL, UR, left);
+                    F[0] = an * (left ? UL[0] : UR[0]);
+                } else {
+                    face_states<DIM, NV, NS, PREC, false>(a, fr, P, N, eno, UL, UR, true);
+                    R sg = fr[4] + fr[5] + (DIM == 3 ? fr[6] : (R)0);
+                    R lam = (R)0.5 * (UL[0] + UR[0]) * sg;       // Roe speed of u^2/2 (1,..,1)
+                    R uu = lam >= (R)0 ? UL[0] : UR[0];
+                    F[0] = (R)0.5 * uu * uu * sg;
+                }
+            } else {
+                face_states<DIM, NV, NS, PREC, false>(a, fr, P, N, eno, UL, UR, true);
+                rusanov<DIM, R>((R)a.gamma, UL, UR, fr[4], fr[5], fr[6], fr[7], F);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) res[v] = side ? res[v] + F[v] : res[v] - F[v];
+    }
+    R iv, dummy0, dummy1, dummy2;
+    ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, dummy0, dummy1, dummy2, iv);
+    const long long n = mesh.n_cells;
+    bool bad = false;
+    if (a.mode == 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            double r = (double)(res[v] * iv);
+            a.out[v * n + c] = r;
+            bad |= !isfinite(r);
+        }
+    } else {
+        R nxt[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            double rr = (double)(res[v] * iv);
+            double o = a.A * a.u0[v * n + c] + a.B * fma(a.dt, rr, a.us[v * n + c]);
+            a.out[v * n + c] = o;
+            nxt[v] = (R)o;
+            bad |= !isfinite(o);
+        }
+        if (a.o0_next)
+            store_rec<typename PrecT<PREC>::T0, NV, ord_stride<DIM, NV, 0, PREC>(), R>(
+                static_cast<typename PrecT<PREC>::T0 *>(a.o0_next), c, nxt);
+    }
+    if (bad) atomicOr(a.status, 1u);
+}
+
+// ------------------------------------------------------------------ face states (diagnostic)
+template <int DIM, int NV, int NS, int PREC>
+__global__ void __launch_bounds__(128) k_faces(DevMesh mesh, StageArgs a, double *fL, double *fR)
+{
+    using R = typename PrecT<PREC>::R;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= mesh.n_faces) return;
+    const int P = mesh.fo[i], N = mesh.fn[i];
+    const long long e = mesh.face_ext[i];
+    const bool flip = mesh.face_flip[i];
+    R fr[8];
+    {
+        const R *p = Geo<R>::face(mesh) + 8ll * i;
+        ld4<R>(p, fr[0], fr[1], fr[2], fr[3]);
+        ld4<R>(p + 4, fr[4], fr[5], fr[6], fr[7]);
+    }
+    R UL[NV], UR[NV];
+    if (N < 0) {
+        load_rec<typename PrecT<PREC>::T0, NV, ord_stride<DIM, NV, 0, PREC>(), R>(
+            static_cast<const typename PrecT<PREC>::T0 *>(a.ord[0]), P, UL);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) UR[v] = UL[v];
+    } else {
+        const bool eno = a.eno_all || (a.flags && (a.flags[P] || a.flags[N]));
+        face_states<DIM, NV, NS, PREC, false>(a, fr, P, N, eno, UL, UR, true);
+    }
+    const long long nf = mesh.n_faces;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        fL[v * nf + e] = (double)(flip ? UR[v] : UL[v]);
+        fR[v * nf + e] = (double)(flip ? UL[v] : UR[v]);
+    }
+}
+
+}  // namespace dol

@@ -1,0 +1,40 @@
+// Host mesh layer of the DOLINC library: validation, FP64 geometry (Sec 2.2),
+// renumbering and the cell -> face slot tables the stage kernels read.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dolinc.h"
+
+namespace dol {
+
+// Slot word: (internal face << 2) | (boundary << 1) | side, side 0 = the cell owns
+// the face (area vector points out of it), side 1 = the cell is the neighbour.
+inline uint32_t slot_word(int64_t f, bool bnd, int side) { return (uint32_t)((f << 2) | (bnd ? 2 : 0) | side); }
+
+struct HostMesh {
+    int dim = 0;
+    int64_t n_cells = 0, n_faces = 0, n_bnd = 0, n_slots = 0;
+    std::vector<int64_t> perm;          // new_of_old
+    // FP64 geometry, library cell order
+    std::vector<double> V, xc;          // [n_cells], [n_cells][3]
+    // internal faces (owner = lower library index; sorted by owner, neighbour)
+    std::vector<int64_t> fo, fn;        // owner / neighbour (-1 boundary)
+    std::vector<double> fS, fxf, fd;    // [nf][3] area vector out of the internal owner, centroid, d
+    std::vector<double> fw, fg;         // Eq 3 weight of the internal owner, Eq 4 growth rate
+    std::vector<int64_t> face_ext;      // internal -> caller face
+    std::vector<int8_t> face_flip;      // 1: internal orientation opposite to the caller's
+    // slots
+    std::vector<int32_t> off;           // [n_cells+1]
+    std::vector<int32_t> snb;           // neighbour cell of each slot (self on boundary)
+    std::vector<uint32_t> sword;        // slot word
+    std::vector<double> ss;             // [n_slots][3] (1-w_c) S_{c,f} / V_c
+    std::vector<double> cw;             // [n_cells][4] (sum_f w_c S_{c,f} / V_c, 1/V_c)
+    double g_min = 0, g_max = 0, h_min = 0, volume = 0;
+};
+
+// Builds the host mesh; returns an empty string on success, else the error message.
+std::string build_host_mesh(const dolinc_mesh_desc &d, HostMesh &m);
+
+}  // namespace dol

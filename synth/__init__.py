@@ -12,9 +12,11 @@ from .meshes import (tri_mesh, strip_mesh, tet_mesh, hexprism_mesh, hex_mesh,
 from .fields import (cell_average, sine2d, gaussian3d, isentropic_vortex,
                      vortex_params, fourier_modes, riemann_quadrants,
                      prim_to_cons)
+from .workloads import workload, WORKLOADS, STENCIL_OF_ORDER
 
 __all__ = [
     "tri_mesh", "strip_mesh", "tet_mesh", "hexprism_mesh", "hex_mesh",
     "mesh_summary", "cell_average", "sine2d", "gaussian3d", "isentropic_vortex",
     "vortex_params", "fourier_modes", "riemann_quadrants", "prim_to_cons",
+    "workload", "WORKLOADS", "STENCIL_OF_ORDER",
 ]
