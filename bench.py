@@ -1,8 +1,8 @@
 """Benchmark of the DOLINC SSP-RK3 stage on one GB300 (or N replicas under torchrun).
 
 Workload (default): euler3d_tet64 — 64^3 hexes x 5 tetrahedra (1,310,720 cells),
-+-15% node jitter, periodic, isentropic vortex, Rusanov flux, scheme order 4
-(stencil (4,1), differentials through order 3), FP32 differentials/reconstruction/
++-15% node jitter, periodic, isentropic vortex, Rusanov flux, scheme order 3
+(stencil (3,1) = USR3, differentials through order 2), FP32 differentials/reconstruction/
 flux with FP64 geometry master and FP64 state update.  A step is one SSP-RK3 time
 step (3 stages, each: differential passes + fused reconstruct/flux/residual/update).
 
@@ -48,10 +48,13 @@ class Clocks:
 
     def __init__(self, index):
         self.index = index
+        self.enabled = index >= 0
         self.proc = None
         self.lines = []
 
     def __enter__(self):
+        if not self.enabled:
+            return self
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -139,27 +142,31 @@ def run_dolinc(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    w = synth.workload(args.workload, order=args.order, q=args.quad)
+    w = synth.workload(args.workload, order=args.order, q=args.quad, size=args.size)
     m, u0, dt = w["mesh"], w["u0"], w["dt"]
     M = dg.Mesh(m, renumber="morton")
     stream = torch.cuda.current_stream()
-    results = {}
-    launches_per_step = None
-    for prec in (args.precision, "fp64"):
-        sch = dg.Scheme(precision=prec, **w["scheme"])
+
+    def timed_run(prec, scheme_kw, steps, clocks):
+        """warm-up + `steps` timed SSP-RK3 steps from u0; returns timing, kernel profile, state."""
+        sch = dg.Scheme(precision=prec, **scheme_kw)
         ws = dg.workspace(M, sch)
         u = torch.from_numpy(M.to_lib(u0)).cuda()
         for _ in range(args.warmup):
             dg.dolinc_rk_step(M, sch, dt, u, ws)
-        dg.dolinc_sync_status(M, ws)
+        finite = True
+        try:
+            dg.dolinc_sync_status(M, ws)
+        except dg.DolincError:
+            finite = False
         dg.dolinc_profile_enable(M, True)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with Clocks(local) as ck:
+        with Clocks(local if clocks else -1) as ck:
             e0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 dg.dolinc_rk_step(M, sch, dt, u, ws)
             e1.record(stream)
             torch.cuda.synchronize()
@@ -170,12 +177,35 @@ def run_dolinc(args):
             ms = float(t.item())
         kms, kn = dg.profile_read(M)
         dg.dolinc_profile_enable(M, False)
-        dg.dolinc_sync_status(M, ws)
-        results[prec] = dict(ms=ms, state=u, kms=kms, kn=kn, clocks=ck.summary(), sch=sch, ws=ws)
-        if prec == args.precision:
-            launches_per_step = int(sum(kn)) / args.steps
-        if prec == args.precision and args.precision == "fp64":
-            break
+        try:
+            dg.dolinc_sync_status(M, ws)
+        except dg.DolincError:
+            finite = False
+        return dict(ms=ms, state=u, kms=kms, kn=kn, clocks=ck.summary() if clocks else None, sch=sch, ws=ws,
+                    finite=finite)
+
+    results = {args.precision: timed_run(args.precision, w["scheme"], args.steps, True)}
+    if args.precision != "fp64":
+        results["fp64"] = timed_run("fp64", w["scheme"], args.steps, False)
+    launches_per_step = int(sum(results[args.precision]["kn"])) / args.steps
+    variants = {}
+    if not args.no_variants and args.workload == "euler3d_tet64":
+        for prec, order in (("fp32_bf16", w["info"]["order"]), (args.precision, 2), (args.precision, 4),
+                            ("fp64", 2), ("fp64", 4)):
+            if order == w["info"]["order"] and prec == args.precision:
+                continue
+            k, r = synth.STENCIL_OF_ORDER[order]
+            kw = dict(w["scheme"], k=k, r=r, n_diff=order - 1)
+            vr = timed_run(prec, kw, args.steps, False)
+            v = {"precision": prec, "scheme_order": order, "stencil_k_r": [k, r], "n_diff": order - 1,
+                 "value": M.n_cells * world * 3 * args.steps / (vr["ms"] / 1e3),
+                 "ms_per_step": vr["ms"] / args.steps, "finite_after_steps": vr["finite"]}
+            if prec == "fp32_bf16" and "fp64" in results:
+                a = vr["state"].double().cpu().numpy()
+                b = results["fp64"]["state"].cpu().numpy()
+                v["l2_rel_vs_fp64_after_steps"] = float(np.sqrt(((a - b) ** 2).sum(axis=1) / (b ** 2).sum(axis=1)).max())
+            variants["%s_order%d" % (prec, order)] = v
+            del vr
     main = results[args.precision]
     cells = M.n_cells
     total_cells = cells * world
@@ -221,6 +251,9 @@ def run_dolinc(args):
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": main["clocks"],
     }
+    if variants:
+        line["variants"] = variants
+    line["finite_after_steps"] = main["finite"]
     if "fp64" in results and args.precision != "fp64":
         f = results["fp64"]
         v64 = total_cells * 3 * args.steps / (f["ms"] / 1e3)
@@ -324,7 +357,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dolinc", choices=["dolinc", "reference"])
     ap.add_argument("--workload", default="euler3d_tet64")
-    ap.add_argument("--order", type=int, default=4)
+    ap.add_argument("--order", type=int, default=3)
+    ap.add_argument("--size", type=int, default=None, help="lattice size (default: the workload's)")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp32_bf16"])
     ap.add_argument("--quad", type=int, default=2, help="quadrature points per direction for initial averages")
     ap.add_argument("--ref-size", type=int, default=20)

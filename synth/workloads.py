@@ -59,7 +59,7 @@ def workload(name, order=None, size=None, q=3, n_meshes=None):
                     info=dict(cells=2 * n * n, h=h))
     if name == "euler3d_tet64":
         n = size or 64
-        order = order or 4
+        order = order or 3
         k, r = STENCIL_OF_ORDER[order]
         m = meshes.tet_mesh(n, jitter=0.15, seed=SEED + 1)
         vf = lambda p: fields.isentropic_vortex(p, dim=3, images=0)

@@ -10,7 +10,9 @@ the face's growth-rate spread G = max(g, 1/g) like G^(Ns(Ns-1)) (checked against
   FP64       1e-12 * 4^Ns     * G^(Ns(Ns-1)) * max|u|
   FP32       1e-5  * 8^(Ns-1) * G^(Ns(Ns-1)) * max|u|      (Ns = 1: the stated 1e-5)
   FP32+BF16  3e-3 (8-bit mantissa on orders >= 2; coarse test meshes)
-Residuals take the same per-face bound through |S_f| * (largest wave speed) / V_c;
+Residuals take the same per-face bound through |S_f| * (largest wave speed) / V_c
+(for FP32 that is 1e-5 relative to the face-flux magnitudes, not to the residual,
+which is their O(h) cancellation);
 differentials of order m are compared with 1e-12 * 4^m (FP64) / 1e-5 * 8^(m-1) (FP32).
 """
 import numpy as np
@@ -256,11 +258,11 @@ def test_residual(prec, case):
     for v in range(nv):
         ct = cell_tol(O, face_tol(O, prec, Ns, np.abs(u).max()), lam) * (2.0 if nv > 1 else 1.0)
         assert np.all(np.abs(got[v] - want[v]) <= base * np.abs(want[v]).max() + ct), (v, rel(got[v], want[v]))
-    if Ns == 1 and prec != "fp32_bf16":
+    if Ns == 1 and prec == "fp64":
         for v in range(nv):
             assert rel(got[v], want[v]) < base, (v, rel(got[v], want[v]))
     # conservation: the face fluxes cancel pairwise on periodic meshes, on the GPU too
-    if name != "tri_bnd" and prec == "fp64":
+    if (O.neigh >= 0).all() and prec == "fp64":
         tot = (got * O.V).sum(axis=1)
         assert np.all(np.abs(tot) < 1e-13 * (np.abs(got) * O.V).sum(axis=1) + 1e-300)
 
