@@ -196,6 +196,25 @@ dolinc_status dolinc_rk_stage(dolinc_mesh *mesh, const dolinc_scheme *scheme, do
 dolinc_status dolinc_rk_step(dolinc_mesh *mesh, const dolinc_scheme *scheme, double dt, double *u_dev,
                              void *ws_dev, size_t ws_bytes, dolinc_stream stream);
 
+/* One SSP-RK3 step, like dolinc_rk_step, without a caller workspace and without any
+ * allocation: for callers that hold only the field's device pointer and cannot obtain
+ * device memory themselves (for example a plugin that a host application hands its
+ * state buffer to, with no allocator of its own).  The paper has no counterpart; this
+ * is a deployment convenience.
+ * The workspace is a fixed device array of DOLINC_NOALLOC_MAX_BYTES inside the library
+ * (32 MiB, held on every GPU that loads the library until the process exits).
+ * Meshes/schemes whose dolinc_workspace_size exceeds it are rejected with
+ * DOLINC_ERR_INVALID_ARG and a message; nothing is allocated, ever.
+ * The first call on a device looks the array's address up and clears it (with that
+ * device current); make that first call before any stream capture.
+ * All calls on a device share the one array, which keeps the last call's contents:
+ * calls that overlap on the GPU (different streams, threads or meshes at once) race
+ * and must be serialised by the caller.  Non-finite results are not reported here
+ * (the status word is cleared at every call). */
+#define DOLINC_NOALLOC_MAX_BYTES ((size_t)32 << 20)
+dolinc_status dolinc_rk_step_noalloc(dolinc_mesh *mesh, const dolinc_scheme *scheme, double dt, double *u_dev,
+                                     dolinc_stream stream);
+
 /* Cell flags for DOLINC_LIMIT_ENO3_FLAGGED: flags_dev [n_cells] uint8 (library order),
  * non-zero = troubled.  The pointer is kept by the mesh until replaced or NULL. */
 dolinc_status dolinc_set_flags(dolinc_mesh *mesh, const uint8_t *flags_dev);

@@ -27,7 +27,7 @@ ABI_SYMBOLS = (
     "dolinc_mesh_geometry", "dolinc_workspace_size", "dolinc_workspace_init", "dolinc_diff_layout",
     "dolinc_differentials", "dolinc_reconstruct_faces", "dolinc_residual", "dolinc_rk_stage",
     "dolinc_rk_step", "dolinc_set_flags", "dolinc_sync_status", "dolinc_profile_enable",
-    "dolinc_profile_read", "dolinc_last_error",
+    "dolinc_profile_read", "dolinc_rk_step_noalloc", "dolinc_last_error",
 )
 KERNEL_KINDS = ("pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces")
 
@@ -80,6 +80,7 @@ def load(path=LIB_PATH):
             "dolinc_rk_step": [P, P, D, P, P, S, P],
             "dolinc_set_flags": [P, P], "dolinc_sync_status": [P, P, P], "dolinc_last_error": [],
             "dolinc_profile_enable": [P, I], "dolinc_profile_read": [P, P, P],
+            "dolinc_rk_step_noalloc": [P, P, D, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -255,6 +256,13 @@ def dolinc_rk_step(mesh, scheme, dt, u, ws, stream=None):
     s = scheme.c()
     _check(load().dolinc_rk_step(mesh.handle, C.byref(s), float(dt), _ptr(u), _ptr(ws), ws.numel(),
                                  _stream(stream)))
+
+
+def dolinc_rk_step_noalloc(mesh, scheme, dt, u, stream=None):
+    """One SSP-RK3 step using the library's fixed internal workspace (no allocation;
+    see include/dolinc.h for its size limit and sharing rules)."""
+    s = scheme.c()
+    _check(load().dolinc_rk_step_noalloc(mesh.handle, C.byref(s), float(dt), _ptr(u), _stream(stream)))
 
 
 def dolinc_set_flags(mesh, flags):

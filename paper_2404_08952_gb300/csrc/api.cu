@@ -47,6 +47,10 @@ size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
 
+namespace dol {
+dolinc_status report_error(dolinc_status s, const std::string &msg) { return fail(s, msg); }
+}  // namespace dol
+
 struct dolinc_mesh {
     HostMesh h;
     DevMesh d{};

@@ -1,0 +1,79 @@
+// dolinc_rk_step_noalloc: the SSP-RK3 step for callers that cannot allocate device
+// memory.  Its workspace is a file-scope device array of fixed size, so the call
+// itself allocates nothing.
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+
+#include "../../include/dolinc.h"
+
+namespace dol {
+dolinc_status report_error(dolinc_status s, const std::string &msg);   // api.cu: sets dolinc_last_error
+}
+
+namespace {
+
+constexpr size_t kNoAllocBytes = DOLINC_NOALLOC_MAX_BYTES;
+
+// Workspace shared by every call on a device.  In host code this name is only a
+// stand-in for the device array: its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_ws[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_addr[kMaxDevices] = {nullptr};
+
+// Device address of the array on the current device, resolved once per device (with
+// that device current) and its status word cleared.  Returns null and sets *err on failure.
+void *device_scratch(std::string *err)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        *err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return nullptr;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        *err = "device index out of range for the no-alloc workspace table";
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_ws);
+        if (e != cudaSuccess || !p) {
+            *err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+            return nullptr;
+        }
+        e = cudaMemset(p, 0, 256);
+        if (e != cudaSuccess) {
+            *err = std::string("cudaMemset: ") + cudaGetErrorString(e);
+            return nullptr;
+        }
+        g_addr[dev] = p;
+    }
+    return g_addr[dev];
+}
+
+}  // namespace
+
+extern "C" dolinc_status dolinc_rk_step_noalloc(dolinc_mesh *mesh, const dolinc_scheme *scheme, double dt,
+                                                double *u_dev, dolinc_stream stream)
+{
+    size_t need = 0;
+    dolinc_status st = dolinc_workspace_size(mesh, scheme, &need);
+    if (st != DOLINC_OK) return st;
+    if (need > kNoAllocBytes)
+        return dol::report_error(DOLINC_ERR_INVALID_ARG,
+                                 "dolinc_rk_step_noalloc: this mesh and scheme need " + std::to_string(need) +
+                                     " bytes of workspace, above the fixed " + std::to_string(kNoAllocBytes) +
+                                     " (DOLINC_NOALLOC_MAX_BYTES); use dolinc_rk_step with a caller workspace");
+    std::string err;
+    void *ws = device_scratch(&err);
+    if (!ws) return dol::report_error(DOLINC_ERR_CUDA, "dolinc_rk_step_noalloc: " + err);
+    cudaError_t e = cudaMemsetAsync(ws, 0, 256, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess)
+        return dol::report_error(DOLINC_ERR_CUDA, std::string("dolinc_rk_step_noalloc: ") + cudaGetErrorString(e));
+    return dolinc_rk_step(mesh, scheme, dt, u_dev, ws, kNoAllocBytes, stream);
+}
