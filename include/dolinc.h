@@ -215,6 +215,24 @@ dolinc_status dolinc_rk_step(dolinc_mesh *mesh, const dolinc_scheme *scheme, dou
 dolinc_status dolinc_rk_step_noalloc(dolinc_mesh *mesh, const dolinc_scheme *scheme, double dt, double *u_dev,
                                      dolinc_stream stream);
 
+/* Launch-shape autotuner (no counterpart in the paper).  Times the differential and
+ * stage kernels of this mesh and scheme on the given state (u_dev, FP64 [v][cell])
+ * for 1, 4 and 8 lanes per cell and blocks of 64, 128, 256 threads, keeps the fastest
+ * shape in the mesh handle for every later call with this scheme, and appends it to
+ * the text file cache_path (one line per GPU name and mesh/scheme key; may be NULL).
+ * A key already in the file is reused without timing.  Synchronous; clears the
+ * workspace status word.  Results: *out (may be NULL). */
+typedef struct {
+    int diff_lanes, diff_block, stage_lanes, stage_block;
+    int from_cache;
+    double diff_ms, stage_ms;        /* best times (all differential passes / one stage) */
+} dolinc_tuning;
+dolinc_status dolinc_autotune(dolinc_mesh *mesh, const dolinc_scheme *scheme, const double *u_dev, void *ws_dev,
+                              size_t ws_bytes, const char *cache_path, dolinc_stream stream, dolinc_tuning *out);
+/* Sets the launch shape used for this mesh and scheme (lanes per cell 1, 4 or 8;
+ * block 32..256, a multiple of 32), e.g. a shape read back from an autotuning cache. */
+dolinc_status dolinc_set_tuning(dolinc_mesh *mesh, const dolinc_scheme *scheme, const dolinc_tuning *tuning);
+
 /* Cell flags for DOLINC_LIMIT_ENO3_FLAGGED: flags_dev [n_cells] uint8 (library order),
  * non-zero = troubled.  The pointer is kept by the mesh until replaced or NULL. */
 dolinc_status dolinc_set_flags(dolinc_mesh *mesh, const uint8_t *flags_dev);

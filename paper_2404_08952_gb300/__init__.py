@@ -27,7 +27,8 @@ ABI_SYMBOLS = (
     "dolinc_mesh_geometry", "dolinc_workspace_size", "dolinc_workspace_init", "dolinc_diff_layout",
     "dolinc_differentials", "dolinc_reconstruct_faces", "dolinc_residual", "dolinc_rk_stage",
     "dolinc_rk_step", "dolinc_set_flags", "dolinc_sync_status", "dolinc_profile_enable",
-    "dolinc_profile_read", "dolinc_rk_step_noalloc", "dolinc_last_error",
+    "dolinc_profile_read", "dolinc_rk_step_noalloc", "dolinc_autotune", "dolinc_set_tuning",
+    "dolinc_last_error",
 )
 KERNEL_KINDS = ("pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces")
 
@@ -81,6 +82,7 @@ def load(path=LIB_PATH):
             "dolinc_set_flags": [P, P], "dolinc_sync_status": [P, P, P], "dolinc_last_error": [],
             "dolinc_profile_enable": [P, I], "dolinc_profile_read": [P, P, P],
             "dolinc_rk_step_noalloc": [P, P, D, P, P],
+            "dolinc_autotune": [P, P, P, P, S, C.c_char_p, P, P], "dolinc_set_tuning": [P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -131,6 +133,12 @@ class Scheme:
         for i in range(3):
             s.adv[i] = self.adv[i]
         return s
+
+
+class _Tuning(C.Structure):
+    _fields_ = [("diff_lanes", C.c_int), ("diff_block", C.c_int), ("stage_lanes", C.c_int),
+                ("stage_block", C.c_int), ("from_cache", C.c_int), ("diff_ms", C.c_double),
+                ("stage_ms", C.c_double)]
 
 
 class Mesh:
@@ -263,6 +271,24 @@ def dolinc_rk_step_noalloc(mesh, scheme, dt, u, stream=None):
     see include/dolinc.h for its size limit and sharing rules)."""
     s = scheme.c()
     _check(load().dolinc_rk_step_noalloc(mesh.handle, C.byref(s), float(dt), _ptr(u), _stream(stream)))
+
+
+def dolinc_autotune(mesh, scheme, u, ws, cache_path=None, stream=None):
+    """Pick lanes-per-cell and block sizes for this mesh and scheme by timing them on u;
+    returns the chosen shape as a dict."""
+    s = scheme.c()
+    t = _Tuning()
+    cp = cache_path.encode() if cache_path else None
+    _check(load().dolinc_autotune(mesh.handle, C.byref(s), _ptr(u), _ptr(ws), ws.numel(), cp, _stream(stream),
+                                  C.byref(t)))
+    return {f: getattr(t, f) for f, _ in _Tuning._fields_}
+
+
+def dolinc_set_tuning(mesh, scheme, diff_lanes=4, diff_block=256, stage_lanes=4, stage_block=128):
+    s = scheme.c()
+    t = _Tuning()
+    t.diff_lanes, t.diff_block, t.stage_lanes, t.stage_block = diff_lanes, diff_block, stage_lanes, stage_block
+    _check(load().dolinc_set_tuning(mesh.handle, C.byref(s), C.byref(t)))
 
 
 def dolinc_set_flags(mesh, flags):

@@ -3,7 +3,11 @@
 
 #include <cstdio>
 #include <cstring>
+#include <chrono>
+#include <fstream>
+#include <map>
 #include <mutex>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -57,6 +61,8 @@ struct dolinc_mesh {
     int device = 0;
     std::vector<void *> allocs;
     const uint8_t *flags = nullptr;
+    int max_faces = 0;                 // largest number of slots of a cell
+    std::map<std::string, Tune> tuned;  // launch shapes chosen by dolinc_autotune, per scheme
     // per-kernel timing (dolinc_profile_enable)
     bool prof = false;
     struct Rec {
@@ -215,12 +221,29 @@ template <class F> void timed(dolinc_mesh *m, int kind, cudaStream_t s, F &&laun
     m->recs.push_back(r);
 }
 
+std::string scheme_key(const dolinc_mesh *m, const dolinc_scheme *s)
+{
+    std::ostringstream k;
+    k << m->h.dim << "d_nv" << s->nv << "_ns" << needed_order(*s) << "_nd" << s->n_diff << "_p" << s->precision
+      << "_c" << m->h.n_cells << "_f" << m->h.n_faces << "_mf" << m->max_faces;
+    return k.str();
+}
+
+Tune tune_for(const dolinc_mesh *m, const dolinc_scheme *s)
+{
+    auto it = m->tuned.find(scheme_key(m, s));
+    if (it != m->tuned.end()) return it->second;
+    Tune t;                                       // heuristic: one lane per face slot
+    t.diff_lpc = t.stage_lpc = m->max_faces <= 4 ? 4 : 8;
+    return t;
+}
+
 // differential passes 1..n from the order-0 record at o0off
 void run_diffs(dolinc_mesh *m, const PathFns *p, void *ws, const WsLayout &L, size_t o0off, int n,
-               cudaStream_t st)
+               const Tune &t, cudaStream_t st)
 {
     for (int mm = 1; mm <= n; ++mm)
-        timed(m, mm, st, [&] { p->diff(m->d, mm, B(ws, mm == 1 ? o0off : L.ord[mm - 1]), B(ws, L.ord[mm]), st); });
+        timed(m, mm, st, [&] { p->diff(m->d, mm, B(ws, mm == 1 ? o0off : L.ord[mm - 1]), B(ws, L.ord[mm]), t, st); });
 }
 
 dolinc_status launch_check()
@@ -292,6 +315,7 @@ dolinc_status dolinc_mesh_create(const dolinc_mesh_desc *desc, dolinc_mesh **out
         ff[f] = h.face_flip[f];
     }
     std::vector<int32_t> off(h.off.begin(), h.off.end());
+    for (int64_t c = 0; c < nc; ++c) m->max_faces = std::max(m->max_faces, (int)(h.off[c + 1] - h.off[c]));
     dolinc_status st = DOLINC_OK;
     DevMesh &d = m->d;
     d.dim = h.dim;
@@ -404,7 +428,7 @@ dolinc_status dolinc_differentials(dolinc_mesh *m, const dolinc_scheme *s, const
     const void *prev = B(ws, L.o0[0]);
     for (int mm = 1; mm <= order; ++mm) {
         const int b = elem_bytes(s->precision, mm), sd = stride_h(m->h.dim, s->nv, mm, s->precision);
-        timed(m, mm, cs, [&] { p->diff(m->d, mm, prev, B(diff, o), cs); });
+        timed(m, mm, cs, [&] { p->diff(m->d, mm, prev, B(diff, o), tune_for(m, s), cs); });
         prev = B(diff, o);
         o += al256((size_t)m->h.n_cells * sd * b);
     }
@@ -423,7 +447,7 @@ dolinc_status dolinc_reconstruct_faces(dolinc_mesh *m, const dolinc_scheme *s, c
     if (!p) return fail(DOLINC_ERR_UNSUPPORTED, "no kernel for this (dim, nv, order, precision)");
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, u, B(ws, L.o0[0]), cs); });
-    run_diffs(m, p, ws, L, L.o0[0], s->n_diff, cs);
+    run_diffs(m, p, ws, L, L.o0[0], s->n_diff, tune_for(m, s), cs);
     StageArgs a = base_args(m, s, ws, L, L.o0[0]);
     timed(m, DOLINC_KERNEL_FACES, cs, [&] { p->faces(m->d, a, fL, fR, cs); });
     return launch_check();
@@ -441,11 +465,11 @@ dolinc_status dolinc_residual(dolinc_mesh *m, const dolinc_scheme *s, const doub
     if (!p) return fail(DOLINC_ERR_UNSUPPORTED, "no kernel for this (dim, nv, order, precision)");
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, u, B(ws, L.o0[0]), cs); });
-    run_diffs(m, p, ws, L, L.o0[0], s->n_diff, cs);
+    run_diffs(m, p, ws, L, L.o0[0], s->n_diff, tune_for(m, s), cs);
     StageArgs a = base_args(m, s, ws, L, L.o0[0]);
     a.mode = 0;
     a.out = R;
-    timed(m, DOLINC_KERNEL_STAGE, cs, [&] { p->stage(m->d, a, cs); });
+    timed(m, DOLINC_KERNEL_STAGE, cs, [&] { p->stage(m->d, a, tune_for(m, s), cs); });
     return launch_check();
 }
 
@@ -463,7 +487,7 @@ dolinc_status dolinc_rk_stage(dolinc_mesh *m, const dolinc_scheme *s, double dt,
     if (!p) return fail(DOLINC_ERR_UNSUPPORTED, "no kernel for this (dim, nv, order, precision)");
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, us, B(ws, L.o0[0]), cs); });
-    run_diffs(m, p, ws, L, L.o0[0], s->n_diff, cs);
+    run_diffs(m, p, ws, L, L.o0[0], s->n_diff, tune_for(m, s), cs);
     StageArgs a = base_args(m, s, ws, L, L.o0[0]);
     a.mode = 1;
     a.u0 = u0;
@@ -473,7 +497,7 @@ dolinc_status dolinc_rk_stage(dolinc_mesh *m, const dolinc_scheme *s, double dt,
     a.B = Bc[stage];
     a.dt = dt;
     a.o0_next = nullptr;
-    timed(m, DOLINC_KERNEL_STAGE, cs, [&] { p->stage(m->d, a, cs); });
+    timed(m, DOLINC_KERNEL_STAGE, cs, [&] { p->stage(m->d, a, tune_for(m, s), cs); });
     return launch_check();
 }
 
@@ -490,10 +514,11 @@ dolinc_status dolinc_rk_step(dolinc_mesh *m, const dolinc_scheme *s, double dt, 
     if (!p) return fail(DOLINC_ERR_UNSUPPORTED, "no kernel for this (dim, nv, order, precision)");
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     double *ust = reinterpret_cast<double *>(B(ws, L.ustage));
+    const Tune tn = tune_for(m, s);
     timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, u, B(ws, L.o0[0]), cs); });
     int cur = 0;
     for (int sg = 0; sg < 3; ++sg) {
-        run_diffs(m, p, ws, L, L.o0[cur], s->n_diff, cs);
+        run_diffs(m, p, ws, L, L.o0[cur], s->n_diff, tn, cs);
         StageArgs a = base_args(m, s, ws, L, L.o0[cur]);
         a.mode = 1;
         a.u0 = u;
@@ -503,7 +528,7 @@ dolinc_status dolinc_rk_step(dolinc_mesh *m, const dolinc_scheme *s, double dt, 
         a.B = Bc[sg];
         a.dt = dt;
         a.o0_next = sg == 2 ? nullptr : B(ws, L.o0[1 - cur]);
-        timed(m, DOLINC_KERNEL_STAGE, cs, [&] { p->stage(m->d, a, cs); });
+        timed(m, DOLINC_KERNEL_STAGE, cs, [&] { p->stage(m->d, a, tune_for(m, s), cs); });
         cur = 1 - cur;
     }
     return launch_check();
@@ -536,6 +561,116 @@ dolinc_status dolinc_profile_read(dolinc_mesh *m, double *ms, int64_t *launches)
         if (ms) ms[k] = m->prof_ms[k];
         if (launches) launches[k] = m->prof_n[k];
     }
+    return DOLINC_OK;
+}
+
+dolinc_status dolinc_autotune(dolinc_mesh *m, const dolinc_scheme *s, const double *u, void *ws, size_t ws_bytes,
+                              const char *cache_path, dolinc_stream stream, dolinc_tuning *out)
+{
+    dolinc_status st = check_scheme(m, s);
+    if (st) return st;
+    WsLayout L;
+    if ((st = check_ws(m, s, ws, ws_bytes, L))) return st;
+    if (!u) return fail(DOLINC_ERR_INVALID_ARG, "null field");
+    const PathFns *p = path_for(m, s, needed_order(*s));
+    if (!p) return fail(DOLINC_ERR_UNSUPPORTED, "no kernel for this (dim, nv, order, precision)");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    cudaDeviceProp prop;
+    CU(cudaGetDeviceProperties(&prop, m->device));
+    const std::string key = std::string(prop.name) + "|" + scheme_key(m, s);
+    Tune best;
+    bool cached = false;
+    if (cache_path) {
+        std::ifstream in(cache_path);
+        std::string line;
+        while (std::getline(in, line)) {
+            std::istringstream ls(line);
+            std::string k;
+            Tune t;
+            if (std::getline(ls, k, '\t') && (ls >> t.diff_lpc >> t.diff_block >> t.stage_lpc >> t.stage_block) &&
+                k == key) {
+                best = t;
+                cached = true;
+            }
+        }
+    }
+    double best_diff = 0, best_stage = 0;
+    if (!cached) {
+        const bool prof = m->prof;
+        m->prof = false;
+        p->pack(m->d, u, B(ws, L.o0[0]), cs);
+        cudaEvent_t e0, e1;
+        CU(cudaEventCreate(&e0));
+        CU(cudaEventCreate(&e1));
+        auto time_it = [&](auto &&launch) {
+            for (int i = 0; i < 2; ++i) launch();
+            cudaEventRecord(e0, cs);
+            for (int i = 0; i < 5; ++i) launch();
+            cudaEventRecord(e1, cs);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            return ms / 5.0;
+        };
+        const int lpcs[3] = {1, 4, 8}, blocks[3] = {64, 128, 256};
+        double bd = 1e30, bs = 1e30;
+        for (int li = 0; li < 3; ++li)
+            for (int bi = 0; bi < 3; ++bi) {
+                Tune t;
+                t.diff_lpc = t.stage_lpc = lpcs[li];
+                t.diff_block = t.stage_block = blocks[bi];
+                double td = time_it([&] {
+                    for (int mm = 1; mm <= s->n_diff; ++mm)
+                        p->diff(m->d, mm, B(ws, mm == 1 ? L.o0[0] : L.ord[mm - 1]), B(ws, L.ord[mm]), t, cs);
+                });
+                StageArgs a = base_args(m, s, ws, L, L.o0[0]);
+                a.mode = 0;
+                a.out = reinterpret_cast<double *>(B(ws, L.ustage));
+                double tsg = time_it([&] { p->stage(m->d, a, t, cs); });
+                if (td < bd) bd = td, best.diff_lpc = t.diff_lpc, best.diff_block = t.diff_block;
+                if (tsg < bs) bs = tsg, best.stage_lpc = t.stage_lpc, best.stage_block = t.stage_block;
+            }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        m->prof = prof;
+        best_diff = bd;
+        best_stage = bs;
+        CU(cudaMemsetAsync(B(ws, L.status), 0, 256, cs));   // the timing runs may have flagged garbage
+        CU(cudaStreamSynchronize(cs));
+        if (cache_path) {
+            std::ofstream o(cache_path, std::ios::app);
+            o << key << '\t' << best.diff_lpc << ' ' << best.diff_block << ' ' << best.stage_lpc << ' '
+              << best.stage_block << '\n';
+        }
+    }
+    m->tuned[scheme_key(m, s)] = best;
+    if (out) {
+        out->diff_lanes = best.diff_lpc;
+        out->diff_block = best.diff_block;
+        out->stage_lanes = best.stage_lpc;
+        out->stage_block = best.stage_block;
+        out->from_cache = cached ? 1 : 0;
+        out->diff_ms = best_diff;
+        out->stage_ms = best_stage;
+    }
+    return launch_check();
+}
+
+dolinc_status dolinc_set_tuning(dolinc_mesh *m, const dolinc_scheme *s, const dolinc_tuning *t)
+{
+    dolinc_status st = check_scheme(m, s);
+    if (st) return st;
+    if (!t) return fail(DOLINC_ERR_INVALID_ARG, "null tuning");
+    auto ok_l = [](int l) { return l == 1 || l == 4 || l == 8; };
+    auto ok_b = [](int b) { return b >= 32 && b <= 256 && b % 32 == 0; };
+    if (!ok_l(t->diff_lanes) || !ok_l(t->stage_lanes) || !ok_b(t->diff_block) || !ok_b(t->stage_block))
+        return fail(DOLINC_ERR_INVALID_ARG, "lanes must be 1, 4 or 8 and blocks a multiple of 32 in 32..256");
+    Tune x;
+    x.diff_lpc = t->diff_lanes;
+    x.diff_block = t->diff_block;
+    x.stage_lpc = t->stage_lanes;
+    x.stage_block = t->stage_block;
+    m->tuned[scheme_key(m, s)] = x;
     return DOLINC_OK;
 }
 

@@ -168,6 +168,35 @@ __device__ __forceinline__ void monomials(R dx, R dy, R dz, R *mono)
 template <int NS, class R>
 __device__ __forceinline__ void dolinc_weights(int k, int r, R g, R *W0, R *W1)
 {
+    if (r == 1 && k >= 2 && k <= 4) {
+        // First-order DOLINC stencils in closed form (Sec 2.4: Eq coeff on geometric
+        // cells combined with Eqs lCoeffDLC1/rCoeffDLC1), G_n = 1 + g + .. + g^(n-1):
+        //  (2,1):      W0 = ((2+g), 1)/G2,                       W1 = (-1, 0)/G2
+        //  (3,1) USR3: W0 = (g(1+3g+g^2), g^2)/(G2 G3),          W1 = (1+g-g^2, 0)/(G2 G3)
+        //  (4,1) CSR4: W0 = (-g+g^2+2g^3+3g^4+g^5, g^4)/(G3 G4), W1 = (1+3g+2g^2+g^3-g^4, -g)/(G3 G4)
+        const R g2 = g * g;
+#pragma unroll
+        for (int m = 0; m <= NS; ++m) W0[m] = W1[m] = (R)0;
+        if (k == 2) {
+            const R iv = (R)1 / ((R)1 + g);
+            W0[0] = ((R)2 + g) * iv;
+            W0[1] = iv;
+            W1[0] = -iv;
+        } else if (k == 3) {
+            const R iv = (R)1 / (((R)1 + g) * ((R)1 + g + g2));
+            W0[0] = g * ((R)1 + (R)3 * g + g2) * iv;
+            W0[1] = g2 * iv;
+            W1[0] = ((R)1 + g - g2) * iv;
+        } else {
+            const R g3 = g2 * g, g4 = g2 * g2;
+            const R iv = (R)1 / (((R)1 + g + g2) * ((R)1 + g + g2 + g3));
+            W0[0] = (-g + g2 + (R)2 * g3 + (R)3 * g4 + g4 * g) * iv;
+            W0[1] = g4 * iv;
+            W1[0] = ((R)1 + (R)3 * g + (R)2 * g2 + g3 - g4) * iv;
+            W1[1] = -g * iv;
+        }
+        return;
+    }
     constexpr int KM = 2 * NS + 2;
     R gi = (R)1 / g;
     // face positions x_q = right face of cell i-r+q-1, q = 0..k
@@ -267,6 +296,31 @@ __device__ __forceinline__ void dolinc_weights(int k, int r, R g, R *W0, R *W1)
     }
 #pragma unroll
     for (int m = 0; m <= NS; ++m) { W0[m] = wt[NS][m]; W1[m] = wt[NS + 1][m]; }
+}
+
+// ------------------------------------------------------------------ lane groups
+// Sum of v[0..P) over the LPC lanes of an aligned group (LPC a power of two dividing
+// 32), by recursive halving: on return lane j of the group holds the total of
+// elements [j*P/LPC, (j+1)*P/LPC) in v[0..P/LPC).  Every lane of the warp must call it.
+template <int P, int LPC, class R>
+__device__ __forceinline__ void group_reduce_scatter(R *v, int lane)
+{
+    static_assert(P % LPC == 0, "pad the array to a multiple of the group size");
+    int sz = P;
+#pragma unroll
+    for (int o = LPC / 2; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+        const int h = sz / 2;
+#pragma unroll
+        for (int i = 0; i < P / 2; ++i) {
+            if (i < h) {
+                R send = up ? v[i] : v[i + h];
+                R keep = up ? v[i + h] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+        sz = h;
+    }
 }
 
 // ------------------------------------------------------------------ fluxes

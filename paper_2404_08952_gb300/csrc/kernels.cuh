@@ -70,7 +70,12 @@ __global__ void __launch_bounds__(256) k_pack(int n, const double *__restrict__ 
 }
 
 // ------------------------------------------------------------------ differential pass
-template <int DIM, int NV, int M, int PREC>
+// LPC lanes per cell: lane l gathers slots l, l+LPC, ... (lane 0 adds the cell's own
+// term), the group sums by recursive halving and each lane stores its slice of the
+// output record.  LPC = 1 is one thread per cell.
+DOL_HD constexpr int round_up(int n, int q) { return ((n + q - 1) / q) * q; }
+
+template <int DIM, int NV, int M, int PREC, int LPC>
 __global__ void __launch_bounds__(256) k_diff(DevMesh mesh, const void *__restrict__ in_v, void *__restrict__ out_v)
 {
     using R = typename PrecT<PREC>::R;
@@ -80,25 +85,57 @@ __global__ void __launch_bounds__(256) k_diff(DevMesh mesh, const void *__restri
     constexpr int SI = ord_stride<DIM, NV, M - 1, PREC>(), SO = ord_stride<DIM, NV, M, PREC>();
     const TI *in = static_cast<const TI *>(in_v);
     TO *out = static_cast<TO *>(out_v);
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= mesh.n_cells) return;
-    R acc[NV * CO];
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (int)(gt / LPC), l = (int)(gt % LPC);
+    const bool valid = c < mesh.n_cells;
+    constexpr int VO = 16 / (int)sizeof(TO);
+    constexpr int P = (LPC == 1) ? NV * CO : round_up(SO, LPC * VO);   // SO >= NV * CO
+    R acc[P];
 #pragma unroll
-    for (int i = 0; i < NV * CO; ++i) acc[i] = (R)0;
-    R x[NV * CI];
-    R wx, wy, wz, iv;
-    ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, wx, wy, wz, iv);
-    load_rec<TI, NV * CI, SI, R>(in, c, x);
-    poly_mul_acc<DIM, NV, M, R>(acc, x, wx, wy, wz);
-    const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
-    for (int s = s0; s < s1; ++s) {
-        R kx, ky, kz, kb;
-        ld4<R>(Geo<R>::slotk(mesh) + 4ll * s, kx, ky, kz, kb);
-        int nb = Geo<R>::nb_of(kb);
-        load_rec<TI, NV * CI, SI, R>(in, nb, x);
-        poly_mul_acc<DIM, NV, M, R>(acc, x, kx, ky, kz);
+    for (int i = 0; i < P; ++i) acc[i] = (R)0;
+    if (valid) {
+        R x[NV * CI];
+        if (l == 0) {
+            R wx, wy, wz, iv;
+            ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, wx, wy, wz, iv);
+            load_rec<TI, NV * CI, SI, R>(in, c, x);
+            poly_mul_acc<DIM, NV, M, R>(acc, x, wx, wy, wz);
+        }
+        const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+        for (int s = s0 + l; s < s1; s += LPC) {
+            R kx, ky, kz, kb;
+            ld4<R>(Geo<R>::slotk(mesh) + 4ll * s, kx, ky, kz, kb);
+            int nb = Geo<R>::nb_of(kb);
+            load_rec<TI, NV * CI, SI, R>(in, nb, x);
+            poly_mul_acc<DIM, NV, M, R>(acc, x, kx, ky, kz);
+        }
     }
-    store_rec<TO, NV * CO, SO, R>(out, c, acc);
+    if constexpr (LPC == 1) {
+        if (valid) store_rec<TO, NV * CO, SO, R>(out, c, acc);
+    } else {
+        group_reduce_scatter<P, LPC, R>(acc, l);
+        if (!valid) return;
+        constexpr int B = P / LPC;                 // elements this lane owns
+        const int e0 = l * B;
+        TO *rec = out + (long long)c * SO;
+        if constexpr ((B * (int)sizeof(TO)) % 16 == 0 && (SO * (int)sizeof(TO)) % 16 == 0) {
+#pragma unroll
+            for (int i = 0; i < B / VO; ++i) {
+                if (e0 + i * VO < SO) {
+                    uint4 q;
+                    TO *e = reinterpret_cast<TO *>(&q);
+#pragma unroll
+                    for (int j = 0; j < VO; ++j)
+                        e[j] = (e0 + i * VO + j < NV * CO) ? to_store<TO, R>(acc[i * VO + j]) : to_store<TO, R>((R)0);
+                    *reinterpret_cast<uint4 *>(rec + e0 + i * VO) = q;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < B; ++i)
+                if (e0 + i < NV * CO) rec[e0 + i] = to_store<TO, R>(acc[i]);
+        }
+    }
 }
 
 // ------------------------------------------------------------------ stage
@@ -249,85 +286,105 @@ __device__ __forceinline__ void phys_flux(const StageArgs &a, const R *U, const 
     }
 }
 
+// Numerical flux of the face in slot s of cell c, signed for c (+ into, - out of c).
 template <int DIM, int NV, int NS, int PREC>
-__global__ void __launch_bounds__(128) k_stage(DevMesh mesh, StageArgs a)
+__device__ __forceinline__ void slot_flux(const DevMesh &mesh, const StageArgs &a, int c, int s, bool own_flag,
+                                          typename PrecT<PREC>::R *F)
 {
     using R = typename PrecT<PREC>::R;
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= mesh.n_cells) return;
-    R res[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) res[v] = (R)0;
-    const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
-    const bool own_flag = a.flags && a.flags[c];
-    for (int s = s0; s < s1; ++s) {
-        const int2 sw = __ldg(mesh.slot2 + s);
-        const int nb = sw.x;
-        const unsigned word = (unsigned)sw.y;
-        const int f = (int)(word >> 2);
-        const int side = word & 1;
-        R fr[8];
-        {
-            const R *p = Geo<R>::face(mesh) + 8ll * f;
-            ld4<R>(p, fr[0], fr[1], fr[2], fr[3]);
-            ld4<R>(p + 4, fr[4], fr[5], fr[6], fr[7]);
-        }
-        R F[NV];
-        if (word & 2) {
-            // zero-gradient boundary (Sec 2.6): the auxiliary cell mirrors the cell value
-            R U[NV];
-            load_rec<typename PrecT<PREC>::T0, NV, ord_stride<DIM, NV, 0, PREC>(), R>(
-                static_cast<const typename PrecT<PREC>::T0 *>(a.ord[0]), c, U);
-            phys_flux<DIM, NV, R>(a, U, fr, F);
-        } else {
-            const int P = side ? nb : c, N = side ? c : nb;
-            const bool eno = a.eno_all || (a.flags && (own_flag || a.flags[nb]));
-            R UL[NV], UR[NV];
-            if constexpr (NV == 1) {
-                if (a.flux == 0) {
-                    R an = (R)a.adv[0] * fr[4] + (R)a.adv[1] * fr[5] + (DIM == 3 ? (R)a.adv[2] * fr[6] : (R)0);
-                    bool left = an >= (R)0;
-                    face_states<DIM, NV, NS, PREC, true>(a, fr, P, N, eno, UL, UR, left);
-                    F[0] = an * (left ? UL[0] : UR[0]);
-                } else {
-                    face_states<DIM, NV, NS, PREC, false>(a, fr, P, N, eno, UL, UR, true);
-                    R sg = fr[4] + fr[5] + (DIM == 3 ? fr[6] : (R)0);
-                    R lam = (R)0.5 * (UL[0] + UR[0]) * sg;       // Roe speed of u^2/2 (1,..,1)
-                    R uu = lam >= (R)0 ? UL[0] : UR[0];
-                    F[0] = (R)0.5 * uu * uu * sg;
-                }
+    const int2 sw = __ldg(mesh.slot2 + s);
+    const int nb = sw.x;
+    const unsigned word = (unsigned)sw.y;
+    const int f = (int)(word >> 2);
+    const int side = word & 1;
+    R fr[8];
+    {
+        const R *p = Geo<R>::face(mesh) + 8ll * f;
+        ld4<R>(p, fr[0], fr[1], fr[2], fr[3]);
+        ld4<R>(p + 4, fr[4], fr[5], fr[6], fr[7]);
+    }
+    if (word & 2) {
+        // zero-gradient boundary (Sec 2.6): the auxiliary cell mirrors the cell value
+        R U[NV];
+        load_rec<typename PrecT<PREC>::T0, NV, ord_stride<DIM, NV, 0, PREC>(), R>(
+            static_cast<const typename PrecT<PREC>::T0 *>(a.ord[0]), c, U);
+        phys_flux<DIM, NV, R>(a, U, fr, F);
+    } else {
+        const int P = side ? nb : c, N = side ? c : nb;
+        const bool eno = a.eno_all || (a.flags && (own_flag || a.flags[nb]));
+        R UL[NV], UR[NV];
+        if constexpr (NV == 1) {
+            if (a.flux == 0) {
+                R an = (R)a.adv[0] * fr[4] + (R)a.adv[1] * fr[5] + (DIM == 3 ? (R)a.adv[2] * fr[6] : (R)0);
+                bool left = an >= (R)0;
+                face_states<DIM, NV, NS, PREC, true>(a, fr, P, N, eno, UL, UR, left);
+                F[0] = an * (left ? UL[0] : UR[0]);
             } else {
                 face_states<DIM, NV, NS, PREC, false>(a, fr, P, N, eno, UL, UR, true);
-                rusanov<DIM, R>((R)a.gamma, UL, UR, fr[4], fr[5], fr[6], fr[7], F);
+                R sg = fr[4] + fr[5] + (DIM == 3 ? fr[6] : (R)0);
+                R lam = (R)0.5 * (UL[0] + UR[0]) * sg;       // Roe speed of u^2/2 (1,..,1)
+                R uu = lam >= (R)0 ? UL[0] : UR[0];
+                F[0] = (R)0.5 * uu * uu * sg;
             }
+        } else {
+            face_states<DIM, NV, NS, PREC, false>(a, fr, P, N, eno, UL, UR, true);
+            rusanov<DIM, R>((R)a.gamma, UL, UR, fr[4], fr[5], fr[6], fr[7], F);
         }
-#pragma unroll
-        for (int v = 0; v < NV; ++v) res[v] = side ? res[v] + F[v] : res[v] - F[v];
     }
+    if (!side) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v] = -F[v];
+    }
+}
+
+// LPC lanes per cell: lane l evaluates slots l, l+LPC, ...; the group sums the signed
+// fluxes by recursive halving and lane l then updates variables [l*B, (l+1)*B).
+template <int DIM, int NV, int NS, int PREC, int LPC>
+__global__ void __launch_bounds__(256) k_stage(DevMesh mesh, StageArgs a)
+{
+    using R = typename PrecT<PREC>::R;
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (int)(gt / LPC), l = (int)(gt % LPC);
+    const bool valid = c < mesh.n_cells;
+    constexpr int P = ((NV + LPC - 1) / LPC) * LPC;
+    R res[P];
+#pragma unroll
+    for (int v = 0; v < P; ++v) res[v] = (R)0;
+    if (valid) {
+        const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+        const bool own_flag = a.flags && a.flags[c];
+        for (int s = s0 + l; s < s1; s += LPC) {
+            R F[NV];
+            slot_flux<DIM, NV, NS, PREC>(mesh, a, c, s, own_flag, F);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) res[v] += F[v];
+        }
+    }
+    constexpr int B = P / LPC;
+    if constexpr (LPC > 1) group_reduce_scatter<P, LPC, R>(res, l);
+    if (!valid) return;
     R iv, dummy0, dummy1, dummy2;
     ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, dummy0, dummy1, dummy2, iv);
     const long long n = mesh.n_cells;
     bool bad = false;
-    if (a.mode == 0) {
+    using T0 = typename PrecT<PREC>::T0;
+    T0 *nxt = static_cast<T0 *>(a.o0_next);
+    constexpr int S0 = ord_stride<DIM, NV, 0, PREC>();
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            double r = (double)(res[v] * iv);
-            a.out[v * n + c] = r;
-            bad |= !isfinite(r);
-        }
-    } else {
-        R nxt[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            double rr = (double)(res[v] * iv);
-            double o = a.A * a.u0[v * n + c] + a.B * fma(a.dt, rr, a.us[v * n + c]);
+    for (int i = 0; i < B; ++i) {
+        const int v = l * B + i;
+        if (v < NV) {
+            const double rr = (double)(res[i] * iv);
+            double o;
+            if (a.mode == 0) {
+                o = rr;
+            } else {
+                o = a.A * a.u0[v * n + c] + a.B * fma(a.dt, rr, a.us[v * n + c]);
+                if (nxt) nxt[c * (long long)S0 + v] = (T0)o;
+            }
             a.out[v * n + c] = o;
-            nxt[v] = (R)o;
             bad |= !isfinite(o);
         }
-        if (a.o0_next)
-            store_rec<typename PrecT<PREC>::T0, NV, ord_stride<DIM, NV, 0, PREC>(), R>(
-                static_cast<typename PrecT<PREC>::T0 *>(a.o0_next), c, nxt);
     }
     if (bad) atomicOr(a.status, 1u);
 }

@@ -4,10 +4,15 @@
 
 namespace dol {
 
+// Launch shape of the gather kernels: lanes per cell (1, 4 or 8) and block size.
+struct Tune {
+    int diff_lpc = 4, diff_block = 256, stage_lpc = 4, stage_block = 128;
+};
+
 struct PathFns {
     void (*pack)(const DevMesh &, const double *, void *, cudaStream_t);
-    void (*diff)(const DevMesh &, int M, const void *, void *, cudaStream_t);
-    void (*stage)(const DevMesh &, const StageArgs &, cudaStream_t);
+    void (*diff)(const DevMesh &, int M, const void *, void *, const Tune &, cudaStream_t);
+    void (*stage)(const DevMesh &, const StageArgs &, const Tune &, cudaStream_t);
     void (*faces)(const DevMesh &, const StageArgs &, double *, double *, cudaStream_t);
 };
 
@@ -19,20 +24,33 @@ template <int DIM, int NV, int NS, int PREC> struct Path {
         k_pack<NV, PREC><<<nblk(m.n_cells, 256), 256, 0, s>>>(m.n_cells, u,
                                                               static_cast<typename PrecT<PREC>::T0 *>(o0));
     }
-    static void diff(const DevMesh &m, int M, const void *in, void *out, cudaStream_t s)
+    template <int LPC> static void diff_l(const DevMesh &m, int M, const void *in, void *out, int bs, cudaStream_t s)
     {
-        const int b = nblk(m.n_cells, 256);
+        const int b = nblk((long long)m.n_cells * LPC, bs);
         switch (M) {
-        case 1: k_diff<DIM, NV, 1, PREC><<<b, 256, 0, s>>>(m, in, out); break;
-        case 2: k_diff<DIM, NV, 2, PREC><<<b, 256, 0, s>>>(m, in, out); break;
-        case 3: k_diff<DIM, NV, 3, PREC><<<b, 256, 0, s>>>(m, in, out); break;
-        case 4: k_diff<DIM, NV, 4, PREC><<<b, 256, 0, s>>>(m, in, out); break;
+        case 1: k_diff<DIM, NV, 1, PREC, LPC><<<b, bs, 0, s>>>(m, in, out); break;
+        case 2: k_diff<DIM, NV, 2, PREC, LPC><<<b, bs, 0, s>>>(m, in, out); break;
+        case 3: k_diff<DIM, NV, 3, PREC, LPC><<<b, bs, 0, s>>>(m, in, out); break;
+        case 4: k_diff<DIM, NV, 4, PREC, LPC><<<b, bs, 0, s>>>(m, in, out); break;
         default: break;
         }
     }
-    static void stage(const DevMesh &m, const StageArgs &a, cudaStream_t s)
+    static void diff(const DevMesh &m, int M, const void *in, void *out, const Tune &t, cudaStream_t s)
     {
-        k_stage<DIM, NV, NS, PREC><<<nblk(m.n_cells, 128), 128, 0, s>>>(m, a);
+        switch (t.diff_lpc) {
+        case 4: diff_l<4>(m, M, in, out, t.diff_block, s); break;
+        case 8: diff_l<8>(m, M, in, out, t.diff_block, s); break;
+        default: diff_l<1>(m, M, in, out, t.diff_block, s); break;
+        }
+    }
+    static void stage(const DevMesh &m, const StageArgs &a, const Tune &t, cudaStream_t s)
+    {
+        const int bs = t.stage_block;
+        switch (t.stage_lpc) {
+        case 4: k_stage<DIM, NV, NS, PREC, 4><<<nblk((long long)m.n_cells * 4, bs), bs, 0, s>>>(m, a); break;
+        case 8: k_stage<DIM, NV, NS, PREC, 8><<<nblk((long long)m.n_cells * 8, bs), bs, 0, s>>>(m, a); break;
+        default: k_stage<DIM, NV, NS, PREC, 1><<<nblk(m.n_cells, bs), bs, 0, s>>>(m, a); break;
+        }
     }
     static void faces(const DevMesh &m, const StageArgs &a, double *fL, double *fR, cudaStream_t s)
     {

@@ -341,3 +341,46 @@ def test_eno3_limiter_fp64(mode, name, nv):
     # stencil choices are taken in FP64 on both sides; smooth random data has no ties
     assert rel(got, want) < 1e-12
     dg.dolinc_set_flags(M, None)
+
+
+# ---------------------------------------------------------------------------- launch shapes
+
+@pytest.mark.parametrize("lanes,block", [(1, 64), (1, 256), (4, 128), (4, 32), (8, 256), (8, 96)])
+@pytest.mark.parametrize("name,nv,prec", [("tet", 5, "fp32"), ("hexprism", 1, "fp64"), ("tri_bnd", 4, "fp64"),
+                                          ("tet", 5, "fp32_bf16")])
+def test_launch_shapes_give_the_same_stage(lanes, block, name, nv, prec):
+    """Every lanes-per-cell / block shape the autotuner may pick computes the same stage."""
+    m, O = mesh(name)
+    M = gpu_mesh(m)
+    u = field(m, nv, seed=50)
+    fx = euler_ok(nv) if nv > 1 else dict(flux="upwind", adv=(1.0, 0.5, 0.3))
+    sch = dg.Scheme(k=3, r=1, n_diff=3, nv=nv, precision=prec, **fx)
+    ws = dg.workspace(M, sch)
+    dg.dolinc_set_tuning(M, sch, lanes, block, lanes, block)
+    x = to_dev(M, u)
+    dt = 1e-3
+    dg.dolinc_rk_step(M, sch, dt, x, ws)
+    dg.dolinc_sync_status(M, ws)
+    got = M.from_lib(x.cpu().numpy())
+    want = O.rk3_step(u, oracle.Scheme(k=3, r=1, n_diff=3, nv=nv, **fx), dt)
+    tol = {"fp64": 1e-12, "fp32": 1e-6, "fp32_bf16": 1e-5}[prec]
+    assert rel(got - u, want - u) < tol * 10 or rel(got, want) < tol
+
+
+def test_autotune_picks_a_valid_shape_and_keeps_parity(tmp_path):
+    m, O = mesh("tet")
+    M = gpu_mesh(m)
+    u = field(m, 5, seed=51)
+    sch = dg.Scheme(k=3, r=1, n_diff=2, nv=5, precision="fp64", **euler_ok(5))
+    ws = dg.workspace(M, sch)
+    x = to_dev(M, u)
+    cache = str(tmp_path / "tune.txt")
+    t = dg.dolinc_autotune(M, sch, x, ws, cache_path=cache)
+    assert t["diff_lanes"] in (1, 4, 8) and t["stage_lanes"] in (1, 4, 8) and not t["from_cache"]
+    t2 = dg.dolinc_autotune(M, sch, x, ws, cache_path=cache)
+    assert t2["from_cache"] and t2["stage_lanes"] == t["stage_lanes"]
+    dt = 1e-3
+    dg.dolinc_rk_step(M, sch, dt, x, ws)
+    dg.dolinc_sync_status(M, ws)
+    want = O.rk3_step(u, oracle.Scheme(k=3, r=1, n_diff=2, nv=5, **euler_ok(5)), dt)
+    assert rel(M.from_lib(x.cpu().numpy()), want) < 1e-12
