@@ -217,11 +217,13 @@ dolinc_status dolinc_rk_step_noalloc(dolinc_mesh *mesh, const dolinc_scheme *sch
 
 /* Launch-shape autotuner (no counterpart in the paper).  Times the differential and
  * stage kernels of this mesh and scheme on the given state (u_dev, FP64 [v][cell])
- * for 1, 4 and 8 lanes per cell and blocks of 64, 128, 256 threads, keeps the fastest
- * shape in the mesh handle for every later call with this scheme, and appends it to
- * the text file cache_path (one line per GPU name and mesh/scheme key; may be NULL).
- * A key already in the file is reused without timing.  Synchronous; clears the
- * workspace status word.  Results: *out (may be NULL). */
+ * for 1, 4 and 8 lanes per cell and blocks of 64, 128, 256 threads, and for tiled
+ * launches (0 lanes: one thread per cell, the block's 64/128/256 cells and the faces
+ * they own staged in shared memory), keeps the fastest shape in the mesh handle for
+ * every later call with this scheme, and appends it to the text file cache_path (one
+ * line per GPU name and mesh/scheme key; may be NULL).  A key already in the file is
+ * reused without timing.  Synchronous; clears the workspace status word.  Results:
+ * *out (may be NULL). */
 typedef struct {
     int diff_lanes, diff_block, stage_lanes, stage_block;
     int from_cache;
@@ -229,9 +231,63 @@ typedef struct {
 } dolinc_tuning;
 dolinc_status dolinc_autotune(dolinc_mesh *mesh, const dolinc_scheme *scheme, const double *u_dev, void *ws_dev,
                               size_t ws_bytes, const char *cache_path, dolinc_stream stream, dolinc_tuning *out);
-/* Sets the launch shape used for this mesh and scheme (lanes per cell 1, 4 or 8;
- * block 32..256, a multiple of 32), e.g. a shape read back from an autotuning cache. */
+/* Sets the launch shape used for this mesh and scheme (lanes per cell 1, 4 or 8 with a
+ * block of 32..256 threads, a multiple of 32; or lanes 0, tiled, with a block of 64,
+ * 128 or 256), e.g. a shape read back from an autotuning cache. */
 dolinc_status dolinc_set_tuning(dolinc_mesh *mesh, const dolinc_scheme *scheme, const dolinc_tuning *tuning);
+
+/* ---------------------------------------------------------------- troubled cells
+ * The paper gives ENO3-DOLINC (Sec 2.4) but no rule for where to use it; the
+ * criterion and the network below are this library's, built from the paper's ENO3
+ * indicators and DOLINC differentials.  All need an Euler scheme (RUSANOV) with
+ * n_diff >= 2 and recompute the differentials of u_dev in the workspace.
+ *
+ * Criterion: flags_dev[c] (uint8, library order) = 1 if at one of c's interior faces
+ *   (i) a reconstructed state (either orientation, the scheme's stencil) has rho <= 0
+ *       or p <= 0, or
+ *   (ii) with c upwind, for rho or rho E, the ENO3-DOLINC three-cell indicators of
+ *       Sec 2.4 satisfy |D_C| > kappa min(|D_L|, |D_R|) and |D_C| > eps (|phi_0|+|phi_1|).
+ * Decisions are taken in the scheme's precision.  Defaults used by the tests and the
+ * bench: kappa = 4, eps = 1e-3. */
+dolinc_status dolinc_criterion(dolinc_mesh *mesh, const dolinc_scheme *scheme, const double *u_dev,
+                               uint8_t *flags_dev, double kappa, double eps, void *ws_dev, size_t ws_bytes,
+                               dolinc_stream stream);
+
+/* Network inputs x24_dev [n_cells][24] (FP32): per cell its own 6 features (m = 1, 2:
+ * the largest |phi^(m)| over its faces of rho, rho E and |momentum|, divided by rho,
+ * |E| and sqrt(rho |E|), mapped by log(1+x)), then those of the three largest face
+ * neighbours in lexicographic order (itself across a boundary face). */
+dolinc_status dolinc_indicator_features(dolinc_mesh *mesh, const dolinc_scheme *scheme, const double *u_dev,
+                                        float *x24_dev, void *ws_dev, size_t ws_bytes, dolinc_stream stream);
+
+/* Indicator network 24 -> 64 -> 64 -> 64 -> 1 (ReLU; cell flagged when the logit is
+ * positive).  Parameters: 9985 FP32 values W1[64][24] b1[64] W2[64][64] b2 W3[64][64]
+ * b3 W4[1][64] b4[1], kept on the device (FP32 master + Adam state); the network
+ * computes with their bfloat16 roundings and FP32 accumulation.  Inference runs on
+ * the tensor cores (BF16 activations); training runs in FP32 on the same bfloat16
+ * weights.  The handle owns its device memory (training scratch grows with the batch). */
+typedef struct dolinc_mlp dolinc_mlp;
+#define DOLINC_MLP_PARAMS 9985
+dolinc_status dolinc_mlp_create(dolinc_mlp **out, uint64_t seed);       /* He-uniform, zero biases */
+void dolinc_mlp_destroy(dolinc_mlp *mlp);
+dolinc_status dolinc_mlp_get_params(const dolinc_mlp *mlp, float *host_params);   /* synchronous */
+dolinc_status dolinc_mlp_set_params(dolinc_mlp *mlp, const float *host_params);   /* synchronous */
+/* logits_dev [n] and/or flags_dev [n] (either may be NULL) of inputs x_dev [n][24]. */
+dolinc_status dolinc_mlp_forward(dolinc_mlp *mlp, const float *x_dev, int64_t n, float *logits_dev,
+                                 uint8_t *flags_dev, dolinc_stream stream);
+/* Mean weighted binary cross-entropy on labels y_dev [n] (0/1) with weight pos_weight on
+ * positives, into *loss_dev (device float, may be NULL), and its gradient with respect
+ * to the parameters into grad_dev [9985] (may be NULL). */
+dolinc_status dolinc_mlp_loss_grad(dolinc_mlp *mlp, const float *x_dev, const uint8_t *y_dev, int64_t n,
+                                   float pos_weight, float *grad_dev, float *loss_dev, dolinc_stream stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) with learning rate lr on one batch. */
+dolinc_status dolinc_mlp_train_step(dolinc_mlp *mlp, const float *x_dev, const uint8_t *y_dev, int64_t n,
+                                    float lr, float pos_weight, float *loss_dev, dolinc_stream stream);
+/* Features + network: flags_dev [n_cells] (and logits_dev, may be NULL); x24_dev is
+ * caller scratch of n_cells x 24 floats. */
+dolinc_status dolinc_indicator_infer(dolinc_mesh *mesh, const dolinc_scheme *scheme, dolinc_mlp *mlp,
+                                     const double *u_dev, float *x24_dev, uint8_t *flags_dev, float *logits_dev,
+                                     void *ws_dev, size_t ws_bytes, dolinc_stream stream);
 
 /* Cell flags for DOLINC_LIMIT_ENO3_FLAGGED: flags_dev [n_cells] uint8 (library order),
  * non-zero = troubled.  The pointer is kept by the mesh until replaced or NULL. */

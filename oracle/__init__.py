@@ -72,9 +72,8 @@ def _declare(L):
     L.or_rk3_step.argtypes = [P, P, P, C.c_double, P]
     L.or_rk3_stage.argtypes = [P, P, P, C.c_double, C.c_int, P, P, P]
     L.or_face_weights.argtypes = [P, P, P, P, P]
-    if hasattr(L, "or_indicator_features"):
-        L.or_criterion.argtypes = [P, P, P, P, C.c_double, C.c_double, P]
-        L.or_indicator_features.argtypes = [P, P, P, P, C.c_double, P]
+    L.or_criterion.argtypes = [P, P, P, P, C.c_double, C.c_double, P]
+    L.or_indicator_features.argtypes = [P, P, P, P, C.c_double, P, P]
 
 
 def _ptr(a):
@@ -199,6 +198,27 @@ class Oracle:
         s = scheme._c()
         lib().or_face_weights(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(WL), _ptr(WR))
         return WL.reshape(self.n_faces, 2, -1), WR.reshape(self.n_faces, 2, -1)
+
+    def criterion(self, u, scheme, kappa=4.0, eps=1e-3):
+        """Troubled-cell flags [n_cells] (uint8) of the criterion in indicator_oracle.c."""
+        _, T = self.differentials(u, scheme.n_diff)
+        flags = np.zeros(self.n_cells, dtype=np.uint8)
+        s = scheme._c()
+        if lib().or_criterion(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(T), float(kappa), float(eps),
+                              _ptr(flags)) != 0:
+            raise ValueError("criterion needs Euler with n_diff >= 2")
+        return flags
+
+    def features(self, u, scheme, tiny=1e-6):
+        """(own [n_cells, 6], x [n_cells, 24]) network inputs of indicator_oracle.c."""
+        _, T = self.differentials(u, scheme.n_diff)
+        own = np.zeros((self.n_cells, 6))
+        x = np.zeros((self.n_cells, 24))
+        s = scheme._c()
+        if lib().or_indicator_features(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(T), float(tiny),
+                                       _ptr(own), _ptr(x)) != 0:
+            raise MemoryError
+        return own, x
 
     def residual(self, u, scheme):
         u = np.ascontiguousarray(np.atleast_2d(u), dtype=np.float64)

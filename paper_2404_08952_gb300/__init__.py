@@ -28,7 +28,9 @@ ABI_SYMBOLS = (
     "dolinc_differentials", "dolinc_reconstruct_faces", "dolinc_residual", "dolinc_rk_stage",
     "dolinc_rk_step", "dolinc_set_flags", "dolinc_sync_status", "dolinc_profile_enable",
     "dolinc_profile_read", "dolinc_rk_step_noalloc", "dolinc_autotune", "dolinc_set_tuning",
-    "dolinc_last_error",
+    "dolinc_criterion", "dolinc_indicator_features", "dolinc_mlp_create", "dolinc_mlp_destroy",
+    "dolinc_mlp_get_params", "dolinc_mlp_set_params", "dolinc_mlp_forward", "dolinc_mlp_loss_grad",
+    "dolinc_mlp_train_step", "dolinc_indicator_infer", "dolinc_last_error",
 )
 KERNEL_KINDS = ("pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces")
 
@@ -83,12 +85,20 @@ def load(path=LIB_PATH):
             "dolinc_profile_enable": [P, I], "dolinc_profile_read": [P, P, P],
             "dolinc_rk_step_noalloc": [P, P, D, P, P],
             "dolinc_autotune": [P, P, P, P, S, C.c_char_p, P, P], "dolinc_set_tuning": [P, P, P],
+            "dolinc_criterion": [P, P, P, P, D, D, P, S, P],
+            "dolinc_indicator_features": [P, P, P, P, P, S, P],
+            "dolinc_mlp_create": [P, C.c_uint64], "dolinc_mlp_destroy": [P],
+            "dolinc_mlp_get_params": [P, P], "dolinc_mlp_set_params": [P, P],
+            "dolinc_mlp_forward": [P, P, C.c_int64, P, P, P],
+            "dolinc_mlp_loss_grad": [P, P, P, C.c_int64, C.c_float, P, P, P],
+            "dolinc_mlp_train_step": [P, P, P, C.c_int64, C.c_float, C.c_float, P, P],
+            "dolinc_indicator_infer": [P, P, P, P, P, P, P, P, S, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args
-            fn.restype = C.c_char_p if name == "dolinc_last_error" else (None if name == "dolinc_mesh_destroy"
-                                                                        else C.c_int)
+            fn.restype = C.c_char_p if name == "dolinc_last_error" else (
+                None if name in ("dolinc_mesh_destroy", "dolinc_mlp_destroy") else C.c_int)
         _lib = L
     return _lib
 
@@ -332,3 +342,63 @@ def diff_to_numpy(mesh, scheme, diff, order):
         blk = blk[:, :scheme.nv * Cm].to(torch.float64).cpu().numpy()
         out.append(blk.reshape(mesh.n_cells, scheme.nv, Cm).transpose(1, 0, 2).copy())
     return out
+
+
+# ---------------------------------------------------------------------------- troubled cells
+
+MLP_PARAMS = 9985
+
+
+def dolinc_criterion(mesh, scheme, u, flags, ws, kappa=4.0, eps=1e-3, stream=None):
+    s = scheme.c()
+    _check(load().dolinc_criterion(mesh.handle, C.byref(s), _ptr(u), _ptr(flags), float(kappa), float(eps),
+                                   _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def dolinc_indicator_features(mesh, scheme, u, x24, ws, stream=None):
+    s = scheme.c()
+    _check(load().dolinc_indicator_features(mesh.handle, C.byref(s), _ptr(u), _ptr(x24), _ptr(ws), ws.numel(),
+                                            _stream(stream)))
+
+
+class MLP:
+    """The indicator network (device-resident parameters, Adam state)."""
+
+    def __init__(self, seed=0):
+        h = C.c_void_p()
+        _check(load().dolinc_mlp_create(C.byref(h), C.c_uint64(seed)))
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.dolinc_mlp_destroy(h)
+            self.handle = None
+
+    def get_params(self):
+        out = np.zeros(MLP_PARAMS, dtype=np.float32)
+        _check(load().dolinc_mlp_get_params(self.handle, _ptr(out)))
+        return out
+
+    def set_params(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        assert theta.shape == (MLP_PARAMS,)
+        _check(load().dolinc_mlp_set_params(self.handle, _ptr(theta)))
+
+    def forward(self, x, logits=None, flags=None, stream=None):
+        _check(load().dolinc_mlp_forward(self.handle, _ptr(x), x.shape[0], _ptr(logits), _ptr(flags),
+                                         _stream(stream)))
+
+    def loss_grad(self, x, y, pos_weight, grad=None, loss=None, stream=None):
+        _check(load().dolinc_mlp_loss_grad(self.handle, _ptr(x), _ptr(y), x.shape[0], float(pos_weight), _ptr(grad),
+                                           _ptr(loss), _stream(stream)))
+
+    def train_step(self, x, y, lr, pos_weight, loss=None, stream=None):
+        _check(load().dolinc_mlp_train_step(self.handle, _ptr(x), _ptr(y), x.shape[0], float(lr), float(pos_weight),
+                                            _ptr(loss), _stream(stream)))
+
+
+def dolinc_indicator_infer(mesh, scheme, mlp, u, x24, flags, ws, logits=None, stream=None):
+    s = scheme.c()
+    _check(load().dolinc_indicator_infer(mesh.handle, C.byref(s), mlp.handle, _ptr(u), _ptr(x24), _ptr(flags),
+                                         _ptr(logits), _ptr(ws), ws.numel(), _stream(stream)))

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/dolinc.h"
+#include "indicator.cuh"
 #include "launch.cuh"
 #include "mesh.hpp"
 
@@ -36,11 +37,14 @@ dolinc_status fail(dolinc_status s, const std::string &msg)
     } while (0)
 
 PathFns g_paths[N_PATHS];
+IndicatorFns g_ind[N_INDICATOR];
 std::once_flag g_once;
 
 void init_paths()
 {
     std::memset(g_paths, 0, sizeof g_paths);
+    std::memset(g_ind, 0, sizeof g_ind);
+    register_indicator(g_ind);
     register_paths_d2s(g_paths);
     register_paths_d2e(g_paths);
     register_paths_d3s(g_paths);
@@ -81,6 +85,31 @@ struct dolinc_mesh {
         cudaGetDevice(&cur);
         cudaSetDevice(device);
         for (void *p : allocs) cudaFree(p);
+        cudaSetDevice(cur);
+    }
+};
+
+struct dolinc_mlp {
+    int device = 0;
+    float *theta = nullptr, *q = nullptr, *m = nullptr, *v = nullptr, *g = nullptr, *loss = nullptr;
+    uint2 *frag = nullptr;
+    bool frag_ok = false;
+    int step = 0;
+    long long cap = 0;
+    float *A1 = nullptr, *A2 = nullptr, *A3 = nullptr, *z = nullptr, *dZa = nullptr, *dZb = nullptr;
+    void free_scratch()
+    {
+        for (float *p : {A1, A2, A3, z, dZa, dZb}) cudaFree(p);
+        A1 = A2 = A3 = z = dZa = dZb = nullptr;
+        cap = 0;
+    }
+    ~dolinc_mlp()
+    {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(device);
+        free_scratch();
+        for (void *p : {(void *)theta, (void *)q, (void *)m, (void *)v, (void *)g, (void *)loss, (void *)frag}) cudaFree(p);
         cudaSetDevice(cur);
     }
 };
@@ -316,17 +345,29 @@ dolinc_status dolinc_mesh_create(const dolinc_mesh_desc *desc, dolinc_mesh **out
     }
     std::vector<int32_t> off(h.off.begin(), h.off.end());
     for (int64_t c = 0; c < nc; ++c) m->max_faces = std::max(m->max_faces, (int)(h.off[c + 1] - h.off[c]));
+    // first internal face owned by each cell (faces are sorted by owner)
+    std::vector<int32_t> fown(nc + 1, 0);
+    for (int64_t f = 0; f < nf; ++f) fown[h.fo[f] + 1]++;
+    for (int64_t c = 0; c < nc; ++c) fown[c + 1] += fown[c];
+    int mtf[3] = {0, 0, 0};
+    const int tiles[3] = {64, 128, 256};
+    for (int ti = 0; ti < 3; ++ti)
+        for (int64_t t0 = 0; t0 < nc; t0 += tiles[ti]) {
+            int64_t t1 = std::min<int64_t>(nc, t0 + tiles[ti]);
+            mtf[ti] = std::max(mtf[ti], fown[t1] - fown[t0]);
+        }
     dolinc_status st = DOLINC_OK;
     DevMesh &d = m->d;
     d.dim = h.dim;
     d.n_cells = (int)nc;
     d.n_faces = (int)nf;
     d.n_slots = (int)ns;
+    for (int ti = 0; ti < 3; ++ti) d.max_tile_faces[ti] = mtf[ti];
     if ((st = upload(m, off, &d.off)) || (st = upload(m, slot2, &d.slot2)) || (st = upload(m, sk64, &d.slotk64)) ||
         (st = upload(m, sk32, &d.slotk32)) || (st = upload(m, ck64, &d.cellk64)) ||
         (st = upload(m, ck32, &d.cellk32)) || (st = upload(m, f64, &d.face64)) || (st = upload(m, f32, &d.face32)) ||
         (st = upload(m, fo, &d.fo)) || (st = upload(m, fn, &d.fn)) || (st = upload(m, fe, &d.face_ext)) ||
-        (st = upload(m, ff, &d.face_flip))) {
+        (st = upload(m, ff, &d.face_flip)) || (st = upload(m, fown, &d.fown))) {
         delete m;
         return st;
     }
@@ -612,9 +653,9 @@ dolinc_status dolinc_autotune(dolinc_mesh *m, const dolinc_scheme *s, const doub
             cudaEventElapsedTime(&ms, e0, e1);
             return ms / 5.0;
         };
-        const int lpcs[3] = {1, 4, 8}, blocks[3] = {64, 128, 256};
+        const int lpcs[4] = {1, 4, 8, 0}, blocks[3] = {64, 128, 256};
         double bd = 1e30, bs = 1e30;
-        for (int li = 0; li < 3; ++li)
+        for (int li = 0; li < 4; ++li)
             for (int bi = 0; bi < 3; ++bi) {
                 Tune t;
                 t.diff_lpc = t.stage_lpc = lpcs[li];
@@ -656,15 +697,217 @@ dolinc_status dolinc_autotune(dolinc_mesh *m, const dolinc_scheme *s, const doub
     return launch_check();
 }
 
+// ------------------------------------------------------------------ indicator and network
+namespace {
+dolinc_status indicator_prep(dolinc_mesh *m, const dolinc_scheme *s, const double *u, void *ws, size_t ws_bytes,
+                             cudaStream_t cs, WsLayout &L, const IndicatorFns **fi)
+{
+    dolinc_status st = check_scheme(m, s);
+    if (st) return st;
+    if ((st = check_ws(m, s, ws, ws_bytes, L))) return st;
+    if (!u) return fail(DOLINC_ERR_INVALID_ARG, "null field");
+    if (s->flux != DOLINC_FLUX_RUSANOV || s->n_diff < 2)
+        return fail(DOLINC_ERR_INVALID_ARG, "the indicator needs an Euler scheme with n_diff >= 2");
+    const PathFns *p = path_for(m, s, needed_order(*s));
+    if (!p) return fail(DOLINC_ERR_UNSUPPORTED, "no kernel for this (dim, nv, order, precision)");
+    const int nsr = needed_order(*s) > 2 ? needed_order(*s) : 2;
+    *fi = &g_ind[indicator_index(m->h.dim, nsr, s->precision)];
+    if (!(*fi)->criterion) return fail(DOLINC_ERR_UNSUPPORTED, "no indicator kernel for this scheme");
+    timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, u, B(ws, L.o0[0]), cs); });
+    run_diffs(m, p, ws, L, L.o0[0], s->n_diff, tune_for(m, s), cs);
+    return DOLINC_OK;
+}
+
+uint64_t splitmix(uint64_t &x)
+{
+    uint64_t z = (x += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+dolinc_status mlp_scratch(dolinc_mlp *m, long long n)
+{
+    if (n <= m->cap) return DOLINC_OK;
+    m->free_scratch();
+    const size_t h = sizeof(float) * (size_t)n * MLP_H;
+    CU(cudaMalloc(&m->A1, h));
+    CU(cudaMalloc(&m->A2, h));
+    CU(cudaMalloc(&m->A3, h));
+    CU(cudaMalloc(&m->z, sizeof(float) * (size_t)n));
+    CU(cudaMalloc(&m->dZa, h));
+    CU(cudaMalloc(&m->dZb, h));
+    m->cap = n;
+    return DOLINC_OK;
+}
+
+// loss and gradient of one batch into m->g (and *loss_dev); forward on the bf16 weights
+dolinc_status mlp_grad(dolinc_mlp *m, const float *x, const uint8_t *y, long long n, float pw, float *loss_dev,
+                       cudaStream_t cs)
+{
+    dolinc_status st = mlp_scratch(m, n);
+    if (st) return st;
+    const float *q = m->q;
+    launch_quantize(m->theta, m->q, cs);
+    launch_dense_fwd(x, MLP_IN, q + OFF_W1, q + OFF_B1, MLP_H, n, m->A1, true, cs);
+    launch_dense_fwd(m->A1, MLP_H, q + OFF_W2, q + OFF_B2, MLP_H, n, m->A2, true, cs);
+    launch_dense_fwd(m->A2, MLP_H, q + OFF_W3, q + OFF_B3, MLP_H, n, m->A3, true, cs);
+    launch_dense_fwd(m->A3, MLP_H, q + OFF_W4, q + OFF_B4, 1, n, m->z, false, cs);
+    CU(cudaMemsetAsync(m->g, 0, sizeof(float) * MLP_PARAMS, cs));
+    if (loss_dev) CU(cudaMemsetAsync(loss_dev, 0, sizeof(float), cs));
+    float *dz = m->dZa;
+    launch_bce(m->z, y, n, pw, dz, loss_dev, cs);
+    launch_dense_bwd_w(dz, m->A3, MLP_H, 1, n, m->g + OFF_W4, m->g + OFF_B4, cs);
+    launch_dense_bwd_x(dz, q + OFF_W4, MLP_H, 1, n, m->A3, m->dZb, cs);              // dZ3
+    launch_dense_bwd_w(m->dZb, m->A2, MLP_H, MLP_H, n, m->g + OFF_W3, m->g + OFF_B3, cs);
+    launch_dense_bwd_x(m->dZb, q + OFF_W3, MLP_H, MLP_H, n, m->A2, m->dZa, cs);     // dZ2
+    launch_dense_bwd_w(m->dZa, m->A1, MLP_H, MLP_H, n, m->g + OFF_W2, m->g + OFF_B2, cs);
+    launch_dense_bwd_x(m->dZa, q + OFF_W2, MLP_H, MLP_H, n, m->A1, m->dZb, cs);     // dZ1
+    launch_dense_bwd_w(m->dZb, x, MLP_IN, MLP_H, n, m->g + OFF_W1, m->g + OFF_B1, cs);
+    return launch_check();
+}
+}  // namespace
+
+dolinc_status dolinc_criterion(dolinc_mesh *m, const dolinc_scheme *s, const double *u, uint8_t *flags, double kappa,
+                               double eps, void *ws, size_t ws_bytes, dolinc_stream stream)
+{
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    WsLayout L;
+    const IndicatorFns *fi = nullptr;
+    if (!flags) return fail(DOLINC_ERR_INVALID_ARG, "null flags");
+    dolinc_status st = indicator_prep(m, s, u, ws, ws_bytes, cs, L, &fi);
+    if (st) return st;
+    StageArgs a = base_args(m, s, ws, L, L.o0[0]);
+    fi->criterion(m->d, a, kappa, eps, flags, cs);
+    return launch_check();
+}
+
+dolinc_status dolinc_indicator_features(dolinc_mesh *m, const dolinc_scheme *s, const double *u, float *x24,
+                                        void *ws, size_t ws_bytes, dolinc_stream stream)
+{
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    WsLayout L;
+    const IndicatorFns *fi = nullptr;
+    if (!x24) return fail(DOLINC_ERR_INVALID_ARG, "null feature buffer");
+    dolinc_status st = indicator_prep(m, s, u, ws, ws_bytes, cs, L, &fi);
+    if (st) return st;
+    StageArgs a = base_args(m, s, ws, L, L.o0[0]);
+    float *own = reinterpret_cast<float *>(B(ws, L.ustage));   // 6 floats per cell fit in nv doubles
+    fi->own_features(m->d, a, own, cs);
+    launch_gather24(m->d, own, x24, cs);
+    return launch_check();
+}
+
+dolinc_status dolinc_mlp_create(dolinc_mlp **out, uint64_t seed)
+{
+    if (!out) return fail(DOLINC_ERR_INVALID_ARG, "null output handle");
+    *out = nullptr;
+    dolinc_mlp *m = new (std::nothrow) dolinc_mlp();
+    if (!m) return fail(DOLINC_ERR_OOM, "host allocation");
+    cudaGetDevice(&m->device);
+    std::vector<float> th(MLP_PARAMS, 0.0f);
+    uint64_t st = seed;
+    const int sizes[4][3] = {{OFF_W1, MLP_H, MLP_IN}, {OFF_W2, MLP_H, MLP_H}, {OFF_W3, MLP_H, MLP_H}, {OFF_W4, 1, MLP_H}};
+    for (auto &L : sizes) {
+        const float lim = std::sqrt(6.0f / (float)L[2]);              // He-uniform
+        for (int i = 0; i < L[1] * L[2]; ++i) {
+            double u01 = (double)(splitmix(st) >> 11) * (1.0 / 9007199254740992.0);
+            th[L[0] + i] = (float)((2.0 * u01 - 1.0) * lim);
+        }
+    }
+    auto al = [&](void **p, size_t b) { return cudaMalloc(p, b); };
+    cudaError_t e = cudaSuccess;
+    for (float **p : {&m->theta, &m->q, &m->m, &m->v, &m->g})
+        if (e == cudaSuccess) e = al((void **)p, sizeof(float) * MLP_PARAMS);
+    if (e == cudaSuccess) e = al((void **)&m->loss, sizeof(float));
+    if (e == cudaSuccess) e = al((void **)&m->frag, sizeof(uint2) * N_FRAGS * 32);
+    if (e == cudaSuccess) e = cudaMemcpy(m->theta, th.data(), sizeof(float) * MLP_PARAMS, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(m->m, 0, sizeof(float) * MLP_PARAMS);
+    if (e == cudaSuccess) e = cudaMemset(m->v, 0, sizeof(float) * MLP_PARAMS);
+    if (e != cudaSuccess) {
+        delete m;
+        return fail(e == cudaErrorMemoryAllocation ? DOLINC_ERR_OOM : DOLINC_ERR_CUDA,
+                    std::string("dolinc_mlp_create: ") + cudaGetErrorString(e));
+    }
+    *out = m;
+    return DOLINC_OK;
+}
+
+void dolinc_mlp_destroy(dolinc_mlp *m) { delete m; }
+
+dolinc_status dolinc_mlp_get_params(const dolinc_mlp *m, float *host)
+{
+    if (!m || !host) return fail(DOLINC_ERR_INVALID_ARG, "null argument");
+    CU(cudaMemcpy(host, m->theta, sizeof(float) * MLP_PARAMS, cudaMemcpyDeviceToHost));
+    return DOLINC_OK;
+}
+
+dolinc_status dolinc_mlp_set_params(dolinc_mlp *m, const float *host)
+{
+    if (!m || !host) return fail(DOLINC_ERR_INVALID_ARG, "null argument");
+    CU(cudaMemcpy(m->theta, host, sizeof(float) * MLP_PARAMS, cudaMemcpyHostToDevice));
+    m->frag_ok = false;
+    return DOLINC_OK;
+}
+
+dolinc_status dolinc_mlp_forward(dolinc_mlp *m, const float *x, int64_t n, float *logits, uint8_t *flags,
+                                 dolinc_stream stream)
+{
+    if (!m || !x || n < 0 || (!logits && !flags)) return fail(DOLINC_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    if (!m->frag_ok) {
+        launch_mlp_frags(m->theta, m->frag, cs);
+        m->frag_ok = true;
+    }
+    if (n > 0) launch_mlp_infer(m->frag, m->theta, x, n, logits, flags, cs);
+    return launch_check();
+}
+
+dolinc_status dolinc_mlp_loss_grad(dolinc_mlp *m, const float *x, const uint8_t *y, int64_t n, float pos_weight,
+                                   float *grad, float *loss, dolinc_stream stream)
+{
+    if (!m || !x || !y || n <= 0) return fail(DOLINC_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    dolinc_status st = mlp_grad(m, x, y, n, pos_weight, loss, cs);
+    if (st) return st;
+    if (grad) CU(cudaMemcpyAsync(grad, m->g, sizeof(float) * MLP_PARAMS, cudaMemcpyDeviceToDevice, cs));
+    return DOLINC_OK;
+}
+
+dolinc_status dolinc_mlp_train_step(dolinc_mlp *m, const float *x, const uint8_t *y, int64_t n, float lr,
+                                    float pos_weight, float *loss, dolinc_stream stream)
+{
+    if (!m || !x || !y || n <= 0) return fail(DOLINC_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    dolinc_status st = mlp_grad(m, x, y, n, pos_weight, loss, cs);
+    if (st) return st;
+    m->step += 1;
+    launch_adam(m->theta, m->m, m->v, m->g, MLP_PARAMS, lr, m->step, cs);
+    m->frag_ok = false;
+    return launch_check();
+}
+
+dolinc_status dolinc_indicator_infer(dolinc_mesh *me, const dolinc_scheme *s, dolinc_mlp *net, const double *u,
+                                     float *x24, uint8_t *flags, float *logits, void *ws, size_t ws_bytes,
+                                     dolinc_stream stream)
+{
+    dolinc_status st = dolinc_indicator_features(me, s, u, x24, ws, ws_bytes, stream);
+    if (st) return st;
+    return dolinc_mlp_forward(net, x24, me->h.n_cells, logits, flags, stream);
+}
+
 dolinc_status dolinc_set_tuning(dolinc_mesh *m, const dolinc_scheme *s, const dolinc_tuning *t)
 {
     dolinc_status st = check_scheme(m, s);
     if (st) return st;
     if (!t) return fail(DOLINC_ERR_INVALID_ARG, "null tuning");
-    auto ok_l = [](int l) { return l == 1 || l == 4 || l == 8; };
-    auto ok_b = [](int b) { return b >= 32 && b <= 256 && b % 32 == 0; };
-    if (!ok_l(t->diff_lanes) || !ok_l(t->stage_lanes) || !ok_b(t->diff_block) || !ok_b(t->stage_block))
-        return fail(DOLINC_ERR_INVALID_ARG, "lanes must be 1, 4 or 8 and blocks a multiple of 32 in 32..256");
+    auto ok = [](int l, int b) {
+        if (l == 0) return b == 64 || b == 128 || b == 256;
+        return (l == 1 || l == 4 || l == 8) && b >= 32 && b <= 256 && b % 32 == 0;
+    };
+    if (!ok(t->diff_lanes, t->diff_block) || !ok(t->stage_lanes, t->stage_block))
+        return fail(DOLINC_ERR_INVALID_ARG,
+                    "lanes 1, 4 or 8 with blocks a multiple of 32 in 32..256, or lanes 0 (tiled) with 64/128/256");
     Tune x;
     x.diff_lpc = t->diff_lanes;
     x.diff_block = t->diff_block;

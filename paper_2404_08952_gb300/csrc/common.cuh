@@ -41,7 +41,15 @@ template <> __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16, dou
 
 // ------------------------------------------------------------------ record load/store
 // Loads the first N elements of a record of stride S (elements of T) into registers.
-template <class T, int N, int S, class R>
+// LDG: read through the read-only data path (global memory only); otherwise a generic
+// load that also serves shared memory.
+template <bool LDG, class V> __device__ __forceinline__ V ldv(const V *p)
+{
+    if constexpr (LDG) return __ldg(p);
+    else return *p;
+}
+
+template <class T, int N, int S, class R, bool LDG = true>
 __device__ __forceinline__ void load_rec(const T *__restrict__ base, long long cell, R *out)
 {
     const T *p = base + cell * (long long)S;
@@ -51,7 +59,7 @@ __device__ __forceinline__ void load_rec(const T *__restrict__ base, long long c
         constexpr int NV = (N + V - 1) / V;
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
-            uint4 q = __ldg(reinterpret_cast<const uint4 *>(p) + i);
+            uint4 q = ldv<LDG>(reinterpret_cast<const uint4 *>(p) + i);
             const T *e = reinterpret_cast<const T *>(&q);
 #pragma unroll
             for (int j = 0; j < V; ++j)
@@ -62,7 +70,7 @@ __device__ __forceinline__ void load_rec(const T *__restrict__ base, long long c
         constexpr int NV = (N + V - 1) / V;
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
-            uint2 q = __ldg(reinterpret_cast<const uint2 *>(p) + i);
+            uint2 q = ldv<LDG>(reinterpret_cast<const uint2 *>(p) + i);
             const T *e = reinterpret_cast<const T *>(&q);
 #pragma unroll
             for (int j = 0; j < V; ++j)
@@ -70,7 +78,7 @@ __device__ __forceinline__ void load_rec(const T *__restrict__ base, long long c
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < N; ++i) out[i] = cvt<R>(p[i]);
+        for (int i = 0; i < N; ++i) out[i] = cvt<R>(ldv<LDG>(p + i));
     }
 }
 

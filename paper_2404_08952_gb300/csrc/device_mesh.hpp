@@ -18,6 +18,8 @@ struct DevMesh {
     const int32_t *fo, *fn;      // [n_faces] internal owner / neighbour (-1 boundary)
     const int32_t *face_ext;     // [n_faces] caller face id
     const int8_t *face_flip;     // [n_faces] 1 if the caller orientation is reversed
+    const int32_t *fown;         // [n_cells+1] first internal face owned by each cell
+    int max_tile_faces[3];       // most faces owned by a tile of 64 / 128 / 256 cells
 };
 
 }  // namespace dol

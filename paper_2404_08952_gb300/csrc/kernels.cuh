@@ -44,14 +44,14 @@ template <> struct Geo<float> {
     static __device__ __forceinline__ int nb_of(float w) { return __float_as_int(w); }
 };
 
-template <class R> __device__ __forceinline__ void ld4(const R *p, R &a, R &b, R &c, R &d)
+template <class R, bool LDG = true> __device__ __forceinline__ void ld4(const R *p, R &a, R &b, R &c, R &d)
 {
     if constexpr (sizeof(R) == 4) {
-        float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+        float4 v = ldv<LDG>(reinterpret_cast<const float4 *>(p));
         a = v.x, b = v.y, c = v.z, d = v.w;
     } else {
-        double2 v0 = __ldg(reinterpret_cast<const double2 *>(p));
-        double2 v1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+        double2 v0 = ldv<LDG>(reinterpret_cast<const double2 *>(p));
+        double2 v1 = ldv<LDG>(reinterpret_cast<const double2 *>(p) + 1);
         a = v0.x, b = v0.y, c = v1.x, d = v1.y;
     }
 }
@@ -152,16 +152,54 @@ struct StageArgs {
     int eno_all;
 };
 
+// Where a kernel reads cell records and face records from.  GlobalSrc: device memory
+// through the read-only path.  TileSrc (k_stage_tile): the block's own cells and the
+// faces they own were staged in shared memory; other cells/faces come from global.
+template <int DIM, int NV, int PREC> struct GlobalSrc {
+    using R = typename PrecT<PREC>::R;
+    static constexpr bool LDG = true;
+    const StageArgs &a;
+    const DevMesh &mesh;
+    template <int M> __device__ __forceinline__ const typename OrdT<PREC, M>::T *rec(int X) const
+    {
+        return static_cast<const typename OrdT<PREC, M>::T *>(a.ord[M]) + (long long)X * ord_stride<DIM, NV, M, PREC>();
+    }
+    __device__ __forceinline__ const R *face(int f) const { return Geo<R>::face(mesh) + 8ll * f; }
+};
+
+template <int DIM, int NV, int NS, int PREC> struct TileSrc {
+    using R = typename PrecT<PREC>::R;
+    static constexpr bool LDG = false;
+    const StageArgs &a;
+    const DevMesh &mesh;
+    const unsigned char *sm;          // staged records of orders 0..NS, then faces
+    int t0, nt, f_lo, f_hi;
+    unsigned off[NS + 2];             // byte offsets of order m (m = 0..NS) and of the faces
+    template <int M> __device__ __forceinline__ const typename OrdT<PREC, M>::T *rec(int X) const
+    {
+        using T = typename OrdT<PREC, M>::T;
+        constexpr int S = ord_stride<DIM, NV, M, PREC>();
+        const unsigned i = (unsigned)(X - t0);
+        if (i < (unsigned)nt) return reinterpret_cast<const T *>(sm + off[M]) + (long long)i * S;
+        return static_cast<const T *>(a.ord[M]) + (long long)X * S;
+    }
+    __device__ __forceinline__ const R *face(int f) const
+    {
+        if (f >= f_lo && f < f_hi) return reinterpret_cast<const R *>(sm + off[NS + 1]) + 8ll * (f - f_lo);
+        return Geo<R>::face(mesh) + 8ll * f;
+    }
+};
+
 // phi^(m) of every variable of cell X along the monomials of d (m = 0..NS)
-template <int DIM, int NV, int NS, int PREC, int M>
-__device__ __forceinline__ void contract_order(const StageArgs &a, int X, const typename PrecT<PREC>::R *mono,
+template <int DIM, int NV, int NS, int PREC, int M, class Src>
+__device__ __forceinline__ void contract_order(const Src &src, int X, const typename PrecT<PREC>::R *mono,
                                                typename PrecT<PREC>::R (*ph)[NS + 1])
 {
     using R = typename PrecT<PREC>::R;
     using T = typename OrdT<PREC, M>::T;
     constexpr int C = ncoef(DIM, M);
     R rec[NV * C];
-    load_rec<T, NV * C, ord_stride<DIM, NV, M, PREC>(), R>(static_cast<const T *>(a.ord[M]), X, rec);
+    load_rec<T, NV * C, ord_stride<DIM, NV, M, PREC>(), R, Src::LDG>(src.template rec<M>(X), 0, rec);
     constexpr int mo = ncum(DIM, M - 1);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -172,22 +210,30 @@ __device__ __forceinline__ void contract_order(const StageArgs &a, int X, const 
     }
 }
 
-template <int DIM, int NV, int NS, int PREC>
-__device__ __forceinline__ void contract_cell(const StageArgs &a, int X, const typename PrecT<PREC>::R *mono,
+template <int DIM, int NV, int NS, int PREC, class Src>
+__device__ __forceinline__ void contract_cell(const Src &src, int X, const typename PrecT<PREC>::R *mono,
                                               typename PrecT<PREC>::R (*ph)[NS + 1])
 {
     using R = typename PrecT<PREC>::R;
     {
         R rec[NV];
-        load_rec<typename PrecT<PREC>::T0, NV, ord_stride<DIM, NV, 0, PREC>(), R>(
-            static_cast<const typename PrecT<PREC>::T0 *>(a.ord[0]), X, rec);
+        load_rec<typename PrecT<PREC>::T0, NV, ord_stride<DIM, NV, 0, PREC>(), R, Src::LDG>(src.template rec<0>(X),
+                                                                                             0, rec);
 #pragma unroll
         for (int v = 0; v < NV; ++v) ph[v][0] = rec[v];
     }
-    if constexpr (NS >= 1) contract_order<DIM, NV, NS, PREC, 1>(a, X, mono, ph);
-    if constexpr (NS >= 2) contract_order<DIM, NV, NS, PREC, 2>(a, X, mono, ph);
-    if constexpr (NS >= 3) contract_order<DIM, NV, NS, PREC, 3>(a, X, mono, ph);
-    if constexpr (NS >= 4) contract_order<DIM, NV, NS, PREC, 4>(a, X, mono, ph);
+    if constexpr (NS >= 1) contract_order<DIM, NV, NS, PREC, 1>(src, X, mono, ph);
+    if constexpr (NS >= 2) contract_order<DIM, NV, NS, PREC, 2>(src, X, mono, ph);
+    if constexpr (NS >= 3) contract_order<DIM, NV, NS, PREC, 3>(src, X, mono, ph);
+    if constexpr (NS >= 4) contract_order<DIM, NV, NS, PREC, 4>(src, X, mono, ph);
+}
+
+template <int DIM, int NV, int NS, int PREC>
+__device__ __forceinline__ void contract_cell(const StageArgs &a, int X, const typename PrecT<PREC>::R *mono,
+                                              typename PrecT<PREC>::R (*ph)[NS + 1], const DevMesh &mesh)
+{
+    GlobalSrc<DIM, NV, PREC> src{a, mesh};
+    contract_cell<DIM, NV, NS, PREC>(src, X, mono, ph);
 }
 
 // ENO3-DOLINC value of one variable (Sec 2.4): far values n = -2..2 by Eq diffDLC, the
@@ -216,18 +262,18 @@ __device__ __forceinline__ R eno3_value(R g, const R *p0, const R *p1)
 }
 
 // Both face states (or the upwind one only for linear advection) of face record fr.
-template <int DIM, int NV, int NS, int PREC, bool UPWIND_ONLY>
-__device__ __forceinline__ void face_states(const StageArgs &a, const typename PrecT<PREC>::R *fr, int P, int N,
-                                            bool eno, typename PrecT<PREC>::R *UL, typename PrecT<PREC>::R *UR,
-                                            bool want_left)
+template <int DIM, int NV, int NS, int PREC, bool UPWIND_ONLY, class Src>
+__device__ __forceinline__ void face_states(const StageArgs &a, const Src &src, const typename PrecT<PREC>::R *fr,
+                                            int P, int N, bool eno, typename PrecT<PREC>::R *UL,
+                                            typename PrecT<PREC>::R *UR, bool want_left)
 {
     using R = typename PrecT<PREC>::R;
     constexpr int NM = ncum(DIM, NS);
     R mono[NM];
     monomials<DIM, NS, R>(fr[0], fr[1], fr[2], mono);
     R phP[NV][NS + 1], phN[NV][NS + 1];
-    contract_cell<DIM, NV, NS, PREC>(a, P, mono, phP);
-    contract_cell<DIM, NV, NS, PREC>(a, N, mono, phN);
+    contract_cell<DIM, NV, NS, PREC>(src, P, mono, phP);
+    contract_cell<DIM, NV, NS, PREC>(src, N, mono, phN);
     const R g = fr[3];
     if constexpr (NS >= 2) {
         if (eno) {
@@ -287,9 +333,9 @@ __device__ __forceinline__ void phys_flux(const StageArgs &a, const R *U, const 
 }
 
 // Numerical flux of the face in slot s of cell c, signed for c (+ into, - out of c).
-template <int DIM, int NV, int NS, int PREC>
-__device__ __forceinline__ void slot_flux(const DevMesh &mesh, const StageArgs &a, int c, int s, bool own_flag,
-                                          typename PrecT<PREC>::R *F)
+template <int DIM, int NV, int NS, int PREC, class Src>
+__device__ __forceinline__ void slot_flux(const DevMesh &mesh, const StageArgs &a, const Src &src, int c, int s,
+                                          bool own_flag, typename PrecT<PREC>::R *F)
 {
     using R = typename PrecT<PREC>::R;
     const int2 sw = __ldg(mesh.slot2 + s);
@@ -299,15 +345,15 @@ __device__ __forceinline__ void slot_flux(const DevMesh &mesh, const StageArgs &
     const int side = word & 1;
     R fr[8];
     {
-        const R *p = Geo<R>::face(mesh) + 8ll * f;
-        ld4<R>(p, fr[0], fr[1], fr[2], fr[3]);
-        ld4<R>(p + 4, fr[4], fr[5], fr[6], fr[7]);
+        const R *p = src.face(f);
+        ld4<R, Src::LDG>(p, fr[0], fr[1], fr[2], fr[3]);
+        ld4<R, Src::LDG>(p + 4, fr[4], fr[5], fr[6], fr[7]);
     }
     if (word & 2) {
         // zero-gradient boundary (Sec 2.6): the auxiliary cell mirrors the cell value
         R U[NV];
-        load_rec<typename PrecT<PREC>::T0, NV, ord_stride<DIM, NV, 0, PREC>(), R>(
-            static_cast<const typename PrecT<PREC>::T0 *>(a.ord[0]), c, U);
+        load_rec<typename PrecT<PREC>::T0, NV, ord_stride<DIM, NV, 0, PREC>(), R, Src::LDG>(src.template rec<0>(c), 0,
+                                                                                            U);
         phys_flux<DIM, NV, R>(a, U, fr, F);
     } else {
         const int P = side ? nb : c, N = side ? c : nb;
@@ -317,17 +363,17 @@ __device__ __forceinline__ void slot_flux(const DevMesh &mesh, const StageArgs &
             if (a.flux == 0) {
                 R an = (R)a.adv[0] * fr[4] + (R)a.adv[1] * fr[5] + (DIM == 3 ? (R)a.adv[2] * fr[6] : (R)0);
                 bool left = an >= (R)0;
-                face_states<DIM, NV, NS, PREC, true>(a, fr, P, N, eno, UL, UR, left);
+                face_states<DIM, NV, NS, PREC, true>(a, src, fr, P, N, eno, UL, UR, left);
                 F[0] = an * (left ? UL[0] : UR[0]);
             } else {
-                face_states<DIM, NV, NS, PREC, false>(a, fr, P, N, eno, UL, UR, true);
+                face_states<DIM, NV, NS, PREC, false>(a, src, fr, P, N, eno, UL, UR, true);
                 R sg = fr[4] + fr[5] + (DIM == 3 ? fr[6] : (R)0);
                 R lam = (R)0.5 * (UL[0] + UR[0]) * sg;       // Roe speed of u^2/2 (1,..,1)
                 R uu = lam >= (R)0 ? UL[0] : UR[0];
                 F[0] = (R)0.5 * uu * uu * sg;
             }
         } else {
-            face_states<DIM, NV, NS, PREC, false>(a, fr, P, N, eno, UL, UR, true);
+            face_states<DIM, NV, NS, PREC, false>(a, src, fr, P, N, eno, UL, UR, true);
             rusanov<DIM, R>((R)a.gamma, UL, UR, fr[4], fr[5], fr[6], fr[7], F);
         }
     }
@@ -353,9 +399,10 @@ __global__ void __launch_bounds__(256) k_stage(DevMesh mesh, StageArgs a)
     if (valid) {
         const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
         const bool own_flag = a.flags && a.flags[c];
+        GlobalSrc<DIM, NV, PREC> src{a, mesh};
         for (int s = s0 + l; s < s1; s += LPC) {
             R F[NV];
-            slot_flux<DIM, NV, NS, PREC>(mesh, a, c, s, own_flag, F);
+            slot_flux<DIM, NV, NS, PREC>(mesh, a, src, c, s, own_flag, F);
 #pragma unroll
             for (int v = 0; v < NV; ++v) res[v] += F[v];
         }
@@ -389,6 +436,143 @@ __global__ void __launch_bounds__(256) k_stage(DevMesh mesh, StageArgs a)
     if (bad) atomicOr(a.status, 1u);
 }
 
+// ------------------------------------------------------------------ tiled variants
+// The block's TILE consecutive (Morton-ordered) cells stage their records, and the
+// faces they own, in shared memory with asynchronous copies; neighbours inside the
+// tile are then read from shared memory and only the tile's halo from global memory.
+__device__ __forceinline__ void block_copy(unsigned char *dst, const unsigned char *src, unsigned bytes)
+{
+    const unsigned n16 = bytes / 16;
+    for (unsigned i = threadIdx.x; i < n16; i += blockDim.x) {
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + 16 * i);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src + 16 * i));
+    }
+    for (unsigned i = 16 * n16 + 2 * threadIdx.x; i < bytes; i += 2 * blockDim.x)
+        *reinterpret_cast<unsigned short *>(dst + i) = *reinterpret_cast<const unsigned short *>(src + i);
+}
+__device__ __forceinline__ void block_copy_wait()
+{
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::);
+    __syncthreads();
+}
+
+DOL_HD constexpr unsigned r16(unsigned b) { return (b + 15u) & ~15u; }
+
+template <int DIM, int NV, int NS, int PREC, int TILE> struct TileLayout {
+    template <int M> static DOL_HD constexpr unsigned bytes()
+    {
+        return r16((unsigned)TILE * ord_stride<DIM, NV, M, PREC>() * (unsigned)sizeof(typename OrdT<PREC, M>::T));
+    }
+    static DOL_HD constexpr unsigned off(int m)
+    {
+        return (m > 0 ? bytes<0>() : 0) + (m > 1 ? bytes<1>() : 0) + (m > 2 ? bytes<2>() : 0) + (m > 3 ? bytes<3>() : 0) +
+               (m > 4 ? bytes<4>() : 0);
+    }
+};
+
+template <int DIM, int NV, int NS, int PREC, int TILE>
+__global__ void __launch_bounds__(TILE) k_stage_tile(DevMesh mesh, StageArgs a)
+{
+    using R = typename PrecT<PREC>::R;
+    using L = TileLayout<DIM, NV, NS, PREC, TILE>;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int t0 = blockIdx.x * TILE;
+    const int nt = min(TILE, mesh.n_cells - t0);
+    TileSrc<DIM, NV, NS, PREC> src{a, mesh, sm, t0, nt, __ldg(mesh.fown + t0), __ldg(mesh.fown + t0 + nt), {}};
+#pragma unroll
+    for (int m = 0; m <= NS + 1; ++m) src.off[m] = L::off(m);
+    auto copy_order = [&](auto mc) {
+        constexpr int M = decltype(mc)::value;
+        using T = typename OrdT<PREC, M>::T;
+        constexpr unsigned rb = ord_stride<DIM, NV, M, PREC>() * (unsigned)sizeof(T);
+        block_copy(sm + L::off(M), static_cast<const unsigned char *>(a.ord[M]) + (long long)t0 * rb, nt * rb);
+    };
+    copy_order(std::integral_constant<int, 0>{});
+    if constexpr (NS >= 1) copy_order(std::integral_constant<int, 1>{});
+    if constexpr (NS >= 2) copy_order(std::integral_constant<int, 2>{});
+    if constexpr (NS >= 3) copy_order(std::integral_constant<int, 3>{});
+    if constexpr (NS >= 4) copy_order(std::integral_constant<int, 4>{});
+    block_copy(sm + L::off(NS + 1), reinterpret_cast<const unsigned char *>(Geo<R>::face(mesh) + 8ll * src.f_lo),
+               (unsigned)(src.f_hi - src.f_lo) * 8u * (unsigned)sizeof(R));
+    block_copy_wait();
+    const int c = t0 + threadIdx.x;
+    if (c >= mesh.n_cells) return;
+    R res[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) res[v] = (R)0;
+    const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+    const bool own_flag = a.flags && a.flags[c];
+    for (int s = s0; s < s1; ++s) {
+        R F[NV];
+        slot_flux<DIM, NV, NS, PREC>(mesh, a, src, c, s, own_flag, F);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) res[v] += F[v];
+    }
+    R iv, dummy0, dummy1, dummy2;
+    ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, dummy0, dummy1, dummy2, iv);
+    const long long n = mesh.n_cells;
+    bool bad = false;
+    using T0 = typename PrecT<PREC>::T0;
+    T0 *nxt = static_cast<T0 *>(a.o0_next);
+    constexpr int S0 = ord_stride<DIM, NV, 0, PREC>();
+    R nv_out[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const double rr = (double)(res[v] * iv);
+        double o;
+        if (a.mode == 0) {
+            o = rr;
+        } else {
+            o = a.A * a.u0[v * n + c] + a.B * fma(a.dt, rr, a.us[v * n + c]);
+        }
+        nv_out[v] = (R)o;
+        a.out[v * n + c] = o;
+        bad |= !isfinite(o);
+    }
+    if (a.mode != 0 && nxt) store_rec<T0, NV, S0, R>(nxt, c, nv_out);
+    if (bad) atomicOr(a.status, 1u);
+}
+
+template <int DIM, int NV, int M, int PREC, int TILE>
+__global__ void __launch_bounds__(TILE) k_diff_tile(DevMesh mesh, const void *__restrict__ in_v, void *__restrict__ out_v)
+{
+    using R = typename PrecT<PREC>::R;
+    using TI = typename OrdT<PREC, M - 1>::T;
+    using TO = typename OrdT<PREC, M>::T;
+    constexpr int CI = ncoef(DIM, M - 1), CO = ncoef(DIM, M);
+    constexpr int SI = ord_stride<DIM, NV, M - 1, PREC>(), SO = ord_stride<DIM, NV, M, PREC>();
+    extern __shared__ __align__(16) unsigned char sm[];
+    const TI *in = static_cast<const TI *>(in_v);
+    TO *out = static_cast<TO *>(out_v);
+    const int t0 = blockIdx.x * TILE;
+    const int nt = min(TILE, mesh.n_cells - t0);
+    block_copy(sm, reinterpret_cast<const unsigned char *>(in + (long long)t0 * SI), (unsigned)nt * SI * sizeof(TI));
+    block_copy_wait();
+    const TI *tin = reinterpret_cast<const TI *>(sm);
+    const int c = t0 + threadIdx.x;
+    if (c >= mesh.n_cells) return;
+    R acc[NV * CO];
+#pragma unroll
+    for (int i = 0; i < NV * CO; ++i) acc[i] = (R)0;
+    R x[NV * CI];
+    R wx, wy, wz, iv;
+    ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, wx, wy, wz, iv);
+    load_rec<TI, NV * CI, SI, R, false>(tin, threadIdx.x, x);
+    poly_mul_acc<DIM, NV, M, R>(acc, x, wx, wy, wz);
+    const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+    for (int s = s0; s < s1; ++s) {
+        R kx, ky, kz, kb;
+        ld4<R>(Geo<R>::slotk(mesh) + 4ll * s, kx, ky, kz, kb);
+        const int nb = Geo<R>::nb_of(kb);
+        const unsigned i = (unsigned)(nb - t0);
+        if (i < (unsigned)nt) load_rec<TI, NV * CI, SI, R, false>(tin, i, x);
+        else load_rec<TI, NV * CI, SI, R>(in, nb, x);
+        poly_mul_acc<DIM, NV, M, R>(acc, x, kx, ky, kz);
+    }
+    store_rec<TO, NV * CO, SO, R>(out, c, acc);
+}
+
 // ------------------------------------------------------------------ face states (diagnostic)
 template <int DIM, int NV, int NS, int PREC>
 __global__ void __launch_bounds__(128) k_faces(DevMesh mesh, StageArgs a, double *fL, double *fR)
@@ -413,7 +597,8 @@ __global__ void __launch_bounds__(128) k_faces(DevMesh mesh, StageArgs a, double
         for (int v = 0; v < NV; ++v) UR[v] = UL[v];
     } else {
         const bool eno = a.eno_all || (a.flags && (a.flags[P] || a.flags[N]));
-        face_states<DIM, NV, NS, PREC, false>(a, fr, P, N, eno, UL, UR, true);
+        GlobalSrc<DIM, NV, PREC> src{a, mesh};
+        face_states<DIM, NV, NS, PREC, false>(a, src, fr, P, N, eno, UL, UR, true);
     }
     const long long nf = mesh.n_faces;
 #pragma unroll

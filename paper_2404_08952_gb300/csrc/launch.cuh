@@ -4,7 +4,8 @@
 
 namespace dol {
 
-// Launch shape of the gather kernels: lanes per cell (1, 4 or 8) and block size.
+// Launch shape of the gather kernels: lanes per cell (1, 4 or 8; 0 = one thread per
+// cell with the block's cells staged in shared memory, tile = block) and block size.
 struct Tune {
     int diff_lpc = 4, diff_block = 256, stage_lpc = 4, stage_block = 128;
 };
@@ -17,6 +18,7 @@ struct PathFns {
 };
 
 inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
+constexpr size_t kMaxSmem = 200 * 1024;   // dynamic shared memory a tiled block may use
 
 template <int DIM, int NV, int NS, int PREC> struct Path {
     static void pack(const DevMesh &m, const double *u, void *o0, cudaStream_t s)
@@ -35,8 +37,63 @@ template <int DIM, int NV, int NS, int PREC> struct Path {
         default: break;
         }
     }
+    template <int TILE> static void diff_t(const DevMesh &m, int M, const void *in, void *out, cudaStream_t s)
+    {
+        const int b = nblk(m.n_cells, TILE);
+        auto sm = [&](auto mc) {
+            constexpr int MM = decltype(mc)::value;
+            return (size_t)TILE * ord_stride<DIM, NV, MM - 1, PREC>() * sizeof(typename OrdT<PREC, MM - 1>::T);
+        };
+        auto go = [&](auto mc) {
+            constexpr int MM = decltype(mc)::value;
+            const size_t bytes = sm(mc);
+            if (bytes > kMaxSmem) {                 // too large to stage: one thread per cell instead
+                k_diff<DIM, NV, MM, PREC, 1><<<nblk(m.n_cells, TILE), TILE, 0, s>>>(m, in, out);
+                return;
+            }
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(k_diff_tile<DIM, NV, MM, PREC, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kMaxSmem);
+                attr = true;
+            }
+            k_diff_tile<DIM, NV, MM, PREC, TILE><<<b, TILE, bytes, s>>>(m, in, out);
+        };
+        switch (M) {
+        case 1: go(std::integral_constant<int, 1>{}); break;
+        case 2: go(std::integral_constant<int, 2>{}); break;
+        case 3: go(std::integral_constant<int, 3>{}); break;
+        case 4: go(std::integral_constant<int, 4>{}); break;
+        default: break;
+        }
+    }
+    template <int TILE> static void stage_t(const DevMesh &m, const StageArgs &a, cudaStream_t s)
+    {
+        using L = TileLayout<DIM, NV, NS, PREC, TILE>;
+        const int ti = TILE == 64 ? 0 : (TILE == 128 ? 1 : 2);
+        const size_t sm = L::off(NS + 1) + (size_t)m.max_tile_faces[ti] * 8 * sizeof(typename PrecT<PREC>::R);
+        if (sm > kMaxSmem) {                        // too large to stage: one thread per cell instead
+            k_stage<DIM, NV, NS, PREC, 1><<<nblk(m.n_cells, TILE), TILE, 0, s>>>(m, a);
+            return;
+        }
+        static bool attr = false;   // opt in to more than 48 KB once per instantiation
+        if (!attr) {
+            cudaFuncSetAttribute(k_stage_tile<DIM, NV, NS, PREC, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kMaxSmem);
+            attr = true;
+        }
+        k_stage_tile<DIM, NV, NS, PREC, TILE><<<nblk(m.n_cells, TILE), TILE, sm, s>>>(m, a);
+    }
     static void diff(const DevMesh &m, int M, const void *in, void *out, const Tune &t, cudaStream_t s)
     {
+        if (t.diff_lpc == 0) {
+            switch (t.diff_block) {
+            case 64: diff_t<64>(m, M, in, out, s); break;
+            case 256: diff_t<256>(m, M, in, out, s); break;
+            default: diff_t<128>(m, M, in, out, s); break;
+            }
+            return;
+        }
         switch (t.diff_lpc) {
         case 4: diff_l<4>(m, M, in, out, t.diff_block, s); break;
         case 8: diff_l<8>(m, M, in, out, t.diff_block, s); break;
@@ -45,6 +102,14 @@ template <int DIM, int NV, int NS, int PREC> struct Path {
     }
     static void stage(const DevMesh &m, const StageArgs &a, const Tune &t, cudaStream_t s)
     {
+        if (t.stage_lpc == 0) {
+            switch (t.stage_block) {
+            case 64: stage_t<64>(m, a, s); break;
+            case 256: stage_t<256>(m, a, s); break;
+            default: stage_t<128>(m, a, s); break;
+            }
+            return;
+        }
         const int bs = t.stage_block;
         switch (t.stage_lpc) {
         case 4: k_stage<DIM, NV, NS, PREC, 4><<<nblk((long long)m.n_cells * 4, bs), bs, 0, s>>>(m, a); break;

@@ -345,7 +345,8 @@ def test_eno3_limiter_fp64(mode, name, nv):
 
 # ---------------------------------------------------------------------------- launch shapes
 
-@pytest.mark.parametrize("lanes,block", [(1, 64), (1, 256), (4, 128), (4, 32), (8, 256), (8, 96)])
+@pytest.mark.parametrize("lanes,block", [(1, 64), (1, 256), (4, 128), (4, 32), (8, 256), (8, 96), (0, 64), (0, 128),
+                                         (0, 256)])
 @pytest.mark.parametrize("name,nv,prec", [("tet", 5, "fp32"), ("hexprism", 1, "fp64"), ("tri_bnd", 4, "fp64"),
                                           ("tet", 5, "fp32_bf16")])
 def test_launch_shapes_give_the_same_stage(lanes, block, name, nv, prec):
@@ -376,7 +377,7 @@ def test_autotune_picks_a_valid_shape_and_keeps_parity(tmp_path):
     x = to_dev(M, u)
     cache = str(tmp_path / "tune.txt")
     t = dg.dolinc_autotune(M, sch, x, ws, cache_path=cache)
-    assert t["diff_lanes"] in (1, 4, 8) and t["stage_lanes"] in (1, 4, 8) and not t["from_cache"]
+    assert t["diff_lanes"] in (0, 1, 4, 8) and t["stage_lanes"] in (0, 1, 4, 8) and not t["from_cache"]
     t2 = dg.dolinc_autotune(M, sch, x, ws, cache_path=cache)
     assert t2["from_cache"] and t2["stage_lanes"] == t["stage_lanes"]
     dt = 1e-3
