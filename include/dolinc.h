@@ -29,7 +29,8 @@
  *   - Workspace: every compute entry point takes a caller-owned device buffer
  *     (ws_dev, ws_bytes) at least dolinc_workspace_size() bytes, 256-byte aligned.
  *     It is scratch: its contents between calls mean nothing, except that the
- *     first 256 bytes hold the device status word read by dolinc_sync_status.
+ *     first 1024 bytes hold the device status word read by dolinc_sync_status and
+ *     the grid-barrier words of the batched steps.
  */
 #ifndef DOLINC_H
 #define DOLINC_H
@@ -153,7 +154,7 @@ dolinc_status dolinc_mesh_geometry(const dolinc_mesh *mesh, double *V, double *x
 dolinc_status dolinc_workspace_size(const dolinc_mesh *mesh, const dolinc_scheme *scheme, size_t *bytes);
 
 /* Clears the device status word at the start of a new workspace (ws_dev, at least
- * 256 bytes, 256-byte aligned).  Call once after allocating a workspace, before the
+ * 1024 bytes, 256-byte aligned).  Call once after allocating a workspace, before the
  * first compute call that uses it; dolinc_sync_status clears it again after reading. */
 dolinc_status dolinc_workspace_init(void *ws_dev, size_t ws_bytes, dolinc_stream stream);
 
@@ -288,6 +289,36 @@ dolinc_status dolinc_mlp_train_step(dolinc_mlp *mlp, const float *x_dev, const u
 dolinc_status dolinc_indicator_infer(dolinc_mesh *mesh, const dolinc_scheme *scheme, dolinc_mlp *mlp,
                                      const double *u_dev, float *x24_dev, uint8_t *flags_dev, float *logits_dev,
                                      void *ws_dev, size_t ws_bytes, dolinc_stream stream);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent meshes advanced together (no counterpart in the paper).  The
+ * meshes' cells, slots and faces are concatenated into one arena: batch fields are
+ * [v][total cells], mesh b occupying cells [cell_offsets[b], cell_offsets[b+1]) in its
+ * own library order.  Each mesh keeps its own time step (dt_dev[b]).
+ * dolinc_batch_rk_step runs each SSP-RK3 stage as ONE persistent cooperative launch over
+ * all meshes: pack, differential passes and the fused reconstruction/flux/update,
+ * separated by grid-wide barriers whose waits are bounded (a wait that gives up makes
+ * dolinc_sync_status report DOLINC_ERR_DEVICE_TIMEOUT and leaves the stage output
+ * unwritten).  With use_graph the three launches are captured once into a CUDA graph
+ * (re-captured when u_dev, ws_dev, dt_dev, the scheme or the launch shape change) and
+ * replayed.  Stencils of DOLINC order <= 2, no limiter.  The meshes may be destroyed
+ * after dolinc_batch_create (it copies what it needs). */
+typedef struct dolinc_batch dolinc_batch;
+dolinc_status dolinc_batch_create(dolinc_mesh *const *meshes, int n, dolinc_batch **out);
+void dolinc_batch_destroy(dolinc_batch *batch);
+dolinc_status dolinc_batch_info(const dolinc_batch *batch, int64_t *n_cells, int64_t *cell_offsets /* [n+1] */);
+/* Polls a grid-barrier wait makes (about 0.1 us each) before it gives up (default 2^23).
+ * 0 makes every wait give up at once: a way to exercise the timeout path. */
+dolinc_status dolinc_batch_set_spin_limit(dolinc_batch *batch, unsigned polls);
+dolinc_status dolinc_batch_workspace_size(const dolinc_batch *batch, const dolinc_scheme *scheme, size_t *bytes);
+dolinc_status dolinc_batch_rk_step(dolinc_batch *batch, const dolinc_scheme *scheme, const double *dt_dev,
+                                   double *u_dev, void *ws_dev, size_t ws_bytes, int use_graph, dolinc_stream stream);
+/* Times the persistent launch for blocks of 64/128/256 threads at full and half
+ * occupancy on a copy of u_dev (restored afterwards) and keeps the fastest shape.
+ * Synchronous. */
+dolinc_status dolinc_batch_autotune(dolinc_batch *batch, const dolinc_scheme *scheme, const double *dt_dev,
+                                    double *u_dev, void *ws_dev, size_t ws_bytes, dolinc_stream stream, int *block,
+                                    int *grid, double *ms_per_step);
 
 /* Cell flags for DOLINC_LIMIT_ENO3_FLAGGED: flags_dev [n_cells] uint8 (library order),
  * non-zero = troubled.  The pointer is kept by the mesh until replaced or NULL. */

@@ -30,7 +30,9 @@ ABI_SYMBOLS = (
     "dolinc_profile_read", "dolinc_rk_step_noalloc", "dolinc_autotune", "dolinc_set_tuning",
     "dolinc_criterion", "dolinc_indicator_features", "dolinc_mlp_create", "dolinc_mlp_destroy",
     "dolinc_mlp_get_params", "dolinc_mlp_set_params", "dolinc_mlp_forward", "dolinc_mlp_loss_grad",
-    "dolinc_mlp_train_step", "dolinc_indicator_infer", "dolinc_last_error",
+    "dolinc_mlp_train_step", "dolinc_indicator_infer", "dolinc_batch_create", "dolinc_batch_destroy",
+    "dolinc_batch_info", "dolinc_batch_set_spin_limit", "dolinc_batch_workspace_size", "dolinc_batch_rk_step",
+    "dolinc_batch_autotune", "dolinc_last_error",
 )
 KERNEL_KINDS = ("pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces")
 
@@ -93,12 +95,16 @@ def load(path=LIB_PATH):
             "dolinc_mlp_loss_grad": [P, P, P, C.c_int64, C.c_float, P, P, P],
             "dolinc_mlp_train_step": [P, P, P, C.c_int64, C.c_float, C.c_float, P, P],
             "dolinc_indicator_infer": [P, P, P, P, P, P, P, P, S, P],
+            "dolinc_batch_create": [P, I, P], "dolinc_batch_destroy": [P], "dolinc_batch_info": [P, P, P],
+            "dolinc_batch_set_spin_limit": [P, C.c_uint], "dolinc_batch_workspace_size": [P, P, P],
+            "dolinc_batch_rk_step": [P, P, P, P, P, S, I, P],
+            "dolinc_batch_autotune": [P, P, P, P, P, S, P, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = C.c_char_p if name == "dolinc_last_error" else (
-                None if name in ("dolinc_mesh_destroy", "dolinc_mlp_destroy") else C.c_int)
+                None if name in ("dolinc_mesh_destroy", "dolinc_mlp_destroy", "dolinc_batch_destroy") else C.c_int)
         _lib = L
     return _lib
 
@@ -402,3 +408,62 @@ def dolinc_indicator_infer(mesh, scheme, mlp, u, x24, flags, ws, logits=None, st
     s = scheme.c()
     _check(load().dolinc_indicator_infer(mesh.handle, C.byref(s), mlp.handle, _ptr(u), _ptr(x24), _ptr(flags),
                                          _ptr(logits), _ptr(ws), ws.numel(), _stream(stream)))
+
+
+# ---------------------------------------------------------------------------- batches
+
+class Batch:
+    """Many meshes advanced together by one persistent launch per SSP-RK3 stage."""
+
+    def __init__(self, meshes):
+        L = load()
+        arr = (C.c_void_p * len(meshes))(*[m.handle.value for m in meshes])
+        h = C.c_void_p()
+        _check(L.dolinc_batch_create(arr, len(meshes), C.byref(h)))
+        self.handle = h
+        n = C.c_int64()
+        offs = np.zeros(len(meshes) + 1, dtype=np.int64)
+        _check(L.dolinc_batch_info(h, C.byref(n), _ptr(offs)))
+        self.n_cells = n.value
+        self.cell_offsets = offs
+        self.meshes = list(meshes)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.dolinc_batch_destroy(h)
+            self.handle = None
+
+    def workspace(self, scheme, stream=None):
+        import torch
+        n = C.c_size_t()
+        s = scheme.c()
+        _check(load().dolinc_batch_workspace_size(self.handle, C.byref(s), C.byref(n)))
+        ws = torch.empty(n.value + 256, dtype=torch.uint8, device="cuda")
+        off = (-ws.data_ptr()) % 256
+        ws = ws[off:off + n.value]
+        _check(load().dolinc_workspace_init(_ptr(ws), n.value, _stream(stream)))
+        return ws
+
+    def to_lib(self, fields):
+        """list of per-mesh caller-order fields [nv, n_b] -> one batch field [nv, total]"""
+        return np.concatenate([m.to_lib(f) for m, f in zip(self.meshes, fields)], axis=-1)
+
+    def from_lib(self, u):
+        o = self.cell_offsets
+        return [m.from_lib(u[..., o[b]:o[b + 1]]) for b, m in enumerate(self.meshes)]
+
+    def set_spin_limit(self, polls):
+        _check(load().dolinc_batch_set_spin_limit(self.handle, int(polls)))
+
+    def rk_step(self, scheme, dt, u, ws, use_graph=True, stream=None):
+        s = scheme.c()
+        _check(load().dolinc_batch_rk_step(self.handle, C.byref(s), _ptr(dt), _ptr(u), _ptr(ws), ws.numel(),
+                                           1 if use_graph else 0, _stream(stream)))
+
+    def autotune(self, scheme, dt, u, ws, stream=None):
+        s = scheme.c()
+        b, g, ms = C.c_int(), C.c_int(), C.c_double()
+        _check(load().dolinc_batch_autotune(self.handle, C.byref(s), _ptr(dt), _ptr(u), _ptr(ws), ws.numel(),
+                                            _stream(stream), C.byref(b), C.byref(g), C.byref(ms)))
+        return dict(block=b.value, grid=g.value, ms_per_step=ms.value)

@@ -38,13 +38,16 @@ dolinc_status fail(dolinc_status s, const std::string &msg)
 
 PathFns g_paths[N_PATHS];
 IndicatorFns g_ind[N_INDICATOR];
+BatchFns g_batch[N_BATCH];
 std::once_flag g_once;
 
 void init_paths()
 {
     std::memset(g_paths, 0, sizeof g_paths);
     std::memset(g_ind, 0, sizeof g_ind);
+    std::memset(g_batch, 0, sizeof g_batch);
     register_indicator(g_ind);
+    register_batch(g_batch);
     register_paths_d2s(g_paths);
     register_paths_d2e(g_paths);
     register_paths_d3s(g_paths);
@@ -114,6 +117,22 @@ struct dolinc_mlp {
     }
 };
 
+struct dolinc_batch {
+    dolinc_mesh *arena = nullptr;      // the concatenated meshes
+    int n = 0;
+    std::vector<int64_t> cell_off;
+    const int32_t *cell_mesh = nullptr;
+    int block = 256, grid = 0;         // persistent launch shape (0: from occupancy)
+    unsigned spin_limit = 1u << 23;    // polls a grid-barrier wait makes before giving up
+    cudaGraphExec_t exec = nullptr;
+    std::string gkey;
+    ~dolinc_batch()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        delete arena;
+    }
+};
+
 namespace {
 
 template <class T> dolinc_status upload(dolinc_mesh *m, const std::vector<T> &v, const T **out)
@@ -174,7 +193,7 @@ WsLayout ws_layout(const dolinc_mesh *m, const dolinc_scheme *s)
     const size_t nc = (size_t)m->h.n_cells;
     size_t o = 0;
     L.status = o;
-    o += 256;
+    o += 1024;                                  // status word, then the batch grid-barrier words
     for (int i = 0; i < 2; ++i) {
         L.o0[i] = o;
         o += al256(nc * stride_h(m->h.dim, s->nv, 0, s->precision) * elem_bytes(s->precision, 0));
@@ -284,6 +303,8 @@ dolinc_status launch_check()
 
 }  // namespace
 
+dolinc_status upload_mesh(dolinc_mesh *m);
+
 extern "C" {
 
 const char *dolinc_last_error(void) { return g_err.c_str(); }
@@ -306,6 +327,20 @@ dolinc_status dolinc_mesh_create(const dolinc_mesh_desc *desc, dolinc_mesh **out
         delete m;
         return fail(DOLINC_ERR_MESH, err);
     }
+    dolinc_status st = upload_mesh(m);
+    if (st) {
+        delete m;
+        return st;
+    }
+    *out = m;
+    return DOLINC_OK;
+}
+
+}  // extern "C"
+
+// Copies the host tables of m->h to the device (FP64 and FP32 derived tables).
+dolinc_status upload_mesh(dolinc_mesh *m)
+{
     cudaGetDevice(&m->device);
     const HostMesh &h = m->h;
     const int64_t nc = h.n_cells, nf = h.n_faces, ns = h.n_slots;
@@ -344,6 +379,7 @@ dolinc_status dolinc_mesh_create(const dolinc_mesh_desc *desc, dolinc_mesh **out
         ff[f] = h.face_flip[f];
     }
     std::vector<int32_t> off(h.off.begin(), h.off.end());
+    m->max_faces = 0;
     for (int64_t c = 0; c < nc; ++c) m->max_faces = std::max(m->max_faces, (int)(h.off[c + 1] - h.off[c]));
     // first internal face owned by each cell (faces are sorted by owner)
     std::vector<int32_t> fown(nc + 1, 0);
@@ -367,13 +403,12 @@ dolinc_status dolinc_mesh_create(const dolinc_mesh_desc *desc, dolinc_mesh **out
         (st = upload(m, sk32, &d.slotk32)) || (st = upload(m, ck64, &d.cellk64)) ||
         (st = upload(m, ck32, &d.cellk32)) || (st = upload(m, f64, &d.face64)) || (st = upload(m, f32, &d.face32)) ||
         (st = upload(m, fo, &d.fo)) || (st = upload(m, fn, &d.fn)) || (st = upload(m, fe, &d.face_ext)) ||
-        (st = upload(m, ff, &d.face_flip)) || (st = upload(m, fown, &d.fown))) {
-        delete m;
+        (st = upload(m, ff, &d.face_flip)) || (st = upload(m, fown, &d.fown)))
         return st;
-    }
-    *out = m;
     return DOLINC_OK;
 }
+
+extern "C" {
 
 void dolinc_mesh_destroy(dolinc_mesh *mesh) { delete mesh; }
 
@@ -428,9 +463,9 @@ dolinc_status dolinc_workspace_size(const dolinc_mesh *m, const dolinc_scheme *s
 
 dolinc_status dolinc_workspace_init(void *ws, size_t bytes, dolinc_stream stream)
 {
-    if (!ws || bytes < 256) return fail(DOLINC_ERR_INVALID_ARG, "workspace must hold at least 256 bytes");
+    if (!ws || bytes < 1024) return fail(DOLINC_ERR_INVALID_ARG, "workspace must hold at least 1024 bytes");
     if (((uintptr_t)ws & 255) != 0) return fail(DOLINC_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
-    CU(cudaMemsetAsync(ws, 0, 256, reinterpret_cast<cudaStream_t>(stream)));
+    CU(cudaMemsetAsync(ws, 0, 1024, reinterpret_cast<cudaStream_t>(stream)));
     return DOLINC_OK;
 }
 
@@ -676,7 +711,7 @@ dolinc_status dolinc_autotune(dolinc_mesh *m, const dolinc_scheme *s, const doub
         m->prof = prof;
         best_diff = bd;
         best_stage = bs;
-        CU(cudaMemsetAsync(B(ws, L.status), 0, 256, cs));   // the timing runs may have flagged garbage
+        CU(cudaMemsetAsync(B(ws, L.status), 0, 1024, cs));   // the timing runs may have flagged garbage
         CU(cudaStreamSynchronize(cs));
         if (cache_path) {
             std::ofstream o(cache_path, std::ios::app);
@@ -896,6 +931,256 @@ dolinc_status dolinc_indicator_infer(dolinc_mesh *me, const dolinc_scheme *s, do
     return dolinc_mlp_forward(net, x24, me->h.n_cells, logits, flags, stream);
 }
 
+// ------------------------------------------------------------------ batches
+dolinc_status dolinc_batch_create(dolinc_mesh *const *meshes, int n, dolinc_batch **out)
+{
+    if (!out) return fail(DOLINC_ERR_INVALID_ARG, "null output handle");
+    *out = nullptr;
+    if (!meshes || n <= 0) return fail(DOLINC_ERR_INVALID_ARG, "empty batch");
+    for (int b = 0; b < n; ++b) {
+        if (!meshes[b]) return fail(DOLINC_ERR_INVALID_ARG, "null mesh in batch");
+        if (meshes[b]->h.dim != meshes[0]->h.dim) return fail(DOLINC_ERR_INVALID_ARG, "meshes of different dimension");
+    }
+    dolinc_batch *bt = new (std::nothrow) dolinc_batch();
+    if (!bt) return fail(DOLINC_ERR_OOM, "host allocation");
+    bt->arena = new (std::nothrow) dolinc_mesh();
+    if (!bt->arena) {
+        delete bt;
+        return fail(DOLINC_ERR_OOM, "host allocation");
+    }
+    HostMesh &H = bt->arena->h;
+    H.dim = meshes[0]->h.dim;
+    H.off.push_back(0);
+    H.g_min = 1e300;
+    H.g_max = 0;
+    H.h_min = 1e300;
+    std::vector<int32_t> cell_mesh;
+    bt->n = n;
+    bt->cell_off.push_back(0);
+    try {
+        for (int b = 0; b < n; ++b) {
+            const HostMesh &h = meshes[b]->h;
+            const int64_t co = H.n_cells, so = H.n_slots, fo = H.n_faces;
+            if (co + h.n_cells > ((int64_t)1 << 30) || fo + h.n_faces > ((int64_t)1 << 29)) {
+                delete bt;
+                return fail(DOLINC_ERR_INVALID_ARG, "batch too large (2^30 cells / 2^29 faces)");
+            }
+            for (int64_t p : h.perm) H.perm.push_back(p + co);
+            H.V.insert(H.V.end(), h.V.begin(), h.V.end());
+            H.xc.insert(H.xc.end(), h.xc.begin(), h.xc.end());
+            H.cw.insert(H.cw.end(), h.cw.begin(), h.cw.end());
+            for (int64_t c = 0; c < h.n_cells; ++c) H.off.push_back((int32_t)(h.off[c + 1] + so));
+            for (int32_t v : h.snb) H.snb.push_back((int32_t)(v + co));
+            for (uint32_t w : h.sword) H.sword.push_back(slot_word((int64_t)(w >> 2) + fo, (w & 2) != 0, (int)(w & 1)));
+            H.ss.insert(H.ss.end(), h.ss.begin(), h.ss.end());
+            for (int64_t v : h.fo) H.fo.push_back(v + co);
+            for (int64_t v : h.fn) H.fn.push_back(v < 0 ? -1 : v + co);
+            for (int64_t v : h.face_ext) H.face_ext.push_back(v + fo);
+            H.face_flip.insert(H.face_flip.end(), h.face_flip.begin(), h.face_flip.end());
+            H.fS.insert(H.fS.end(), h.fS.begin(), h.fS.end());
+            H.fxf.insert(H.fxf.end(), h.fxf.begin(), h.fxf.end());
+            H.fd.insert(H.fd.end(), h.fd.begin(), h.fd.end());
+            H.fw.insert(H.fw.end(), h.fw.begin(), h.fw.end());
+            H.fg.insert(H.fg.end(), h.fg.begin(), h.fg.end());
+            H.n_cells += h.n_cells;
+            H.n_faces += h.n_faces;
+            H.n_slots += h.n_slots;
+            H.n_bnd += h.n_bnd;
+            H.volume += h.volume;
+            H.g_min = std::min(H.g_min, h.g_min);
+            H.g_max = std::max(H.g_max, h.g_max);
+            H.h_min = std::min(H.h_min, h.h_min);
+            cell_mesh.insert(cell_mesh.end(), (size_t)h.n_cells, (int32_t)b);
+            bt->cell_off.push_back(H.n_cells);
+        }
+    } catch (const std::bad_alloc &) {
+        delete bt;
+        return fail(DOLINC_ERR_OOM, "host allocation while concatenating the batch");
+    }
+    dolinc_status st = upload_mesh(bt->arena);
+    if (!st) st = upload(bt->arena, cell_mesh, &bt->cell_mesh);
+    if (st) {
+        delete bt;
+        return st;
+    }
+    *out = bt;
+    return DOLINC_OK;
+}
+
+void dolinc_batch_destroy(dolinc_batch *b) { delete b; }
+
+dolinc_status dolinc_batch_set_spin_limit(dolinc_batch *b, unsigned polls)
+{
+    if (!b) return fail(DOLINC_ERR_INVALID_ARG, "null batch");
+    b->spin_limit = polls;
+    return DOLINC_OK;
+}
+
+dolinc_status dolinc_batch_info(const dolinc_batch *b, int64_t *n_cells, int64_t *cell_offsets)
+{
+    if (!b) return fail(DOLINC_ERR_INVALID_ARG, "null batch");
+    if (n_cells) *n_cells = b->arena->h.n_cells;
+    if (cell_offsets) std::memcpy(cell_offsets, b->cell_off.data(), sizeof(int64_t) * (b->n + 1));
+    return DOLINC_OK;
+}
+
+dolinc_status dolinc_batch_workspace_size(const dolinc_batch *b, const dolinc_scheme *s, size_t *bytes)
+{
+    if (!b) return fail(DOLINC_ERR_INVALID_ARG, "null batch");
+    return dolinc_workspace_size(b->arena, s, bytes);
+}
+
+namespace {
+dolinc_status batch_launch_step(dolinc_batch *bt, const dolinc_scheme *s, const BatchFns *bf, const double *dt,
+                                double *u, void *ws, const WsLayout &L, cudaStream_t cs)
+{
+    static const double A[3] = {0.0, 0.75, 1.0 / 3.0}, Bc[3] = {1.0, 0.25, 2.0 / 3.0};
+    dolinc_mesh *m = bt->arena;
+    double *ust = reinterpret_cast<double *>(B(ws, L.ustage));
+    int cur = 0;
+    for (int sg = 0; sg < 3; ++sg) {
+        StageArgs a = base_args(m, s, ws, L, L.o0[cur]);
+        a.mode = 1;
+        a.u0 = u;
+        a.us = sg == 0 ? u : ust;
+        a.out = sg == 2 ? u : ust;
+        a.A = A[sg];
+        a.B = Bc[sg];
+        a.o0_next = sg == 2 ? nullptr : B(ws, L.o0[1 - cur]);
+        BatchArgs b{};
+        b.pack_src = sg == 0 ? u : nullptr;
+        b.ord[0] = B(ws, L.o0[cur]);
+        for (int mm = 1; mm <= MAXN; ++mm) b.ord[mm] = B(ws, L.ord[mm]);
+        b.n_diff = s->n_diff;
+        b.cell_mesh = bt->cell_mesh;
+        b.dt_tab = dt;
+        b.bar = reinterpret_cast<unsigned *>(B(ws, L.status + 256));
+        b.spin_limit = bt->spin_limit;
+        cudaError_t e = bf->launch(m->d, a, b, bt->grid, bt->block, cs);
+        if (e != cudaSuccess) return fail(DOLINC_ERR_CUDA, std::string("cooperative launch: ") + cudaGetErrorString(e));
+        cur = 1 - cur;
+    }
+    return DOLINC_OK;
+}
+
+dolinc_status batch_prepare(dolinc_batch *bt, const dolinc_scheme *s, const double *dt, double *u, void *ws,
+                            size_t ws_bytes, WsLayout &L, const BatchFns **bf)
+{
+    dolinc_mesh *m = bt->arena;
+    dolinc_status st = check_scheme(m, s);
+    if (st) return st;
+    if ((st = check_ws(m, s, ws, ws_bytes, L))) return st;
+    if (!u || !dt) return fail(DOLINC_ERR_INVALID_ARG, "null field or time steps");
+    if (s->limiter != DOLINC_LIMIT_NONE) return fail(DOLINC_ERR_UNSUPPORTED, "batched steps take no limiter");
+    const int ns = needed_order(*s);
+    if (ns > 2) return fail(DOLINC_ERR_UNSUPPORTED, "batched steps support stencils of DOLINC order <= 2");
+    std::call_once(g_once, init_paths);
+    *bf = &g_batch[batch_index(m->h.dim, s->nv, ns, s->precision)];
+    if (!(*bf)->launch) return fail(DOLINC_ERR_UNSUPPORTED, "no batched kernel for this scheme");
+    if (bt->grid <= 0) {
+        int sms = 0;
+        CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+        const int per = (*bf)->blocks_per_sm(bt->block);
+        if (per <= 0) return fail(DOLINC_ERR_UNSUPPORTED, "batched kernel does not fit on an SM");
+        bt->grid = per * sms;
+    }
+    return DOLINC_OK;
+}
+}  // namespace
+
+dolinc_status dolinc_batch_rk_step(dolinc_batch *bt, const dolinc_scheme *s, const double *dt, double *u, void *ws,
+                                   size_t ws_bytes, int use_graph, dolinc_stream stream)
+{
+    if (!bt) return fail(DOLINC_ERR_INVALID_ARG, "null batch");
+    WsLayout L;
+    const BatchFns *bf = nullptr;
+    dolinc_status st = batch_prepare(bt, s, dt, u, ws, ws_bytes, L, &bf);
+    if (st) return st;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    if (!use_graph) return batch_launch_step(bt, s, bf, dt, u, ws, L, cs);
+    std::ostringstream k;
+    k << (const void *)u << '|' << ws << '|' << (const void *)dt << '|' << scheme_key(bt->arena, s) << '|' << s->k << ','
+      << s->r << ',' << s->flux << ',' << s->gamma << ',' << s->adv[0] << ',' << s->adv[1] << ',' << s->adv[2] << '|'
+      << bt->block << ',' << bt->grid << ',' << bt->spin_limit;
+    if (!bt->exec || bt->gkey != k.str()) {
+        if (bt->exec) {
+            cudaGraphExecDestroy(bt->exec);
+            bt->exec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        dolinc_status ls = batch_launch_step(bt, s, bf, dt, u, ws, L, cs);
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (ls) {
+            if (g) cudaGraphDestroy(g);
+            return ls;
+        }
+        if (e != cudaSuccess) return fail(DOLINC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&bt->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            bt->exec = nullptr;
+            return fail(DOLINC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        }
+        bt->gkey = k.str();
+    }
+    CU(cudaGraphLaunch(bt->exec, cs));
+    return DOLINC_OK;
+}
+
+dolinc_status dolinc_batch_autotune(dolinc_batch *bt, const dolinc_scheme *s, const double *dt, double *u, void *ws,
+                                    size_t ws_bytes, dolinc_stream stream, int *block_out, int *grid_out,
+                                    double *ms_out)
+{
+    if (!bt) return fail(DOLINC_ERR_INVALID_ARG, "null batch");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    const int blocks[3] = {64, 128, 256};
+    const double fracs[2] = {1.0, 0.5};
+    int best_b = 256, best_g = 0;
+    double best = 1e30;
+    int sms = 0;
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, bt->arena->device));
+    // time on a copy of the state so the caller's field is left as it was
+    const size_t ubytes = sizeof(double) * (size_t)s->nv * (size_t)bt->arena->h.n_cells;
+    WsLayout L0 = ws_layout(bt->arena, s);
+    if (!ws || ws_bytes < L0.total) return fail(DOLINC_ERR_INVALID_ARG, "workspace too small");
+    std::vector<char> keep(ubytes);
+    CU(cudaMemcpyAsync(keep.data(), u, ubytes, cudaMemcpyDeviceToHost, cs));
+    CU(cudaStreamSynchronize(cs));
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    for (int bi = 0; bi < 3; ++bi)
+        for (int fi = 0; fi < 2; ++fi) {
+            bt->block = blocks[bi];
+            bt->grid = 0;
+            WsLayout L;
+            const BatchFns *bf = nullptr;
+            dolinc_status st = batch_prepare(bt, s, dt, u, ws, ws_bytes, L, &bf);
+            if (st) continue;
+            bt->grid = std::max(1, (int)(bt->grid * fracs[fi]));
+            if (batch_launch_step(bt, s, bf, dt, u, ws, L, cs)) continue;
+            cudaEventRecord(e0, cs);
+            for (int r = 0; r < 3; ++r) batch_launch_step(bt, s, bf, dt, u, ws, L, cs);
+            cudaEventRecord(e1, cs);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms / 3 < best) best = ms / 3, best_b = bt->block, best_g = bt->grid;
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    bt->block = best_b;
+    bt->grid = best_g;
+    CU(cudaMemcpyAsync(u, keep.data(), ubytes, cudaMemcpyHostToDevice, cs));
+    CU(cudaMemsetAsync(ws, 0, 1024, cs));
+    CU(cudaStreamSynchronize(cs));
+    if (block_out) *block_out = best_b;
+    if (grid_out) *grid_out = best_g;
+    if (ms_out) *ms_out = best;
+    return launch_check();
+}
+
 dolinc_status dolinc_set_tuning(dolinc_mesh *m, const dolinc_scheme *s, const dolinc_tuning *t)
 {
     dolinc_status st = check_scheme(m, s);
@@ -931,7 +1216,7 @@ dolinc_status dolinc_sync_status(dolinc_mesh *m, void *ws, dolinc_stream stream)
     unsigned h = 0;
     CU(cudaMemcpyAsync(&h, ws, sizeof h, cudaMemcpyDeviceToHost, cs));
     CU(cudaStreamSynchronize(cs));
-    CU(cudaMemsetAsync(ws, 0, sizeof h, cs));
+    CU(cudaMemsetAsync(ws, 0, 1024, cs));      // status and the batch barrier words
     CU(cudaStreamSynchronize(cs));
     if (h & 2u) return fail(DOLINC_ERR_DEVICE_TIMEOUT, "a device-side wait gave up");
     if (h & 1u) return fail(DOLINC_ERR_NONFINITE, "a stage produced NaN or Inf");

@@ -573,6 +573,160 @@ __global__ void __launch_bounds__(TILE) k_diff_tile(DevMesh mesh, const void *__
     store_rec<TO, NV * CO, SO, R>(out, c, acc);
 }
 
+// ------------------------------------------------------------------ persistent batched stage
+// One cooperative launch runs a whole stage over the concatenated meshes of a batch:
+// [pack the FP64 field] | differential pass 1 | ... | pass n_diff | reconstruction,
+// flux, residual and update, the phases separated by a grid-wide barrier.  Records
+// written in one phase are read in a later phase of the same launch, so this kernel
+// reads through the coherent path (no read-only loads).  Each barrier waits at most
+// `spin_limit` polls; a wait that gives up sets status bit 1 and an abort word that
+// makes every later barrier of the launch return at once.
+struct BatchArgs {
+    const double *pack_src;      // non-null: phase 0 packs this FP64 field into ord[0]
+    void *ord[MAXN + 1];         // order records 0..n_diff
+    int n_diff;
+    const int32_t *cell_mesh;    // mesh of each cell
+    const double *dt_tab;        // per-mesh time step
+    unsigned *bar;               // [0] arrivals, [32] generation, [64] abort
+    unsigned spin_limit;
+};
+
+__device__ __forceinline__ void grid_barrier(unsigned *bar, unsigned *status, unsigned limit)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 32, *abort = bar + 64;
+        if (!*abort) {
+            const unsigned g = *gen;
+            __threadfence();
+            const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+            if (atomicAdd(bar, 1u) == nb - 1) {
+                atomicExch(bar, 0u);
+                __threadfence();
+                atomicAdd(const_cast<unsigned *>(gen), 1u);
+            } else {
+                unsigned it = 0;
+                while (*gen == g && !*abort) {
+                    if (++it > limit) {
+                        atomicOr(status, 2u);
+                        atomicExch(const_cast<unsigned *>(abort), 1u);
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+            }
+            __threadfence();
+        }
+    }
+    __syncthreads();
+}
+
+template <int DIM, int NV, int M, int PREC>
+__device__ __forceinline__ void diff_cell(const DevMesh &mesh, const void *in_v, void *out_v, int c)
+{
+    using R = typename PrecT<PREC>::R;
+    using TI = typename OrdT<PREC, M - 1>::T;
+    using TO = typename OrdT<PREC, M>::T;
+    constexpr int CI = ncoef(DIM, M - 1), CO = ncoef(DIM, M);
+    constexpr int SI = ord_stride<DIM, NV, M - 1, PREC>(), SO = ord_stride<DIM, NV, M, PREC>();
+    const TI *in = static_cast<const TI *>(in_v);
+    R acc[NV * CO];
+#pragma unroll
+    for (int i = 0; i < NV * CO; ++i) acc[i] = (R)0;
+    R x[NV * CI];
+    R wx, wy, wz, iv;
+    ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, wx, wy, wz, iv);
+    load_rec<TI, NV * CI, SI, R, false>(in, c, x);
+    poly_mul_acc<DIM, NV, M, R>(acc, x, wx, wy, wz);
+    const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+    for (int s = s0; s < s1; ++s) {
+        R kx, ky, kz, kb;
+        ld4<R>(Geo<R>::slotk(mesh) + 4ll * s, kx, ky, kz, kb);
+        load_rec<TI, NV * CI, SI, R, false>(in, Geo<R>::nb_of(kb), x);
+        poly_mul_acc<DIM, NV, M, R>(acc, x, kx, ky, kz);
+    }
+    store_rec<TO, NV * CO, SO, R>(static_cast<TO *>(out_v), c, acc);
+}
+
+template <int DIM, int NV, int PREC> struct CoherentSrc {
+    using R = typename PrecT<PREC>::R;
+    static constexpr bool LDG = false;
+    const StageArgs &a;
+    const DevMesh &mesh;
+    template <int M> __device__ __forceinline__ const typename OrdT<PREC, M>::T *rec(int X) const
+    {
+        return static_cast<const typename OrdT<PREC, M>::T *>(a.ord[M]) + (long long)X * ord_stride<DIM, NV, M, PREC>();
+    }
+    __device__ __forceinline__ const R *face(int f) const { return Geo<R>::face(mesh) + 8ll * f; }
+};
+
+template <int DIM, int NV, int NS, int PREC>
+__global__ void __launch_bounds__(256) k_batch_stage(DevMesh mesh, StageArgs a, BatchArgs b)
+{
+    using R = typename PrecT<PREC>::R;
+    using T0 = typename PrecT<PREC>::T0;
+    const int nthr = gridDim.x * blockDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = mesh.n_cells;
+    constexpr int S0 = ord_stride<DIM, NV, 0, PREC>();
+    if (b.pack_src) {
+        for (int c = tid; c < n; c += nthr) {
+            R v[NV];
+#pragma unroll
+            for (int i = 0; i < NV; ++i) v[i] = (R)b.pack_src[(long long)i * n + c];
+            store_rec<T0, NV, S0, R>(static_cast<T0 *>(b.ord[0]), c, v);
+        }
+        grid_barrier(b.bar, a.status, b.spin_limit);
+    }
+    if (b.n_diff >= 1) {
+        for (int c = tid; c < n; c += nthr) diff_cell<DIM, NV, 1, PREC>(mesh, b.ord[0], b.ord[1], c);
+        grid_barrier(b.bar, a.status, b.spin_limit);
+    }
+    if (b.n_diff >= 2) {
+        for (int c = tid; c < n; c += nthr) diff_cell<DIM, NV, 2, PREC>(mesh, b.ord[1], b.ord[2], c);
+        grid_barrier(b.bar, a.status, b.spin_limit);
+    }
+    if (b.n_diff >= 3) {
+        for (int c = tid; c < n; c += nthr) diff_cell<DIM, NV, 3, PREC>(mesh, b.ord[2], b.ord[3], c);
+        grid_barrier(b.bar, a.status, b.spin_limit);
+    }
+    if (b.n_diff >= 4) {
+        for (int c = tid; c < n; c += nthr) diff_cell<DIM, NV, 4, PREC>(mesh, b.ord[3], b.ord[4], c);
+        grid_barrier(b.bar, a.status, b.spin_limit);
+    }
+    if (*(volatile unsigned *)(b.bar + 64)) return;      // a barrier gave up: leave the state untouched
+    CoherentSrc<DIM, NV, PREC> src{a, mesh};
+    T0 *nxt = static_cast<T0 *>(a.o0_next);
+    for (int c = tid; c < n; c += nthr) {
+        R res[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) res[v] = (R)0;
+        const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+        const bool own_flag = a.flags && a.flags[c];
+        for (int s = s0; s < s1; ++s) {
+            R F[NV];
+            slot_flux<DIM, NV, NS, PREC>(mesh, a, src, c, s, own_flag, F);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) res[v] += F[v];
+        }
+        R iv, d0, d1, d2;
+        ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, d0, d1, d2, iv);
+        const double dt = b.dt_tab[__ldg(b.cell_mesh + c)];
+        bool bad = false;
+        R o32[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const double rr = (double)(res[v] * iv);
+            const double o = a.A * a.u0[(long long)v * n + c] + a.B * fma(dt, rr, a.us[(long long)v * n + c]);
+            a.out[(long long)v * n + c] = o;
+            o32[v] = (R)o;
+            bad |= !isfinite(o);
+        }
+        if (nxt) store_rec<T0, NV, S0, R>(nxt, c, o32);
+        if (bad) atomicOr(a.status, 1u);
+    }
+}
+
 // ------------------------------------------------------------------ face states (diagnostic)
 template <int DIM, int NV, int NS, int PREC>
 __global__ void __launch_bounds__(128) k_faces(DevMesh mesh, StageArgs a, double *fL, double *fR)

@@ -124,6 +124,41 @@ template <int DIM, int NV, int NS, int PREC> struct Path {
     static PathFns fns() { return PathFns{&pack, &diff, &stage, &faces}; }
 };
 
+// Persistent batched stage (k_batch_stage), launched cooperatively.
+struct BatchFns {
+    cudaError_t (*launch)(const DevMesh &, const StageArgs &, const BatchArgs &, int grid, int block, cudaStream_t);
+    int (*blocks_per_sm)(int block);
+};
+
+template <int DIM, int NV, int NS, int PREC> struct BatchPath {
+    static cudaError_t launch(const DevMesh &m, const StageArgs &a, const BatchArgs &b, int grid, int block,
+                              cudaStream_t s)
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(block);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_batch_stage<DIM, NV, NS, PREC>, m, a, b);
+    }
+    static int blocks_per_sm(int block)
+    {
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_stage<DIM, NV, NS, PREC>, block, 0);
+        return n;
+    }
+    static BatchFns fns() { return BatchFns{&launch, &blocks_per_sm}; }
+};
+
+// batch table index: dim (2,3) x nv-class x NS (1, 2) x precision
+inline int batch_index(int dim, int nv, int ns, int prec) { return (((dim - 2) * 2 + (nv == 1 ? 0 : 1)) * 2 + (ns - 1)) * 3 + prec; }
+constexpr int N_BATCH = 2 * 2 * 2 * 3;
+void register_batch(BatchFns *t);
+
 // table index: dim (2,3) x nv-class (scalar, Euler) x NS (1..4) x precision (3)
 inline int path_index(int dim, int nv, int ns, int prec)
 {

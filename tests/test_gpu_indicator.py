@@ -64,6 +64,10 @@ def test_criterion_flags(name, prec):
 @pytest.mark.parametrize("name", ["riemann2d", "tet3d"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_network_inputs(name, prec):
+    """Own features element by element; the three neighbour blocks are the top three of
+    the cell's face neighbours in lexicographic order, which is not unique on near-ties
+    (piecewise-constant data makes many), so each block must be one of the cell's
+    neighbours' feature vectors and the blocks' first keys must sum to the oracle's."""
     w = case(name)
     O = w["O"]
     M = dg.Mesh(w["mesh"])
@@ -72,12 +76,20 @@ def test_network_inputs(name, prec):
     x = torch.zeros((M.n_cells, 24), dtype=torch.float32, device="cuda")
     dg.dolinc_indicator_features(M, sch, dev(M, w["u0"]), x, ws)
     got = x.cpu().numpy()[M.perm]
-    _, want = O.features(w["u0"], oracle.Scheme(**w["scheme"]))
-    # own features exactly comparable; neighbour blocks may swap only on lexicographic near-ties
-    tol = 1e-5 if prec == "fp64" else 3e-4
-    np.testing.assert_allclose(got[:, :6], want[:, :6], atol=tol * (1 + np.abs(want[:, :6]).max()))
-    nb_ok = np.all(np.abs(got - want) <= tol * (1 + np.abs(want).max()), axis=1)
-    assert nb_ok.mean() > 0.99
+    own, want = O.features(w["u0"], oracle.Scheme(**w["scheme"]))
+    tol = (1e-5 if prec == "fp64" else 3e-4) * (1 + np.abs(want).max())
+    np.testing.assert_allclose(got[:, :6], want[:, :6], atol=tol)
+    nbrs = [[] for _ in range(O.n_cells)]
+    for P, Q in zip(O.owner, O.neigh):
+        nbrs[P].append(Q if Q >= 0 else P)
+        if Q >= 0:
+            nbrs[Q].append(P)
+    for c in range(O.n_cells):
+        cand = own[nbrs[c]]
+        for a in range(3):
+            blk = got[c, 6 + 6 * a: 12 + 6 * a]
+            assert np.abs(cand - blk).max(axis=1).min() <= tol, (c, a)
+        assert abs(got[c, 6::6][:3].sum() - want[c, 6::6][:3].sum()) <= 3 * tol, c
 
 
 def test_tensor_core_inference_matches_bf16_reference():
