@@ -327,6 +327,149 @@ def run_dolinc(args):
         dist.destroy_process_group()
 
 
+def _sync_cpu(t):
+    return t.cpu().numpy()
+
+
+def run_indicator(args):
+    """Learned troubled-cell indicator on the four-quadrant Riemann workload.
+
+    Trains the network on criterion labels of seeded runs (smaller mesh), judges its
+    misclassification on held-out runs, then advances one held-out problem on the full
+    mesh with the limiter switched by (a) the network, FP32, (b) the criterion, FP32,
+    (c) the criterion, FP64 (the plain FP64 GPU method), (d) no limiter, and reports
+    cell-updates/s per stage (indicator included) and the L1 distance of (a), (b) to (c)."""
+    import torch
+    import paper_2404_08952_gb300 as dg
+    from paper_2404_08952_gb300 import indicator as ind
+    import synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    t_all = time.perf_counter()
+    train_size, run_steps, every = args.ind_train_size, args.ind_train_steps, 4
+    mk = lambda sd: synth.workload("euler2d_riemann", size=train_size, order=sd, q=2)
+    Xs, Ys = [], []
+    for x, y in ind.riemann_runs(mk, range(args.ind_runs), run_steps, every, precision=args.precision):
+        Xs.append(x)
+        Ys.append(y)
+    X, Y = torch.cat(Xs), torch.cat(Ys)
+    net = dg.MLP(seed=args.seed)
+    t0 = time.perf_counter()
+    hist, pw = ind.train(net, X, Y, epochs=args.ind_epochs, batch=8192, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    # held-out judgement (seeds never trained on)
+    Xh, Yh = [], []
+    for x, y in ind.riemann_runs(mk, range(1000, 1000 + args.ind_eval_runs), run_steps, every,
+                                 precision=args.precision):
+        Xh.append(x)
+        Yh.append(y)
+    Xh, Yh = torch.cat(Xh), torch.cat(Yh)
+    pred = torch.zeros_like(Yh)
+    net.forward(Xh, None, pred)
+    conf = ind.confusion(_sync_cpu(pred), _sync_cpu(Yh))
+    # full-size comparison on one held-out problem
+    w = synth.workload("euler2d_riemann", size=args.size or 724, order=2000, q=2)
+    cells = int(w["u0"].shape[1])
+    steps = args.steps
+    res = {}
+    for name, switch, prec in (("network_fp32", "network", "fp32"), ("criterion_fp32", "criterion", "fp32"),
+                               ("criterion_fp64", "criterion", "fp64"), ("none_fp32", "none", "fp32"),
+                               ("eno3_all_fp32", "all", "fp32")):
+        st, finite, sec, flagged = ind.run_with(w, switch, steps, precision=prec, net=net)
+        res[name] = dict(state=st, finite=finite, sec_per_step=sec, flagged=flagged,
+                         value=cells * 3 / sec)
+    ref = res["criterion_fp64"]["state"]
+    vol = None
+    out = {}
+    for k, r in res.items():
+        d = r["state"] - ref
+        l1 = float(np.abs(d).sum() / max(np.abs(ref).sum(), 1e-300)) if r["finite"] else None
+        out[k] = {"value": r["value"], "ms_per_step": r["sec_per_step"] * 1e3, "finite_after_steps": r["finite"],
+                  "flagged_fraction": r["flagged"], "l1_rel_vs_criterion_fp64": l1}
+    line = {"metric": METRIC, "value": out["network_fp32"]["value"], "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": 0, "ms_per_step": out["network_fp32"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "euler2d_riemann", "cells": cells, "stencil_k_r": [3, 1], "n_diff": 2,
+                       "limiter": "ENO3-DOLINC on flagged cells", "indicator": "MLP 24-64-64-64-1 (bf16 weights)",
+                       "train_mesh_cells": int(2 * train_size ** 2), "train_runs": args.ind_runs,
+                       "train_samples": int(X.shape[0]), "eval_runs": args.ind_eval_runs},
+            "indicator": {"train_seconds": t_train, "epochs": args.ind_epochs, "final_loss": hist[-1],
+                          "first_loss": hist[0], "pos_weight": pw, "heldout_vs_criterion": conf},
+            "forms": out, "seconds_total": time.perf_counter() - t_all}
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args):
+    """Batched ensemble of 2D Burgers meshes: one persistent cooperative launch per
+    stage replayed from a CUDA graph (FP32 bulk, FP64 update), against the plain FP64
+    GPU method (each mesh stepped by its own launches)."""
+    import torch
+    import paper_2404_08952_gb300 as dg
+    import synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    t_all = time.perf_counter()
+    wl = synth.workload("burgers_batch", q=2, n_meshes=args.batch_meshes)
+    ms_ = wl["meshes"]
+    meshes = [dg.Mesh(x["mesh"]) for x in ms_]
+    bt = dg.Batch(meshes)
+    cells = int(bt.n_cells)
+    dt = torch.tensor([x["dt"] for x in ms_], dtype=torch.float64, device="cuda")
+    u0 = bt.to_lib([x["u0"] for x in ms_])
+    out = {}
+    for prec in (args.precision, "fp64"):
+        sch = dg.Scheme(precision=prec, **wl["scheme"])
+        ws = bt.workspace(sch)
+        u = torch.from_numpy(u0).cuda()
+        tune = bt.autotune(sch, dt, u, ws)
+        for _ in range(args.warmup):
+            bt.rk_step(sch, dt, u, ws, use_graph=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            bt.rk_step(sch, dt, u, ws, use_graph=True)
+        e1.record()
+        torch.cuda.synchronize()
+        dg.dolinc_sync_status(meshes[0], ws)
+        msb = e0.elapsed_time(e1) / args.steps
+        out["batched_" + prec] = {"value": cells * 3 / (msb / 1e3), "ms_per_step": msb, "launch_shape": tune,
+                                  "gpu_launches_per_step": 3, "state": u.cpu().numpy()}
+        del ws
+    # plain per-mesh FP64 path (each mesh: its own pack/differential/stage launches)
+    sch = dg.Scheme(precision="fp64", **wl["scheme"])
+    wss = [dg.workspace(M, sch) for M in meshes]
+    us = [torch.from_numpy(M.to_lib(x["u0"])).cuda() for M, x in zip(meshes, ms_)]
+    for _ in range(args.warmup):
+        for M, x, u, ws in zip(meshes, ms_, us, wss):
+            dg.dolinc_rk_step(M, sch, x["dt"], u, ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        for M, x, u, ws in zip(meshes, ms_, us, wss):
+            dg.dolinc_rk_step(M, sch, x["dt"], u, ws)
+    e1.record()
+    torch.cuda.synchronize()
+    msp = e0.elapsed_time(e1) / args.steps
+    per_mesh = np.concatenate([u.cpu().numpy() for u in us], axis=-1)
+    out["per_mesh_fp64"] = {"value": cells * 3 / (msp / 1e3), "ms_per_step": msp,
+                            "gpu_launches_per_step": len(meshes) * (1 + 3 * (sch.n_diff + 1))}
+    ref = out["batched_fp64"]["state"]
+    for k in ("batched_" + args.precision, "batched_fp64"):
+        st = out[k].pop("state")
+        out[k]["l2_rel_vs_per_mesh_fp64"] = float(np.sqrt(((st - per_mesh) ** 2).sum() / (per_mesh ** 2).sum()))
+    line = {"metric": METRIC, "value": out["batched_" + args.precision]["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["batched_" + args.precision]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64",
+            "data": "synthetic",
+            "config": {"workload": "burgers_batch", "meshes": len(meshes), "cells": cells,
+                       "min_cells": int(min(M.n_cells for M in meshes)), "max_cells": int(max(M.n_cells for M in meshes)),
+                       "stencil_k_r": [3, 1], "n_diff": 2, "flux": "burgers"},
+            "forms": out, "seconds_total": time.perf_counter() - t_all}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     """The oracle as the reference arm: host cores, a bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -362,7 +505,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dolinc", choices=["dolinc", "reference"])
     ap.add_argument("--workload", default="euler3d_tet64")
@@ -370,6 +513,13 @@ def main():
     ap.add_argument("--size", type=int, default=None, help="lattice size (default: the workload's)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--ind-runs", type=int, default=12)
+    ap.add_argument("--ind-eval-runs", type=int, default=3)
+    ap.add_argument("--ind-train-size", type=int, default=160)
+    ap.add_argument("--ind-train-steps", type=int, default=60)
+    ap.add_argument("--ind-epochs", type=int, default=30)
+    ap.add_argument("--batch-meshes", type=int, default=512)
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp32_bf16"])
     ap.add_argument("--quad", type=int, default=2, help="quadrature points per direction for initial averages")
     ap.add_argument("--ref-size", type=int, default=20)
@@ -379,6 +529,10 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "euler2d_riemann":
+        run_indicator(args)
+    elif args.workload == "burgers_batch":
+        run_batch(args)
     else:
         run_dolinc(args)
 

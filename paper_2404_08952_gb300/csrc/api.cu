@@ -28,12 +28,16 @@ dolinc_status fail(dolinc_status s, const std::string &msg)
     return s;
 }
 
+// On failure: report, and clear CUDA's last-error state so that it does not resurface
+// in a later call's launch check.
 #define CU(call)                                                                                          \
     do {                                                                                                  \
         cudaError_t e_ = (call);                                                                          \
-        if (e_ != cudaSuccess)                                                                            \
+        if (e_ != cudaSuccess) {                                                                          \
+            cudaGetLastError();                                                                           \
             return fail(e_ == cudaErrorMemoryAllocation ? DOLINC_ERR_OOM : DOLINC_ERR_CUDA,               \
                         std::string(#call) + ": " + cudaGetErrorString(e_));                              \
+        }                                                                                                 \
     } while (0)
 
 PathFns g_paths[N_PATHS];
@@ -125,10 +129,12 @@ struct dolinc_batch {
     int block = 256, grid = 0;         // persistent launch shape (0: from occupancy)
     unsigned spin_limit = 1u << 23;    // polls a grid-barrier wait makes before giving up
     cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;        // private stream the graph is captured on
     std::string gkey;
     ~dolinc_batch()
     {
         if (exec) cudaGraphExecDestroy(exec);
+        if (cap) cudaStreamDestroy(cap);
         delete arena;
     }
 };
@@ -1107,10 +1113,14 @@ dolinc_status dolinc_batch_rk_step(dolinc_batch *bt, const dolinc_scheme *s, con
             cudaGraphExecDestroy(bt->exec);
             bt->exec = nullptr;
         }
+        // capture on a private stream (the caller's may be the legacy stream, which
+        // cannot be captured); the graph is then launched on the caller's stream
+        if (!bt->cap) CU(cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
-        CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        dolinc_status ls = batch_launch_step(bt, s, bf, dt, u, ws, L, cs);
-        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        CU(cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeThreadLocal));
+        dolinc_status ls = batch_launch_step(bt, s, bf, dt, u, ws, L, bt->cap);
+        cudaError_t e = cudaStreamEndCapture(bt->cap, &g);
+        cudaGetLastError();
         if (ls) {
             if (g) cudaGraphDestroy(g);
             return ls;

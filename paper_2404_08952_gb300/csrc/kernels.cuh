@@ -386,7 +386,7 @@ __device__ __forceinline__ void slot_flux(const DevMesh &mesh, const StageArgs &
 // LPC lanes per cell: lane l evaluates slots l, l+LPC, ...; the group sums the signed
 // fluxes by recursive halving and lane l then updates variables [l*B, (l+1)*B).
 template <int DIM, int NV, int NS, int PREC, int LPC>
-__global__ void __launch_bounds__(256) k_stage(DevMesh mesh, StageArgs a)
+__global__ void __launch_bounds__(256, (PREC != PREC_F64 && NS <= 1) ? 4 : 1) k_stage(DevMesh mesh, StageArgs a)
 {
     using R = typename PrecT<PREC>::R;
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -400,6 +400,7 @@ __global__ void __launch_bounds__(256) k_stage(DevMesh mesh, StageArgs a)
         const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
         const bool own_flag = a.flags && a.flags[c];
         GlobalSrc<DIM, NV, PREC> src{a, mesh};
+#pragma unroll 2
         for (int s = s0 + l; s < s1; s += LPC) {
             R F[NV];
             slot_flux<DIM, NV, NS, PREC>(mesh, a, src, c, s, own_flag, F);
