@@ -99,6 +99,28 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def reduce_max(x, dist=None):
+    """Max over ranks of a host float (the job's time is its slowest replica)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x, dist=None):
+    """Sum over ranks (the job's work is every replica's)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return type(x)(t.item())
+
+
 def _ncoef(dim, m):
     return m + 1 if dim == 2 else (m + 1) * (m + 2) // 2
 
@@ -159,7 +181,12 @@ def run_dolinc(args):
         sch = dg.Scheme(precision=prec, **scheme_kw)
         ws = dg.workspace(M, sch)
         u = torch.from_numpy(M.to_lib(u0)).cuda()
-        tune = dg.dolinc_autotune(M, sch, u, ws) if not args.no_tune else None
+        if args.shape:
+            dl, db, sl, sb = (int(x) for x in args.shape.split(","))
+            dg.dolinc_set_tuning(M, sch, dl, db, sl, sb)
+            tune = dict(diff_lanes=dl, diff_block=db, stage_lanes=sl, stage_block=sb, forced=True)
+        else:
+            tune = dg.dolinc_autotune(M, sch, u, ws) if not args.no_tune else None
         for _ in range(args.warmup):
             dg.dolinc_rk_step(M, sch, dt, u, ws)
         finite = True
@@ -178,11 +205,7 @@ def run_dolinc(args):
                 dg.dolinc_rk_step(M, sch, dt, u, ws)
             e1.record(stream)
             torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = reduce_max(e0.elapsed_time(e1), dist)
         kms, kn = dg.profile_read(M)
         dg.dolinc_profile_enable(M, False)
         try:
@@ -216,7 +239,7 @@ def run_dolinc(args):
             del vr
     main = results[args.precision]
     cells = M.n_cells
-    total_cells = cells * world
+    total_cells = reduce_sum(cells, dist)
     ms_step = main["ms"] / args.steps
     value = total_cells * 3 * args.steps / (main["ms"] / 1e3)
     # dominant kernel and its roofline
@@ -290,11 +313,7 @@ def run_dolinc(args):
         uh.copy_(ud, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    ems = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ems], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ems = float(t.item())
+    ems = reduce_max(e0.elapsed_time(e1), dist)
     nbytes = uh.numel() * 8
     line["e2e"] = {"value": total_cells * 3 * args.steps / (ems / 1e3), "unit": UNIT,
                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
@@ -514,6 +533,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--shape", default=None, help="force diff_lanes,diff_block,stage_lanes,stage_block")
     ap.add_argument("--ind-runs", type=int, default=12)
     ap.add_argument("--ind-eval-runs", type=int, default=3)
     ap.add_argument("--ind-train-size", type=int, default=160)
