@@ -356,8 +356,10 @@ def run_indicator(args):
     Trains the network on criterion labels of seeded runs (smaller mesh), judges its
     misclassification on held-out runs, then advances one held-out problem on the full
     mesh with the limiter switched by (a) the network, FP32, (b) the criterion, FP32,
-    (c) the criterion, FP64 (the plain FP64 GPU method), (d) no limiter, and reports
-    cell-updates/s per stage (indicator included) and the L1 distance of (a), (b) to (c)."""
+    (c) the criterion, FP64 (the plain FP64 GPU method), flagged faces taking the
+    first-order fallback; the same with ENO3-DOLINC on flagged faces; no limiter; ENO3
+    everywhere.  Reports cell-updates/s per stage (indicator included), whether each
+    run stayed finite, and the L1 distance to (c)."""
     import torch
     import paper_2404_08952_gb300 as dg
     from paper_2404_08952_gb300 import indicator as ind
@@ -391,10 +393,13 @@ def run_indicator(args):
     cells = int(w["u0"].shape[1])
     steps = args.steps
     res = {}
-    for name, switch, prec in (("network_fp32", "network", "fp32"), ("criterion_fp32", "criterion", "fp32"),
-                               ("criterion_fp64", "criterion", "fp64"), ("none_fp32", "none", "fp32"),
-                               ("eno3_all_fp32", "all", "fp32")):
-        st, finite, sec, flagged = ind.run_with(w, switch, steps, precision=prec, net=net)
+    fo, eno = "first_order_flagged", "eno3_flagged"
+    for name, switch, prec, lim in (("network_fp32", "network", "fp32", fo), ("criterion_fp32", "criterion", "fp32", fo),
+                                    ("criterion_fp64", "criterion", "fp64", fo),
+                                    ("network_eno3_fp32", "network", "fp32", eno),
+                                    ("criterion_eno3_fp64", "criterion", "fp64", eno),
+                                    ("none_fp32", "none", "fp32", fo), ("eno3_all_fp32", "all", "fp32", fo)):
+        st, finite, sec, flagged = ind.run_with(w, switch, steps, precision=prec, net=net, flagged_limiter=lim)
         res[name] = dict(state=st, finite=finite, sec_per_step=sec, flagged=flagged,
                          value=cells * 3 / sec)
     ref = res["criterion_fp64"]["state"]
@@ -409,7 +414,8 @@ def run_indicator(args):
             "warmup": 0, "ms_per_step": out["network_fp32"]["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "euler2d_riemann", "cells": cells, "stencil_k_r": [3, 1], "n_diff": 2,
-                       "limiter": "ENO3-DOLINC on flagged cells", "indicator": "MLP 24-64-64-64-1 (bf16 weights)",
+                       "limiter": "first-order fallback on faces of flagged cells (ENO3-DOLINC rows: *_eno3_*)",
+                       "indicator": "MLP 24-64-64-64-1 (bf16 weights)",
                        "train_mesh_cells": int(2 * train_size ** 2), "train_runs": args.ind_runs,
                        "train_samples": int(X.shape[0]), "eval_runs": args.ind_eval_runs},
             "indicator": {"train_seconds": t_train, "epochs": args.ind_epochs, "final_loss": hist[-1],

@@ -57,7 +57,8 @@ typedef enum {
 
 enum { DOLINC_FLUX_UPWIND = 0, DOLINC_FLUX_BURGERS = 1, DOLINC_FLUX_RUSANOV = 2 };
 enum { DOLINC_FP64 = 0, DOLINC_FP32 = 1, DOLINC_FP32_BF16 = 2 };
-enum { DOLINC_LIMIT_NONE = 0, DOLINC_LIMIT_ENO3_ALL = 1, DOLINC_LIMIT_ENO3_FLAGGED = 2 };
+enum { DOLINC_LIMIT_NONE = 0, DOLINC_LIMIT_ENO3_ALL = 1, DOLINC_LIMIT_ENO3_FLAGGED = 2,
+       DOLINC_LIMIT_FIRST_ORDER_FLAGGED = 3 };
 enum { DOLINC_RENUMBER_NONE = 0, DOLINC_RENUMBER_MORTON = 1 };
 
 /* Mesh in owner/neighbour face form (Sec 2.1: a cell knows its neighbours only
@@ -111,7 +112,10 @@ typedef struct {
  *               flux in FP32, geometry master and state update FP64.
  *               DOLINC_FP32_BF16: as FP32 with differential orders >= 2 stored in BF16.
  *   limiter     DOLINC_LIMIT_*: ENO3-DOLINC (Sec 2.4) on every face, or on faces touching
- *               a cell flagged with dolinc_set_flags / dolinc_indicator_infer
+ *               a cell flagged with dolinc_set_flags / dolinc_indicator_infer; or
+ *               FIRST_ORDER_FLAGGED: on faces touching a flagged cell each orientation
+ *               takes its upwind cell's average (first-order Godunov fallback, not a
+ *               scheme of the paper; it needs no second-order differentials)
  *   gamma       ratio of specific heats (RUSANOV)
  *   adv         advection velocity (UPWIND); Burgers flux is u^2/2 (1,..,1)          */
 typedef struct {
@@ -320,7 +324,7 @@ dolinc_status dolinc_batch_autotune(dolinc_batch *batch, const dolinc_scheme *sc
                                     double *u_dev, void *ws_dev, size_t ws_bytes, dolinc_stream stream, int *block,
                                     int *grid, double *ms_per_step);
 
-/* Cell flags for DOLINC_LIMIT_ENO3_FLAGGED: flags_dev [n_cells] uint8 (library order),
+/* Cell flags for DOLINC_LIMIT_ENO3_FLAGGED / FIRST_ORDER_FLAGGED: flags_dev [n_cells] uint8 (library order),
  * non-zero = troubled.  The pointer is kept by the mesh until replaced or NULL. */
 dolinc_status dolinc_set_flags(dolinc_mesh *mesh, const uint8_t *flags_dev);
 

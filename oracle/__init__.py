@@ -105,7 +105,7 @@ class Scheme:
     def __init__(self, k=3, r=1, n_diff=None, flux="upwind", nv=1, gamma=1.4, adv=(1.0, 1.0, 0.0), eno=0,
                  troubled=None):
         need = max(r, k - r - 2)
-        if eno:
+        if eno in (1, 2):
             need = max(need, 2)
         self.k, self.r = k, r
         self.n_diff = need if n_diff is None else n_diff

@@ -63,8 +63,9 @@ typedef struct {
     int flux;         /* 0 linear advection upwind, 1 Burgers Roe, 2 Euler Rusanov */
     double gamma;     /* ratio of specific heats (Euler) */
     double adv[3];    /* advection velocity (flux 0) */
-    int eno;          /* 0 fixed stencil, 1 ENO3 on every face, 2 ENO3 on faces touching a troubled cell */
-    const unsigned char *troubled;   /* [n_cells] for eno == 2 */
+    int eno;          /* 0 fixed stencil, 1 ENO3 on every face, 2 ENO3 on faces touching a troubled cell,
+                         3 first-order upwind (the cell's own average) on faces touching a troubled cell */
+    const unsigned char *troubled;   /* [n_cells] for eno == 2, 3 */
 } or_scheme;
 
 static int ipow(int b, int e) { int p = 1; while (e-- > 0) p *= b; return p; }
@@ -371,7 +372,17 @@ static void face_states(const or_mesh *m, const or_geom *g, const or_scheme *s, 
     vsub(xQ, xf, a); vsub(xf, &g->xc[3*P], b);
     double gL = vnorm(a) / vnorm(b);            /* Eq 4 from the owner */
     double gR = vnorm(b) / vnorm(a);            /* Eq 4 from the neighbour */
-    int eno = s->eno == 1 || (s->eno == 2 && s->troubled && (s->troubled[P] || s->troubled[Q]));
+    const int touched = s->troubled && (s->troubled[P] || s->troubled[Q]);
+    if (s->eno == 3 && touched) {
+        /* first-order fallback: each orientation takes its upwind cell's average */
+        for (int v = 0; v < nv; ++v) {
+            UL[v] = T[(long)v * nc + P];
+            UR[v] = T[(long)v * nc + Q];
+            if (rL) rL[v] = rR[v] = 0;
+        }
+        return;
+    }
+    int eno = s->eno == 1 || (s->eno == 2 && touched);
     for (int v = 0; v < nv; ++v) {
         double pP[OR_MAXN + 1], pQ[OR_MAXN + 1], qP[OR_MAXN + 1], qQ[OR_MAXN + 1];
         for (int mm = 0; mm <= N; ++mm) {

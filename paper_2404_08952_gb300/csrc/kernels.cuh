@@ -148,9 +148,18 @@ struct StageArgs {
     unsigned *status;            // bit 0: non-finite output
     int k, r, mode, flux;
     double gamma, adv[3];
-    const uint8_t *flags;        // ENO3 on faces touching a flagged cell (null: none)
-    int eno_all;
+    const uint8_t *flags;        // faces touching a flagged cell are limited (null: none)
+    int eno_all;                 // ENO3 on every face
+    int flag_mode;               // limit of flagged faces: LIM_ENO3 or LIM_FIRST_ORDER
 };
+
+// Face limit: none, ENO3-DOLINC, or first-order upwind (each side's own cell average)
+enum { LIM_NONE = 0, LIM_ENO3 = 1, LIM_FIRST_ORDER = 2 };
+
+__device__ __forceinline__ int face_limit(const StageArgs &a, bool flagged)
+{
+    return a.eno_all ? LIM_ENO3 : (flagged ? a.flag_mode : LIM_NONE);
+}
 
 // Where a kernel reads cell records and face records from.  GlobalSrc: device memory
 // through the read-only path.  TileSrc (k_stage_tile): the block's own cells and the
@@ -264,10 +273,16 @@ __device__ __forceinline__ R eno3_value(R g, const R *p0, const R *p1)
 // Both face states (or the upwind one only for linear advection) of face record fr.
 template <int DIM, int NV, int NS, int PREC, bool UPWIND_ONLY, class Src>
 __device__ __forceinline__ void face_states(const StageArgs &a, const Src &src, const typename PrecT<PREC>::R *fr,
-                                            int P, int N, bool eno, typename PrecT<PREC>::R *UL,
+                                            int P, int N, int lim, typename PrecT<PREC>::R *UL,
                                             typename PrecT<PREC>::R *UR, bool want_left)
 {
     using R = typename PrecT<PREC>::R;
+    if (lim == LIM_FIRST_ORDER) {
+        constexpr int S0 = ord_stride<DIM, NV, 0, PREC>();
+        load_rec<typename PrecT<PREC>::T0, NV, S0, R, Src::LDG>(src.template rec<0>(P), 0, UL);
+        load_rec<typename PrecT<PREC>::T0, NV, S0, R, Src::LDG>(src.template rec<0>(N), 0, UR);
+        return;
+    }
     constexpr int NM = ncum(DIM, NS);
     R mono[NM];
     monomials<DIM, NS, R>(fr[0], fr[1], fr[2], mono);
@@ -276,7 +291,7 @@ __device__ __forceinline__ void face_states(const StageArgs &a, const Src &src, 
     contract_cell<DIM, NV, NS, PREC>(src, N, mono, phN);
     const R g = fr[3];
     if constexpr (NS >= 2) {
-        if (eno) {
+        if (lim == LIM_ENO3) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 R q0[3], q1[3];
@@ -357,23 +372,23 @@ __device__ __forceinline__ void slot_flux(const DevMesh &mesh, const StageArgs &
         phys_flux<DIM, NV, R>(a, U, fr, F);
     } else {
         const int P = side ? nb : c, N = side ? c : nb;
-        const bool eno = a.eno_all || (a.flags && (own_flag || a.flags[nb]));
+        const int lim = face_limit(a, a.flags && (own_flag || a.flags[nb]));
         R UL[NV], UR[NV];
         if constexpr (NV == 1) {
             if (a.flux == 0) {
                 R an = (R)a.adv[0] * fr[4] + (R)a.adv[1] * fr[5] + (DIM == 3 ? (R)a.adv[2] * fr[6] : (R)0);
                 bool left = an >= (R)0;
-                face_states<DIM, NV, NS, PREC, true>(a, src, fr, P, N, eno, UL, UR, left);
+                face_states<DIM, NV, NS, PREC, true>(a, src, fr, P, N, lim, UL, UR, left);
                 F[0] = an * (left ? UL[0] : UR[0]);
             } else {
-                face_states<DIM, NV, NS, PREC, false>(a, src, fr, P, N, eno, UL, UR, true);
+                face_states<DIM, NV, NS, PREC, false>(a, src, fr, P, N, lim, UL, UR, true);
                 R sg = fr[4] + fr[5] + (DIM == 3 ? fr[6] : (R)0);
                 R lam = (R)0.5 * (UL[0] + UR[0]) * sg;       // Roe speed of u^2/2 (1,..,1)
                 R uu = lam >= (R)0 ? UL[0] : UR[0];
                 F[0] = (R)0.5 * uu * uu * sg;
             }
         } else {
-            face_states<DIM, NV, NS, PREC, false>(a, src, fr, P, N, eno, UL, UR, true);
+            face_states<DIM, NV, NS, PREC, false>(a, src, fr, P, N, lim, UL, UR, true);
             rusanov<DIM, R>((R)a.gamma, UL, UR, fr[4], fr[5], fr[6], fr[7], F);
         }
     }
@@ -381,6 +396,22 @@ __device__ __forceinline__ void slot_flux(const DevMesh &mesh, const StageArgs &
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] = -F[v];
     }
+}
+
+// SSP-RK3 combination A u0 + B (us + dt R) with the increment dt R already formed in
+// the bulk precision (R carries that precision's rounding anyway); FP64 then does only
+// the state arithmetic: one add in stage 0 (A = 0, B = 1), add + mul + fma otherwise.
+// NaN/Inf test on the bit pattern (integer pipe; keeps the scarce FP64 pipe free)
+__device__ __forceinline__ bool nonfinite64(double x)
+{
+    return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) == 0x7ff0000000000000ull;
+}
+
+template <class R>
+__device__ __forceinline__ double stage_update(const StageArgs &a, long long i, R dtR)
+{
+    const double t = a.us[i] + (double)dtR;
+    return a.A == 0.0 ? a.B * t : fma(a.B, t, a.A * a.u0[i]);
 }
 
 // LPC lanes per cell: lane l evaluates slots l, l+LPC, ...; the group sums the signed
@@ -418,20 +449,22 @@ __global__ void __launch_bounds__(256, (PREC != PREC_F64 && NS <= 1) ? 4 : 1) k_
     using T0 = typename PrecT<PREC>::T0;
     T0 *nxt = static_cast<T0 *>(a.o0_next);
     constexpr int S0 = ord_stride<DIM, NV, 0, PREC>();
+    const R dtr = (R)a.dt;
 #pragma unroll
     for (int i = 0; i < B; ++i) {
         const int v = l * B + i;
         if (v < NV) {
-            const double rr = (double)(res[i] * iv);
+            const R r = res[i] * iv;
             double o;
             if (a.mode == 0) {
-                o = rr;
+                o = (double)r;
+                bad |= !isfinite(r);
             } else {
-                o = a.A * a.u0[v * n + c] + a.B * fma(a.dt, rr, a.us[v * n + c]);
+                o = stage_update(a, v * n + c, r * dtr);
+                bad |= nonfinite64(o);
                 if (nxt) nxt[c * (long long)S0 + v] = (T0)o;
             }
             a.out[v * n + c] = o;
-            bad |= !isfinite(o);
         }
     }
     if (bad) atomicOr(a.status, 1u);
@@ -518,18 +551,14 @@ __global__ void __launch_bounds__(TILE) k_stage_tile(DevMesh mesh, StageArgs a)
     T0 *nxt = static_cast<T0 *>(a.o0_next);
     constexpr int S0 = ord_stride<DIM, NV, 0, PREC>();
     R nv_out[NV];
+    const R dtr = (R)a.dt;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        const double rr = (double)(res[v] * iv);
-        double o;
-        if (a.mode == 0) {
-            o = rr;
-        } else {
-            o = a.A * a.u0[v * n + c] + a.B * fma(a.dt, rr, a.us[v * n + c]);
-        }
+        const R r = res[v] * iv;
+        const double o = a.mode == 0 ? (double)r : stage_update(a, v * n + c, r * dtr);
         nv_out[v] = (R)o;
         a.out[v * n + c] = o;
-        bad |= !isfinite(o);
+        bad |= nonfinite64(o);
     }
     if (a.mode != 0 && nxt) store_rec<T0, NV, S0, R>(nxt, c, nv_out);
     if (bad) atomicOr(a.status, 1u);
@@ -712,16 +741,16 @@ __global__ void __launch_bounds__(256) k_batch_stage(DevMesh mesh, StageArgs a, 
         }
         R iv, d0, d1, d2;
         ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, d0, d1, d2, iv);
-        const double dt = b.dt_tab[__ldg(b.cell_mesh + c)];
+        const R dtr = (R)b.dt_tab[__ldg(b.cell_mesh + c)];
         bool bad = false;
         R o32[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            const double rr = (double)(res[v] * iv);
-            const double o = a.A * a.u0[(long long)v * n + c] + a.B * fma(dt, rr, a.us[(long long)v * n + c]);
+            const R r = res[v] * iv;
+            const double o = stage_update(a, (long long)v * n + c, r * dtr);
             a.out[(long long)v * n + c] = o;
             o32[v] = (R)o;
-            bad |= !isfinite(o);
+            bad |= nonfinite64(o);
         }
         if (nxt) store_rec<T0, NV, S0, R>(nxt, c, o32);
         if (bad) atomicOr(a.status, 1u);
@@ -751,9 +780,9 @@ __global__ void __launch_bounds__(128) k_faces(DevMesh mesh, StageArgs a, double
 #pragma unroll
         for (int v = 0; v < NV; ++v) UR[v] = UL[v];
     } else {
-        const bool eno = a.eno_all || (a.flags && (a.flags[P] || a.flags[N]));
+        const int lim = face_limit(a, a.flags && (a.flags[P] || a.flags[N]));
         GlobalSrc<DIM, NV, PREC> src{a, mesh};
-        face_states<DIM, NV, NS, PREC, false>(a, src, fr, P, N, eno, UL, UR, true);
+        face_states<DIM, NV, NS, PREC, false>(a, src, fr, P, N, lim, UL, UR, true);
     }
     const long long nf = mesh.n_faces;
 #pragma unroll

@@ -2,10 +2,17 @@
 
 Orchestration only: every step runs in libdolinc's kernels (stage, criterion,
 features, network forward/backward/Adam).  The criterion labels the cells of
-seeded four-quadrant Riemann runs in which it also drives the ENO3-DOLINC limiter;
-the network is trained on (features, labels) sampled along those runs and then
-replaces the criterion as the limiter's switch, the criterion judging its
+seeded four-quadrant Riemann runs in which it also drives the limiter of flagged
+faces; the network is trained on (features, labels) sampled along those runs and
+then replaces the criterion as the limiter's switch, the criterion judging its
 misclassification rate.
+
+The limiter of flagged faces is either ENO3-DOLINC (Sec 2.4) or the first-order
+fallback (each side's own cell average).  On these Riemann problems ENO3-DOLINC
+alone does not keep the runs bounded: its far values are inverted from the cell's
+Gauss differentials, which carry the jump at the cell's other faces, so a flagged
+cell's face values can all exceed its average and drain it; the fallback is the
+default here.
 """
 import numpy as np
 
@@ -13,14 +20,15 @@ from . import (MLP, Mesh, Scheme, dolinc_criterion, dolinc_indicator_features, d
                dolinc_sync_status, workspace)
 
 
-def riemann_runs(make_workload, seeds, steps, sample_every, precision="fp32", kappa=4.0, eps=1e-3):
+def riemann_runs(make_workload, seeds, steps, sample_every, precision="fp32", kappa=4.0, eps=1e-3,
+                 limiter="first_order_flagged"):
     """Yields (x24 [n,24] float32 cuda, labels [n] uint8 cuda) samples along criterion-
     limited runs of the given seeds.  make_workload(seed) -> synth workload dict."""
     import torch
     for seed in seeds:
         w = make_workload(seed)
         M = Mesh(w["mesh"])
-        sch = Scheme(precision=precision, limiter="eno3_flagged", **w["scheme"])
+        sch = Scheme(precision=precision, limiter=limiter, **w["scheme"])
         flags = torch.zeros(M.n_cells, dtype=torch.uint8, device="cuda")
         dolinc_set_flags(M, flags)
         ws = workspace(M, sch)
@@ -69,22 +77,24 @@ def confusion(pred, label):
                 precision=tp / max(tp + fp, 1), flagged=(tp + fp) / n, troubled=(tp + fn) / n)
 
 
-def run_with(w, switch, steps, precision="fp32", net=None, kappa=4.0, eps=1e-3):
+def run_with(w, switch, steps, precision="fp32", net=None, kappa=4.0, eps=1e-3, flagged_limiter="first_order_flagged"):
     """Advance one workload with the limiter driven by `switch`: 'none' (fixed stencil),
-    'criterion', 'network' or 'all' (ENO3 everywhere).  Returns (state in caller order,
-    finite flag, seconds per step of indicator + stage, flagged fraction)."""
+    'criterion', 'network' or 'all' (ENO3 everywhere); flagged faces take
+    `flagged_limiter`.  Returns (state in caller order, finite flag, seconds per step of
+    indicator + stage, flagged fraction)."""
     import torch
     M = Mesh(w["mesh"])
-    limiter = {"none": "none", "all": "eno3_all"}.get(switch, "eno3_flagged")
+    limiter = {"none": "none", "all": "eno3_all"}.get(switch, flagged_limiter)
+    flagged = limiter in ("eno3_flagged", "first_order_flagged")
     sch = Scheme(precision=precision, limiter=limiter, **w["scheme"])
     flags = torch.zeros(M.n_cells, dtype=torch.uint8, device="cuda")
-    if limiter == "eno3_flagged":
+    if flagged:
         dolinc_set_flags(M, flags)
     ws = workspace(M, sch)
     u = torch.from_numpy(M.to_lib(w["u0"])).cuda()
     x = torch.zeros((M.n_cells, 24), dtype=torch.float32, device="cuda") if switch == "network" else None
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    flagged = 0.0
+    frac = 0.0
     torch.cuda.synchronize()
     e0.record()
     for _ in range(steps):
@@ -96,8 +106,8 @@ def run_with(w, switch, steps, precision="fp32", net=None, kappa=4.0, eps=1e-3):
         dolinc_rk_step(M, sch, w["dt"], u, ws)
     e1.record()
     torch.cuda.synchronize()
-    if limiter == "eno3_flagged":
-        flagged = float(flags.float().mean().item())
+    if flagged:
+        frac = float(flags.float().mean().item())
     finite = True
     try:
         dolinc_sync_status(M, ws)
@@ -105,9 +115,9 @@ def run_with(w, switch, steps, precision="fp32", net=None, kappa=4.0, eps=1e-3):
         finite = False
     st = M.from_lib(u.cpu().numpy())
     finite = finite and bool(np.all(np.isfinite(st)))
-    if limiter == "eno3_flagged":
+    if flagged:
         dolinc_set_flags(M, None)
-    return st, finite, e0.elapsed_time(e1) / 1e3 / steps, flagged
+    return st, finite, e0.elapsed_time(e1) / 1e3 / steps, frac
 
 
 __all__ = ["riemann_runs", "train", "confusion", "run_with", "MLP"]

@@ -319,7 +319,7 @@ def test_renumbering_does_not_change_results(renumber):
 
 # ---------------------------------------------------------------------------- ENO3 limiter
 
-@pytest.mark.parametrize("mode", ["eno3_all", "eno3_flagged"])
+@pytest.mark.parametrize("mode", ["eno3_all", "eno3_flagged", "first_order_flagged"])
 @pytest.mark.parametrize("name,nv", [("tri", 1), ("tri_bnd", 4), ("tet", 5)])
 def test_eno3_limiter_fp64(mode, name, nv):
     m, O = mesh(name)
@@ -335,11 +335,36 @@ def test_eno3_limiter_fp64(mode, name, nv):
     Rg = torch.zeros((nv, M.n_cells), dtype=torch.float64, device="cuda")
     dg.dolinc_residual(M, sch, to_dev(M, u), Rg, ws)
     got = M.from_lib(Rg.cpu().numpy())
-    osch = oracle.Scheme(k=3, r=1, n_diff=2, nv=nv, eno=1 if mode == "eno3_all" else 2,
-                         troubled=flags if mode == "eno3_flagged" else None, **fx)
+    eno = {"eno3_all": 1, "eno3_flagged": 2, "first_order_flagged": 3}[mode]
+    osch = oracle.Scheme(k=3, r=1, n_diff=2, nv=nv, eno=eno, troubled=flags if eno > 1 else None, **fx)
     want = O.residual(u, osch)
     # stencil choices are taken in FP64 on both sides; smooth random data has no ties
     assert rel(got, want) < 1e-12
+    dg.dolinc_set_flags(M, None)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name,nv", [("tri_bnd", 4), ("tet", 5), ("hexprism", 1)])
+def test_first_order_fallback_csr4_one_differential(prec, name, nv):
+    """The first-order fallback needs no second-order differentials: CSR4 (n_diff = 1)
+    with flagged faces, one full SSP-RK3 step against the oracle."""
+    m, O = mesh(name)
+    M = gpu_mesh(m)
+    u = field(m, nv, seed=34)
+    flags = (np.random.default_rng(35).uniform(size=O.n_cells) < 0.4).astype(np.uint8)
+    fx = euler_ok(nv) if nv > 1 else dict(flux="upwind", adv=(1.0, 0.7, 0.4))
+    sch = dg.Scheme(k=4, r=1, n_diff=1, nv=nv, precision=prec, limiter="first_order_flagged", **fx)
+    dg.dolinc_set_flags(M, torch.from_numpy(M.to_lib(flags)).cuda())
+    ws = dg.workspace(M, sch)
+    x = to_dev(M, u)
+    dt = 2e-3
+    dg.dolinc_rk_step(M, sch, dt, x, ws)
+    dg.dolinc_sync_status(M, ws)
+    got = M.from_lib(x.cpu().numpy())
+    want = O.rk3_step(u, oracle.Scheme(k=4, r=1, n_diff=1, nv=nv, eno=3, troubled=flags, **fx), dt)
+    base = O.rk3_step(u, oracle.Scheme(k=4, r=1, n_diff=1, nv=nv, **fx), dt)
+    assert rel(got - u, want - u) < (1e-11 if prec == "fp64" else 2e-4)
+    assert rel(base - u, want - u) > 1e-3          # the fallback changed the step
     dg.dolinc_set_flags(M, None)
 
 

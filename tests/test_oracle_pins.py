@@ -332,3 +332,47 @@ def test_isentropic_vortex_converges_to_exact_translation():
                                                                    u_inf=(1.0, 0.5, 0.0)), q=3, nv=4)
         errs.append(np.sqrt(np.sum(O.V * (U[0] - ex[0]) ** 2)))
     assert errs[1] < errs[0] / 2.5, errs
+
+
+def test_first_order_fallback_is_textbook_upwind():
+    """Faces touching a troubled cell take each side's own average (first-order
+    fallback, eno = 3): on a non-uniform 1D strip a cell whose two faces are both
+    touched has R_i = -a (u_i - u_{i-1}) / dx_i, the textbook upwind difference;
+    cells whose faces are untouched keep the fixed-stencil residual."""
+    rng = np.random.default_rng(8)
+    n = 14
+    widths = rng.uniform(0.5, 1.5, n)
+    widths /= widths.sum()
+    m = synth.strip_mesh(widths)
+    O = oracle.Oracle(m)
+    u = rng.normal(size=(1, n))
+    a = 1.7
+    troubled = np.zeros(n, dtype=np.uint8)
+    troubled[4:8] = 1
+    fo = O.residual(u, oracle.Scheme(k=3, r=1, n_diff=2, flux="upwind", adv=(a, 0.0), eno=3, troubled=troubled))
+    ho = O.residual(u, oracle.Scheme(k=3, r=1, n_diff=2, flux="upwind", adv=(a, 0.0)))
+    # x-faces of the strip are the only faces carrying flux (a has no y component)
+    xc = O.xc[:, 0]
+    order = np.argsort(xc)
+    assert np.all(order == np.arange(n))
+    for i in range(4, 8):                      # both faces touch a troubled cell
+        want = -a * (u[0, i] - u[0, i - 1]) / widths[i]
+        assert abs(fo[0, i] - want) < 1e-12 * max(1.0, abs(want))
+    far = [0, 1, 11, 12]                      # faces two or more cells from the troubled block
+    np.testing.assert_allclose(fo[0, far], ho[0, far], rtol=1e-13, atol=1e-13)
+
+
+def test_first_order_fallback_keeps_the_discrete_maximum_principle():
+    """With every cell troubled the update is first-order upwind, a convex combination
+    of neighbouring averages for dt sum_f |a.S_f| / V <= 1: a step profile stays within
+    its initial bounds on jittered triangles, where the fixed stencil overshoots."""
+    m = synth.tri_mesh(16, 16, 0.2, 12)
+    O = oracle.Oracle(m)
+    u0 = synth.cell_average(m, lambda p: ((p[:, 0] > 0.3) & (p[:, 0] < 0.6)).astype(float), q=3)[None]
+    adv = (1.0, 0.5)
+    dt = 0.25 / 16 / 3
+    troubled = np.ones(O.n_cells, dtype=np.uint8)
+    fo = O.run(u0, oracle.Scheme(k=3, r=1, n_diff=2, flux="upwind", adv=adv, eno=3, troubled=troubled), dt, 40)
+    assert fo.min() >= u0.min() - 1e-13 and fo.max() <= u0.max() + 1e-13
+    ho = O.run(u0, oracle.Scheme(k=3, r=1, n_diff=2, flux="upwind", adv=adv), dt, 40)
+    assert ho.min() < u0.min() - 1e-3 or ho.max() > u0.max() + 1e-3
