@@ -495,6 +495,126 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_hexprism(args):
+    """Gaussian-pulse advection on the mixed hex/prism mesh (+-20% jitter, periodic).
+
+    Throughput of scheme orders 2..5 (differentials through order p-1) in FP64, FP32
+    and FP32 with BF16-stored orders >= 2 at one lattice size, and a convergence sweep:
+    each order advanced in FP32 and FP64 to t = T on several lattice sizes, the L2 error
+    sqrt(sum V e^2 / sum V) against the exact cell averages of the translated pulse, and
+    the measured order between consecutive sizes."""
+    import synth
+    from synth import fields
+    t_all = time.perf_counter()
+    workers = max(1, min(16, os.cpu_count() or 1))
+    size = args.size or 140
+    sizes = sorted(int(x) for x in args.hp_sizes.split(",") if x)
+    T = args.hp_time
+    orders = (2, 3, 4, 5)
+    # host inputs first: the forked quadrature runs before CUDA is initialised
+    host = {}
+    for n in sorted(set(sizes + [size])):
+        t0 = time.perf_counter()
+        w = synth.workload("adv3d_hexprism", order=5, size=n, q=args.hp_quad, workers=workers)
+        a = np.asarray(w["scheme"]["adv"], dtype=np.float64)
+        exact = None
+        if n in sizes:
+            c = tuple(0.5 + a[k] * T for k in range(3))
+            exact = fields.cell_average(w["mesh"], lambda p, c=c: fields.gaussian3d(p, centre=c), q=args.hp_quad,
+                                        workers=workers)
+        host[n] = (w, exact, time.perf_counter() - t0)
+    import torch
+    import paper_2404_08952_gb300 as dg
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    thr = {}
+    w, _, _ = host[size]
+    M = dg.Mesh(w["mesh"], renumber="morton")
+    cells = M.n_cells
+    peak, peak_src = _peaks()
+    for order in orders:
+        k, r = synth.STENCIL_OF_ORDER[order]
+        for prec in ("fp64", "fp32", "fp32_bf16"):
+            if prec == "fp32_bf16" and order < 3:
+                continue
+            sch = dg.Scheme(precision=prec, **dict(w["scheme"], k=k, r=r, n_diff=order - 1))
+            ws = dg.workspace(M, sch)
+            u = torch.from_numpy(M.to_lib(w["u0"])).cuda()
+            tune = dg.dolinc_autotune(M, sch, u, ws)
+            for _ in range(args.warmup):
+                dg.dolinc_rk_step(M, sch, w["dt"], u, ws)
+            dg.dolinc_profile_enable(M, True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                dg.dolinc_rk_step(M, sch, w["dt"], u, ws)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            kms, kn = dg.profile_read(M)
+            dg.dolinc_profile_enable(M, False)
+            finite = True
+            try:
+                dg.dolinc_sync_status(M, ws)
+            except dg.DolincError:
+                finite = False
+            top = int(np.argmax(kms))
+            pl = kms[top] / max(kn[top], 1)
+            ab = alg_bytes(KINDS[top], M, sch)
+            thr["%s_order%d" % (prec, order)] = {
+                "value": cells * 3 * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                "finite_after_steps": finite, "launch_shape": tune,
+                "top_kernel": KINDS[top], "top_share": round(kms[top] / sum(kms), 4),
+                "top_alg_GBs": round(ab / (pl / 1e3) / 1e9, 1), "top_frac_of_peak": round(ab / (pl / 1e3) / 1e9 / peak, 4)}
+            del ws, u
+    del M
+    conv = {}
+    for prec in ("fp32", "fp64"):
+        for order in orders:
+            k, r = synth.STENCIL_OF_ORDER[order]
+            row = []
+            for n in sizes:
+                w, exact, _ = host[n]
+                Mn = dg.Mesh(w["mesh"], renumber="morton")
+                sch = dg.Scheme(precision=prec, **dict(w["scheme"], k=k, r=r, n_diff=order - 1))
+                ws = dg.workspace(Mn, sch)
+                u = torch.from_numpy(Mn.to_lib(w["u0"])).cuda()
+                dg.dolinc_autotune(Mn, sch, u, ws)
+                nsteps = int(np.ceil(T / w["dt"] - 1e-9))
+                dt = T / nsteps
+                for _ in range(nsteps):
+                    dg.dolinc_rk_step(Mn, sch, dt, u, ws)
+                finite = True
+                try:
+                    dg.dolinc_sync_status(Mn, ws)
+                except dg.DolincError:
+                    finite = False
+                got = Mn.from_lib(u.cpu().numpy())[0]
+                V = Mn.from_lib(Mn.geometry()["V"])
+                e = got - exact
+                l2 = float(np.sqrt((V * e * e).sum() / V.sum())) if finite else None
+                row.append({"lattice": n, "cells": Mn.n_cells, "steps": nsteps, "finite": finite, "l2": l2,
+                            "linf": float(np.abs(e).max()) if finite else None})
+                del ws, u, Mn
+            for a_, b_ in zip(row, row[1:]):
+                if a_["l2"] and b_["l2"]:
+                    b_["order_vs_previous"] = float(np.log(a_["l2"] / b_["l2"]) / np.log(b_["lattice"] / a_["lattice"]))
+            conv["%s_order%d" % (prec, order)] = row
+    main = thr["fp32_order5"]
+    line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "adv3d_hexprism", "lattice": size, "cells": cells, "headline": "fp32_order5",
+                       "flux": "upwind", "adv": list(w["scheme"]["adv"]), "jitter": 0.2,
+                       "convergence_time": T, "convergence_lattices": sizes, "quad": args.hp_quad,
+                       "peak_GBs": peak, "peak_source": peak_src},
+            "forms": thr, "convergence": conv,
+            "host_input_seconds": {str(n): round(v[2], 1) for n, v in host.items()},
+            "seconds_total": time.perf_counter() - t_all}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     """The oracle as the reference arm: host cores, a bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -550,6 +670,9 @@ def main():
     ap.add_argument("--quad", type=int, default=2, help="quadrature points per direction for initial averages")
     ap.add_argument("--ref-size", type=int, default=20)
     ap.add_argument("--no-oracle", action="store_true")
+    ap.add_argument("--hp-sizes", default="35,70,140", help="adv3d_hexprism convergence lattices")
+    ap.add_argument("--hp-time", type=float, default=0.05, help="adv3d_hexprism convergence end time")
+    ap.add_argument("--hp-quad", type=int, default=3, help="adv3d_hexprism quadrature points per direction")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -559,6 +682,8 @@ def main():
         run_indicator(args)
     elif args.workload == "burgers_batch":
         run_batch(args)
+    elif args.workload == "adv3d_hexprism":
+        run_hexprism(args)
     else:
         run_dolinc(args)
 

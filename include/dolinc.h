@@ -197,7 +197,12 @@ dolinc_status dolinc_rk_stage(dolinc_mesh *mesh, const dolinc_scheme *scheme, do
                               size_t ws_bytes, dolinc_stream stream);
 
 /* One full SSP-RK3 step of u_dev in place (three stages, each: n_diff differential
- * passes + one fused reconstruction/flux/residual/update pass). */
+ * passes + one fused reconstruction/flux/residual/update pass).  In FP64 every stage
+ * value is formed in FP64 as dolinc_rk_stage does.  Below FP64 the step runs in the
+ * equivalent increment form: with d_k = dt R(u_k), u1 = u0 + D0, u2 = u0 + D1 and
+ * u^{n+1} = u0 + (2/3)(D1 + d2), where D0 = d0, D1 = (D0 + d1)/4 are kept per cell in
+ * the bulk precision; the stage inputs exist only as bulk-precision records and the
+ * FP64 state receives one add per step. */
 dolinc_status dolinc_rk_step(dolinc_mesh *mesh, const dolinc_scheme *scheme, double dt, double *u_dev,
                              void *ws_dev, size_t ws_bytes, dolinc_stream stream);
 

@@ -308,7 +308,10 @@ def dolinc_set_tuning(mesh, scheme, diff_lanes=4, diff_block=256, stage_lanes=4,
 
 
 def dolinc_set_flags(mesh, flags):
+    """The library keeps the device pointer, so the mesh object keeps the tensor alive
+    until the flags are replaced or cleared (None)."""
     _check(load().dolinc_set_flags(mesh.handle, _ptr(flags)))
+    mesh._flags = flags
 
 
 def dolinc_sync_status(mesh, ws, stream=None):

@@ -190,7 +190,7 @@ int ncoef_h(int dim, int m) { return dim == 2 ? m + 1 : (m + 1) * (m + 2) / 2; }
 int stride_h(int dim, int nv, int m, int prec) { return rec_stride(nv * ncoef_h(dim, m), elem_bytes(prec, m)); }
 
 struct WsLayout {
-    size_t status, o0[2], ord[MAXN + 1], ustage, total;
+    size_t status, o0[3], ord[MAXN + 1], ustage, dacc, total;
 };
 
 WsLayout ws_layout(const dolinc_mesh *m, const dolinc_scheme *s)
@@ -200,9 +200,12 @@ WsLayout ws_layout(const dolinc_mesh *m, const dolinc_scheme *s)
     size_t o = 0;
     L.status = o;
     o += 1024;                                  // status word, then the batch grid-barrier words
-    for (int i = 0; i < 2; ++i) {
+    // order-0 records: step start and two stage inputs (the third only for the
+    // increment form of bulk precisions below FP64)
+    const int n_o0 = s->precision == DOLINC_FP64 ? 2 : 3;
+    for (int i = 0; i < 3; ++i) {
         L.o0[i] = o;
-        o += al256(nc * stride_h(m->h.dim, s->nv, 0, s->precision) * elem_bytes(s->precision, 0));
+        if (i < n_o0) o += al256(nc * stride_h(m->h.dim, s->nv, 0, s->precision) * elem_bytes(s->precision, 0));
     }
     L.ord[0] = L.o0[0];
     for (int mm = 1; mm <= MAXN; ++mm) {
@@ -211,6 +214,8 @@ WsLayout ws_layout(const dolinc_mesh *m, const dolinc_scheme *s)
     }
     L.ustage = o;
     o += al256(nc * s->nv * sizeof(double));
+    L.dacc = o;                                 // increment accumulator (bulk precision below FP64)
+    if (s->precision != DOLINC_FP64) o += al256(nc * s->nv * sizeof(float));
     L.total = o;
     return L;
 }
@@ -600,6 +605,23 @@ dolinc_status dolinc_rk_step(dolinc_mesh *m, const dolinc_scheme *s, double dt, 
     double *ust = reinterpret_cast<double *>(B(ws, L.ustage));
     const Tune tn = tune_for(m, s);
     timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, u, B(ws, L.o0[0]), cs); });
+    if (s->precision != DOLINC_FP64) {
+        // increment form: stage k reads record o0[k], writes o0[k+1] and the accumulator
+        for (int sg = 0; sg < 3; ++sg) {
+            run_diffs(m, p, ws, L, L.o0[sg], s->n_diff, tn, cs);
+            StageArgs a = base_args(m, s, ws, L, L.o0[sg]);
+            a.mode = 2;
+            a.rk = sg;
+            a.u0 = u;
+            a.out = u;
+            a.dt = dt;
+            a.dacc = reinterpret_cast<float *>(B(ws, L.dacc));
+            a.rec_start = B(ws, L.o0[0]);
+            a.o0_next = sg == 2 ? nullptr : B(ws, L.o0[sg + 1]);
+            timed(m, DOLINC_KERNEL_STAGE, cs, [&] { p->stage(m->d, a, tn, cs); });
+        }
+        return launch_check();
+    }
     int cur = 0;
     for (int sg = 0; sg < 3; ++sg) {
         run_diffs(m, p, ws, L, L.o0[cur], s->n_diff, tn, cs);
@@ -707,9 +729,23 @@ dolinc_status dolinc_autotune(dolinc_mesh *m, const dolinc_scheme *s, const doub
                     for (int mm = 1; mm <= s->n_diff; ++mm)
                         p->diff(m->d, mm, B(ws, mm == 1 ? L.o0[0] : L.ord[mm - 1]), B(ws, L.ord[mm]), t, cs);
                 });
+                // the stage as rk_step runs it (middle stage), on scratch outputs
                 StageArgs a = base_args(m, s, ws, L, L.o0[0]);
-                a.mode = 0;
-                a.out = reinterpret_cast<double *>(B(ws, L.ustage));
+                double *scratch = reinterpret_cast<double *>(B(ws, L.ustage));
+                a.u0 = a.us = a.out = scratch;
+                a.dt = 0.0;
+                if (s->precision != DOLINC_FP64) {
+                    a.mode = 2;
+                    a.rk = 1;
+                    a.dacc = reinterpret_cast<float *>(B(ws, L.dacc));
+                    a.rec_start = B(ws, L.o0[0]);
+                    a.o0_next = B(ws, L.o0[2]);
+                } else {
+                    a.mode = 1;
+                    a.A = 0.75;
+                    a.B = 0.25;
+                    a.o0_next = B(ws, L.o0[1]);
+                }
                 double tsg = time_it([&] { p->stage(m->d, a, t, cs); });
                 if (td < bd) bd = td, best.diff_lpc = t.diff_lpc, best.diff_block = t.diff_block;
                 if (tsg < bs) bs = tsg, best.stage_lpc = t.stage_lpc, best.stage_block = t.stage_block;

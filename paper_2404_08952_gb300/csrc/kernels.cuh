@@ -143,8 +143,12 @@ struct StageArgs {
     const void *ord[MAXN + 1];   // order records 0..NS (order 0 = bulk copy of the stage input)
     void *o0_next;               // order-0 record of the stage output (may be null)
     const double *u0, *us;       // FP64 step start and stage input [v][c]
-    double *out;                 // FP64 output [v][c]: residual (mode 0) or stage value (mode 1)
+    double *out;                 // FP64 output [v][c]: residual (mode 0), stage value (mode 1),
+                                 // or the step's new state (mode 2, last stage)
     double A, B, dt;             // out = A u0 + B (us + dt R)
+    float *dacc;                 // mode 2: increment accumulator D [v][c] (bulk precision)
+    const void *rec_start;       // mode 2: order-0 record of the step's start state
+    int rk;                      // mode 2: SSP-RK3 stage index 0, 1, 2
     unsigned *status;            // bit 0: non-finite output
     int k, r, mode, flux;
     double gamma, adv[3];
@@ -414,6 +418,43 @@ __device__ __forceinline__ double stage_update(const StageArgs &a, long long i, 
     return a.A == 0.0 ? a.B * t : fma(a.B, t, a.A * a.u0[i]);
 }
 
+// Increment form of the SSP-RK3 step (mode 2, bulk precision below FP64).  With
+// d_k = dt R(u_k) the three Shu-Osher stages expand to
+//   u1 = u0 + D0,  u2 = u0 + D1,  u^{n+1} = u0 + (2/3)(D1 + d2),
+//   D0 = d0,  D1 = (D0 + d1)/4,
+// so the increment D of each cell is carried in the bulk precision between stages,
+// the next stage's order-0 record is formed as (start record + D), and the FP64 state
+// is touched once per step: one add in the last stage.
+template <class R>
+__device__ __forceinline__ bool nonfinite32(R x)
+{
+    return (__float_as_uint((float)x) & 0x7f800000u) == 0x7f800000u;
+}
+
+// Variable v of cell c; d = dt R.  Returns true on NaN/Inf.
+template <class R, class T0, int S0>
+__device__ __forceinline__ bool incr_update(const StageArgs &a, int c, int v, long long n, R d, T0 *nxt)
+{
+    const long long i = v * n + c;
+    if (a.rk == 0) {
+        a.dacc[i] = (float)d;
+        const R u0 = (R)static_cast<const T0 *>(a.rec_start)[c * (long long)S0 + v];
+        nxt[c * (long long)S0 + v] = (T0)(u0 + d);
+        return nonfinite32(d);
+    }
+    if (a.rk == 1) {
+        const R D = (R)0.25 * ((R)a.dacc[i] + d);
+        a.dacc[i] = (float)D;
+        const R u0 = (R)static_cast<const T0 *>(a.rec_start)[c * (long long)S0 + v];
+        nxt[c * (long long)S0 + v] = (T0)(u0 + D);
+        return nonfinite32(D);
+    }
+    const R D = (R)(2.0 / 3.0) * ((R)a.dacc[i] + d);
+    const double o = a.u0[i] + (double)D;
+    a.out[i] = o;
+    return nonfinite64(o);
+}
+
 // LPC lanes per cell: lane l evaluates slots l, l+LPC, ...; the group sums the signed
 // fluxes by recursive halving and lane l then updates variables [l*B, (l+1)*B).
 template <int DIM, int NV, int NS, int PREC, int LPC>
@@ -455,6 +496,12 @@ __global__ void __launch_bounds__(256, (PREC != PREC_F64 && NS <= 1) ? 4 : 1) k_
         const int v = l * B + i;
         if (v < NV) {
             const R r = res[i] * iv;
+            if constexpr (PREC != PREC_F64) {
+                if (a.mode == 2) {
+                    bad |= incr_update<R, T0, S0>(a, c, v, n, r * dtr, nxt);
+                    continue;
+                }
+            }
             double o;
             if (a.mode == 0) {
                 o = (double)r;
@@ -552,6 +599,14 @@ __global__ void __launch_bounds__(TILE) k_stage_tile(DevMesh mesh, StageArgs a)
     constexpr int S0 = ord_stride<DIM, NV, 0, PREC>();
     R nv_out[NV];
     const R dtr = (R)a.dt;
+    if constexpr (PREC != PREC_F64) {
+        if (a.mode == 2) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) bad |= incr_update<R, T0, S0>(a, c, v, n, res[v] * iv * dtr, nxt);
+            if (bad) atomicOr(a.status, 1u);
+            return;
+        }
+    }
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         const R r = res[v] * iv;

@@ -11,28 +11,17 @@ collapsed onto the simplex (Duffy map), exact for polynomials of total degree
 import numpy as np
 
 
-def _simplices(mesh):
-    """Signed simplices (apex first) of each cell, as (cell id, vertex coordinates)."""
+def _simplices(mesh, apex, c0, lo, hi):
+    """Signed simplices (apex first) of half-faces lo..hi, as (cell id - c0, vertices);
+    apex is indexed by cell id - c0."""
     dim = mesh["dim"]
     nodes = mesh["nodes"]
-    hc = mesh["_hf_cell"]
-    hf = mesh["_hf_nodes"]
-    n_cells = mesh["cell_face_offsets"].shape[0] - 1
-    # apex: mean of each cell's distinct half-face nodes (duplicates don't matter for
-    # correctness: any point gives the same signed integral)
-    valid = hf >= 0
-    pts = nodes[np.maximum(hf, 0)] * valid[..., None]
-    cnt = np.zeros(n_cells)
-    np.add.at(cnt, hc, valid.sum(axis=1))
-    apex = np.zeros((n_cells, dim))
-    np.add.at(apex, hc, pts.sum(axis=1))
-    apex /= cnt[:, None]
+    hc = mesh["_hf_cell"][lo:hi] - c0
+    hf = mesh["_hf_nodes"][lo:hi]
     if dim == 2:
-        a = nodes[hf[:, 0]]
-        b = nodes[hf[:, 1]]
-        verts = np.stack([apex[hc], a, b], axis=1)
+        verts = np.stack([apex[hc], nodes[hf[:, 0]], nodes[hf[:, 1]]], axis=1)
         return hc, verts
-    nf = valid.sum(axis=1)
+    nf = (hf >= 0).sum(axis=1)
     cells, verts = [], []
     tri = nf == 3
     if tri.any():
@@ -47,7 +36,58 @@ def _simplices(mesh):
             v = np.stack([apex[hc[quad]], fc, nodes[q[:, e]], nodes[q[:, (e + 1) % 4]]], axis=1)
             cells.append(hc[quad])
             verts.append(v)
+    if not cells:
+        return np.zeros(0, dtype=np.int64), np.zeros((0, dim + 1, dim))
     return np.concatenate(cells), np.concatenate(verts)
+
+
+def _average_range(mesh, func, q, c0, c1, chunk):
+    """Integrals and measures of cells c0..c1-1 (half-faces are sorted by cell)."""
+    dim = mesh["dim"]
+    nodes = mesh["nodes"]
+    hcell = mesh["_hf_cell"]
+    lo, hi = (int(x) for x in np.searchsorted(hcell, [c0, c1]))
+    n = c1 - c0
+    # apex: mean of the cell's half-face node occurrences (any interior point gives the
+    # same signed integral; duplicates do not matter)
+    cnt = np.zeros(n)
+    apex = np.zeros((n, dim))
+    for s in range(lo, hi, chunk):
+        h = mesh["_hf_nodes"][s:min(s + chunk, hi)]
+        c = hcell[s:min(s + chunk, hi)] - c0
+        valid = h >= 0
+        pts = (nodes[np.maximum(h, 0)] * valid[..., None]).sum(axis=1)
+        cnt += np.bincount(c, weights=valid.sum(axis=1), minlength=n)
+        for k in range(dim):
+            apex[:, k] += np.bincount(c, weights=pts[:, k], minlength=n)
+    apex /= cnt[:, None]
+    ref, wt = _duffy_rule(dim, q)
+    acc = None
+    vol = np.zeros(n)
+    for s in range(lo, hi, chunk):
+        c, v = _simplices(mesh, apex, c0, s, min(s + chunk, hi))
+        if c.shape[0] == 0:
+            continue
+        E = v[:, 1:, :] - v[:, :1, :]                         # edge vectors [n, dim, dim]
+        det = np.linalg.det(np.transpose(E, (0, 2, 1)))       # signed measure * dim!
+        pts = v[:, None, 0, :] + np.einsum("pk,nkd->npd", ref, E)
+        val = np.asarray(func(pts.reshape(-1, dim)), dtype=np.float64)
+        val = val.reshape(pts.shape[0], pts.shape[1], -1)
+        contrib = np.einsum("npv,p,n->nv", val, wt, det)
+        if acc is None:
+            acc = np.zeros((n, val.shape[2]))
+        for j in range(val.shape[2]):
+            acc[:, j] += np.bincount(c, weights=contrib[:, j], minlength=n)
+        vol += np.bincount(c, weights=det * wt.sum(), minlength=n)
+    return acc, vol
+
+
+_FORKED = {}
+
+
+def _forked_range(r):
+    a = _FORKED
+    return _average_range(a["mesh"], a["func"], a["q"], r[0], r[1], a["chunk"])
 
 
 def _duffy_rule(dim, q):
@@ -70,31 +110,30 @@ def _duffy_rule(dim, q):
     return bary, wt
 
 
-def cell_average(mesh, func, q=4, nv=None, chunk=1 << 18):
+def cell_average(mesh, func, q=4, nv=None, chunk=1 << 16, workers=1):
     """Cell averages of func over every cell.
 
     func maps points [P, dim] to values [P] or [P, nv].
     Returns [n_cells] or [nv, n_cells] (variables first, the library's layout).
+    Half-faces are taken `chunk` at a time, so memory stays bounded on large meshes.
+    workers > 1 splits the cells over forked processes: only for callers that have not
+    initialised CUDA (a process forked after that can hang).
     """
-    dim = mesh["dim"]
     n_cells = mesh["cell_face_offsets"].shape[0] - 1
-    cid, verts = _simplices(mesh)
-    ref, wt = _duffy_rule(dim, q)
-    acc = None
-    vol = np.zeros(n_cells)
-    for s in range(0, cid.shape[0], chunk):
-        c = cid[s:s + chunk]
-        v = verts[s:s + chunk]
-        E = v[:, 1:, :] - v[:, :1, :]                         # edge vectors [n, dim, dim]
-        det = np.linalg.det(np.transpose(E, (0, 2, 1)))       # signed measure * dim!
-        pts = v[:, None, 0, :] + np.einsum("pk,nkd->npd", ref, E)
-        val = np.asarray(func(pts.reshape(-1, dim)), dtype=np.float64)
-        val = val.reshape(pts.shape[0], pts.shape[1], -1)
-        contrib = np.einsum("npv,p,n->nv", val, wt, det)
-        if acc is None:
-            acc = np.zeros((n_cells, val.shape[2]))
-        np.add.at(acc, c, contrib)
-        np.add.at(vol, c, det * wt.sum())
+    if workers <= 1 or n_cells < 4 * workers:
+        acc, vol = _average_range(mesh, func, q, 0, n_cells, chunk)
+    else:
+        import multiprocessing as mp
+        cuts = np.linspace(0, n_cells, 4 * workers + 1).astype(np.int64)
+        ranges = [(int(cuts[i]), int(cuts[i + 1])) for i in range(4 * workers)]
+        _FORKED.update(mesh=mesh, func=func, q=q, chunk=chunk)
+        try:
+            with mp.get_context("fork").Pool(workers) as pool:
+                parts = pool.map(_forked_range, ranges)
+        finally:
+            _FORKED.clear()
+        acc = np.concatenate([p[0] for p in parts])
+        vol = np.concatenate([p[1] for p in parts])
     avg = acc / vol[:, None]
     if avg.shape[1] == 1 and nv is None:
         return avg[:, 0]
@@ -111,14 +150,16 @@ def sine2d(p):
 
 def gaussian3d(p, sigma=0.1, centre=(0.5, 0.5, 0.5), images=1):
     """Gaussian pulse of width sigma on the unit periodic cube, periodised by
-    summing the images within `images` periods."""
-    out = np.zeros(p.shape[0])
-    rng = range(-images, images + 1)
-    for a in rng:
-        for b in rng:
-            for c in rng:
-                d = p - (np.asarray(centre) + np.array([a, b, c], dtype=np.float64))
-                out += np.exp(-0.5 * np.einsum("ij,ij->i", d, d) / sigma ** 2)
+    summing the images within `images` periods in each direction.  The pulse is a
+    product over the axes, so the sum over the (2 images + 1)^3 shifted copies is the
+    product of the three one-axis image sums."""
+    out = np.ones(p.shape[0])
+    for k in range(3):
+        s = np.zeros(p.shape[0])
+        for a in range(-images, images + 1):
+            d = p[:, k] - (centre[k] + a)
+            s += np.exp(-0.5 * d * d / sigma ** 2)
+        out *= s
     return out
 
 

@@ -46,12 +46,13 @@ def _lam_euler(prim_fn, dim, n=64):
     return float((np.abs(vel).sum(1) + np.sqrt(dim) * c).max())
 
 
-def workload(name, order=None, size=None, q=3, n_meshes=None):
-    """Returns dict(mesh, u0 [nv, n_cells] caller order, scheme kwargs, dt, steps, info)."""
+def workload(name, order=None, size=None, q=3, n_meshes=None, workers=1):
+    """Returns dict(mesh, u0 [nv, n_cells] caller order, scheme kwargs, dt, steps, info).
+    workers > 1 forks processes for the initial averages (only before CUDA is initialised)."""
     if name == "adv2d_tri64":
         n = size or 64
         m = meshes.tri_mesh(n, n, jitter=0.2, seed=SEED + 0)
-        u0 = fields.cell_average(m, fields.sine2d, q=q)[None]
+        u0 = fields.cell_average(m, fields.sine2d, q=q, workers=workers)[None]
         h = 1.0 / n
         dt = 0.5 * h / 2.0                        # CFL 0.5 on |a|_1 = 2
         return dict(mesh=m, u0=u0, dt=dt, steps=100,
@@ -63,7 +64,7 @@ def workload(name, order=None, size=None, q=3, n_meshes=None):
         k, r = STENCIL_OF_ORDER[order]
         m = meshes.tet_mesh(n, jitter=0.15, seed=SEED + 1)
         vf = lambda p: fields.isentropic_vortex(p, dim=3, images=0)
-        u0 = fields.cell_average(m, vf, q=q, nv=5)
+        u0 = fields.cell_average(m, vf, q=q, workers=workers, nv=5)
         h = 1.0 / n
         lam = _lam_euler(vf, 3)
         dt = 0.3 * (h / 4.0) / lam               # tetrahedra of the 5-split: width ~ h/4
@@ -75,7 +76,7 @@ def workload(name, order=None, size=None, q=3, n_meshes=None):
         order = order or 5
         k, r = STENCIL_OF_ORDER[order]
         m = meshes.hexprism_mesh(n, jitter=0.2, seed=SEED + 2)
-        u0 = fields.cell_average(m, fields.gaussian3d, q=q)[None]
+        u0 = fields.cell_average(m, fields.gaussian3d, q=q, workers=workers)[None]
         h = 1.0 / n
         dt = 0.3 * (h / 2.0) / 3.0
         return dict(mesh=m, u0=u0, dt=dt, steps=10,
@@ -86,7 +87,7 @@ def workload(name, order=None, size=None, q=3, n_meshes=None):
         m = meshes.tri_mesh(n, n, jitter=0.2, seed=SEED + 3, boundary="transmissive")
         rq = fields.riemann_quadrants(SEED + 3 + (order or 0))
         cons = lambda p: fields.prim_to_cons(rq(p))
-        u0 = fields.cell_average(m, cons, q=q, nv=4)
+        u0 = fields.cell_average(m, cons, q=q, workers=workers, nv=4)
         h = 1.0 / n
         lam = _lam_euler(cons, 2)
         dt = 0.3 * (h / 3.0) / lam
@@ -102,7 +103,7 @@ def workload(name, order=None, size=None, q=3, n_meshes=None):
             nn = max(4, int(round(np.sqrt(cells[i] / 2))))
             m = meshes.tri_mesh(nn, nn, jitter=0.2, seed=SEED + 4 + i)
             f = fields.fourier_modes(SEED + 4 + i)
-            u0 = fields.cell_average(m, f, q=q)[None]
+            u0 = fields.cell_average(m, f, q=q, workers=workers)[None]
             h = 1.0 / nn
             dt = 0.3 * (h / 3.0) / 2.0
             out.append(dict(mesh=m, u0=u0, dt=dt))
