@@ -36,6 +36,24 @@ template <class R> DOL_HD R cvt(double x) { return (R)x; }
 template <class R> DOL_HD R cvt(float x) { return (R)x; }
 template <class R> __device__ __forceinline__ R cvt(__nv_bfloat16 x) { return (R)__bfloat162float(x); }
 template <class T, class R> __device__ __forceinline__ T to_store(R x) { return (T)x; }
+
+// Reciprocal and square root of the bulk arithmetic.  FP64 keeps the correctly rounded
+// operations; FP32 uses the PTX approximate forms (rcp.approx: <= 1 ulp, sqrt.approx:
+// relative error ~2^-23), below the FP32 path's own rounding of the face values.
+template <class R> __device__ __forceinline__ R rcp_bulk(R x) { return (R)1 / x; }
+template <> __device__ __forceinline__ float rcp_bulk<float>(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+template <class R> __device__ __forceinline__ R sqrt_bulk(R x) { return sqrt(x); }
+template <> __device__ __forceinline__ float sqrt_bulk<float>(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 template <> __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16, float>(float x) { return __float2bfloat16_rn(x); }
 template <> __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16, double>(double x) { return __float2bfloat16_rn((float)x); }
 
@@ -186,18 +204,18 @@ __device__ __forceinline__ void dolinc_weights(int k, int r, R g, R *W0, R *W1)
 #pragma unroll
         for (int m = 0; m <= NS; ++m) W0[m] = W1[m] = (R)0;
         if (k == 2) {
-            const R iv = (R)1 / ((R)1 + g);
+            const R iv = rcp_bulk((R)1 + g);
             W0[0] = ((R)2 + g) * iv;
             W0[1] = iv;
             W1[0] = -iv;
         } else if (k == 3) {
-            const R iv = (R)1 / (((R)1 + g) * ((R)1 + g + g2));
+            const R iv = rcp_bulk(((R)1 + g) * ((R)1 + g + g2));
             W0[0] = g * ((R)1 + (R)3 * g + g2) * iv;
             W0[1] = g2 * iv;
             W1[0] = ((R)1 + g - g2) * iv;
         } else {
             const R g3 = g2 * g, g4 = g2 * g2;
-            const R iv = (R)1 / (((R)1 + g + g2) * ((R)1 + g + g2 + g3));
+            const R iv = rcp_bulk(((R)1 + g + g2) * ((R)1 + g + g2 + g3));
             W0[0] = (-g + g2 + (R)2 * g3 + (R)3 * g4 + g4 * g) * iv;
             W0[1] = g4 * iv;
             W1[0] = ((R)1 + (R)3 * g + (R)2 * g2 + g3 - g4) * iv;
@@ -336,7 +354,7 @@ template <int DIM, class R>
 __device__ __forceinline__ void euler_phys(R gam, const R *U, R sx, R sy, R sz, R *F, R &un, R &c2)
 {
     R rho = U[0];
-    R ir = (R)1 / rho;
+    R ir = rcp_bulk(rho);
     R vx = U[1] * ir, vy = U[2] * ir, vz = DIM == 3 ? U[3] * ir : (R)0;
     R ke = vx * U[1] + vy * U[2] + (DIM == 3 ? vz * U[3] : (R)0);
     R E = U[DIM + 1];
@@ -358,7 +376,7 @@ __device__ __forceinline__ void rusanov(R gam, const R *UL, const R *UR, R sx, R
     R FL[DIM + 2], FR[DIM + 2], unL, unR, c2L, c2R;
     euler_phys<DIM, R>(gam, UL, sx, sy, sz, FL, unL, c2L);
     euler_phys<DIM, R>(gam, UR, sx, sy, sz, FR, unR, c2R);
-    R a = fmax(fabs(unL) + sqrt(c2L) * smag, fabs(unR) + sqrt(c2R) * smag);
+    R a = fmax(fabs(unL) + sqrt_bulk(c2L) * smag, fabs(unR) + sqrt_bulk(c2R) * smag);
 #pragma unroll
     for (int v = 0; v < DIM + 2; ++v) F[v] = (R)0.5 * (FL[v] + FR[v]) - (R)0.5 * a * (UR[v] - UL[v]);
 }

@@ -302,7 +302,7 @@ __device__ __forceinline__ void face_states(const StageArgs &a, const Src &src, 
 #pragma unroll
                 for (int m = 0; m < 3; ++m) { q0[m] = (m & 1) ? -phN[v][m] : phN[v][m]; q1[m] = (m & 1) ? -phP[v][m] : phP[v][m]; }
                 if (!UPWIND_ONLY || want_left) UL[v] = eno3_value<NS, R>(g, phP[v], phN[v]);
-                if (!UPWIND_ONLY || !want_left) UR[v] = eno3_value<NS, R>((R)1 / g, q0, q1);
+                if (!UPWIND_ONLY || !want_left) UR[v] = eno3_value<NS, R>(rcp_bulk(g), q0, q1);
             }
             return;
         }
@@ -320,7 +320,7 @@ __device__ __forceinline__ void face_states(const StageArgs &a, const Src &src, 
     }
     if (!UPWIND_ONLY || !want_left) {
         // neighbour upwind: d -> -d, g -> 1/g, phi^(m) -> (-1)^m phi^(m)
-        dolinc_weights<NS, R>(a.k, a.r, (R)1 / g, W0, W1);
+        dolinc_weights<NS, R>(a.k, a.r, rcp_bulk(g), W0, W1);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             R s = (R)0;

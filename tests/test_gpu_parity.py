@@ -303,6 +303,27 @@ def test_c1_workload_100_steps_fp64():
     assert rel(got, want) < 1e-10
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp32_bf16"])
+def test_c1_workload_100_steps_below_fp64(prec):
+    """The same 100 steps in the increment form of the step (bulk precision below FP64,
+    one FP64 add per step): each stage's increment carries the bulk precision's
+    relative rounding (~1e-7 in FP32), which 300 stages accumulate to a few 1e-6 of the
+    field.  USR3 reads orders <= 1, so BF16 storage of order 2 does not reach the faces."""
+    w = synth.workload("adv2d_tri64", size=32)
+    m = w["mesh"]
+    O = oracle.Oracle(m)
+    M = gpu_mesh(m)
+    sch = dg.Scheme(precision=prec, **w["scheme"])
+    ws = dg.workspace(M, sch)
+    u = to_dev(M, w["u0"])
+    for _ in range(w["steps"]):
+        dg.dolinc_rk_step(M, sch, w["dt"], u, ws)
+    dg.dolinc_sync_status(M, ws)
+    got = M.from_lib(u.cpu().numpy())
+    want = O.run(w["u0"], oracle.Scheme(**w["scheme"]), w["dt"], w["steps"])
+    assert rel(got, want) < 2e-5
+
+
 @pytest.mark.parametrize("renumber", ["none", "morton"])
 def test_renumbering_does_not_change_results(renumber):
     m, O = mesh("tet")
