@@ -229,7 +229,13 @@ dolinc_status dolinc_rk_step_noalloc(dolinc_mesh *mesh, const dolinc_scheme *sch
  * stage kernels of this mesh and scheme on the given state (u_dev, FP64 [v][cell])
  * for 1, 4 and 8 lanes per cell and blocks of 64, 128, 256 threads, and for tiled
  * launches (0 lanes: one thread per cell, the block's 64/128/256 cells and the faces
- * they own staged in shared memory), keeps the fastest shape in the mesh handle for
+ * they own staged in shared memory), and for the differential passes also the
+ * persistent pipelined launch (-1 / -4 lanes: 1 / 4 lanes per cell, 128 or 256
+ * threads per CTA, one CTA per resident slot, each CTA walking over tiles of cells
+ * whose records and geometry arrive by bulk asynchronous copies into two
+ * shared-memory buffers while the previous tile is computed; a bounded barrier wait
+ * that gives up is reported as DOLINC_ERR_DEVICE_TIMEOUT by dolinc_sync_status),
+ * keeps the fastest shape in the mesh handle for
  * every later call with this scheme, and appends it to the text file cache_path (one
  * line per GPU name and mesh/scheme key; may be NULL).  A key already in the file is
  * reused without timing.  Synchronous; clears the workspace status word.  Results:
@@ -243,7 +249,8 @@ dolinc_status dolinc_autotune(dolinc_mesh *mesh, const dolinc_scheme *scheme, co
                               size_t ws_bytes, const char *cache_path, dolinc_stream stream, dolinc_tuning *out);
 /* Sets the launch shape used for this mesh and scheme (lanes per cell 1, 4 or 8 with a
  * block of 32..256 threads, a multiple of 32; or lanes 0, tiled, with a block of 64,
- * 128 or 256), e.g. a shape read back from an autotuning cache. */
+ * 128 or 256; differential passes also lanes -1 or -4, pipelined, with 128 or 256),
+ * e.g. a shape read back from an autotuning cache. */
 dolinc_status dolinc_set_tuning(dolinc_mesh *mesh, const dolinc_scheme *scheme, const dolinc_tuning *tuning);
 
 /* ---------------------------------------------------------------- troubled cells

@@ -304,7 +304,10 @@ void run_diffs(dolinc_mesh *m, const PathFns *p, void *ws, const WsLayout &L, si
                const Tune &t, cudaStream_t st)
 {
     for (int mm = 1; mm <= n; ++mm)
-        timed(m, mm, st, [&] { p->diff(m->d, mm, B(ws, mm == 1 ? o0off : L.ord[mm - 1]), B(ws, L.ord[mm]), t, st); });
+        timed(m, mm, st, [&] {
+            p->diff(m->d, mm, B(ws, mm == 1 ? o0off : L.ord[mm - 1]), B(ws, L.ord[mm]), t,
+                    reinterpret_cast<unsigned *>(B(ws, L.status)), st);
+        });
 }
 
 dolinc_status launch_check()
@@ -412,6 +415,7 @@ dolinc_status upload_mesh(dolinc_mesh *m)
     d.n_faces = (int)nf;
     d.n_slots = (int)ns;
     for (int ti = 0; ti < 3; ++ti) d.max_tile_faces[ti] = mtf[ti];
+    d.max_slots = m->max_faces;
     if ((st = upload(m, off, &d.off)) || (st = upload(m, slot2, &d.slot2)) || (st = upload(m, sk64, &d.slotk64)) ||
         (st = upload(m, sk32, &d.slotk32)) || (st = upload(m, ck64, &d.cellk64)) ||
         (st = upload(m, ck32, &d.cellk32)) || (st = upload(m, f64, &d.face64)) || (st = upload(m, f32, &d.face32)) ||
@@ -517,7 +521,9 @@ dolinc_status dolinc_differentials(dolinc_mesh *m, const dolinc_scheme *s, const
     const void *prev = B(ws, L.o0[0]);
     for (int mm = 1; mm <= order; ++mm) {
         const int b = elem_bytes(s->precision, mm), sd = stride_h(m->h.dim, s->nv, mm, s->precision);
-        timed(m, mm, cs, [&] { p->diff(m->d, mm, prev, B(diff, o), tune_for(m, s), cs); });
+        timed(m, mm, cs, [&] {
+            p->diff(m->d, mm, prev, B(diff, o), tune_for(m, s), reinterpret_cast<unsigned *>(B(ws, L.status)), cs);
+        });
         prev = B(diff, o);
         o += al256((size_t)m->h.n_cells * sd * b);
     }
@@ -718,17 +724,23 @@ dolinc_status dolinc_autotune(dolinc_mesh *m, const dolinc_scheme *s, const doub
             cudaEventElapsedTime(&ms, e0, e1);
             return ms / 5.0;
         };
-        const int lpcs[4] = {1, 4, 8, 0}, blocks[3] = {64, 128, 256};
+        // diff shapes: lanes 1/4/8, tiled (0), persistent pipelined (-1/-4); stage shapes:
+        // lanes 1/4/8 and tiled
+        const int lpcs[6] = {1, 4, 8, 0, -1, -4}, blocks[3] = {64, 128, 256};
         double bd = 1e30, bs = 1e30;
-        for (int li = 0; li < 4; ++li)
+        for (int li = 0; li < 6; ++li)
             for (int bi = 0; bi < 3; ++bi) {
+                if (lpcs[li] < 0 && blocks[bi] < 128) continue;
                 Tune t;
                 t.diff_lpc = t.stage_lpc = lpcs[li];
                 t.diff_block = t.stage_block = blocks[bi];
                 double td = time_it([&] {
                     for (int mm = 1; mm <= s->n_diff; ++mm)
-                        p->diff(m->d, mm, B(ws, mm == 1 ? L.o0[0] : L.ord[mm - 1]), B(ws, L.ord[mm]), t, cs);
+                        p->diff(m->d, mm, B(ws, mm == 1 ? L.o0[0] : L.ord[mm - 1]), B(ws, L.ord[mm]), t,
+                                reinterpret_cast<unsigned *>(B(ws, L.status)), cs);
                 });
+                if (td < bd) bd = td, best.diff_lpc = t.diff_lpc, best.diff_block = t.diff_block;
+                if (lpcs[li] < 0) continue;
                 // the stage as rk_step runs it (middle stage), on scratch outputs
                 StageArgs a = base_args(m, s, ws, L, L.o0[0]);
                 double *scratch = reinterpret_cast<double *>(B(ws, L.ustage));
@@ -747,7 +759,6 @@ dolinc_status dolinc_autotune(dolinc_mesh *m, const dolinc_scheme *s, const doub
                     a.o0_next = B(ws, L.o0[1]);
                 }
                 double tsg = time_it([&] { p->stage(m->d, a, t, cs); });
-                if (td < bd) bd = td, best.diff_lpc = t.diff_lpc, best.diff_block = t.diff_block;
                 if (tsg < bs) bs = tsg, best.stage_lpc = t.stage_lpc, best.stage_block = t.stage_block;
             }
         cudaEventDestroy(e0);
@@ -1238,9 +1249,11 @@ dolinc_status dolinc_set_tuning(dolinc_mesh *m, const dolinc_scheme *s, const do
         if (l == 0) return b == 64 || b == 128 || b == 256;
         return (l == 1 || l == 4 || l == 8) && b >= 32 && b <= 256 && b % 32 == 0;
     };
-    if (!ok(t->diff_lanes, t->diff_block) || !ok(t->stage_lanes, t->stage_block))
+    const bool diff_pipe = (t->diff_lanes == -1 || t->diff_lanes == -4) && (t->diff_block == 128 || t->diff_block == 256);
+    if (!(ok(t->diff_lanes, t->diff_block) || diff_pipe) || !ok(t->stage_lanes, t->stage_block))
         return fail(DOLINC_ERR_INVALID_ARG,
-                    "lanes 1, 4 or 8 with blocks a multiple of 32 in 32..256, or lanes 0 (tiled) with 64/128/256");
+                    "lanes 1, 4 or 8 with blocks a multiple of 32 in 32..256, or lanes 0 (tiled) with 64/128/256; "
+                    "differential passes also lanes -1 / -4 (persistent pipelined) with 128/256");
     Tune x;
     x.diff_lpc = t->diff_lanes;
     x.diff_block = t->diff_block;

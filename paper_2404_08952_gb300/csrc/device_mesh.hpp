@@ -20,6 +20,7 @@ struct DevMesh {
     const int8_t *face_flip;     // [n_faces] 1 if the caller orientation is reversed
     const int32_t *fown;         // [n_cells+1] first internal face owned by each cell
     int max_tile_faces[3];       // most faces owned by a tile of 64 / 128 / 256 cells
+    int max_slots;               // most slots of one cell
 };
 
 }  // namespace dol

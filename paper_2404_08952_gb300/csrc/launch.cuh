@@ -1,18 +1,42 @@
 // Host launchers of the templated stage kernels and the table the C ABI dispatches on.
 #pragma once
-#include "kernels.cuh"
+#include <map>
+#include <mutex>
+#include "pipe.cuh"
 
 namespace dol {
 
 // Launch shape of the gather kernels: lanes per cell (1, 4 or 8; 0 = one thread per
-// cell with the block's cells staged in shared memory, tile = block) and block size.
+// cell with the block's cells staged in shared memory, tile = block; -1 / -4 = the
+// persistent pipelined kernel with 1 / 4 lanes per cell, block threads per CTA) and
+// block size.
 struct Tune {
     int diff_lpc = 4, diff_block = 256, stage_lpc = 4, stage_block = 128;
 };
 
+// Grid of a persistent kernel: resident CTAs per SM x SMs (cached per kernel and
+// shared-memory size on the current device).
+inline int persistent_grid(const void *kernel, int threads, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void *, size_t>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_tuple(dev, kernel, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+    const int grid = std::max(1, sms * std::max(per, 1));
+    cache[key] = grid;
+    return grid;
+}
+
 struct PathFns {
     void (*pack)(const DevMesh &, const double *, void *, cudaStream_t);
-    void (*diff)(const DevMesh &, int M, const void *, void *, const Tune &, cudaStream_t);
+    void (*diff)(const DevMesh &, int M, const void *, void *, const Tune &, unsigned *, cudaStream_t);
     void (*stage)(const DevMesh &, const StageArgs &, const Tune &, cudaStream_t);
     void (*faces)(const DevMesh &, const StageArgs &, double *, double *, cudaStream_t);
 };
@@ -84,8 +108,44 @@ template <int DIM, int NV, int NS, int PREC> struct Path {
         }
         k_stage_tile<DIM, NV, NS, PREC, TILE><<<nblk(m.n_cells, TILE), TILE, sm, s>>>(m, a);
     }
-    static void diff(const DevMesh &m, int M, const void *in, void *out, const Tune &t, cudaStream_t s)
+    template <int LPC, int NT>
+    static void diff_p(const DevMesh &m, int M, const void *in, void *out, unsigned *status, cudaStream_t s)
     {
+        auto go = [&](auto mc) {
+            constexpr int MM = decltype(mc)::value;
+            using L = DiffPipeLayout<DIM, NV, MM, PREC, NT / LPC>;
+            const size_t bytes = L::smem_bytes(m.max_slots);
+            if (bytes > kMaxSmem) {                 // too large to stage: one thread per cell instead
+                k_diff<DIM, NV, MM, PREC, 1><<<nblk(m.n_cells, NT), NT, 0, s>>>(m, in, out);
+                return;
+            }
+            auto kern = k_diff_pipe<DIM, NV, MM, PREC, LPC, NT>;
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+                attr = true;
+            }
+            const int tiles = nblk(m.n_cells, NT / LPC);
+            const int grid = std::min(tiles, persistent_grid((const void *)kern, NT, bytes));
+            kern<<<grid, NT, bytes, s>>>(m, in, out, status, m.max_slots);
+        };
+        switch (M) {
+        case 1: go(std::integral_constant<int, 1>{}); break;
+        case 2: go(std::integral_constant<int, 2>{}); break;
+        case 3: go(std::integral_constant<int, 3>{}); break;
+        case 4: go(std::integral_constant<int, 4>{}); break;
+        default: break;
+        }
+    }
+    static void diff(const DevMesh &m, int M, const void *in, void *out, const Tune &t, unsigned *status,
+                     cudaStream_t s)
+    {
+        if (t.diff_lpc < 0) {
+            const bool big = t.diff_block >= 256;
+            if (t.diff_lpc == -4) big ? diff_p<4, 256>(m, M, in, out, status, s) : diff_p<4, 128>(m, M, in, out, status, s);
+            else big ? diff_p<1, 256>(m, M, in, out, status, s) : diff_p<1, 128>(m, M, in, out, status, s);
+            return;
+        }
         if (t.diff_lpc == 0) {
             switch (t.diff_block) {
             case 64: diff_t<64>(m, M, in, out, s); break;

@@ -1,0 +1,180 @@
+// Persistent, pipelined gather kernels for sm_103a.
+//
+// A CTA walks over tiles of consecutive (Morton-ordered) cells.  For each tile one
+// elected thread issues bulk asynchronous copies (cp.async.bulk, the TMA 1D form)
+// of the tile's contiguous arrays -- its input records, per-cell and per-slot
+// geometry -- into one of two shared-memory buffers, completing on an mbarrier;
+// while the CTA computes tile j from one buffer, tile j+1 is already in flight into
+// the other.  Neighbours inside the tile are read from shared memory, the tile's
+// halo from global memory.  The arithmetic and its order are those of the
+// non-pipelined kernels, so results are bit-identical for the same lanes per cell.
+//
+// Every mbarrier wait is bounded; a wait that gives up sets status bit 1 (reported
+// as DOLINC_ERR_DEVICE_TIMEOUT), waits (bounded again) for the CTA's other copy in
+// flight and leaves the kernel without writing the tile.
+#pragma once
+#include "kernels.cuh"
+
+namespace dol {
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// The calling thread arrives once and announces `bytes` of asynchronous transfer.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Bounded wait for phase `parity` of the barrier; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned limit)
+{
+    const unsigned a = smem_u32(bar);
+    for (unsigned it = 0; it < limit; ++it) {
+        unsigned ok;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(ok)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+constexpr unsigned kPipeWaitLimit = 1u << 22;   // try_wait polls before a wait gives up
+
+DOL_HD constexpr unsigned al128(unsigned b) { return (b + 127u) & ~127u; }
+
+// ------------------------------------------------------------------ differential pass
+// Shared-memory buffer of one tile: input records, cell geometry, slot geometry.
+template <int DIM, int NV, int M, int PREC, int TC> struct DiffPipeLayout {
+    using R = typename PrecT<PREC>::R;
+    using TI = typename OrdT<PREC, M - 1>::T;
+    static constexpr unsigned RB = ord_stride<DIM, NV, M - 1, PREC>() * (unsigned)sizeof(TI);
+    static constexpr unsigned rec_bytes = al128(TC * RB);
+    static constexpr unsigned cell_bytes = al128(TC * 4u * (unsigned)sizeof(R));
+    static DOL_HD unsigned slot_bytes(int max_faces) { return al128((unsigned)(TC * max_faces) * 4u * (unsigned)sizeof(R)); }
+    static DOL_HD unsigned buf_bytes(int max_faces) { return rec_bytes + cell_bytes + slot_bytes(max_faces); }
+    static DOL_HD unsigned smem_bytes(int max_faces) { return 128u + 2u * buf_bytes(max_faces); }
+};
+
+template <int DIM, int NV, int M, int PREC, int LPC, int NT>
+__global__ void __launch_bounds__(NT) k_diff_pipe(DevMesh mesh, const void *__restrict__ in_v, void *__restrict__ out_v,
+                                                 unsigned *status, int max_faces)
+{
+    using R = typename PrecT<PREC>::R;
+    using TI = typename OrdT<PREC, M - 1>::T;
+    using TO = typename OrdT<PREC, M>::T;
+    constexpr int TC = NT / LPC;
+    using L = DiffPipeLayout<DIM, NV, M, PREC, TC>;
+    constexpr int CI = ncoef(DIM, M - 1), CO = ncoef(DIM, M);
+    constexpr int SI = ord_stride<DIM, NV, M - 1, PREC>(), SO = ord_stride<DIM, NV, M, PREC>();
+    const TI *in = static_cast<const TI *>(in_v);
+    TO *out = static_cast<TO *>(out_v);
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
+    const unsigned bb = L::buf_bytes(max_faces);
+    const int n_tiles = (mesh.n_cells + TC - 1) / TC;
+    if ((int)blockIdx.x >= n_tiles) return;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    // producer: tile -> buffer b
+    auto issue = [&](int tile, int b) {
+        const int t0 = tile * TC, nt = min(TC, mesh.n_cells - t0);
+        unsigned char *buf = sm + 128 + b * bb;
+        const unsigned rb = ((unsigned)nt * L::RB) & ~15u;
+        const unsigned cb = (unsigned)nt * 4u * (unsigned)sizeof(R);
+        const int s_lo = __ldg(mesh.off + t0), s_hi = __ldg(mesh.off + t0 + nt);
+        const unsigned sb = (unsigned)(s_hi - s_lo) * 4u * (unsigned)sizeof(R);
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar + b, rb + cb + sb);
+        if (rb) bulk_g2s(buf, reinterpret_cast<const unsigned char *>(in) + (long long)t0 * L::RB, rb, bar + b);
+        bulk_g2s(buf + L::rec_bytes, Geo<R>::cellk(mesh) + 4ll * t0, cb, bar + b);
+        if (sb) bulk_g2s(buf + L::rec_bytes + L::cell_bytes, Geo<R>::slotk(mesh) + 4ll * s_lo, sb, bar + b);
+    };
+
+    if (threadIdx.x == 0) issue(blockIdx.x, 0);
+    const int l = threadIdx.x % LPC, ci = threadIdx.x / LPC;
+    for (int j = 0, tile = blockIdx.x; tile < n_tiles; ++j, tile += gridDim.x) {
+        const int b = j & 1;
+        const int next = tile + gridDim.x;
+        if (threadIdx.x == 0 && next < n_tiles) issue(next, b ^ 1);
+        if (!mbar_wait(bar + b, (unsigned)(j >> 1) & 1u, kPipeWaitLimit)) {
+            if (threadIdx.x == 0) atomicOr(status, 2u);
+            if (next < n_tiles) mbar_wait(bar + (b ^ 1), (unsigned)((j + 1) >> 1) & 1u, kPipeWaitLimit);
+            return;
+        }
+        const unsigned char *buf = sm + 128 + b * bb;
+        const TI *trec = reinterpret_cast<const TI *>(buf);
+        const R *tcell = reinterpret_cast<const R *>(buf + L::rec_bytes);
+        const R *tslot = reinterpret_cast<const R *>(buf + L::rec_bytes + L::cell_bytes);
+        const int t0 = tile * TC, nt = min(TC, mesh.n_cells - t0);
+        const int n_staged = (int)((((unsigned)nt * L::RB) & ~15u) / L::RB);   // records fully in the buffer
+        const int c = t0 + ci;
+        const bool valid = ci < nt;
+        constexpr int VO = 16 / (int)sizeof(TO);
+        constexpr int P = (LPC == 1) ? NV * CO : round_up(SO, LPC * VO);
+        R acc[P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) acc[i] = (R)0;
+        if (valid) {
+            R x[NV * CI];
+            const int s_base = __ldg(mesh.off + t0);
+            if (l == 0) {
+                R wx, wy, wz, iv;
+                ld4<R, false>(tcell + 4 * ci, wx, wy, wz, iv);
+                if (ci < n_staged) load_rec<TI, NV * CI, SI, R, false>(trec, ci, x);
+                else load_rec<TI, NV * CI, SI, R>(in, c, x);
+                poly_mul_acc<DIM, NV, M, R>(acc, x, wx, wy, wz);
+            }
+            const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+            for (int s = s0 + l; s < s1; s += LPC) {
+                R kx, ky, kz, kb;
+                ld4<R, false>(tslot + 4 * (s - s_base), kx, ky, kz, kb);
+                const int nb = Geo<R>::nb_of(kb);
+                const unsigned i = (unsigned)(nb - t0);
+                if (i < (unsigned)n_staged) load_rec<TI, NV * CI, SI, R, false>(trec, i, x);
+                else load_rec<TI, NV * CI, SI, R>(in, nb, x);
+                poly_mul_acc<DIM, NV, M, R>(acc, x, kx, ky, kz);
+            }
+        }
+        if constexpr (LPC == 1) {
+            if (valid) store_rec<TO, NV * CO, SO, R>(out, c, acc);
+        } else {
+            group_reduce_scatter<P, LPC, R>(acc, l);
+            if (valid) {
+                constexpr int B = P / LPC;
+                const int e0 = l * B;
+                TO *rec = out + (long long)c * SO;
+#pragma unroll
+                for (int i = 0; i < B; ++i)
+                    if (e0 + i < NV * CO) rec[e0 + i] = to_store<TO, R>(acc[i]);
+            }
+        }
+        __syncthreads();   // buffer b is free for tile j+2
+    }
+}
+
+}  // namespace dol
