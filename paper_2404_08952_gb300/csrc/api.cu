@@ -360,7 +360,7 @@ dolinc_status upload_mesh(dolinc_mesh *m)
     cudaGetDevice(&m->device);
     const HostMesh &h = m->h;
     const int64_t nc = h.n_cells, nf = h.n_faces, ns = h.n_slots;
-    std::vector<int2> slot2(ns);
+    std::vector<int2> slot2(ns + 2, make_int2(0, 0));   // two spare entries: bulk copies round to 16 bytes
     std::vector<double> sk64(4 * ns), ck64(4 * nc), f64(8 * nf);
     std::vector<float> sk32(4 * ns), ck32(4 * nc), f32(8 * nf);
     for (int64_t s = 0; s < ns; ++s) {
@@ -724,23 +724,27 @@ dolinc_status dolinc_autotune(dolinc_mesh *m, const dolinc_scheme *s, const doub
             cudaEventElapsedTime(&ms, e0, e1);
             return ms / 5.0;
         };
-        // diff shapes: lanes 1/4/8, tiled (0), persistent pipelined (-1/-4); stage shapes:
-        // lanes 1/4/8 and tiled
+        // diff shapes: lanes 1/4/8, tiled (0), persistent pipelined (-1/-4 with 128/256
+        // threads); stage shapes: lanes 1/4/8, tiled, persistent pipelined (-1 with tiles
+        // of 64/128 cells)
         const int lpcs[6] = {1, 4, 8, 0, -1, -4}, blocks[3] = {64, 128, 256};
         double bd = 1e30, bs = 1e30;
         for (int li = 0; li < 6; ++li)
             for (int bi = 0; bi < 3; ++bi) {
-                if (lpcs[li] < 0 && blocks[bi] < 128) continue;
                 Tune t;
                 t.diff_lpc = t.stage_lpc = lpcs[li];
                 t.diff_block = t.stage_block = blocks[bi];
-                double td = time_it([&] {
-                    for (int mm = 1; mm <= s->n_diff; ++mm)
-                        p->diff(m->d, mm, B(ws, mm == 1 ? L.o0[0] : L.ord[mm - 1]), B(ws, L.ord[mm]), t,
-                                reinterpret_cast<unsigned *>(B(ws, L.status)), cs);
-                });
-                if (td < bd) bd = td, best.diff_lpc = t.diff_lpc, best.diff_block = t.diff_block;
-                if (lpcs[li] < 0) continue;
+                const bool diff_ok = lpcs[li] >= 0 || blocks[bi] >= 128;
+                const bool stage_ok = lpcs[li] >= -1 && (lpcs[li] >= 0 || blocks[bi] <= 128);
+                if (diff_ok) {
+                    double td = time_it([&] {
+                        for (int mm = 1; mm <= s->n_diff; ++mm)
+                            p->diff(m->d, mm, B(ws, mm == 1 ? L.o0[0] : L.ord[mm - 1]), B(ws, L.ord[mm]), t,
+                                    reinterpret_cast<unsigned *>(B(ws, L.status)), cs);
+                    });
+                    if (td < bd) bd = td, best.diff_lpc = t.diff_lpc, best.diff_block = t.diff_block;
+                }
+                if (!stage_ok) continue;
                 // the stage as rk_step runs it (middle stage), on scratch outputs
                 StageArgs a = base_args(m, s, ws, L, L.o0[0]);
                 double *scratch = reinterpret_cast<double *>(B(ws, L.ustage));
@@ -1250,10 +1254,12 @@ dolinc_status dolinc_set_tuning(dolinc_mesh *m, const dolinc_scheme *s, const do
         return (l == 1 || l == 4 || l == 8) && b >= 32 && b <= 256 && b % 32 == 0;
     };
     const bool diff_pipe = (t->diff_lanes == -1 || t->diff_lanes == -4) && (t->diff_block == 128 || t->diff_block == 256);
-    if (!(ok(t->diff_lanes, t->diff_block) || diff_pipe) || !ok(t->stage_lanes, t->stage_block))
+    const bool stage_pipe = t->stage_lanes == -1 && (t->stage_block == 64 || t->stage_block == 128);
+    if (!(ok(t->diff_lanes, t->diff_block) || diff_pipe) || !(ok(t->stage_lanes, t->stage_block) || stage_pipe))
         return fail(DOLINC_ERR_INVALID_ARG,
                     "lanes 1, 4 or 8 with blocks a multiple of 32 in 32..256, or lanes 0 (tiled) with 64/128/256; "
-                    "differential passes also lanes -1 / -4 (persistent pipelined) with 128/256");
+                    "differential passes also lanes -1 / -4 (persistent pipelined) with 128/256, the stage "
+                    "lanes -1 (persistent pipelined) with tiles of 64/128 cells");
     Tune x;
     x.diff_lpc = t->diff_lanes;
     x.diff_block = t->diff_block;

@@ -351,15 +351,14 @@ __device__ __forceinline__ void phys_flux(const StageArgs &a, const R *U, const 
     }
 }
 
-// Numerical flux of the face in slot s of cell c, signed for c (+ into, - out of c).
+// Numerical flux of the face of slot (nb, word) of cell c in the face's canonical
+// owner -> neighbour orientation (a boundary slot: the flux of c's own state).  The
+// operands and their order depend only on the face, not on which cell asks.
 template <int DIM, int NV, int NS, int PREC, class Src>
-__device__ __forceinline__ void slot_flux(const DevMesh &mesh, const StageArgs &a, const Src &src, int c, int s,
-                                          bool own_flag, typename PrecT<PREC>::R *F)
+__device__ __forceinline__ void canon_flux(const StageArgs &a, const Src &src, int c, int nb, unsigned word,
+                                           bool own_flag, typename PrecT<PREC>::R *F)
 {
     using R = typename PrecT<PREC>::R;
-    const int2 sw = __ldg(mesh.slot2 + s);
-    const int nb = sw.x;
-    const unsigned word = (unsigned)sw.y;
     const int f = (int)(word >> 2);
     const int side = word & 1;
     R fr[8];
@@ -396,7 +395,16 @@ __device__ __forceinline__ void slot_flux(const DevMesh &mesh, const StageArgs &
             rusanov<DIM, R>((R)a.gamma, UL, UR, fr[4], fr[5], fr[6], fr[7], F);
         }
     }
-    if (!side) {
+}
+
+// Numerical flux of the face in slot s of cell c, signed for c (+ into, - out of c).
+template <int DIM, int NV, int NS, int PREC, class Src>
+__device__ __forceinline__ void slot_flux(const DevMesh &mesh, const StageArgs &a, const Src &src, int c, int s,
+                                          bool own_flag, typename PrecT<PREC>::R *F)
+{
+    const int2 sw = __ldg(mesh.slot2 + s);
+    canon_flux<DIM, NV, NS, PREC>(a, src, c, sw.x, (unsigned)sw.y, own_flag, F);
+    if (!(sw.y & 1)) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] = -F[v];
     }
@@ -517,6 +525,43 @@ __global__ void __launch_bounds__(256, (PREC != PREC_F64 && NS <= 1) ? 4 : 1) k_
     if (bad) atomicOr(a.status, 1u);
 }
 
+// Residual R_c = res / V_c and the stage output of one cell (one thread per cell):
+// mode 0 the FP64 residual, mode 1 the FP64 stage value (+ next order-0 record),
+// mode 2 the increment form.
+template <int DIM, int NV, int PREC>
+__device__ __forceinline__ void cell_epilogue(const DevMesh &mesh, const StageArgs &a, int c,
+                                              const typename PrecT<PREC>::R *res)
+{
+    using R = typename PrecT<PREC>::R;
+    R iv, dummy0, dummy1, dummy2;
+    ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, dummy0, dummy1, dummy2, iv);
+    const long long n = mesh.n_cells;
+    bool bad = false;
+    using T0 = typename PrecT<PREC>::T0;
+    T0 *nxt = static_cast<T0 *>(a.o0_next);
+    constexpr int S0 = ord_stride<DIM, NV, 0, PREC>();
+    R nv_out[NV];
+    const R dtr = (R)a.dt;
+    if constexpr (PREC != PREC_F64) {
+        if (a.mode == 2) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) bad |= incr_update<R, T0, S0>(a, c, v, n, res[v] * iv * dtr, nxt);
+            if (bad) atomicOr(a.status, 1u);
+            return;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const R r = res[v] * iv;
+        const double o = a.mode == 0 ? (double)r : stage_update(a, v * n + c, r * dtr);
+        nv_out[v] = (R)o;
+        a.out[v * n + c] = o;
+        bad |= nonfinite64(o);
+    }
+    if (a.mode != 0 && nxt) store_rec<T0, NV, S0, R>(nxt, c, nv_out);
+    if (bad) atomicOr(a.status, 1u);
+}
+
 // ------------------------------------------------------------------ tiled variants
 // The block's TILE consecutive (Morton-ordered) cells stage their records, and the
 // faces they own, in shared memory with asynchronous copies; neighbours inside the
@@ -590,33 +635,7 @@ __global__ void __launch_bounds__(TILE) k_stage_tile(DevMesh mesh, StageArgs a)
 #pragma unroll
         for (int v = 0; v < NV; ++v) res[v] += F[v];
     }
-    R iv, dummy0, dummy1, dummy2;
-    ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, dummy0, dummy1, dummy2, iv);
-    const long long n = mesh.n_cells;
-    bool bad = false;
-    using T0 = typename PrecT<PREC>::T0;
-    T0 *nxt = static_cast<T0 *>(a.o0_next);
-    constexpr int S0 = ord_stride<DIM, NV, 0, PREC>();
-    R nv_out[NV];
-    const R dtr = (R)a.dt;
-    if constexpr (PREC != PREC_F64) {
-        if (a.mode == 2) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) bad |= incr_update<R, T0, S0>(a, c, v, n, res[v] * iv * dtr, nxt);
-            if (bad) atomicOr(a.status, 1u);
-            return;
-        }
-    }
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        const R r = res[v] * iv;
-        const double o = a.mode == 0 ? (double)r : stage_update(a, v * n + c, r * dtr);
-        nv_out[v] = (R)o;
-        a.out[v * n + c] = o;
-        bad |= nonfinite64(o);
-    }
-    if (a.mode != 0 && nxt) store_rec<T0, NV, S0, R>(nxt, c, nv_out);
-    if (bad) atomicOr(a.status, 1u);
+    cell_epilogue<DIM, NV, PREC>(mesh, a, c, res);
 }
 
 template <int DIM, int NV, int M, int PREC, int TILE>

@@ -160,8 +160,32 @@ template <int DIM, int NV, int NS, int PREC> struct Path {
         default: diff_l<1>(m, M, in, out, t.diff_block, s); break;
         }
     }
+    template <int TC> static void stage_p(const DevMesh &m, const StageArgs &a, cudaStream_t s)
+    {
+        constexpr int NT = 256;
+        using L = StagePipeLayout<DIM, NV, NS, PREC, TC>;
+        const int max_tf = m.max_tile_faces[TC == 64 ? 0 : 1];
+        const size_t bytes = L::smem_bytes(m.max_slots, max_tf);
+        if (bytes > kMaxSmem) {                     // too large to stage: one thread per cell instead
+            k_stage<DIM, NV, NS, PREC, 1><<<nblk(m.n_cells, 128), 128, 0, s>>>(m, a);
+            return;
+        }
+        auto kern = k_stage_pipe<DIM, NV, NS, PREC, TC, NT>;
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+            attr = true;
+        }
+        const int grid = std::min(nblk(m.n_cells, TC), persistent_grid((const void *)kern, NT, bytes));
+        kern<<<grid, NT, bytes, s>>>(m, a, max_tf);
+    }
     static void stage(const DevMesh &m, const StageArgs &a, const Tune &t, cudaStream_t s)
     {
+        if (t.stage_lpc < 0) {
+            if (t.stage_block >= 128) stage_p<128>(m, a, s);
+            else stage_p<64>(m, a, s);
+            return;
+        }
         if (t.stage_lpc == 0) {
             switch (t.stage_block) {
             case 64: stage_t<64>(m, a, s); break;

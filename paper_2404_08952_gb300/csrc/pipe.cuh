@@ -121,8 +121,10 @@ __global__ void __launch_bounds__(NT) k_diff_pipe(DevMesh mesh, const void *__re
         const int b = j & 1;
         const int next = tile + gridDim.x;
         if (threadIdx.x == 0 && next < n_tiles) issue(next, b ^ 1);
-        if (!mbar_wait(bar + b, (unsigned)(j >> 1) & 1u, kPipeWaitLimit)) {
+        const bool ok = mbar_wait(bar + b, (unsigned)(j >> 1) & 1u, kPipeWaitLimit);
+        if (!__syncthreads_and(ok)) {
             if (threadIdx.x == 0) atomicOr(status, 2u);
+            if (!ok) mbar_wait(bar + b, (unsigned)(j >> 1) & 1u, kPipeWaitLimit);
             if (next < n_tiles) mbar_wait(bar + (b ^ 1), (unsigned)((j + 1) >> 1) & 1u, kPipeWaitLimit);
             return;
         }
@@ -174,6 +176,171 @@ __global__ void __launch_bounds__(NT) k_diff_pipe(DevMesh mesh, const void *__re
             }
         }
         __syncthreads();   // buffer b is free for tile j+2
+    }
+}
+
+// ------------------------------------------------------------------ fused stage
+// Tile-local face-centric stage.  Phase A evaluates each face the tile needs once:
+// the faces its cells own (flux kept per face) and the faces whose owner lies in an
+// earlier tile or outside the mesh (boundary slots; flux kept per slot); a face
+// between two tiles is thus evaluated by both tiles, with identical operands in the
+// canonical orientation, so the two results are bit-identical.  Phase B sums each
+// cell's signed fluxes in slot order (the order of the one-thread-per-cell kernel,
+// hence bit-identical results) and applies the stage epilogue.
+template <int DIM, int NV, int NS, int PREC, int TC> struct StagePipeLayout {
+    using R = typename PrecT<PREC>::R;
+    template <int M> static DOL_HD constexpr unsigned RB()
+    {
+        return ord_stride<DIM, NV, M, PREC>() * (unsigned)sizeof(typename OrdT<PREC, M>::T);
+    }
+    // record bytes of order m (m = 0..4)
+    static DOL_HD constexpr unsigned RBm(int m)
+    {
+        return m == 0 ? RB<0>() : m == 1 ? RB<1>() : m == 2 ? RB<2>() : m == 3 ? RB<3>() : RB<4>();
+    }
+    static DOL_HD constexpr unsigned rec_bytes(int m) { return al128(TC * RBm(m)); }
+    static DOL_HD constexpr unsigned roff(int m)
+    {
+        unsigned o = 0;
+        for (int i = 0; i < m; ++i) o += rec_bytes(i);
+        return o;
+    }
+    static DOL_HD unsigned soff() { return roff(NS + 1); }
+    static DOL_HD unsigned slot_bytes(int max_slots) { return al128((unsigned)(TC * max_slots + 2) * 8u); }
+    static DOL_HD unsigned foff(int max_slots) { return soff() + slot_bytes(max_slots); }
+    static DOL_HD unsigned face_bytes(int max_tf) { return al128((unsigned)max_tf * 8u * (unsigned)sizeof(R)); }
+    static DOL_HD unsigned buf_bytes(int max_slots, int max_tf) { return foff(max_slots) + face_bytes(max_tf); }
+    static DOL_HD unsigned fbuf_bytes(int max_tf) { return al128((unsigned)max_tf * NV * (unsigned)sizeof(R)); }
+    static DOL_HD unsigned xbuf_bytes(int max_slots) { return al128((unsigned)(TC * max_slots) * NV * (unsigned)sizeof(R)); }
+    static DOL_HD unsigned smem_bytes(int max_slots, int max_tf)
+    {
+        return 128u + 2u * buf_bytes(max_slots, max_tf) + fbuf_bytes(max_tf) + xbuf_bytes(max_slots);
+    }
+};
+
+template <int DIM, int NV, int NS, int PREC, int TC, int NT>
+__global__ void __launch_bounds__(NT) k_stage_pipe(DevMesh mesh, StageArgs a, int max_tf)
+{
+    using R = typename PrecT<PREC>::R;
+    using L = StagePipeLayout<DIM, NV, NS, PREC, TC>;
+    static_assert(NT % TC == 0, "threads per CTA must be a multiple of the tile");
+    constexpr int LN = NT / TC;                  // phase-A lanes per cell
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
+    const int max_slots = mesh.max_slots;
+    const unsigned bb = L::buf_bytes(max_slots, max_tf);
+    R *fbuf = reinterpret_cast<R *>(sm + 128 + 2 * bb);
+    R *xbuf = reinterpret_cast<R *>(sm + 128 + 2 * bb + L::fbuf_bytes(max_tf));
+    const int n_tiles = (mesh.n_cells + TC - 1) / TC;
+    if ((int)blockIdx.x >= n_tiles) return;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int tile, int b) {
+        const int t0 = tile * TC, nt = min(TC, mesh.n_cells - t0);
+        unsigned char *buf = sm + 128 + b * bb;
+        const int s_lo = __ldg(mesh.off + t0), s_hi = __ldg(mesh.off + t0 + nt);
+        const int a_lo = s_lo & ~1;
+        const unsigned sb = ((unsigned)(s_hi - a_lo) * 8u + 15u) & ~15u;
+        const int f_lo = __ldg(mesh.fown + t0), f_hi = __ldg(mesh.fown + t0 + nt);
+        const unsigned fb = (unsigned)(f_hi - f_lo) * 8u * (unsigned)sizeof(R);
+        unsigned rb[NS + 1];
+        unsigned tx = sb + fb;
+#pragma unroll
+        for (int m = 0; m <= NS; ++m) {
+            const unsigned rbm = L::RBm(m);
+            rb[m] = ((unsigned)nt * rbm) & ~15u;
+            tx += rb[m];
+        }
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar + b, tx);
+#pragma unroll
+        for (int m = 0; m <= NS; ++m) {
+            const unsigned rbm = L::RBm(m);
+            if (rb[m])
+                bulk_g2s(buf + L::roff(m), static_cast<const unsigned char *>(a.ord[m]) + (long long)t0 * rbm, rb[m],
+                         bar + b);
+        }
+        if (sb) bulk_g2s(buf + L::soff(), mesh.slot2 + a_lo, sb, bar + b);
+        if (fb) bulk_g2s(buf + L::foff(max_slots), Geo<R>::face(mesh) + 8ll * f_lo, fb, bar + b);
+    };
+
+    if (threadIdx.x == 0) issue(blockIdx.x, 0);
+    for (int j = 0, tile = blockIdx.x; tile < n_tiles; ++j, tile += gridDim.x) {
+        const int b = j & 1;
+        const int next = tile + gridDim.x;
+        if (threadIdx.x == 0 && next < n_tiles) issue(next, b ^ 1);
+        const bool ok = mbar_wait(bar + b, (unsigned)(j >> 1) & 1u, kPipeWaitLimit);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) atomicOr(a.status, 2u);
+            if (!ok) mbar_wait(bar + b, (unsigned)(j >> 1) & 1u, kPipeWaitLimit);
+            if (next < n_tiles) mbar_wait(bar + (b ^ 1), (unsigned)((j + 1) >> 1) & 1u, kPipeWaitLimit);
+            return;
+        }
+        const unsigned char *buf = sm + 128 + b * bb;
+        const int t0 = tile * TC, nt = min(TC, mesh.n_cells - t0);
+        const int s_lo = __ldg(mesh.off + t0);
+        const int a_lo = s_lo & ~1;
+        const int f_lo = __ldg(mesh.fown + t0), f_hi = __ldg(mesh.fown + t0 + nt);
+        // records of cells [t0, t0 + n_staged) are in the buffer for every order
+        int n_staged = nt;
+#pragma unroll
+        for (int m = 0; m <= NS; ++m) {
+            const unsigned rbm = L::RBm(m);
+            n_staged = min(n_staged, (int)((((unsigned)nt * rbm) & ~15u) / rbm));
+        }
+        TileSrc<DIM, NV, NS, PREC> src{a, mesh, buf, t0, n_staged, f_lo, f_hi, {}};
+#pragma unroll
+        for (int m = 0; m <= NS; ++m) src.off[m] = L::roff(m);
+        src.off[NS + 1] = L::foff(max_slots);
+        const int2 *ts = reinterpret_cast<const int2 *>(buf + L::soff());
+        // phase A: the faces this tile evaluates
+        {
+            const int ci = threadIdx.x / LN, l = threadIdx.x % LN;
+            if (ci < nt) {
+                const int c = t0 + ci;
+                const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+                const bool own_flag = a.flags && a.flags[c];
+                for (int s = s0 + l; s < s1; s += LN) {
+                    const int2 sw = ts[s - a_lo];
+                    const unsigned word = (unsigned)sw.y;
+                    const bool bnd = word & 2u, side = word & 1u;
+                    const bool incoming = side && (unsigned)(sw.x - t0) >= (unsigned)nt;
+                    if (side && !incoming) continue;        // the owner, in this tile, evaluates it
+                    R F[NV];
+                    canon_flux<DIM, NV, NS, PREC>(a, src, c, sw.x, word, own_flag, F);
+                    R *dst = (bnd || incoming) ? xbuf + (long long)(s - s_lo) * NV
+                                               : fbuf + (long long)((int)(word >> 2) - f_lo) * NV;
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) dst[v] = F[v];
+                }
+            }
+        }
+        __syncthreads();
+        // phase B: each cell sums its signed fluxes in slot order
+        if ((int)threadIdx.x < nt) {
+            const int c = t0 + threadIdx.x;
+            const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+            R res[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) res[v] = (R)0;
+            for (int s = s0; s < s1; ++s) {
+                const int2 sw = ts[s - a_lo];
+                const unsigned word = (unsigned)sw.y;
+                const bool side = word & 1u;
+                const bool per_slot = (word & 2u) || (side && (unsigned)(sw.x - t0) >= (unsigned)nt);
+                const R *F = per_slot ? xbuf + (long long)(s - s_lo) * NV : fbuf + (long long)((int)(word >> 2) - f_lo) * NV;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) res[v] += side ? F[v] : -F[v];
+            }
+            cell_epilogue<DIM, NV, PREC>(mesh, a, c, res);
+        }
+        (void)f_hi;
+        __syncthreads();   // buffer b and the flux area are free
     }
 }
 
