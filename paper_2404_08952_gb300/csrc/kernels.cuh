@@ -439,26 +439,32 @@ __device__ __forceinline__ bool nonfinite32(R x)
     return (__float_as_uint((float)x) & 0x7f800000u) == 0x7f800000u;
 }
 
-// Variable v of cell c; d = dt R.  Returns true on NaN/Inf.
+// Correctly rounded products and sums that the compiler may not fuse: the increment
+// arithmetic is then the same in every stage kernel, whatever each one inlines.
+__device__ __forceinline__ float mul_rn(float x, float y) { return __fmul_rn(x, y); }
+__device__ __forceinline__ float add_rn(float x, float y) { return __fadd_rn(x, y); }
+
+// Variable v of cell c; r = R_c (residual).  Returns true on NaN/Inf.
 template <class R, class T0, int S0>
-__device__ __forceinline__ bool incr_update(const StageArgs &a, int c, int v, long long n, R d, T0 *nxt)
+__device__ __forceinline__ bool incr_update(const StageArgs &a, int c, int v, long long n, R r, R dtr, T0 *nxt)
 {
     const long long i = v * n + c;
+    const R d = mul_rn(r, dtr);
     if (a.rk == 0) {
         a.dacc[i] = (float)d;
         const R u0 = (R)static_cast<const T0 *>(a.rec_start)[c * (long long)S0 + v];
-        nxt[c * (long long)S0 + v] = (T0)(u0 + d);
+        nxt[c * (long long)S0 + v] = (T0)add_rn(u0, d);
         return nonfinite32(d);
     }
     if (a.rk == 1) {
-        const R D = (R)0.25 * ((R)a.dacc[i] + d);
+        const R D = mul_rn((R)0.25, add_rn((R)a.dacc[i], d));
         a.dacc[i] = (float)D;
         const R u0 = (R)static_cast<const T0 *>(a.rec_start)[c * (long long)S0 + v];
-        nxt[c * (long long)S0 + v] = (T0)(u0 + D);
+        nxt[c * (long long)S0 + v] = (T0)add_rn(u0, D);
         return nonfinite32(D);
     }
-    const R D = (R)(2.0 / 3.0) * ((R)a.dacc[i] + d);
-    const double o = a.u0[i] + (double)D;
+    const R D = mul_rn((R)(2.0 / 3.0), add_rn((R)a.dacc[i], d));
+    const double o = __dadd_rn(a.u0[i], (double)D);
     a.out[i] = o;
     return nonfinite64(o);
 }
@@ -506,7 +512,7 @@ __global__ void __launch_bounds__(256, (PREC != PREC_F64 && NS <= 1) ? 4 : 1) k_
             const R r = res[i] * iv;
             if constexpr (PREC != PREC_F64) {
                 if (a.mode == 2) {
-                    bad |= incr_update<R, T0, S0>(a, c, v, n, r * dtr, nxt);
+                    bad |= incr_update<R, T0, S0>(a, c, v, n, r, dtr, nxt);
                     continue;
                 }
             }
@@ -545,7 +551,7 @@ __device__ __forceinline__ void cell_epilogue(const DevMesh &mesh, const StageAr
     if constexpr (PREC != PREC_F64) {
         if (a.mode == 2) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) bad |= incr_update<R, T0, S0>(a, c, v, n, res[v] * iv * dtr, nxt);
+            for (int v = 0; v < NV; ++v) bad |= incr_update<R, T0, S0>(a, c, v, n, res[v] * iv, dtr, nxt);
             if (bad) atomicOr(a.status, 1u);
             return;
         }
