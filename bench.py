@@ -125,15 +125,44 @@ def _ncoef(dim, m):
     return m + 1 if dim == 2 else (m + 1) * (m + 2) // 2
 
 
-def alg_bytes(kind, M, sch):
-    """Algorithmic bytes of one launch: every array the kernel needs read or written
-    once (neighbour re-reads served on chip), at the stored element widths and
-    without record padding.  kind: 'pack', 'diff<m>', 'stage'."""
-    nc, nf, ns, dim, nv = M.n_cells, M.n_faces, M.n_slots, M.dim, sch.nv
+def _widths(sch):
     sg = 8 if sch.precision == "fp64" else 4
 
     def sb(m):
         return 8 if sch.precision == "fp64" else (2 if sch.precision == "fp32_bf16" and m >= 2 else 4)
+    return sg, sb
+
+
+def alg_bytes(kind, M, sch):
+    """Algorithmic bytes of one launch, per cell as the scope table's measurement
+    section defines them (B_alg), times the cells:
+      diff m:  nv (s_{m-1} c_{m-1} + s_m c_m) + Gp
+      stage:   nv sum_{m<=N_d} s_m c_m + Gr + nv (16 + 8 + s_0)
+      Gp = nfc 8 + (nfc/2)(D 8 + 8) + 12,  Gr = Gp + (nfc/2) D 8
+    (c_m components of order m, s_m its stored width, nfc slots per cell, D the
+    dimension; geometry counted in FP64, the state as FP64 reads of u^n and u^(k), an
+    FP64 write and a bulk-precision copy).  pack (not in B_alg): nv (8 + s_0)."""
+    nc, nv, dim = M.n_cells, sch.nv, M.dim
+    _, sb = _widths(sch)
+    nfc = M.n_slots / nc
+    gp = nfc * 8 + (nfc / 2) * (dim * 8 + 8) + 12
+    gr = gp + (nfc / 2) * dim * 8
+    if kind == "pack":
+        return nc * nv * (8 + sb(0))
+    if kind.startswith("diff"):
+        m = int(kind[4:])
+        return nc * (nv * (_ncoef(dim, m - 1) * sb(m - 1) + _ncoef(dim, m) * sb(m)) + gp)
+    return nc * (nv * sum(_ncoef(dim, m) * sb(m) for m in range(sch.n_diff + 1)) + gr + nv * (16 + 8 + sb(0)))
+
+
+def kernel_bytes(kind, M, sch):
+    """Fewest bytes this library's kernel must move per launch: every array it reads
+    or writes once (neighbour re-reads served on chip), at the stored widths (FP32
+    geometry tables below FP64), without record padding; the stage reads only the
+    orders its stencil needs and, below FP64, the increment form's state traffic
+    (averaged over the three stages)."""
+    nc, nf, ns, dim, nv = M.n_cells, M.n_faces, M.n_slots, M.dim, sch.nv
+    sg, sb = _widths(sch)
     if kind == "pack":
         return nc * nv * (8 + sb(0))
     if kind.startswith("diff"):
@@ -143,7 +172,10 @@ def alg_bytes(kind, M, sch):
         return data + geo
     NS = max(sch.r, sch.k - sch.r - 2, 1)
     data = nc * nv * sum(_ncoef(dim, m) * sb(m) for m in range(NS + 1))
-    state = nc * nv * 8 * (5.0 / 3.0 + 1.0) + nc * nv * sb(0) * (2.0 / 3.0)   # u0/us reads, out write, next record
+    if sch.precision == "fp64":
+        state = nc * nv * 8 * (5.0 / 3.0 + 1.0) + nc * nv * sb(0) * (2.0 / 3.0)   # u0/us reads, out, next record
+    else:
+        state = nc * nv * (8 + 16 + 20) / 3.0    # increment form: D, start record, next record, u0/u in the last
     geo = nc * (4 + 4 * sg) + ns * 8 + nf * 8 * sg
     return data + state + geo
 
@@ -221,21 +253,23 @@ def run_dolinc(args):
     launches_per_step = int(sum(results[args.precision]["kn"])) / args.steps
     variants = {}
     if not args.no_variants and args.workload == "euler3d_tet64":
-        for prec, order in (("fp32_bf16", w["info"]["order"]), (args.precision, 2), (args.precision, 4),
-                            ("fp64", 2), ("fp64", 4)):
-            if order == w["info"]["order"] and prec == args.precision:
-                continue
+        o0 = w["info"]["order"]
+        k0, r0 = synth.STENCIL_OF_ORDER[o0]
+        minimal = max(r0, k0 - r0 - 2, 1)     # differentials the stencil itself reads
+        for prec, order, nd, tag in (("fp32_bf16", o0, o0 - 1, ""), (args.precision, o0, minimal, "_minimal"),
+                                     ("fp64", o0, minimal, "_minimal"), (args.precision, 2, 1, ""),
+                                     (args.precision, 4, 3, ""), ("fp64", 2, 1, ""), ("fp64", 4, 3, "")):
             k, r = synth.STENCIL_OF_ORDER[order]
-            kw = dict(w["scheme"], k=k, r=r, n_diff=order - 1)
+            kw = dict(w["scheme"], k=k, r=r, n_diff=nd)
             vr = timed_run(prec, kw, args.steps, False)
-            v = {"precision": prec, "scheme_order": order, "stencil_k_r": [k, r], "n_diff": order - 1,
+            v = {"precision": prec, "scheme_order": order, "stencil_k_r": [k, r], "n_diff": nd,
                  "value": M.n_cells * world * 3 * args.steps / (vr["ms"] / 1e3),
                  "ms_per_step": vr["ms"] / args.steps, "finite_after_steps": vr["finite"]}
-            if prec == "fp32_bf16" and "fp64" in results:
+            if order == o0 and "fp64" in results:
                 a = vr["state"].double().cpu().numpy()
                 b = results["fp64"]["state"].cpu().numpy()
                 v["l2_rel_vs_fp64_after_steps"] = _l2_rel(a, b)
-            variants["%s_order%d" % (prec, order)] = v
+            variants["%s_order%d%s" % (prec, order, tag)] = v
             del vr
     main = results[args.precision]
     cells = M.n_cells
@@ -249,6 +283,7 @@ def run_dolinc(args):
     per_launch_ms = kms[top] / max(kn[top], 1)
     bytes_alg = alg_bytes(KINDS[top], M, main["sch"])
     achieved = bytes_alg / (per_launch_ms / 1e3) / 1e9
+    bytes_kern = kernel_bytes(KINDS[top], M, main["sch"])
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
@@ -261,7 +296,9 @@ def run_dolinc(args):
     kernels = {KINDS[i]: {"ms_per_launch": round(kms[i] / kn[i], 5), "launches": int(kn[i]),
                           "share": round(kms[i] / sum(kms), 4),
                           "alg_bytes": int(alg_bytes(KINDS[i], M, main["sch"])),
-                          "alg_GBs": round(alg_bytes(KINDS[i], M, main["sch"]) / (kms[i] / kn[i] / 1e3) / 1e9, 1)}
+                          "alg_GBs": round(alg_bytes(KINDS[i], M, main["sch"]) / (kms[i] / kn[i] / 1e3) / 1e9, 1),
+                          "kernel_bytes": int(kernel_bytes(KINDS[i], M, main["sch"])),
+                          "kernel_GBs": round(kernel_bytes(KINDS[i], M, main["sch"]) / (kms[i] / kn[i] / 1e3) / 1e9, 1)}
                for i in range(len(KINDS)) if kn[i] > 0}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -278,6 +315,8 @@ def run_dolinc(args):
         "roofline": {"bound": "hbm", "kernel": KINDS[top], "achieved": round(achieved, 1), "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "alg_bytes_per_launch": int(bytes_alg),
+                     "kernel_bytes_per_launch": int(bytes_kern),
+                     "kernel_bytes_frac": round(bytes_kern / (per_launch_ms / 1e3) / 1e9 / peak, 4),
                      "ms_per_launch": round(per_launch_ms, 5)},
         "kernels": kernels,
         "gpu_launches": int(round(launches_per_step * args.steps)),
