@@ -74,6 +74,8 @@ __global__ void __launch_bounds__(256) k_pack(int n, const double *__restrict__ 
 // term), the group sums by recursive halving and each lane stores its slice of the
 // output record.  LPC = 1 is one thread per cell.
 DOL_HD constexpr int round_up(int n, int q) { return ((n + q - 1) / q) * q; }
+// slots gathered per batch, by the size of the input record (registers held per slot)
+DOL_HD constexpr int diff_batch(int rec_values) { return rec_values <= 8 ? 4 : (rec_values <= 16 ? 2 : 1); }
 
 template <int DIM, int NV, int M, int PREC, int LPC>
 __global__ void __launch_bounds__(256) k_diff(DevMesh mesh, const void *__restrict__ in_v, void *__restrict__ out_v)
@@ -102,12 +104,29 @@ __global__ void __launch_bounds__(256) k_diff(DevMesh mesh, const void *__restri
             poly_mul_acc<DIM, NV, M, R>(acc, x, wx, wy, wz);
         }
         const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
-        for (int s = s0 + l; s < s1; s += LPC) {
-            R kx, ky, kz, kb;
-            ld4<R>(Geo<R>::slotk(mesh) + 4ll * s, kx, ky, kz, kb);
-            int nb = Geo<R>::nb_of(kb);
-            load_rec<TI, NV * CI, SI, R>(in, nb, x);
-            poly_mul_acc<DIM, NV, M, R>(acc, x, kx, ky, kz);
+        // slots in batches of UB: all slot records, then all neighbour records of the
+        // batch are requested before the first is used (the sums keep slot order)
+        constexpr int UB = diff_batch(NV * CI);
+        for (int s = s0 + l; s < s1; s += LPC * UB) {
+            R kx[UB], ky[UB], kz[UB];
+            int nbv[UB];
+            bool ok[UB];
+#pragma unroll
+            for (int u = 0; u < UB; ++u) {
+                const int su = s + u * LPC;
+                ok[u] = su < s1;
+                R kb = (R)0;
+                kx[u] = ky[u] = kz[u] = (R)0;
+                if (ok[u]) ld4<R>(Geo<R>::slotk(mesh) + 4ll * su, kx[u], ky[u], kz[u], kb);
+                nbv[u] = Geo<R>::nb_of(kb);
+            }
+            R xs[UB][NV * CI];
+#pragma unroll
+            for (int u = 0; u < UB; ++u)
+                if (ok[u]) load_rec<TI, NV * CI, SI, R>(in, nbv[u], xs[u]);
+#pragma unroll
+            for (int u = 0; u < UB; ++u)
+                if (ok[u]) poly_mul_acc<DIM, NV, M, R>(acc, xs[u], kx[u], ky[u], kz[u]);
         }
     }
     if constexpr (LPC == 1) {
@@ -671,14 +690,30 @@ __global__ void __launch_bounds__(TILE) k_diff_tile(DevMesh mesh, const void *__
     load_rec<TI, NV * CI, SI, R, false>(tin, threadIdx.x, x);
     poly_mul_acc<DIM, NV, M, R>(acc, x, wx, wy, wz);
     const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
-    for (int s = s0; s < s1; ++s) {
-        R kx, ky, kz, kb;
-        ld4<R>(Geo<R>::slotk(mesh) + 4ll * s, kx, ky, kz, kb);
-        const int nb = Geo<R>::nb_of(kb);
-        const unsigned i = (unsigned)(nb - t0);
-        if (i < (unsigned)nt) load_rec<TI, NV * CI, SI, R, false>(tin, i, x);
-        else load_rec<TI, NV * CI, SI, R>(in, nb, x);
-        poly_mul_acc<DIM, NV, M, R>(acc, x, kx, ky, kz);
+    constexpr int UB = diff_batch(NV * CI);
+    for (int s = s0; s < s1; s += UB) {
+        R kx[UB], ky[UB], kz[UB];
+        int nbv[UB];
+        bool ok[UB];
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            ok[u] = s + u < s1;
+            R kb = (R)0;
+            kx[u] = ky[u] = kz[u] = (R)0;
+            if (ok[u]) ld4<R>(Geo<R>::slotk(mesh) + 4ll * (s + u), kx[u], ky[u], kz[u], kb);
+            nbv[u] = Geo<R>::nb_of(kb);
+        }
+        R xs[UB][NV * CI];
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            if (!ok[u]) continue;
+            const unsigned i = (unsigned)(nbv[u] - t0);
+            if (i < (unsigned)nt) load_rec<TI, NV * CI, SI, R, false>(tin, i, xs[u]);
+            else load_rec<TI, NV * CI, SI, R>(in, nbv[u], xs[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < UB; ++u)
+            if (ok[u]) poly_mul_acc<DIM, NV, M, R>(acc, xs[u], kx[u], ky[u], kz[u]);
     }
     store_rec<TO, NV * CO, SO, R>(out, c, acc);
 }
