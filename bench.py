@@ -183,6 +183,15 @@ def kernel_bytes(kind, M, sch):
 KINDS = ["pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces"]
 
 
+def _stage_roofline(M, sch, ms_stage, peak):
+    """B_alg of one whole RK stage (all differential passes + the fused stage) per
+    cell, and the achieved GB/s and fraction of the measured peak at ms_stage."""
+    b = sum(alg_bytes("diff%d" % m, M, sch) for m in range(1, sch.n_diff + 1)) + alg_bytes("stage", M, sch)
+    gbs = b / (ms_stage / 1e3) / 1e9
+    return {"alg_bytes_per_cell": round(b / M.n_cells, 1), "ms_per_stage": round(ms_stage, 5),
+            "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4)}
+
+
 def _l2_rel(a, b):
     """max over variables of ||a_v - b_v||_2 / ||b||_2 (all variables' norm, so a
     variable that is zero in the data, e.g. z-momentum, is measured against the state)."""
@@ -319,6 +328,9 @@ def run_dolinc(args):
                      "kernel_bytes_frac": round(bytes_kern / (per_launch_ms / 1e3) / 1e9 / peak, 4),
                      "ms_per_launch": round(per_launch_ms, 5)},
         "kernels": kernels,
+        # the whole stage (differential passes + fused stage; pack per step) against the
+        # scope table's B_alg per cell per stage
+        "stage_roofline": _stage_roofline(M, main["sch"], ms_step / 3.0, peak),
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": main["clocks"],
     }

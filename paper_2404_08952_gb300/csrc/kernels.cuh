@@ -14,6 +14,7 @@
 #pragma once
 #include "common.cuh"
 #include "device_mesh.hpp"
+#include "tma.cuh"
 
 namespace dol {
 
@@ -130,7 +131,22 @@ __global__ void __launch_bounds__(256) k_diff(DevMesh mesh, const void *__restri
         }
     }
     if constexpr (LPC == 1) {
-        if (valid) store_rec<TO, NV * CO, SO, R>(out, c, acc);
+        constexpr unsigned RBO = SO * (unsigned)sizeof(TO);
+        if constexpr (RBO % 16 == 0) {
+            // the block's records are contiguous: stage them in shared memory and write
+            // them with one bulk copy
+            extern __shared__ __align__(16) unsigned char smo[];
+            if (valid) store_rec<TO, NV * CO, SO, R>(reinterpret_cast<TO *>(smo), threadIdx.x, acc);
+            fence_proxy_async_smem();
+            __syncthreads();
+            const long long c0 = (long long)blockIdx.x * blockDim.x;
+            if (threadIdx.x == 0 && c0 < mesh.n_cells) {
+                const unsigned n = (unsigned)min((long long)blockDim.x, (long long)mesh.n_cells - c0);
+                bulk_s2g_wait(out + c0 * SO, smo, n * RBO);
+            }
+        } else {
+            if (valid) store_rec<TO, NV * CO, SO, R>(out, c, acc);
+        }
     } else {
         group_reduce_scatter<P, LPC, R>(acc, l);
         if (!valid) return;
@@ -680,42 +696,54 @@ __global__ void __launch_bounds__(TILE) k_diff_tile(DevMesh mesh, const void *__
     block_copy_wait();
     const TI *tin = reinterpret_cast<const TI *>(sm);
     const int c = t0 + threadIdx.x;
-    if (c >= mesh.n_cells) return;
+    constexpr unsigned RBO = SO * (unsigned)sizeof(TO);
+    const bool valid = c < mesh.n_cells;
     R acc[NV * CO];
 #pragma unroll
     for (int i = 0; i < NV * CO; ++i) acc[i] = (R)0;
-    R x[NV * CI];
-    R wx, wy, wz, iv;
-    ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, wx, wy, wz, iv);
-    load_rec<TI, NV * CI, SI, R, false>(tin, threadIdx.x, x);
-    poly_mul_acc<DIM, NV, M, R>(acc, x, wx, wy, wz);
-    const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
-    constexpr int UB = diff_batch(NV * CI);
-    for (int s = s0; s < s1; s += UB) {
-        R kx[UB], ky[UB], kz[UB];
-        int nbv[UB];
-        bool ok[UB];
+    if (valid) {
+        R x[NV * CI];
+        R wx, wy, wz, iv;
+        ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, wx, wy, wz, iv);
+        load_rec<TI, NV * CI, SI, R, false>(tin, threadIdx.x, x);
+        poly_mul_acc<DIM, NV, M, R>(acc, x, wx, wy, wz);
+        const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+        constexpr int UB = diff_batch(NV * CI);
+        for (int s = s0; s < s1; s += UB) {
+            R kx[UB], ky[UB], kz[UB];
+            int nbv[UB];
+            bool ok[UB];
 #pragma unroll
-        for (int u = 0; u < UB; ++u) {
-            ok[u] = s + u < s1;
-            R kb = (R)0;
-            kx[u] = ky[u] = kz[u] = (R)0;
-            if (ok[u]) ld4<R>(Geo<R>::slotk(mesh) + 4ll * (s + u), kx[u], ky[u], kz[u], kb);
-            nbv[u] = Geo<R>::nb_of(kb);
+            for (int u = 0; u < UB; ++u) {
+                ok[u] = s + u < s1;
+                R kb = (R)0;
+                kx[u] = ky[u] = kz[u] = (R)0;
+                if (ok[u]) ld4<R>(Geo<R>::slotk(mesh) + 4ll * (s + u), kx[u], ky[u], kz[u], kb);
+                nbv[u] = Geo<R>::nb_of(kb);
+            }
+            R xs[UB][NV * CI];
+#pragma unroll
+            for (int u = 0; u < UB; ++u) {
+                if (!ok[u]) continue;
+                const unsigned i = (unsigned)(nbv[u] - t0);
+                if (i < (unsigned)nt) load_rec<TI, NV * CI, SI, R, false>(tin, i, xs[u]);
+                else load_rec<TI, NV * CI, SI, R>(in, nbv[u], xs[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < UB; ++u)
+                if (ok[u]) poly_mul_acc<DIM, NV, M, R>(acc, xs[u], kx[u], ky[u], kz[u]);
         }
-        R xs[UB][NV * CI];
-#pragma unroll
-        for (int u = 0; u < UB; ++u) {
-            if (!ok[u]) continue;
-            const unsigned i = (unsigned)(nbv[u] - t0);
-            if (i < (unsigned)nt) load_rec<TI, NV * CI, SI, R, false>(tin, i, xs[u]);
-            else load_rec<TI, NV * CI, SI, R>(in, nbv[u], xs[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < UB; ++u)
-            if (ok[u]) poly_mul_acc<DIM, NV, M, R>(acc, xs[u], kx[u], ky[u], kz[u]);
     }
-    store_rec<TO, NV * CO, SO, R>(out, c, acc);
+    if constexpr (RBO % 16 == 0) {
+        // the tile's output records are contiguous: one bulk copy from shared memory
+        unsigned char *so = sm + r16((unsigned)TILE * SI * (unsigned)sizeof(TI));
+        if (valid) store_rec<TO, NV * CO, SO, R>(reinterpret_cast<TO *>(so), threadIdx.x, acc);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) bulk_s2g_wait(out + (long long)t0 * SO, so, (unsigned)nt * RBO);
+    } else {
+        if (valid) store_rec<TO, NV * CO, SO, R>(out, c, acc);
+    }
 }
 
 // ------------------------------------------------------------------ persistent batched stage

@@ -50,9 +50,40 @@ template <int DIM, int NV, int NS, int PREC> struct Path {
         k_pack<NV, PREC><<<nblk(m.n_cells, 256), 256, 0, s>>>(m.n_cells, u,
                                                               static_cast<typename PrecT<PREC>::T0 *>(o0));
     }
+    // bytes of one output record of order MM, and the shared memory a block of bs
+    // threads (one cell each) needs to stage its output records for the bulk store
+    template <int MM> static constexpr unsigned out_rec_bytes()
+    {
+        return ord_stride<DIM, NV, MM, PREC>() * (unsigned)sizeof(typename OrdT<PREC, MM>::T);
+    }
+    template <int MM> static size_t out_smem(int bs)
+    {
+        return out_rec_bytes<MM>() % 16 == 0 ? (size_t)bs * out_rec_bytes<MM>() : 0;
+    }
+    // one thread per cell (lanes 1), output staged for the bulk store
+    template <int MM> static void diff_1(const DevMesh &m, const void *in, void *out, int bs, cudaStream_t s)
+    {
+        static bool attr = false;   // opt in to more than 48 KB once per instantiation
+        if (!attr) {
+            cudaFuncSetAttribute(k_diff<DIM, NV, MM, PREC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kMaxSmem);
+            attr = true;
+        }
+        k_diff<DIM, NV, MM, PREC, 1><<<nblk(m.n_cells, bs), bs, out_smem<MM>(bs), s>>>(m, in, out);
+    }
     template <int LPC> static void diff_l(const DevMesh &m, int M, const void *in, void *out, int bs, cudaStream_t s)
     {
         const int b = nblk((long long)m.n_cells * LPC, bs);
+        if constexpr (LPC == 1) {
+            switch (M) {
+            case 1: diff_1<1>(m, in, out, bs, s); break;
+            case 2: diff_1<2>(m, in, out, bs, s); break;
+            case 3: diff_1<3>(m, in, out, bs, s); break;
+            case 4: diff_1<4>(m, in, out, bs, s); break;
+            default: break;
+            }
+            return;
+        }
         switch (M) {
         case 1: k_diff<DIM, NV, 1, PREC, LPC><<<b, bs, 0, s>>>(m, in, out); break;
         case 2: k_diff<DIM, NV, 2, PREC, LPC><<<b, bs, 0, s>>>(m, in, out); break;
@@ -66,13 +97,14 @@ template <int DIM, int NV, int NS, int PREC> struct Path {
         const int b = nblk(m.n_cells, TILE);
         auto sm = [&](auto mc) {
             constexpr int MM = decltype(mc)::value;
-            return (size_t)TILE * ord_stride<DIM, NV, MM - 1, PREC>() * sizeof(typename OrdT<PREC, MM - 1>::T);
+            const size_t in_b = (size_t)TILE * ord_stride<DIM, NV, MM - 1, PREC>() * sizeof(typename OrdT<PREC, MM - 1>::T);
+            return ((in_b + 15) & ~(size_t)15) + out_smem<MM>(TILE);
         };
         auto go = [&](auto mc) {
             constexpr int MM = decltype(mc)::value;
             const size_t bytes = sm(mc);
             if (bytes > kMaxSmem) {                 // too large to stage: one thread per cell instead
-                k_diff<DIM, NV, MM, PREC, 1><<<nblk(m.n_cells, TILE), TILE, 0, s>>>(m, in, out);
+                diff_1<MM>(m, in, out, TILE, s);
                 return;
             }
             static bool attr = false;
@@ -116,7 +148,7 @@ template <int DIM, int NV, int NS, int PREC> struct Path {
             using L = DiffPipeLayout<DIM, NV, MM, PREC, NT / LPC>;
             const size_t bytes = L::smem_bytes(m.max_slots);
             if (bytes > kMaxSmem) {                 // too large to stage: one thread per cell instead
-                k_diff<DIM, NV, MM, PREC, 1><<<nblk(m.n_cells, NT), NT, 0, s>>>(m, in, out);
+                diff_1<MM>(m, in, out, NT, s);
                 return;
             }
             auto kern = k_diff_pipe<DIM, NV, MM, PREC, LPC, NT>;
