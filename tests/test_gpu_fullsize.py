@@ -6,6 +6,13 @@ times (Morton renumbering, autotuned launch shape).
                  every cell (the oracle runs one stage in a few seconds).
   euler2d_riemann ~1.05M triangles, residual with the criterion-flagged ENO3 limiter,
                  FP64, every cell.
+  adv3d_hexprism 140^3 hexes, half split into prisms (4,116,000 cells): scheme order 3
+                 one full stage FP64 against the oracle at every cell; order 5 (the
+                 oracle's order-4 tensors would need 13 GB) by properties that hold
+                 at any size: exact periodic conservation and FP32 within the FP64
+                 GPU stage.
+  burgers_batch  512 meshes (~23M cells) in one batched launch per stage: every
+                 mesh against the per-mesh path, four meshes against the oracle.
 """
 import numpy as np
 import pytest
@@ -87,3 +94,73 @@ def test_euler2d_riemann_full_residual_with_limiter():
     want = O.residual(w["u0"], oracle.Scheme(eno=2, troubled=flags, **w["scheme"]))
     assert rel(got, want) < 1e-11
     dg.dolinc_set_flags(M, None)
+
+
+@pytest.fixture(scope="module")
+def hexprism140():
+    # initial averages with the one-point rule: parity does not depend on their accuracy
+    return synth.workload("adv3d_hexprism", order=5, size=140, q=1)
+
+
+def test_adv3d_hexprism_full_stage_order3_fp64(hexprism140):
+    w = hexprism140
+    sch = dict(w["scheme"], k=3, r=1, n_diff=2)
+    M = dg.Mesh(w["mesh"])
+    s = dg.Scheme(precision="fp64", **sch)
+    ws = dg.workspace(M, s)
+    u = torch.from_numpy(M.to_lib(w["u0"])).cuda()
+    dg.dolinc_autotune(M, s, u, ws)
+    out = torch.zeros_like(u)
+    dg.dolinc_rk_stage(M, s, w["dt"], 0, u, u, out, ws)
+    dg.dolinc_sync_status(M, ws)
+    got = M.from_lib(out.cpu().numpy())
+    want = oracle.Oracle(w["mesh"]).rk3_stage(w["u0"], w["u0"], oracle.Scheme(**sch), w["dt"], 0)
+    assert rel(got - w["u0"], want - w["u0"]) < 1e-11
+
+
+def test_adv3d_hexprism_full_order5_properties(hexprism140):
+    w = hexprism140
+    M = dg.Mesh(w["mesh"])
+    V = torch.from_numpy(M.geometry()["V"]).cuda()
+    R = {}
+    for prec in ("fp64", "fp32"):
+        s = dg.Scheme(precision=prec, **w["scheme"])
+        ws = dg.workspace(M, s)
+        u = torch.from_numpy(M.to_lib(w["u0"])).cuda()
+        dg.dolinc_autotune(M, s, u, ws)
+        r = torch.zeros_like(u)
+        dg.dolinc_residual(M, s, u, r, ws)
+        dg.dolinc_sync_status(M, ws)
+        R[prec] = r
+        tot = float((r[0] * V).sum())
+        mag = float((r[0].abs() * V).sum())
+        # every face enters its two cells with opposite bit-identical fluxes
+        assert abs(tot) < (1e-13 if prec == "fp64" else 1e-6) * mag
+    r64, r32 = R["fp64"].cpu().numpy(), R["fp32"].cpu().numpy()
+    # FP32 bulk: stencil (5,2) weights carry g^(+-4) conditioning; a few 1e-4 of the scale
+    assert np.abs(r32 - r64).max() < 5e-3 * np.abs(r64).max()
+
+
+def test_burgers_batch_full_size():
+    wl = synth.workload("burgers_batch", q=1)
+    ms_ = wl["meshes"]
+    meshes = [dg.Mesh(x["mesh"]) for x in ms_]
+    bt = dg.Batch(meshes)
+    s = dg.Scheme(precision="fp64", **wl["scheme"])
+    ws = bt.workspace(s)
+    u = torch.from_numpy(bt.to_lib([x["u0"] for x in ms_])).cuda()
+    dt = torch.tensor([x["dt"] for x in ms_], dtype=torch.float64, device="cuda")
+    bt.autotune(s, dt, u, ws)
+    bt.rk_step(s, dt, u, ws, use_graph=True)
+    dg.dolinc_sync_status(meshes[0], ws)
+    got = bt.from_lib(u.cpu().numpy())
+    sizes = np.array([M.n_cells for M in meshes])
+    pick = {int(np.argmin(sizes)), int(np.argmax(sizes)), 7, 300}
+    for i, (M, x, g) in enumerate(zip(meshes, ms_, got)):
+        w1 = dg.workspace(M, s)
+        ref = torch.from_numpy(M.to_lib(x["u0"])).cuda()
+        dg.dolinc_rk_step(M, s, x["dt"], ref, w1)
+        assert rel(g, M.from_lib(ref.cpu().numpy())) < 1e-13, i
+        if i in pick:
+            want = oracle.Oracle(x["mesh"]).rk3_step(x["u0"], oracle.Scheme(**wl["scheme"]), x["dt"])
+            assert rel(g, want) < 1e-12, i
