@@ -235,7 +235,10 @@ dolinc_status dolinc_rk_step_noalloc(dolinc_mesh *mesh, const dolinc_scheme *sch
  * whose records and geometry arrive by bulk asynchronous copies into two
  * shared-memory buffers while the previous tile is computed; a bounded barrier wait
  * that gives up is reported as DOLINC_ERR_DEVICE_TIMEOUT by dolinc_sync_status),
- * keeps the fastest shape in the mesh handle for
+ * and for the stage the face-centric pair (-2 lanes: one thread per face evaluates
+ * every face once into a workspace flux array, then one thread per cell, in blocks of
+ * 64/128/256, sums its signed fluxes in slot order), keeps the fastest shape in the
+ * mesh handle for
  * every later call with this scheme, and appends it to the text file cache_path (one
  * line per GPU name and mesh/scheme key; may be NULL).  A key already in the file is
  * reused without timing.  Synchronous; clears the workspace status word.  Results:
@@ -249,8 +252,10 @@ dolinc_status dolinc_autotune(dolinc_mesh *mesh, const dolinc_scheme *scheme, co
                               size_t ws_bytes, const char *cache_path, dolinc_stream stream, dolinc_tuning *out);
 /* Sets the launch shape used for this mesh and scheme (lanes per cell 1, 4 or 8 with a
  * block of 32..256 threads, a multiple of 32; or lanes 0, tiled, with a block of 64,
- * 128 or 256; differential passes also lanes -1 or -4, pipelined, with 128 or 256),
- * e.g. a shape read back from an autotuning cache. */
+ * 128 or 256; differential passes also lanes -1 or -4, pipelined, with 128 or 256;
+ * the stage also lanes -1, pipelined, with tiles of 64 or 128 cells, or -2, the
+ * face-centric pair, with 64, 128 or 256), e.g. a shape read back from an autotuning
+ * cache. */
 dolinc_status dolinc_set_tuning(dolinc_mesh *mesh, const dolinc_scheme *scheme, const dolinc_tuning *tuning);
 
 /* ---------------------------------------------------------------- troubled cells

@@ -190,7 +190,7 @@ int ncoef_h(int dim, int m) { return dim == 2 ? m + 1 : (m + 1) * (m + 2) / 2; }
 int stride_h(int dim, int nv, int m, int prec) { return rec_stride(nv * ncoef_h(dim, m), elem_bytes(prec, m)); }
 
 struct WsLayout {
-    size_t status, o0[3], ord[MAXN + 1], ustage, dacc, total;
+    size_t status, o0[3], ord[MAXN + 1], ustage, dacc, flux, total;
 };
 
 WsLayout ws_layout(const dolinc_mesh *m, const dolinc_scheme *s)
@@ -216,6 +216,8 @@ WsLayout ws_layout(const dolinc_mesh *m, const dolinc_scheme *s)
     o += al256(nc * s->nv * sizeof(double));
     L.dacc = o;                                 // increment accumulator (bulk precision below FP64)
     if (s->precision != DOLINC_FP64) o += al256(nc * s->nv * sizeof(float));
+    L.flux = o;                                 // per-face fluxes of the face-centric stage
+    o += al256((size_t)m->h.n_faces * s->nv * (s->precision == DOLINC_FP64 ? sizeof(double) : sizeof(float)));
     L.total = o;
     return L;
 }
@@ -253,6 +255,7 @@ StageArgs base_args(const dolinc_mesh *m, const dolinc_scheme *s, void *ws, cons
     a.flags = flagged ? m->flags : nullptr;
     a.eno_all = s->limiter == DOLINC_LIMIT_ENO3_ALL;
     a.flag_mode = s->limiter == DOLINC_LIMIT_FIRST_ORDER_FLAGGED ? LIM_FIRST_ORDER : LIM_ENO3;
+    a.face_flux = B(ws, L.flux);
     return a;
 }
 
@@ -727,15 +730,16 @@ dolinc_status dolinc_autotune(dolinc_mesh *m, const dolinc_scheme *s, const doub
         // diff shapes: lanes 1/4/8, tiled (0), persistent pipelined (-1/-4 with 128/256
         // threads); stage shapes: lanes 1/4/8, tiled, persistent pipelined (-1 with tiles
         // of 64/128 cells)
-        const int lpcs[6] = {1, 4, 8, 0, -1, -4}, blocks[3] = {64, 128, 256};
+        const int lpcs[7] = {1, 4, 8, 0, -1, -4, -2}, blocks[3] = {64, 128, 256};
         double bd = 1e30, bs = 1e30;
-        for (int li = 0; li < 6; ++li)
+        for (int li = 0; li < 7; ++li)
             for (int bi = 0; bi < 3; ++bi) {
                 Tune t;
                 t.diff_lpc = t.stage_lpc = lpcs[li];
                 t.diff_block = t.stage_block = blocks[bi];
-                const bool diff_ok = lpcs[li] >= 0 || blocks[bi] >= 128;
-                const bool stage_ok = lpcs[li] >= -1 && (lpcs[li] >= 0 || blocks[bi] <= 128);
+                const bool diff_ok = (lpcs[li] >= 0 || blocks[bi] >= 128) && lpcs[li] != -2;
+                const bool stage_ok = lpcs[li] == -2 || (lpcs[li] >= -1 && (lpcs[li] >= 0 || blocks[bi] <= 128));
+                if (!diff_ok) t.diff_lpc = best.diff_lpc, t.diff_block = best.diff_block;
                 if (diff_ok) {
                     double td = time_it([&] {
                         for (int mm = 1; mm <= s->n_diff; ++mm)
@@ -1254,12 +1258,13 @@ dolinc_status dolinc_set_tuning(dolinc_mesh *m, const dolinc_scheme *s, const do
         return (l == 1 || l == 4 || l == 8) && b >= 32 && b <= 256 && b % 32 == 0;
     };
     const bool diff_pipe = (t->diff_lanes == -1 || t->diff_lanes == -4) && (t->diff_block == 128 || t->diff_block == 256);
-    const bool stage_pipe = t->stage_lanes == -1 && (t->stage_block == 64 || t->stage_block == 128);
+    const bool stage_pipe = (t->stage_lanes == -1 && (t->stage_block == 64 || t->stage_block == 128)) ||
+                            (t->stage_lanes == -2 && (t->stage_block == 64 || t->stage_block == 128 || t->stage_block == 256));
     if (!(ok(t->diff_lanes, t->diff_block) || diff_pipe) || !(ok(t->stage_lanes, t->stage_block) || stage_pipe))
         return fail(DOLINC_ERR_INVALID_ARG,
                     "lanes 1, 4 or 8 with blocks a multiple of 32 in 32..256, or lanes 0 (tiled) with 64/128/256; "
                     "differential passes also lanes -1 / -4 (persistent pipelined) with 128/256, the stage "
-                    "lanes -1 (persistent pipelined) with tiles of 64/128 cells");
+                    "lanes -1 (persistent pipelined) with tiles of 64/128 cells or -2 (face-centric) with 64/128/256");
     Tune x;
     x.diff_lpc = t->diff_lanes;
     x.diff_block = t->diff_block;

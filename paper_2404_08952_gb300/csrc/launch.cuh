@@ -213,6 +213,11 @@ template <int DIM, int NV, int NS, int PREC> struct Path {
     }
     static void stage(const DevMesh &m, const StageArgs &a, const Tune &t, cudaStream_t s)
     {
+        if (t.stage_lpc == -2) {                    // face-centric pair
+            k_flux<DIM, NV, NS, PREC><<<nblk(m.n_faces, 256), 256, 0, s>>>(m, a);
+            k_gather<DIM, NV, PREC><<<nblk(m.n_cells, t.stage_block), t.stage_block, 0, s>>>(m, a);
+            return;
+        }
         if (t.stage_lpc < 0) {
             if (t.stage_block >= 128) stage_p<128>(m, a, s);
             else stage_p<64>(m, a, s);

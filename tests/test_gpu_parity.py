@@ -448,19 +448,21 @@ def test_pipelined_differentials_are_bit_identical(lanes, block, name, nv, prec)
     assert rel(got - u, want - u) < tol * 10 or rel(got, want) < tol
 
 
-@pytest.mark.parametrize("block", [64, 128])
+@pytest.mark.parametrize("lanes,block", [(-1, 64), (-1, 128), (-2, 64), (-2, 256)])
 @pytest.mark.parametrize("name,nv,prec,limiter", [("tet", 5, "fp32", "none"), ("hexprism", 1, "fp64", "none"),
                                                   ("tri_bnd", 4, "fp64", "none"), ("tet", 5, "fp32_bf16", "none"),
                                                   ("strip", 1, "fp32", "none"), ("tri", 1, "fp64", "none"),
                                                   ("tri_bnd", 4, "fp64", "eno3_flagged"),
                                                   ("tet", 5, "fp32", "first_order_flagged")])
-def test_pipelined_stage_is_bit_identical(block, name, nv, prec, limiter):
-    """The persistent pipelined stage evaluates each face once per tile that needs it
-    (in the canonical orientation, the same operands as the one-thread-per-cell
-    kernel) and sums each cell's fluxes in slot order: without a limiter the residual
-    and the full step are bit-identical to that kernel's.  With the ENO3 limiter the
-    compiler is free to fuse the stencil-choice arithmetic differently in the two
-    kernels, so agreement is to rounding (a few ulp).  The step matches the oracle."""
+def test_face_centric_stages_are_bit_identical(lanes, block, name, nv, prec, limiter):
+    """The persistent pipelined stage (lanes -1: each face once per tile that needs it)
+    and the face-centric pair (lanes -2: each face once, then a slot-ordered gather)
+    evaluate faces in the canonical orientation with the operands of the
+    one-thread-per-cell kernel and sum each cell's fluxes in slot order: without a
+    limiter the residual and the full step are bit-identical to that kernel's.  With
+    the ENO3 limiter the compiler is free to fuse the stencil-choice arithmetic
+    differently in the kernels, so agreement is to rounding (a few ulp).  The step
+    matches the oracle."""
     m, O = mesh(name)
     M = gpu_mesh(m)
     u = field(m, nv, seed=53)
@@ -472,7 +474,7 @@ def test_pipelined_stage_is_bit_identical(block, name, nv, prec, limiter):
         dg.dolinc_set_flags(M, torch.from_numpy(M.to_lib(flags)).cuda())
     ws = dg.workspace(M, sch)
     res, step = {}, {}
-    for sl, sb in ((1, 128), (-1, block)):
+    for sl, sb in ((1, 128), (lanes, block)):
         dg.dolinc_set_tuning(M, sch, 1, 128, sl, sb)
         R = torch.zeros((nv, M.n_cells), dtype=torch.float64, device="cuda")
         dg.dolinc_residual(M, sch, to_dev(M, u), R, ws)
@@ -482,14 +484,14 @@ def test_pipelined_stage_is_bit_identical(block, name, nv, prec, limiter):
         dg.dolinc_sync_status(M, ws)
         res[sl], step[sl] = R.cpu().numpy(), x.cpu().numpy()
     if limiter == "none":
-        assert np.array_equal(res[1], res[-1])
-        assert np.array_equal(step[1], step[-1])
+        assert np.array_equal(res[1], res[lanes])
+        assert np.array_equal(step[1], step[lanes])
     else:
         ulp = 1e-14 if prec == "fp64" else 1e-6
-        assert rel(res[-1], res[1]) < ulp
+        assert rel(res[lanes], res[1]) < ulp
         inc = step[1] - to_dev(M, u).cpu().numpy()
-        assert np.abs(step[-1] - step[1]).max() < 100 * ulp * np.abs(inc).max()
-    got = M.from_lib(step[-1])
+        assert np.abs(step[lanes] - step[1]).max() < 100 * ulp * np.abs(inc).max()
+    got = M.from_lib(step[lanes])
     eno = {"none": 0, "eno3_flagged": 2, "first_order_flagged": 3}[limiter]
     want = O.run(u, oracle.Scheme(k=3, r=1, n_diff=2, nv=nv, eno=eno, troubled=flags, **fx), 1e-3, 2)
     tol = {"fp64": 1e-12, "fp32": 1e-6, "fp32_bf16": 1e-5}[prec]
@@ -506,7 +508,7 @@ def test_autotune_picks_a_valid_shape_and_keeps_parity(tmp_path):
     x = to_dev(M, u)
     cache = str(tmp_path / "tune.txt")
     t = dg.dolinc_autotune(M, sch, x, ws, cache_path=cache)
-    assert t["diff_lanes"] in (0, 1, 4, 8, -1, -4) and t["stage_lanes"] in (0, 1, 4, 8, -1) and not t["from_cache"]
+    assert t["diff_lanes"] in (0, 1, 4, 8, -1, -4) and t["stage_lanes"] in (0, 1, 4, 8, -1, -2) and not t["from_cache"]
     t2 = dg.dolinc_autotune(M, sch, x, ws, cache_path=cache)
     assert t2["from_cache"] and t2["stage_lanes"] == t["stage_lanes"]
     dt = 1e-3
