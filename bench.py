@@ -259,7 +259,10 @@ def run_dolinc(args):
     results = {args.precision: timed_run(args.precision, w["scheme"], args.steps, True)}
     if args.precision != "fp64":
         results["fp64"] = timed_run("fp64", w["scheme"], args.steps, False)
-    launches_per_step = int(sum(results[args.precision]["kn"])) / args.steps
+    kn_main = results[args.precision]["kn"]
+    # the profile brackets the face-centric stage pair (k_flux + k_gather) as one entry
+    pair = 2 if (results[args.precision]["tune"] or {}).get("stage_lanes") == -2 else 1
+    launches_per_step = (int(sum(kn_main)) + (pair - 1) * int(kn_main[KINDS.index("stage")])) / args.steps
     variants = {}
     if not args.no_variants and args.workload == "euler3d_tet64":
         o0 = w["info"]["order"]
