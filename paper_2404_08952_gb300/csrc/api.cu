@@ -216,11 +216,8 @@ WsLayout ws_layout(const dolinc_mesh *m, const dolinc_scheme *s)
     o += al256(nc * s->nv * sizeof(double));
     L.dacc = o;                                 // increment accumulator (bulk precision below FP64)
     if (s->precision != DOLINC_FP64) o += al256(nc * s->nv * sizeof(float));
-    L.flux = o;                                 // per-face flux records of the face-centric stage
-    {
-        const int fb = s->precision == DOLINC_FP64 ? 8 : 4;
-        o += al256((size_t)m->h.n_faces * rec_stride(s->nv, fb) * fb);
-    }
+    L.flux = o;                                 // per-face fluxes of the face-centric stage
+    o += al256((size_t)m->h.n_faces * s->nv * (s->precision == DOLINC_FP64 ? sizeof(double) : sizeof(float)));
     L.total = o;
     return L;
 }

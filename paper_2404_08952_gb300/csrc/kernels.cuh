@@ -184,7 +184,7 @@ struct StageArgs {
     float *dacc;                 // mode 2: increment accumulator D [v][c] (bulk precision)
     const void *rec_start;       // mode 2: order-0 record of the step's start state
     int rk;                      // mode 2: SSP-RK3 stage index 0, 1, 2
-    void *face_flux;             // face-centric stage: per-face flux records (bulk precision)
+    void *face_flux;             // face-centric stage: per-face fluxes [v][face] (bulk precision)
     unsigned *status;            // bit 0: non-finite output
     int k, r, mode, flux;
     double gamma, adv[3];
@@ -607,12 +607,9 @@ __device__ __forceinline__ void cell_epilogue(const DevMesh &mesh, const StageAr
 // ------------------------------------------------------------------ face-centric pair
 // k_flux evaluates every face once (thread per face, faces in owner order, canonical
 // owner -> neighbour orientation, a boundary face the flux of its cell's state) into
-// face_flux, one record of flux_stride values per face (16-byte vectors); k_gather
-// then sums each cell's signed fluxes in slot order and applies the stage epilogue.
-// The operands and the order of the sums are those of the one-thread-per-cell
-// kernel, whose results this pair reproduces.
-template <int NV, class R> DOL_HD constexpr int flux_stride() { return rec_stride(NV, (int)sizeof(R)); }
-
+// face_flux; k_gather then sums each cell's signed fluxes in slot order and applies
+// the stage epilogue.  The operands and the order of the sums are those of the
+// one-thread-per-cell kernel, whose results this pair reproduces.
 template <int DIM, int NV, int NS, int PREC>
 __global__ void __launch_bounds__(256) k_flux(DevMesh mesh, StageArgs a)
 {
@@ -625,7 +622,10 @@ __global__ void __launch_bounds__(256) k_flux(DevMesh mesh, StageArgs a)
     const bool own_flag = a.flags && a.flags[P];
     R F[NV];
     canon_flux<DIM, NV, NS, PREC>(a, src, P, N < 0 ? P : N, word, own_flag, F);
-    store_rec<R, NV, flux_stride<NV, R>(), R>(static_cast<R *>(a.face_flux), f, F);
+    R *out = static_cast<R *>(a.face_flux);
+    const long long nf = mesh.n_faces;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v * nf + f] = F[v];
 }
 
 template <int DIM, int NV, int PREC>
@@ -635,6 +635,7 @@ __global__ void __launch_bounds__(256) k_gather(DevMesh mesh, StageArgs a)
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= mesh.n_cells) return;
     const R *flux = static_cast<const R *>(a.face_flux);
+    const long long nf = mesh.n_faces;
     R res[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) res[v] = (R)0;
@@ -643,10 +644,11 @@ __global__ void __launch_bounds__(256) k_gather(DevMesh mesh, StageArgs a)
         const int2 sw = __ldg(mesh.slot2 + s);
         const long long f = (long long)((unsigned)sw.y >> 2);
         const bool side = sw.y & 1;
-        R F[NV];
-        load_rec<R, NV, flux_stride<NV, R>(), R>(flux, f, F);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) res[v] += side ? F[v] : -F[v];
+        for (int v = 0; v < NV; ++v) {
+            const R F = __ldg(flux + v * nf + f);
+            res[v] += side ? F : -F;
+        }
     }
     cell_epilogue<DIM, NV, PREC>(mesh, a, c, res);
 }
