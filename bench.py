@@ -407,7 +407,7 @@ def _sync_cpu(t):
 def run_indicator(args):
     """Learned troubled-cell indicator on the four-quadrant Riemann workload.
 
-    Trains the network on criterion labels of seeded runs (smaller mesh), judges its
+    Trains the network on criterion labels of seeded runs (smaller mesh), measures its
     misclassification on held-out runs, then advances one held-out problem on the full
     mesh with the limiter switched by (a) the network, FP32, (b) the criterion, FP32,
     (c) the criterion, FP64 (the plain FP64 GPU method), flagged faces taking the
@@ -432,7 +432,7 @@ def run_indicator(args):
     hist, pw = ind.train(net, X, Y, epochs=args.ind_epochs, batch=8192, lr=2e-3)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    # held-out judgement (seeds never trained on)
+    # held-out evaluation (seeds never trained on)
     Xh, Yh = [], []
     for x, y in ind.riemann_runs(mk, range(1000, 1000 + args.ind_eval_runs), run_steps, every,
                                  precision=args.precision):

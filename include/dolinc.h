@@ -48,7 +48,7 @@ typedef enum {
     DOLINC_OK = 0,
     DOLINC_ERR_INVALID_ARG = 1,     /* bad pointer, size, or scheme parameter */
     DOLINC_ERR_MESH = 2,            /* mesh descriptor fails validation */
-    DOLINC_ERR_UNSUPPORTED = 3,     /* valid request this build does not implement */
+    DOLINC_ERR_UNSUPPORTED = 3,     /* valid request the library does not implement */
     DOLINC_ERR_CUDA = 4,            /* a CUDA runtime call failed (message has the CUDA error) */
     DOLINC_ERR_DEVICE_TIMEOUT = 5,  /* a bounded device-side wait gave up */
     DOLINC_ERR_NONFINITE = 6,       /* a stage produced NaN or Inf */

@@ -4,7 +4,7 @@ Orchestration only: every step runs in libdolinc's kernels (stage, criterion,
 features, network forward/backward/Adam).  The criterion labels the cells of
 seeded four-quadrant Riemann runs in which it also drives the limiter of flagged
 faces; the network is trained on (features, labels) sampled along those runs and
-then replaces the criterion as the limiter's switch, the criterion judging its
+then replaces the criterion as the limiter's switch, the criterion measuring its
 misclassification rate.
 
 The limiter of flagged faces is either ENO3-DOLINC (Sec 2.4) or the first-order
