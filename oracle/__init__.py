@@ -57,13 +57,15 @@ class _Geom(C.Structure):
 
 class _Scheme(C.Structure):
     _fields_ = [("nv", C.c_int), ("k", C.c_int), ("r", C.c_int), ("n_diff", C.c_int), ("flux", C.c_int),
-                ("gamma", C.c_double), ("adv", C.c_double * 3), ("eno", C.c_int), ("troubled", C.c_void_p)]
+                ("gamma", C.c_double), ("adv", C.c_double * 3), ("eno", C.c_int), ("troubled", C.c_void_p),
+                ("bkind", C.c_void_p), ("bval", C.c_void_p)]
 
 
 def _declare(L):
     P = C.c_void_p
     L.or_geometry.argtypes = [P, P]
     L.or_differentials.argtypes = [P, P, C.c_int, C.c_int, P, P]
+    L.or_differentials_bc.argtypes = [P, P, C.c_int, C.c_int, P, P, P, P]
     L.or_coeff.argtypes = [C.c_int, C.c_int, C.c_double, P]
     L.or_phantoms.argtypes = [C.c_int, C.c_double, P, P, P]
     L.or_face_values.argtypes = [P, P, P, P, P, P, P, P]
@@ -103,7 +105,10 @@ class Scheme:
     n_diff: differential orders computed (>= what the stencil needs)."""
 
     def __init__(self, k=3, r=1, n_diff=None, flux="upwind", nv=1, gamma=1.4, adv=(1.0, 1.0, 0.0), eno=0,
-                 troubled=None):
+                 troubled=None, bkind=None, bval=None):
+        """bkind [n_faces] int (0/1 zero-gradient, 2 Dirichlet, 3 Neumann) and bval
+        [nv, n_faces] (face value, or outward normal gradient) describe the boundary
+        faces (Sec 2.6); None: every boundary face zero-gradient."""
         need = max(r, k - r - 2)
         if eno in (1, 2):
             need = max(need, 2)
@@ -115,6 +120,10 @@ class Scheme:
         self.adv = tuple(float(a) for a in adv) + (0.0,) * (3 - len(adv))
         self.eno = eno
         self.troubled = None if troubled is None else np.ascontiguousarray(troubled, dtype=np.uint8)
+        self.bkind = None if bkind is None else np.ascontiguousarray(bkind, dtype=np.int32)
+        self.bval = None if bval is None else np.ascontiguousarray(np.atleast_2d(bval), dtype=np.float64)
+        if (self.bkind is None) != (self.bval is None):
+            raise ValueError("bkind and bval go together")
 
     def _c(self):
         s = _Scheme()
@@ -124,6 +133,8 @@ class Scheme:
             s.adv[i] = self.adv[i]
         s.eno = self.eno
         s.troubled = _ptr(self.troubled) if self.troubled is not None else None
+        s.bkind = _ptr(self.bkind) if self.bkind is not None else None
+        s.bval = _ptr(self.bval) if self.bval is not None else None
         return s
 
 
@@ -162,13 +173,18 @@ class Oracle:
         self.neigh = k["face_neighbour"]
 
     # differentials: list of arrays, order m -> [nv, n_cells, dim**m]
-    def differentials(self, u, N, nv=None):
+    def differentials(self, u, N, nv=None, scheme=None):
+        """scheme (optional) supplies the boundary conditions (Scheme bkind/bval)."""
         u = np.ascontiguousarray(np.atleast_2d(u), dtype=np.float64)
         nv = u.shape[0]
         D = self.dim
         sizes = [nv * self.n_cells * D ** m for m in range(N + 1)]
         T = np.zeros(sum(sizes))
-        lib().or_differentials(C.byref(self._m), C.byref(self._g), nv, N, _ptr(u), _ptr(T))
+        if scheme is not None and scheme.bkind is not None:
+            lib().or_differentials_bc(C.byref(self._m), C.byref(self._g), nv, N, _ptr(u), _ptr(scheme.bkind),
+                                      _ptr(scheme.bval), _ptr(T))
+        else:
+            lib().or_differentials(C.byref(self._m), C.byref(self._g), nv, N, _ptr(u), _ptr(T))
         out, o = [], 0
         for m in range(N + 1):
             out.append(T[o:o + sizes[m]].reshape(nv, self.n_cells, D ** m))
@@ -178,7 +194,7 @@ class Oracle:
     def face_values(self, u, scheme):
         """(phiL, phiR, rL, rR): [nv, n_faces] owner-upwind / neighbour-upwind states
         and the ENO3 stencil offsets chosen (-1 on boundary faces)."""
-        _, T = self.differentials(u, scheme.n_diff)
+        _, T = self.differentials(u, scheme.n_diff, scheme=scheme)
         nv = scheme.nv
         L = np.zeros((nv, self.n_faces))
         R = np.zeros((nv, self.n_faces))
@@ -201,7 +217,7 @@ class Oracle:
 
     def criterion(self, u, scheme, kappa=4.0, eps=1e-3):
         """Troubled-cell flags [n_cells] (uint8) of the criterion in indicator_oracle.c."""
-        _, T = self.differentials(u, scheme.n_diff)
+        _, T = self.differentials(u, scheme.n_diff, scheme=scheme)
         flags = np.zeros(self.n_cells, dtype=np.uint8)
         s = scheme._c()
         if lib().or_criterion(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(T), float(kappa), float(eps),
@@ -211,7 +227,7 @@ class Oracle:
 
     def features(self, u, scheme, tiny=1e-6):
         """(own [n_cells, 6], x [n_cells, 24]) network inputs of indicator_oracle.c."""
-        _, T = self.differentials(u, scheme.n_diff)
+        _, T = self.differentials(u, scheme.n_diff, scheme=scheme)
         own = np.zeros((self.n_cells, 6))
         x = np.zeros((self.n_cells, 24))
         s = scheme._c()

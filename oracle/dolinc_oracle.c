@@ -66,6 +66,10 @@ typedef struct {
     int eno;          /* 0 fixed stencil, 1 ENO3 on every face, 2 ENO3 on faces touching a troubled cell,
                          3 first-order upwind (the cell's own average) on faces touching a troubled cell */
     const unsigned char *troubled;   /* [n_cells] for eno == 2, 3 */
+    const int *bkind;                /* [n_faces] boundary kind per face (NULL: every boundary face
+                                        zero-gradient): 0/1 zero-gradient, 2 Dirichlet, 3 Neumann */
+    const double *bval;              /* [nv][n_faces]: the face value (2) or the outward normal
+                                        gradient (3) */
 } or_scheme;
 
 static int ipow(int b, int e) { int p = 1; while (e-- > 0) p *= b; return p; }
@@ -215,12 +219,41 @@ static long toff(int D, int nv, long nc, int mm)
     return o * nv * nc;
 }
 
+/* Value of variable v on boundary face f of cell P (Sec 2.6): the prescribed value
+ * on a Dirichlet face; T_C + q delta on a Neumann face, q the outward normal gradient
+ * and delta the distance from the cell centroid to the face along the outward unit
+ * normal; the cell value on a zero-gradient face. */
+static double boundary_value(const or_geom *g, const int *bkind, const double *bval, long n_faces, long f, long P,
+                             int v, double tP)
+{
+    const int kind = bkind ? bkind[f] : 1;
+    if (kind == 2) return bval[(long)v * n_faces + f];
+    if (kind == 3) {
+        const double *S = &g->S[3*f];
+        double r[3];
+        vsub(&g->xf[3*f], &g->xc[3*P], r);
+        return tP + bval[(long)v * n_faces + f] * vdot(r, S) / vnorm(S);
+    }
+    return tP;
+}
+
 /* DOLINC differentials, Sec 2.3: T^(0) is the cell average; T^(m) is the
  * central-differencing (Gauss, linearly interpolated) gradient of T^(m-1):
  *   T^(m)_c = (1/V_c) sum_f S_{c,f} (x) [ w T^(m-1)_c + (1-w) T^(m-1)_nb ].
- * The new gradient index is the leading one.  Zero-gradient boundary faces carry
- * the cell value (Sec 2.6).  Buffer: order m at toff(m), laid out [v][c][D^m]. */
+ * The new gradient index is the leading one.  Boundary faces (Sec 2.6): the first
+ * gradient takes the boundary face value (boundary_value); higher orders take the
+ * cell's own differential (the auxiliary cell beyond the face carries the boundary
+ * cell's differentials).  Buffer: order m at toff(m), laid out [v][c][D^m]. */
+int or_differentials_bc(const or_mesh *m, const or_geom *g, int nv, int N, const double *u, const int *bkind,
+                        const double *bval, double *T);
+
 int or_differentials(const or_mesh *m, const or_geom *g, int nv, int N, const double *u, double *T)
+{
+    return or_differentials_bc(m, g, nv, N, u, NULL, NULL, T);
+}
+
+int or_differentials_bc(const or_mesh *m, const or_geom *g, int nv, int N, const double *u, const int *bkind,
+                        const double *bval, double *T)
 {
     const int D = m->dim;
     const long nc = m->n_cells;
@@ -237,7 +270,8 @@ int or_differentials(const or_mesh *m, const or_geom *g, int nv, int N, const do
             for (int v = 0; v < nv; ++v)
                 for (int a = 0; a < Ain; ++a) {
                     double tP = Ti[((long)v * nc + P) * Ain + a];
-                    double tf = Q >= 0 ? w * tP + (1.0 - w) * Ti[((long)v * nc + Q) * Ain + a] : tP;
+                    double tf = Q >= 0 ? w * tP + (1.0 - w) * Ti[((long)v * nc + Q) * Ain + a]
+                                       : (mm == 1 ? boundary_value(g, bkind, bval, m->n_faces, f, P, v, tP) : tP);
                     for (int k = 0; k < D; ++k) {
                         To[((long)v * nc + P) * Aout + k * Ain + a] += S[k] * tf / g->V[P];
                         if (Q >= 0) To[((long)v * nc + Q) * Aout + k * Ain + a] -= S[k] * tf / g->V[Q];
@@ -360,7 +394,10 @@ static void face_states(const or_mesh *m, const or_geom *g, const or_scheme *s, 
     const long nc = m->n_cells;
     long P = m->owner[f], Q = m->neigh[f];
     if (Q < 0) {
-        for (int v = 0; v < nv; ++v) { UL[v] = UR[v] = T[(long)v * nc + P]; if (rL) rL[v] = rR[v] = -1; }
+        for (int v = 0; v < nv; ++v) {
+            UL[v] = UR[v] = boundary_value(g, s->bkind, s->bval, m->n_faces, f, P, v, T[(long)v * nc + P]);
+            if (rL) rL[v] = rR[v] = -1;
+        }
         return;
     }
     double sh[3], xQ[3], dL[3], dR[3], a[3], b[3];
@@ -477,7 +514,7 @@ int or_residual(const or_mesh *m, const or_geom *g, const or_scheme *s, const do
 {
     double *T = malloc(sizeof(double) * (size_t)tsize(m->dim, s->nv, m->n_cells, s->n_diff));
     if (!T) return -1;
-    or_differentials(m, g, s->nv, s->n_diff, u, T);
+    or_differentials_bc(m, g, s->nv, s->n_diff, u, s->bkind, s->bval, T);
     or_residual_T(m, g, s, T, R);
     free(T);
     return 0;

@@ -376,3 +376,68 @@ def test_first_order_fallback_keeps_the_discrete_maximum_principle():
     assert fo.min() >= u0.min() - 1e-13 and fo.max() <= u0.max() + 1e-13
     ho = O.run(u0, oracle.Scheme(k=3, r=1, n_diff=2, flux="upwind", adv=adv), dt, 40)
     assert ho.min() < u0.min() - 1e-3 or ho.max() > u0.max() + 1e-3
+
+
+def _wall_channel(growth, ny=8, h0=0.02):
+    """Hexes periodic in x and z, walls at y = 0 and at the top; wall-normal spacing
+    growing by `growth` from h0 (a boundary-layer mesh)."""
+    ys = np.concatenate([[0.0], np.cumsum(h0 * growth ** np.arange(ny))])
+    return synth.hex_mesh(np.linspace(0.0, 1.0, 6), ys, np.linspace(0.0, 0.6, 4), periodic=(True, False, True))
+
+
+def _linear(O, a=(0.3, -1.7, 0.0), b=2.0):
+    return b + O.xc @ np.asarray(a)
+
+
+@pytest.mark.parametrize("growth", [1.0, 1.3, 1.5])
+def test_dirichlet_and_neumann_faces_make_the_gradient_exact(growth):
+    """Sec 2.6: a Dirichlet face carries its prescribed value, a Neumann face T_C +
+    q delta (delta the normal centroid-to-face distance).  On a stretched wall mesh
+    a linear field's Gauss gradient is then exact in every cell, the wall cells
+    included, and its second differential vanishes; zero-gradient walls give neither."""
+    m = _wall_channel(growth)
+    O = oracle.Oracle(m)
+    a = np.array([0.0, -1.7, 0.0])         # periodic in x and z: only the wall-normal slope
+    u = (2.0 + O.xc @ a)[None]
+    bnd = O.neigh < 0
+    n_hat = O.S / np.linalg.norm(O.S, axis=1)[:, None]
+    exact_f = 2.0 + O.xf @ a
+    for kind, val in ((2, exact_f), (3, n_hat @ a)):
+        bkind = np.where(bnd, kind, 0).astype(np.int32)
+        bval = np.where(bnd, val, 0.0)[None]
+        s = oracle.Scheme(k=3, r=1, n_diff=2, flux="upwind", adv=(1.0, 0.0, 0.0), bkind=bkind, bval=bval)
+        T, _ = O.differentials(u, 2, scheme=s)
+        assert np.abs(T[1][0] - a[None, :]).max() < 1e-11, kind
+        assert np.abs(T[2][0]).max() < 1e-8, kind
+    T0, _ = O.differentials(u, 2)
+    assert np.abs(T0[1][0] - a[None, :]).max() > 0.1             # zero-gradient walls are wrong here
+
+
+def test_boundary_face_states_and_near_wall_reconstruction():
+    """The face state on a Dirichlet face is the prescribed value, on a Neumann face
+    T_C + q delta; with exact wall data the USR3/CSR4 face values of a linear field
+    are exact at every interior face of a geometric (growth 1.4) strip, the faces
+    next to the wall included."""
+    widths = 0.03 * 1.4 ** np.arange(10)
+    m = synth.strip_mesh(widths, height=0.05, boundary="transmissive")
+    O = oracle.Oracle(m)
+    u = (1.0 + 3.0 * O.xc[:, 0])[None]
+    bnd = O.neigh < 0
+    bval = np.where(bnd, 1.0 + 3.0 * O.xf[:, 0], 0.0)[None]
+    bkind = np.where(bnd, 2, 0).astype(np.int32)
+    for k in (3, 4):
+        s = oracle.Scheme(k=k, r=1, n_diff=2, flux="upwind", adv=(1.0, 0.0), bkind=bkind, bval=bval)
+        L, R, _, _ = O.face_values(u, s)
+        xf = O.xf[:, 0]
+        np.testing.assert_allclose(L[0][bnd], bval[0][bnd], rtol=0, atol=1e-14)
+        inner = ~bnd & (np.abs(O.S[:, 0]) > 0)
+        np.testing.assert_allclose(L[0][inner], 1.0 + 3.0 * xf[inner], rtol=0, atol=1e-11)
+        np.testing.assert_allclose(R[0][inner], 1.0 + 3.0 * xf[inner], rtol=0, atol=1e-11)
+    # Neumann: T_C + q delta on the boundary faces
+    q = np.where(bnd, 3.0 * np.sign(O.S[:, 0]), 0.0)[None]
+    s = oracle.Scheme(k=3, r=1, n_diff=2, flux="upwind", adv=(1.0, 0.0), bkind=np.where(bnd, 3, 0), bval=q)
+    L, _, _, _ = O.face_values(u, s)
+    P = O.owner[bnd]
+    delta = np.abs(O.xf[bnd, 0] - O.xc[P, 0])            # normal distance to the end faces
+    np.testing.assert_allclose(L[0][bnd], u[0][P] + q[0][bnd] * delta, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(L[0][bnd], 1.0 + 3.0 * O.xf[bnd, 0], rtol=0, atol=1e-13)
