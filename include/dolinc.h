@@ -74,7 +74,10 @@ enum { DOLINC_RENUMBER_NONE = 0, DOLINC_RENUMBER_MORTON = 1 };
  *   face_neighbour       [n_faces] neighbour cell, or -1 on a boundary face
  *   face_periodic_shift  [n_faces][dim] translation carrying the neighbour cell next to
  *                        the owner across a periodic face (0 elsewhere); NULL = none
- *   boundary_kind        [n_faces] 0 interior/periodic, 1 zero-gradient (transmissive);
+ *   boundary_kind        [n_faces] 0 interior/periodic; on boundary faces (Sec 2.6)
+ *                        1 zero-gradient (transmissive), 2 Dirichlet (prescribed face
+ *                        value), 3 Neumann (prescribed outward normal gradient); the
+ *                        values of 2 and 3 come from dolinc_set_boundary_values.
  *                        NULL = all boundary faces zero-gradient
  *   cell_face_offsets,   optional CSR cell -> faces (NULL to skip); when given, every
  *   cell_faces           face must appear in its owner's and neighbour's lists
@@ -344,6 +347,20 @@ dolinc_status dolinc_batch_autotune(dolinc_batch *batch, const dolinc_scheme *sc
 /* Cell flags for DOLINC_LIMIT_ENO3_FLAGGED / FIRST_ORDER_FLAGGED: flags_dev [n_cells] uint8 (library order),
  * non-zero = troubled.  The pointer is kept by the mesh until replaced or NULL. */
 dolinc_status dolinc_set_flags(dolinc_mesh *mesh, const uint8_t *flags_dev);
+
+/* Values of the Dirichlet and Neumann boundary faces (Sec 2.6: the boundary needs no
+ * special treatment beyond the low-order one; the auxiliary cell beyond a face obeys
+ * the condition).  values_host [nv][n_faces] in the caller's face order (entries of
+ * other faces are not read): the face value T_f on a Dirichlet face, the outward
+ * normal gradient q on a Neumann face, where T_f = T_C + q delta with delta the
+ * distance from the cell centroid to the face along the outward unit normal.  The
+ * first differential pass takes T_f as the face value of the Gauss gradient; higher
+ * orders take the boundary cell's own differential; the face state (both
+ * orientations) is T_f.  The library copies the values (synchronous); every compute
+ * call with a scheme of nv variables needs values set for that nv.  Errors:
+ * INVALID_ARG for nv outside 1..5, a mesh without such faces, null or non-finite
+ * values.  Batches take no such meshes. */
+dolinc_status dolinc_set_boundary_values(dolinc_mesh *mesh, int nv, const double *values_host);
 
 /* Synchronises `stream`, reads and clears the device status word in ws_dev:
  * DOLINC_ERR_NONFINITE if a stage wrote NaN/Inf since the last call,

@@ -26,7 +26,7 @@ ABI_SYMBOLS = (
     "dolinc_mesh_create", "dolinc_mesh_destroy", "dolinc_mesh_get_info", "dolinc_mesh_permutation",
     "dolinc_mesh_geometry", "dolinc_workspace_size", "dolinc_workspace_init", "dolinc_diff_layout",
     "dolinc_differentials", "dolinc_reconstruct_faces", "dolinc_residual", "dolinc_rk_stage",
-    "dolinc_rk_step", "dolinc_set_flags", "dolinc_sync_status", "dolinc_profile_enable",
+    "dolinc_rk_step", "dolinc_set_flags", "dolinc_set_boundary_values", "dolinc_sync_status", "dolinc_profile_enable",
     "dolinc_profile_read", "dolinc_rk_step_noalloc", "dolinc_autotune", "dolinc_set_tuning",
     "dolinc_criterion", "dolinc_indicator_features", "dolinc_mlp_create", "dolinc_mlp_destroy",
     "dolinc_mlp_get_params", "dolinc_mlp_set_params", "dolinc_mlp_forward", "dolinc_mlp_loss_grad",
@@ -83,7 +83,8 @@ def load(path=LIB_PATH):
             "dolinc_residual": [P, P, P, P, P, S, P],
             "dolinc_rk_stage": [P, P, D, I, P, P, P, P, S, P],
             "dolinc_rk_step": [P, P, D, P, P, S, P],
-            "dolinc_set_flags": [P, P], "dolinc_sync_status": [P, P, P], "dolinc_last_error": [],
+            "dolinc_set_flags": [P, P], "dolinc_set_boundary_values": [P, C.c_int, P],
+            "dolinc_sync_status": [P, P, P], "dolinc_last_error": [],
             "dolinc_profile_enable": [P, I], "dolinc_profile_read": [P, P, P],
             "dolinc_rk_step_noalloc": [P, P, D, P, P],
             "dolinc_autotune": [P, P, P, P, S, C.c_char_p, P, P], "dolinc_set_tuning": [P, P, P],
@@ -305,6 +306,13 @@ def dolinc_set_tuning(mesh, scheme, diff_lanes=4, diff_block=256, stage_lanes=4,
     t = _Tuning()
     t.diff_lanes, t.diff_block, t.stage_lanes, t.stage_block = diff_lanes, diff_block, stage_lanes, stage_block
     _check(load().dolinc_set_tuning(mesh.handle, C.byref(s), C.byref(t)))
+
+
+def dolinc_set_boundary_values(mesh, values):
+    """values [nv, n_faces] (caller face order): Dirichlet face values / Neumann outward
+    normal gradients of the faces whose boundary_kind is 2 / 3."""
+    v = np.ascontiguousarray(np.atleast_2d(values), dtype=np.float64)
+    _check(load().dolinc_set_boundary_values(mesh.handle, int(v.shape[0]), _ptr(v)))
 
 
 def dolinc_set_flags(mesh, flags):

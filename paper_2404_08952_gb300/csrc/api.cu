@@ -1,6 +1,7 @@
 // C ABI of the DOLINC stage library (include/dolinc.h).
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <chrono>
@@ -72,6 +73,8 @@ struct dolinc_mesh {
     int device = 0;
     std::vector<void *> allocs;
     const uint8_t *flags = nullptr;
+    int bv_nv = 0;                     // variables of the boundary values set (0: none yet)
+    std::vector<int32_t> bidx_h;       // host copy of DevMesh::bidx
     int max_faces = 0;                 // largest number of slots of a cell
     std::map<std::string, Tune> tuned;  // launch shapes chosen by dolinc_autotune, per scheme
     // per-kernel timing (dolinc_profile_enable)
@@ -180,6 +183,9 @@ dolinc_status check_scheme(const dolinc_mesh *m, const dolinc_scheme *s)
     } else {
         return fail(DOLINC_ERR_INVALID_ARG, "unknown flux");
     }
+    if (m->d.n_bv > 0 && m->bv_nv != s->nv)
+        return fail(DOLINC_ERR_INVALID_ARG, "the mesh has Dirichlet/Neumann faces: set their values for nv = " +
+                                                std::to_string(s->nv) + " with dolinc_set_boundary_values");
     if ((s->limiter == DOLINC_LIMIT_ENO3_FLAGGED || s->limiter == DOLINC_LIMIT_FIRST_ORDER_FLAGGED) && !m->flags)
         return fail(DOLINC_ERR_INVALID_ARG, "flagged limiter without flags (dolinc_set_flags)");
     return DOLINC_OK;
@@ -310,6 +316,7 @@ void run_diffs(dolinc_mesh *m, const PathFns *p, void *ws, const WsLayout &L, si
         timed(m, mm, st, [&] {
             p->diff(m->d, mm, B(ws, mm == 1 ? o0off : L.ord[mm - 1]), B(ws, L.ord[mm]), t,
                     reinterpret_cast<unsigned *>(B(ws, L.status)), st);
+            if (mm == 1) p->bnd_grad(m->d, B(ws, o0off), B(ws, L.ord[1]), st);
         });
 }
 
@@ -419,6 +426,45 @@ dolinc_status upload_mesh(dolinc_mesh *m)
     d.n_slots = (int)ns;
     for (int ti = 0; ti < 3; ++ti) d.max_tile_faces[ti] = mtf[ti];
     d.max_slots = m->max_faces;
+    // Dirichlet / Neumann faces: index, kind, normal distance, and the cells holding them
+    std::vector<int32_t> bidx(nf, -1), bcell, bcell_off(1, 0), bcell_face;
+    std::vector<int8_t> bkind;
+    std::vector<double> bdelta64;
+    std::vector<float> bdelta32;
+    for (int64_t f = 0; f < nf && !h.fkind.empty(); ++f) {
+        if (h.fkind[f] < 2) continue;
+        bidx[f] = (int32_t)bkind.size();
+        bkind.push_back(h.fkind[f]);
+        const double *S = &h.fS[3 * f], *xf = &h.fxf[3 * f], *xc = &h.xc[3 * h.fo[f]];
+        const double sn = std::sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+        const double dl = ((xf[0] - xc[0]) * S[0] + (xf[1] - xc[1]) * S[1] + (xf[2] - xc[2]) * S[2]) / sn;
+        bdelta64.push_back(dl);
+        bdelta32.push_back((float)dl);
+    }
+    // faces are sorted by owner, so a cell's boundary faces are consecutive
+    for (int64_t f = 0; f < nf; ++f) {
+        if (bidx[f] < 0) continue;
+        if (bcell.empty() || bcell.back() != (int32_t)h.fo[f]) {
+            if (!bcell.empty()) bcell_off.push_back((int32_t)bcell_face.size());
+            bcell.push_back((int32_t)h.fo[f]);
+        }
+        bcell_face.push_back((int32_t)f);
+    }
+    if (!bcell.empty()) bcell_off.push_back((int32_t)bcell_face.size());
+    m->bidx_h = bidx;
+    d.n_bv = (int)bkind.size();
+    d.n_bcell = (int)bcell.size();
+    d.bval64 = nullptr;
+    d.bval32 = nullptr;
+    if (d.n_bv > 0) {
+        if ((st = upload(m, bidx, &d.bidx)) || (st = upload(m, bkind, &d.bkind)) ||
+            (st = upload(m, bdelta64, &d.bdelta64)) || (st = upload(m, bdelta32, &d.bdelta32)) ||
+            (st = upload(m, bcell, &d.bcell)) || (st = upload(m, bcell_off, &d.bcell_off)) ||
+            (st = upload(m, bcell_face, &d.bcell_face)))
+            return st;
+    } else {
+        d.bidx = nullptr;
+    }
     if ((st = upload(m, off, &d.off)) || (st = upload(m, slot2, &d.slot2)) || (st = upload(m, sk64, &d.slotk64)) ||
         (st = upload(m, sk32, &d.slotk32)) || (st = upload(m, ck64, &d.cellk64)) ||
         (st = upload(m, ck32, &d.cellk32)) || (st = upload(m, f64, &d.face64)) || (st = upload(m, f32, &d.face32)) ||
@@ -526,6 +572,7 @@ dolinc_status dolinc_differentials(dolinc_mesh *m, const dolinc_scheme *s, const
         const int b = elem_bytes(s->precision, mm), sd = stride_h(m->h.dim, s->nv, mm, s->precision);
         timed(m, mm, cs, [&] {
             p->diff(m->d, mm, prev, B(diff, o), tune_for(m, s), reinterpret_cast<unsigned *>(B(ws, L.status)), cs);
+            if (mm == 1) p->bnd_grad(m->d, prev, B(diff, o), cs);
         });
         prev = B(diff, o);
         o += al256((size_t)m->h.n_cells * sd * b);
@@ -1003,6 +1050,8 @@ dolinc_status dolinc_batch_create(dolinc_mesh *const *meshes, int n, dolinc_batc
     for (int b = 0; b < n; ++b) {
         if (!meshes[b]) return fail(DOLINC_ERR_INVALID_ARG, "null mesh in batch");
         if (meshes[b]->h.dim != meshes[0]->h.dim) return fail(DOLINC_ERR_INVALID_ARG, "meshes of different dimension");
+        if (meshes[b]->d.n_bv > 0)
+            return fail(DOLINC_ERR_UNSUPPORTED, "batched steps take no Dirichlet/Neumann boundary faces");
     }
     dolinc_batch *bt = new (std::nothrow) dolinc_batch();
     if (!bt) return fail(DOLINC_ERR_OOM, "host allocation");
@@ -1271,6 +1320,44 @@ dolinc_status dolinc_set_tuning(dolinc_mesh *m, const dolinc_scheme *s, const do
     x.stage_lpc = t->stage_lanes;
     x.stage_block = t->stage_block;
     m->tuned[scheme_key(m, s)] = x;
+    return DOLINC_OK;
+}
+
+dolinc_status dolinc_set_boundary_values(dolinc_mesh *m, int nv, const double *values)
+{
+    if (!m) return fail(DOLINC_ERR_INVALID_ARG, "null mesh");
+    if (nv < 1 || nv > 5) return fail(DOLINC_ERR_INVALID_ARG, "nv must be in 1..5");
+    if (m->d.n_bv == 0) return fail(DOLINC_ERR_INVALID_ARG, "the mesh has no Dirichlet/Neumann faces");
+    if (!values) return fail(DOLINC_ERR_INVALID_ARG, "null values");
+    const HostMesh &h = m->h;
+    const int nb = m->d.n_bv;
+    std::vector<double> v64((size_t)nv * nb);
+    std::vector<float> v32((size_t)nv * nb);
+    for (int64_t f = 0; f < h.n_faces; ++f) {
+        if (h.fkind[f] < 2) continue;
+        const int b = m->bidx_h[f];
+        const int64_t ext = h.face_ext[f];
+        for (int v = 0; v < nv; ++v) {
+            double x = values[(int64_t)v * h.n_faces + ext];
+            // a Neumann gradient is given along the caller's outward normal, which is
+            // the internal one (a boundary face's owner is its only cell)
+            if (!std::isfinite(x)) return fail(DOLINC_ERR_INVALID_ARG, "non-finite boundary value");
+            v64[(size_t)v * nb + b] = x;
+            v32[(size_t)v * nb + b] = (float)x;
+        }
+    }
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != m->device) CU(cudaSetDevice(m->device));
+    dolinc_status st = DOLINC_OK;
+    const double *p64 = nullptr;
+    const float *p32 = nullptr;
+    if (!(st = upload(m, v64, &p64))) st = upload(m, v32, &p32);
+    if (cur != m->device) cudaSetDevice(cur);
+    if (st) return st;
+    m->d.bval64 = p64;
+    m->d.bval32 = p32;
+    m->bv_nv = nv;
     return DOLINC_OK;
 }
 

@@ -21,6 +21,16 @@ struct DevMesh {
     const int32_t *fown;         // [n_cells+1] first internal face owned by each cell
     int max_tile_faces[3];       // most faces owned by a tile of 64 / 128 / 256 cells
     int max_slots;               // most slots of one cell
+    // Dirichlet / Neumann boundary faces (Sec 2.6), n_bv of them
+    int n_bv;
+    const int32_t *bidx;         // [n_faces] index of the face among them, -1 otherwise (null: none)
+    const int8_t *bkind;         // [n_bv] 2 Dirichlet, 3 Neumann
+    const double *bdelta64;      // [n_bv] centroid-to-face distance along the outward unit normal
+    const float *bdelta32;
+    const double *bval64;        // [nv][n_bv] face value (Dirichlet) or outward normal gradient
+    const float *bval32;         //   (Neumann), set by dolinc_set_boundary_values (null until then)
+    int n_bcell;                 // cells with such faces, and their faces (CSR)
+    const int32_t *bcell, *bcell_off, *bcell_face;
 };
 
 }  // namespace dol

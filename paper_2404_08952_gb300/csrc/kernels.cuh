@@ -37,13 +37,36 @@ template <> struct Geo<double> {
     static __device__ __forceinline__ const double *cellk(const DevMesh &m) { return m.cellk64; }
     static __device__ __forceinline__ const double *face(const DevMesh &m) { return m.face64; }
     static __device__ __forceinline__ int nb_of(double w) { return (int)__double_as_longlong(w); }
+    static __device__ __forceinline__ const double *bval(const DevMesh &m) { return m.bval64; }
+    static __device__ __forceinline__ const double *bdelta(const DevMesh &m) { return m.bdelta64; }
 };
 template <> struct Geo<float> {
     static __device__ __forceinline__ const float *slotk(const DevMesh &m) { return m.slotk32; }
     static __device__ __forceinline__ const float *cellk(const DevMesh &m) { return m.cellk32; }
     static __device__ __forceinline__ const float *face(const DevMesh &m) { return m.face32; }
     static __device__ __forceinline__ int nb_of(float w) { return __float_as_int(w); }
+    static __device__ __forceinline__ const float *bval(const DevMesh &m) { return m.bval32; }
+    static __device__ __forceinline__ const float *bdelta(const DevMesh &m) { return m.bdelta32; }
 };
+
+// State on boundary face f of a cell whose state is U (Sec 2.6): a Dirichlet face
+// takes its prescribed value, a Neumann face U + q delta (q the outward normal
+// gradient, delta the centroid-to-face normal distance); other faces keep U.
+template <int NV, class R>
+__device__ __forceinline__ void boundary_state(const DevMesh &mesh, int f, R *U)
+{
+    if (!mesh.bidx) return;
+    const int b = __ldg(mesh.bidx + f);
+    if (b < 0) return;
+    const R *val = Geo<R>::bval(mesh);
+    const bool dirichlet = __ldg(mesh.bkind + b) == 2;
+    const R delta = __ldg(Geo<R>::bdelta(mesh) + b);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const R x = __ldg(val + (long long)v * mesh.n_bv + b);
+        U[v] = dirichlet ? x : U[v] + x * delta;
+    }
+}
 
 template <class R, bool LDG = true> __device__ __forceinline__ void ld4(const R *p, R &a, R &b, R &c, R &d)
 {
@@ -408,6 +431,7 @@ __device__ __forceinline__ void canon_flux(const StageArgs &a, const Src &src, i
         R U[NV];
         load_rec<typename PrecT<PREC>::T0, NV, ord_stride<DIM, NV, 0, PREC>(), R, Src::LDG>(src.template rec<0>(c), 0,
                                                                                             U);
+        boundary_state<NV, R>(src.mesh, f, U);
         phys_flux<DIM, NV, R>(a, U, fr, F);
     } else {
         const int P = side ? nb : c, N = side ? c : nb;
@@ -602,6 +626,50 @@ __device__ __forceinline__ void cell_epilogue(const DevMesh &mesh, const StageAr
     }
     if (a.mode != 0 && nxt) store_rec<T0, NV, S0, R>(nxt, c, nv_out);
     if (bad) atomicOr(a.status, 1u);
+}
+
+// ------------------------------------------------------------------ Dirichlet / Neumann faces
+// After the first differential pass (which gives every boundary face the cell's own
+// value): each cell with Dirichlet/Neumann faces adds S_f (T_f - T_C) / V_c per such
+// face to its first-order record, so that the Gauss gradient takes the boundary face
+// value T_f (Sec 2.6).  Higher orders keep the cell's own differentials on the face.
+template <int DIM, int NV, int PREC>
+__global__ void __launch_bounds__(128) k_bnd_grad(DevMesh mesh, const void *__restrict__ o0_v, void *__restrict__ o1_v)
+{
+    using R = typename PrecT<PREC>::R;
+    using T0 = typename OrdT<PREC, 0>::T;
+    using T1 = typename OrdT<PREC, 1>::T;
+    constexpr int S0 = ord_stride<DIM, NV, 0, PREC>(), S1 = ord_stride<DIM, NV, 1, PREC>();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= mesh.n_bcell) return;
+    const int c = __ldg(mesh.bcell + i);
+    R U[NV], G[NV * DIM];
+    load_rec<T0, NV, S0, R>(static_cast<const T0 *>(o0_v), c, U);
+    T1 *o1 = static_cast<T1 *>(o1_v);
+    load_rec<T1, NV * DIM, S1, R, false>(o1, c, G);
+    R w0, w1, w2, iv;
+    ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, w0, w1, w2, iv);
+    for (int k = __ldg(mesh.bcell_off + i); k < __ldg(mesh.bcell_off + i + 1); ++k) {
+        const int f = __ldg(mesh.bcell_face + k);
+        R fr[8];
+        {
+            const R *p = Geo<R>::face(mesh) + 8ll * f;
+            ld4<R>(p, fr[0], fr[1], fr[2], fr[3]);
+            ld4<R>(p + 4, fr[4], fr[5], fr[6], fr[7]);
+        }
+        R Uf[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Uf[v] = U[v];
+        boundary_state<NV, R>(mesh, f, Uf);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const R dT = (Uf[v] - U[v]) * iv;
+            G[v * DIM + 0] += fr[4] * dT;
+            G[v * DIM + 1] += fr[5] * dT;
+            if constexpr (DIM == 3) G[v * DIM + 2] += fr[6] * dT;
+        }
+    }
+    store_rec<T1, NV * DIM, S1, R>(o1, c, G);
 }
 
 // ------------------------------------------------------------------ face-centric pair
@@ -970,6 +1038,7 @@ __global__ void __launch_bounds__(128) k_faces(DevMesh mesh, StageArgs a, double
     if (N < 0) {
         load_rec<typename PrecT<PREC>::T0, NV, ord_stride<DIM, NV, 0, PREC>(), R>(
             static_cast<const typename PrecT<PREC>::T0 *>(a.ord[0]), P, UL);
+        boundary_state<NV, R>(mesh, i, UL);
 #pragma unroll
         for (int v = 0; v < NV; ++v) UR[v] = UL[v];
     } else {

@@ -39,6 +39,7 @@ struct PathFns {
     void (*diff)(const DevMesh &, int M, const void *, void *, const Tune &, unsigned *, cudaStream_t);
     void (*stage)(const DevMesh &, const StageArgs &, const Tune &, cudaStream_t);
     void (*faces)(const DevMesh &, const StageArgs &, double *, double *, cudaStream_t);
+    void (*bnd_grad)(const DevMesh &, const void *, void *, cudaStream_t);
 };
 
 inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
@@ -242,7 +243,11 @@ template <int DIM, int NV, int NS, int PREC> struct Path {
     {
         k_faces<DIM, NV, NS, PREC><<<nblk(m.n_faces, 128), 128, 0, s>>>(m, a, fL, fR);
     }
-    static PathFns fns() { return PathFns{&pack, &diff, &stage, &faces}; }
+    static void bnd_grad(const DevMesh &m, const void *o0, void *o1, cudaStream_t s)
+    {
+        if (m.n_bcell > 0) k_bnd_grad<DIM, NV, PREC><<<nblk(m.n_bcell, 128), 128, 0, s>>>(m, o0, o1);
+    }
+    static PathFns fns() { return PathFns{&pack, &diff, &stage, &faces, &bnd_grad}; }
 };
 
 // Persistent batched stage (k_batch_stage), launched cooperatively.

@@ -123,8 +123,8 @@ std::string build_host_mesh(const dolinc_mesh_desc &d, HostMesh &m)
         if (N < -1 || N >= nc) return fmt("face %lld: neighbour %lld out of range", f, N);
         if (N < 0) {
             ++nb;
-            if (d.boundary_kind && d.boundary_kind[f] != 1)
-                return fmt("face %lld: boundary kind %lld unsupported (only 1 = zero-gradient)", f,
+            if (d.boundary_kind && (d.boundary_kind[f] < 1 || d.boundary_kind[f] > 3))
+                return fmt("face %lld: boundary kind %lld unsupported (1 zero-gradient, 2 Dirichlet, 3 Neumann)", f,
                            (long long)d.boundary_kind[f]);
         } else if (d.boundary_kind && d.boundary_kind[f] != 0) {
             return fmt("face %lld: interior face with boundary kind %lld", f, (long long)d.boundary_kind[f]);
@@ -267,6 +267,7 @@ std::string build_host_mesh(const dolinc_mesh_desc &d, HostMesh &m)
     m.fg.resize(nf);
     m.face_ext.resize(nf);
     m.face_flip.resize(nf);
+    m.fkind.assign(nf, 0);
     m.g_min = 1e300;
     m.g_max = 0;
     for (int64_t i = 0; i < nf; ++i) {
@@ -276,6 +277,7 @@ std::string build_host_mesh(const dolinc_mesh_desc &d, HostMesh &m)
         m.fn[i] = k.n;
         m.face_ext[i] = f;
         m.face_flip[i] = k.flip ? 1 : 0;
+        if (k.n < 0) m.fkind[i] = (int8_t)(d.boundary_kind ? d.boundary_kind[f] : 1);
         // caller-orientation quantities first
         V3 s = S[f], x = xf[f];
         V3 xP = xcold[d.face_owner[f]];

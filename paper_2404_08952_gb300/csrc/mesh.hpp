@@ -25,6 +25,7 @@ struct HostMesh {
     std::vector<double> fw, fg;         // Eq 3 weight of the internal owner, Eq 4 growth rate
     std::vector<int64_t> face_ext;      // internal -> caller face
     std::vector<int8_t> face_flip;      // 1: internal orientation opposite to the caller's
+    std::vector<int8_t> fkind;          // 0 interior, boundary: 1 zero-gradient, 2 Dirichlet, 3 Neumann
     // slots
     std::vector<int32_t> off;           // [n_cells+1]
     std::vector<int32_t> snb;           // neighbour cell of each slot (self on boundary)
