@@ -669,6 +669,113 @@ def run_hexprism(args):
     print(json.dumps(line), flush=True)
 
 
+def bl_mesh(growth, h0=0.002, ymax=0.3, nx=12, nz=3, x0=0.5, x1=1.0, dz=0.01):
+    """Boundary-layer mesh: hexes over x in [x0, x1] (transmissive ends), wall-normal
+    spacing h0 growing by `growth` up to ymax, nz cells of width dz across
+    (periodic); Dirichlet faces on the wall (y = 0) and on the top."""
+    import synth
+    ys = [0.0]
+    h = h0
+    while ys[-1] < ymax:
+        ys.append(ys[-1] + h)
+        h *= growth
+    m = synth.hex_mesh(np.linspace(x0, x1, nx + 1), np.array(ys), np.linspace(0.0, nz * dz, nz + 1),
+                       periodic=(False, False, True))
+    return m
+
+
+def run_blasius(args):
+    """Single-step reconstruction on laminar boundary-layer meshes (the paper's
+    boundary-layer case, with its own Blasius data: cell averages of the Blasius
+    velocity, Dirichlet wall and top faces).  For wall-normal growth rates 1.1..1.5 and
+    stencils USR3, CSR4, USR5: the L2 error of the reconstructed wall-parallel face
+    values (both orientations) against the Blasius solution at the face centres, the
+    GPU's agreement with the oracle, and the residual throughput with Dirichlet walls
+    on a 1.2M-cell mesh of the same family."""
+    import synth
+    from synth import fields
+    import oracle
+    t_all = time.perf_counter()
+    growths = (1.1, 1.2, 1.3, 1.4, 1.5)
+    stencils = ((3, 1, 1), (4, 1, 1), (5, 2, 2))
+    host = {}
+    for g in growths:
+        m = bl_mesh(g)
+        O = oracle.Oracle(m)
+        bnd = O.neigh < 0
+        cap = bnd & ((np.abs(O.xf[:, 1]) < 1e-12) | (O.xf[:, 1] > 0.29))
+        m["boundary_kind"] = np.where(cap, 2, np.where(bnd, 1, 0)).astype(np.int32)
+        ex = fields.blasius(O.xf)
+        u0 = synth.cell_average(m, fields.blasius, q=4, nv=2)
+        rows = (~bnd) & (np.abs(O.S[:, 1]) > 0.5 * np.linalg.norm(O.S, axis=1))
+        host[g] = (m, O, cap, ex, u0, rows)
+    import torch
+    import paper_2404_08952_gb300 as dg
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    forms = {}
+    worst = 0.0
+    for g in growths:
+        m, O, cap, ex, u0, rows = host[g]
+        M = dg.Mesh(m)
+        for (k, r, nd) in stencils:
+            key = "growth%.1f_k%d_r%d" % (g, k, r)
+            out = {"cells": M.n_cells}
+            for prec in ("fp64", "fp32"):
+                errs = []
+                for v, name in ((0, "u"), (1, "v")):
+                    bval = np.where(cap, np.where(np.abs(O.xf[:, 1]) < 1e-12, 0.0, ex[:, v]), 0.0)[None]
+                    dg.dolinc_set_boundary_values(M, bval)
+                    sch = dg.Scheme(k=k, r=r, n_diff=nd, nv=1, precision=prec, flux="upwind", adv=(1.0, 0.0, 0.0))
+                    ws = dg.workspace(M, sch)
+                    fL = torch.zeros((1, O.n_faces), dtype=torch.float64, device="cuda")
+                    fR = torch.zeros_like(fL)
+                    dg.dolinc_reconstruct_faces(M, sch, torch.from_numpy(M.to_lib(u0[v:v + 1])).cuda(), fL, fR, ws)
+                    L, R = fL.cpu().numpy()[0], fR.cpu().numpy()[0]
+                    e = np.concatenate([L[rows] - ex[rows, v], R[rows] - ex[rows, v]])
+                    errs.append(float(np.sqrt(np.mean(e ** 2)) / np.abs(ex[rows, v]).max()))
+                    if prec == "fp64":
+                        osch = oracle.Scheme(k=k, r=r, n_diff=nd, flux="upwind", adv=(1.0, 0.0, 0.0),
+                                             bkind=m["boundary_kind"], bval=bval)
+                        OL, OR, _, _ = O.face_values(u0[v:v + 1], osch)
+                        d = max(np.abs(L - OL[0]).max(), np.abs(R - OR[0]).max()) / np.abs(OL).max()
+                        worst = max(worst, float(d))
+                out["l2_rel_error_u_" + prec], out["l2_rel_error_v_" + prec] = errs
+            forms[key] = out
+    # residual throughput with Dirichlet walls on a large mesh of the family
+    m = bl_mesh(1.1, nx=400, nz=100)
+    bnd = np.asarray(m["face_neighbour"]) < 0
+    nb = np.asarray(m["face_owner"]).shape[0]
+    kinds = np.where(bnd, 2, 0).astype(np.int32)
+    m["boundary_kind"] = kinds
+    M = dg.Mesh(m)
+    dg.dolinc_set_boundary_values(M, np.zeros((1, nb)))
+    sch = dg.Scheme(k=3, r=1, n_diff=2, nv=1, precision="fp32", flux="upwind", adv=(1.0, 0.0, 0.0))
+    ws = dg.workspace(M, sch)
+    u = torch.ones((1, M.n_cells), dtype=torch.float64, device="cuda")
+    Rr = torch.zeros_like(u)
+    dg.dolinc_autotune(M, sch, u, ws)
+    for _ in range(args.warmup):
+        dg.dolinc_residual(M, sch, u, Rr, ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        dg.dolinc_residual(M, sch, u, Rr, ws)
+    e1.record()
+    torch.cuda.synchronize()
+    dg.dolinc_sync_status(M, ws)
+    ms = e0.elapsed_time(e1) / args.steps
+    line = {"metric": METRIC, "value": M.n_cells / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "blasius_bl", "growth_rates": list(growths),
+                       "stencils_k_r": [[k, r] for k, r, _ in stencils], "nu": 1e-3, "x_range": [0.5, 1.0],
+                       "first_cell": 0.002, "y_max": 0.3, "value_from": "residual evaluations, %d cells, "
+                       "Dirichlet walls, FP32 USR3 n_diff 2" % M.n_cells},
+            "forms": forms, "gpu_vs_oracle_fp64_max_rel": worst, "seconds_total": time.perf_counter() - t_all}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     """The oracle as the reference arm: host cores, a bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -738,6 +845,8 @@ def main():
         run_batch(args)
     elif args.workload == "adv3d_hexprism":
         run_hexprism(args)
+    elif args.workload == "blasius_bl":
+        run_blasius(args)
     else:
         run_dolinc(args)
 

@@ -163,7 +163,21 @@ int needed_order(const dolinc_scheme &s)
     return need < 1 ? 1 : need;
 }
 
+dolinc_status check_scheme_shape(const dolinc_mesh *m, const dolinc_scheme *s);
+
+// A compute call: the scheme fits the mesh, and the Dirichlet/Neumann values are set.
 dolinc_status check_scheme(const dolinc_mesh *m, const dolinc_scheme *s)
+{
+    dolinc_status st = check_scheme_shape(m, s);
+    if (st) return st;
+    if (m->d.n_bv > 0 && m->bv_nv != s->nv)
+        return fail(DOLINC_ERR_INVALID_ARG, "the mesh has Dirichlet/Neumann faces: set their values for nv = " +
+                                                std::to_string(s->nv) + " with dolinc_set_boundary_values");
+    return DOLINC_OK;
+}
+
+// The scheme's parameters and their fit to the mesh (sizes, layouts, tuning).
+dolinc_status check_scheme_shape(const dolinc_mesh *m, const dolinc_scheme *s)
 {
     if (!m || !s) return fail(DOLINC_ERR_INVALID_ARG, "null mesh or scheme");
     if (s->k < 1 || s->r < 0 || s->r >= s->k) return fail(DOLINC_ERR_INVALID_ARG, "bad stencil (k, r)");
@@ -183,9 +197,6 @@ dolinc_status check_scheme(const dolinc_mesh *m, const dolinc_scheme *s)
     } else {
         return fail(DOLINC_ERR_INVALID_ARG, "unknown flux");
     }
-    if (m->d.n_bv > 0 && m->bv_nv != s->nv)
-        return fail(DOLINC_ERR_INVALID_ARG, "the mesh has Dirichlet/Neumann faces: set their values for nv = " +
-                                                std::to_string(s->nv) + " with dolinc_set_boundary_values");
     if ((s->limiter == DOLINC_LIMIT_ENO3_FLAGGED || s->limiter == DOLINC_LIMIT_FIRST_ORDER_FLAGGED) && !m->flags)
         return fail(DOLINC_ERR_INVALID_ARG, "flagged limiter without flags (dolinc_set_flags)");
     return DOLINC_OK;
@@ -520,7 +531,7 @@ dolinc_status dolinc_mesh_geometry(const dolinc_mesh *m, double *V, double *xc, 
 
 dolinc_status dolinc_workspace_size(const dolinc_mesh *m, const dolinc_scheme *s, size_t *bytes)
 {
-    dolinc_status st = check_scheme(m, s);
+    dolinc_status st = check_scheme_shape(m, s);
     if (st) return st;
     if (!bytes) return fail(DOLINC_ERR_INVALID_ARG, "null bytes");
     *bytes = ws_layout(m, s).total;
@@ -538,7 +549,7 @@ dolinc_status dolinc_workspace_init(void *ws, size_t bytes, dolinc_stream stream
 dolinc_status dolinc_diff_layout(const dolinc_mesh *m, const dolinc_scheme *s, int order, int64_t *offset,
                                  int *stride, int *eb, int64_t *total_bytes)
 {
-    dolinc_status st = check_scheme(m, s);
+    dolinc_status st = check_scheme_shape(m, s);
     if (st) return st;
     if (order < 1 || order > s->n_diff) return fail(DOLINC_ERR_INVALID_ARG, "order must be in 1..n_diff");
     size_t o = 0;
@@ -1299,7 +1310,7 @@ dolinc_status dolinc_batch_autotune(dolinc_batch *bt, const dolinc_scheme *s, co
 
 dolinc_status dolinc_set_tuning(dolinc_mesh *m, const dolinc_scheme *s, const dolinc_tuning *t)
 {
-    dolinc_status st = check_scheme(m, s);
+    dolinc_status st = check_scheme_shape(m, s);
     if (st) return st;
     if (!t) return fail(DOLINC_ERR_INVALID_ARG, "null tuning");
     auto ok = [](int l, int b) {

@@ -245,3 +245,69 @@ def prim_to_cons(prim, gamma=1.4):
     p = prim[:, -1]
     E = p / (gamma - 1) + 0.5 * rho * (vel * vel).sum(axis=1)
     return np.concatenate([rho[:, None], rho[:, None] * vel, E[:, None]], axis=1)
+
+
+# ----------------------------------------------------------------------------------------
+# laminar flat-plate boundary layer (Blasius)
+
+_BLASIUS = {}
+
+
+def _blasius_table(eta_max=12.0, n=24000):
+    """f(eta), f'(eta) of f''' + f f'' / 2 = 0, f(0) = f'(0) = 0, f'(inf) = 1, by
+    classical RK4 on a uniform eta grid and bisection on f''(0)."""
+    if "tab" in _BLASIUS:
+        return _BLASIUS["tab"]
+    h = eta_max / n
+
+    def integrate(s, keep=False):
+        y = np.array([0.0, 0.0, s])
+        rhs = lambda y: np.array([y[1], y[2], -0.5 * y[0] * y[2]])
+        out = [y.copy()] if keep else None
+        for _ in range(n):
+            k1 = rhs(y)
+            k2 = rhs(y + 0.5 * h * k1)
+            k3 = rhs(y + 0.5 * h * k2)
+            k4 = rhs(y + h * k3)
+            y = y + h / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+            if keep:
+                out.append(y.copy())
+        return (np.array(out) if keep else y)
+
+    lo, hi = 0.2, 0.5
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if integrate(mid)[1] > 1.0:
+            hi = mid
+        else:
+            lo = mid
+    s = 0.5 * (lo + hi)
+    Y = integrate(s, keep=True)
+    eta = np.linspace(0.0, eta_max, n + 1)
+    _BLASIUS["tab"] = (eta, Y[:, 0], Y[:, 1], Y[:, 2], s)
+    return _BLASIUS["tab"]
+
+
+def _hermite(x, xt, y, dy):
+    """Cubic Hermite interpolation on the uniform grid xt (values y, slopes dy)."""
+    h = xt[1] - xt[0]
+    i = np.clip(((x - xt[0]) / h).astype(np.int64), 0, xt.shape[0] - 2)
+    t = (x - xt[i]) / h
+    h00, h10 = 2 * t**3 - 3 * t**2 + 1, t**3 - 2 * t**2 + t
+    h01, h11 = -2 * t**3 + 3 * t**2, t**3 - t**2
+    return h00 * y[i] + h10 * h * dy[i] + h01 * y[i + 1] + h11 * h * dy[i + 1]
+
+
+def blasius(p, nu=1e-3, U=1.0, x0=0.0):
+    """Velocity (u, v) of the Blasius boundary layer over a plate along y = 0 starting
+    at x = x0: u = U f'(eta), v = (1/2) sqrt(nu U / x) (eta f' - f),
+    eta = y sqrt(U / (nu x)).  Rows are points; returns [P, 2]."""
+    eta_t, f_t, fp_t, fpp_t, _ = _blasius_table()
+    x = p[:, 0] - x0
+    eta = p[:, 1] * np.sqrt(U / (nu * x))
+    e = np.clip(eta, 0.0, eta_t[-1])
+    f = _hermite(e, eta_t, f_t, fp_t) + np.where(eta > eta_t[-1], eta - eta_t[-1], 0.0)
+    fp = np.where(eta > eta_t[-1], 1.0, _hermite(e, eta_t, fp_t, fpp_t))
+    u = U * fp
+    v = 0.5 * np.sqrt(nu * U / x) * (eta * fp - f)
+    return np.stack([u, v], axis=1)
