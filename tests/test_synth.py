@@ -34,3 +34,15 @@ def test_cell_average_of_a_linear_field_is_its_centroid_value():
     # centroid from first moments of the coordinates
     xc = np.stack([synth.cell_average(m, lambda p, k=k: p[:, k], q=2) for k in range(3)], axis=1)
     assert np.abs(avg - f(xc)).max() < 1e-12
+
+
+def test_blasius_profile_constants():
+    """The Blasius solution behind the boundary-layer inputs: wall curvature
+    f''(0) = 0.33206 and displacement eta - f -> 1.7208 (classical values), u rising
+    from 0 at the wall to 1 outside the layer."""
+    from synth import fields
+    eta, f, fp, fpp, s = fields._blasius_table()
+    assert abs(s - 0.33206) < 2e-5
+    assert abs((eta[-1] - f[-1]) - 1.7208) < 2e-4
+    uv = fields.blasius(np.array([[1.0, 0.0], [1.0, 0.02], [1.0, 0.4]]))
+    assert uv[0, 0] == 0.0 and 0.0 < uv[1, 0] < 1.0 and abs(uv[2, 0] - 1.0) < 1e-9
