@@ -110,7 +110,7 @@ class Scheme:
         [nv, n_faces] (face value, or outward normal gradient) describe the boundary
         faces (Sec 2.6); None: every boundary face zero-gradient."""
         need = max(r, k - r - 2)
-        if eno in (1, 2):
+        if eno in (1, 2, 4, 5):
             need = max(need, 2)
         self.k, self.r = k, r
         self.n_diff = need if n_diff is None else n_diff

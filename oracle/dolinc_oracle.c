@@ -64,8 +64,9 @@ typedef struct {
     double gamma;     /* ratio of specific heats (Euler) */
     double adv[3];    /* advection velocity (flux 0) */
     int eno;          /* 0 fixed stencil, 1 ENO3 on every face, 2 ENO3 on faces touching a troubled cell,
-                         3 first-order upwind (the cell's own average) on faces touching a troubled cell */
-    const unsigned char *troubled;   /* [n_cells] for eno == 2, 3 */
+                         3 first-order upwind (the cell's own average) on faces touching a troubled cell,
+                         4 WENO5 on every face, 5 WENO5 on faces touching a troubled cell */
+    const unsigned char *troubled;   /* [n_cells] for eno == 2, 3, 5 */
     const int *bkind;                /* [n_faces] boundary kind per face (NULL: every boundary face
                                         zero-gradient): 0/1 zero-gradient, 2 Dirichlet, 3 Neumann */
     const double *bval;              /* [nv][n_faces]: the face value (2) or the outward normal
@@ -371,13 +372,71 @@ static int eno3_choose(double g, const double *ph)
     return fabs(dR) < fabs(dC) ? 0 : 1;
 }
 
-/* Face value of one variable for one orientation (upwind cell i, downwind i+1). */
+/* WENO5-DOLINC (Sec 2.4 names it: the fixed stencils plus stencil weights).  The
+ * three 3-cell candidates r = 0, 1, 2 (Eq coeff weights on the geometric cells) are
+ * combined with the nonlinear weights of Jiang and Shu,
+ *   w_r = a_r / sum a,  a_r = d_r / (1e-6 + beta_r)^2,
+ * where the linear weights d_r make the combination the 5-cell stencil (5, 2) (they
+ * follow from its two end coefficients: only r = 2 reaches cell i-2 and only r = 0
+ * cell i+2), and beta_r is the Jiang-Shu smoothness measure of the candidate's
+ * quadratic p_r on the upwind cell, in units of that cell's width:
+ *   beta_r = int_cell (p_r')^2 + (p_r'')^2 dx,
+ * p_r the derivative of the cubic interpolating the primitive at the candidate's four
+ * faces.  On uniform cells this is the classical WENO5.  ph[n+2] = phi_n, n = -2..2. */
+static double weno5_value(double g, const double *ph)
+{
+    double c5[5], c3[3], q[3], d[3], beta[3];
+    or_coeff(5, 2, g, c5);
+    for (int r = 0; r < 3; ++r) {
+        or_coeff(3, r, g, c3);
+        q[r] = 0.0;
+        for (int j = 0; j < 3; ++j) q[r] += c3[j] * ph[2 + j - r];
+        if (r == 2) d[2] = c5[0] / c3[0];
+        if (r == 0) d[0] = c5[4] / c3[2];
+        /* primitive at the candidate's faces X_0..X_3 (cells i-r .. i-r+2) */
+        double X[4], Pf[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int t = 0; t < 4; ++t) X[t] = face_pos(g, -r + t - 1);
+        for (int t = 1; t < 4; ++t) Pf[t] = Pf[t - 1] + ph[2 - r + t - 1] * (X[t] - X[t - 1]);
+        /* cubic P = a0 + a1 x + a2 x^2 + a3 x^3 through (X_t, Pf_t): Vandermonde solve */
+        double A[4][5];
+        for (int t = 0; t < 4; ++t) {
+            double xp = 1.0;
+            for (int e = 0; e < 4; ++e) { A[t][e] = xp; xp *= X[t]; }
+            A[t][4] = Pf[t];
+        }
+        for (int col = 0; col < 4; ++col) {                /* Gaussian elimination, partial pivoting */
+            int piv = col;
+            for (int t = col + 1; t < 4; ++t) if (fabs(A[t][col]) > fabs(A[piv][col])) piv = t;
+            for (int e = 0; e < 5; ++e) { double tmp = A[col][e]; A[col][e] = A[piv][e]; A[piv][e] = tmp; }
+            for (int t = 0; t < 4; ++t) {
+                if (t == col) continue;
+                double f = A[t][col] / A[col][col];
+                for (int e = col; e < 5; ++e) A[t][e] -= f * A[col][e];
+            }
+        }
+        const double a2 = A[2][4] / A[2][2], a3 = A[3][4] / A[3][3];
+        /* p' = 2 a2 + 6 a3 x, p'' = 6 a3 over the upwind cell [-1, 0] */
+        const double b = 2.0 * a2, cc = 6.0 * a3;
+        beta[r] = (b * b - b * cc + cc * cc / 3.0) + cc * cc;   /* int_{-1}^{0} (b + cc x)^2 dx + cc^2 */
+    }
+    d[1] = 1.0 - d[0] - d[2];
+    double a[3], sa = 0.0;
+    for (int r = 0; r < 3; ++r) { a[r] = d[r] / ((1e-6 + beta[r]) * (1e-6 + beta[r])); sa += a[r]; }
+    return (a[0] * q[0] + a[1] * q[1] + a[2] * q[2]) / sa;
+}
+
+/* Face value of one variable for one orientation (upwind cell i, downwind i+1);
+ * use_eno: 1 ENO3-DOLINC, 2 WENO5-DOLINC. */
 static double reconstruct(const or_scheme *s, int N, double g, const double *phi0, const double *phi1, int use_eno,
                           int *r_used)
 {
     double ph[2 * OR_MAXN + 2], c[OR_MAXK];
     or_phantoms(N, g, phi0, phi1, ph);
     int k = s->k, r = s->r;
+    if (use_eno == 2) {
+        if (r_used) *r_used = -2;
+        return weno5_value(g, &ph[N - 2]);
+    }
     if (use_eno) { k = 3; r = eno3_choose(g, &ph[N - 2]); }
     if (r_used) *r_used = r;
     or_coeff(k, r, g, c);
@@ -419,7 +478,7 @@ static void face_states(const or_mesh *m, const or_geom *g, const or_scheme *s, 
         }
         return;
     }
-    int eno = s->eno == 1 || (s->eno == 2 && touched);
+    int eno = (s->eno == 1 || (s->eno == 2 && touched)) ? 1 : (s->eno == 4 || (s->eno == 5 && touched)) ? 2 : 0;
     for (int v = 0; v < nv; ++v) {
         double pP[OR_MAXN + 1], pQ[OR_MAXN + 1], qP[OR_MAXN + 1], qQ[OR_MAXN + 1];
         for (int mm = 0; mm <= N; ++mm) {

@@ -232,17 +232,20 @@ def _sine_run(n, k, r, eno=0, cfl=0.05, adv=1.0, mirror=False):
 
 def test_l2_errors_match_paper_tables():
     """Sec 3.2, Tables orderPScheme and orderHOScheme: L2 error of one period of
-    sin(2 pi x) advection on 10..80 uniform cells.  The paper does not state its
+    sin(2 pi x) advection on 10..80 uniform cells (WENO5 with the Jiang-Shu weights
+    of the oracle's WENO5-DOLINC).  The paper does not state its
     time integrator settings; with a small SSP-RK3 step the oracle reproduces every
     printed error within 6% and the orders within 0.1."""
     rows = _read_table("paper_l2_1d_sine.txt")[:4]
-    got = {name: [] for name in ("USR3", "CSR4", "ENO3")}
+    names = ("USR3", "CSR4", "ENO3", "WENO5")
+    got = {name: [] for name in names}
     for row in rows:
         n = int(row[0])
-        for name, (k, r, eno) in (("USR3", (3, 1, 0)), ("CSR4", (4, 1, 0)), ("ENO3", (3, 1, 1))):
+        for name, (k, r, eno) in (("USR3", (3, 1, 0)), ("CSR4", (4, 1, 0)), ("ENO3", (3, 1, 1)),
+                                  ("WENO5", (3, 1, 4))):
             u, u0 = _sine_run(n, k, r, eno)
             got[name].append(np.sqrt(np.mean((u - u0) ** 2)))
-    for col, name in enumerate(("USR3", "CSR4", "ENO3")):
+    for col, name in enumerate(names):
         want = np.array([float(row[1 + col]) for row in rows])
         e = np.array(got[name])
         assert np.all(np.abs(e / want - 1) < 0.06), (name, e, want)
@@ -441,3 +444,27 @@ def test_boundary_face_states_and_near_wall_reconstruction():
     delta = np.abs(O.xf[bnd, 0] - O.xc[P, 0])            # normal distance to the end faces
     np.testing.assert_allclose(L[0][bnd], u[0][P] + q[0][bnd] * delta, rtol=0, atol=1e-13)
     np.testing.assert_allclose(L[0][bnd], 1.0 + 3.0 * O.xf[bnd, 0], rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("g", [0.8, 1.25])
+def test_weno5_exact_for_quadratics_on_geometric_strips(g):
+    """Every WENO5 candidate is exact for quadratic cell averages, so any weights are:
+    on a geometric strip the WENO5-DOLINC face values of a quadratic equal its point
+    values at the faces, in both orientations."""
+    widths = 0.05 * g ** np.arange(14)
+    m = synth.strip_mesh(widths, height=0.02, boundary="transmissive")
+    O = oracle.Oracle(m)
+    xs = np.concatenate([[0.0], np.cumsum(widths)])
+    P = lambda x: 0.3 * x + 1.7 * x ** 2 - 0.4 * x ** 3 / 3.0       # primitive of u = 0.3 + 3.4 x - 0.4 x^2
+    avg = (P(xs[1:]) - P(xs[:-1])) / widths
+    u = avg[np.argsort(np.argsort(O.xc[:, 0]))][None]
+    s = oracle.Scheme(k=3, r=1, n_diff=2, flux="upwind", adv=(1.0, 0.0), eno=4)
+    L, R, _, _ = O.face_values(u, s)
+    x = O.xf[:, 0]
+    exact = 0.3 + 3.4 * x - 0.4 * x ** 2
+    inner = (O.neigh >= 0) & (np.abs(O.S[:, 0]) > 0)
+    # faces whose whole 5-cell stencil lies inside the strip
+    ok = inner & (x > xs[3] - 1e-12) & (x < xs[-4] + 1e-12)
+    assert ok.sum() >= 6
+    np.testing.assert_allclose(L[0][ok], exact[ok], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(R[0][ok], exact[ok], rtol=0, atol=1e-10)
