@@ -58,7 +58,7 @@ typedef enum {
 enum { DOLINC_FLUX_UPWIND = 0, DOLINC_FLUX_BURGERS = 1, DOLINC_FLUX_RUSANOV = 2 };
 enum { DOLINC_FP64 = 0, DOLINC_FP32 = 1, DOLINC_FP32_BF16 = 2 };
 enum { DOLINC_LIMIT_NONE = 0, DOLINC_LIMIT_ENO3_ALL = 1, DOLINC_LIMIT_ENO3_FLAGGED = 2,
-       DOLINC_LIMIT_FIRST_ORDER_FLAGGED = 3 };
+       DOLINC_LIMIT_FIRST_ORDER_FLAGGED = 3, DOLINC_LIMIT_WENO5_ALL = 4, DOLINC_LIMIT_WENO5_FLAGGED = 5 };
 enum { DOLINC_RENUMBER_NONE = 0, DOLINC_RENUMBER_MORTON = 1 };
 
 /* Mesh in owner/neighbour face form (Sec 2.1: a cell knows its neighbours only
@@ -118,7 +118,12 @@ typedef struct {
  *               a cell flagged with dolinc_set_flags / dolinc_indicator_infer; or
  *               FIRST_ORDER_FLAGGED: on faces touching a flagged cell each orientation
  *               takes its upwind cell's average (first-order Godunov fallback, not a
- *               scheme of the paper; it needs no second-order differentials)
+ *               scheme of the paper; it needs no second-order differentials); or
+ *               WENO5-DOLINC (Sec 2.4: the three 3-cell DOLINC candidates with
+ *               Jiang-Shu weights, linear weights reproducing the 5-cell stencil,
+ *               smoothness of the candidates' quadratics on the non-uniform cells) on
+ *               every face (WENO5_ALL) or on faces touching a flagged cell; ENO3 and
+ *               WENO5 need n_diff >= 2
  *   gamma       ratio of specific heats (RUSANOV)
  *   adv         advection velocity (UPWIND); Burgers flux is u^2/2 (1,..,1)          */
 typedef struct {

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libdolinc.so")
 
 FLUX = {"upwind": 0, "burgers": 1, "rusanov": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_bf16": 2}
-LIMITER = {"none": 0, "eno3_all": 1, "eno3_flagged": 2, "first_order_flagged": 3}
+LIMITER = {"none": 0, "eno3_all": 1, "eno3_flagged": 2, "first_order_flagged": 3, "weno5_all": 4, "weno5_flagged": 5}
 RENUMBER = {"none": 0, "morton": 1}
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "MESH", 3: "UNSUPPORTED", 4: "CUDA", 5: "DEVICE_TIMEOUT",
           6: "NONFINITE", 7: "OOM"}
@@ -132,11 +132,11 @@ def _stream(stream):
 
 class Scheme:
     """dolinc_scheme.  precision: 'fp64' | 'fp32' | 'fp32_bf16'; limiter: 'none' |
-    'eno3_all' | 'eno3_flagged' | 'first_order_flagged'."""
+    'eno3_all' | 'eno3_flagged' | 'first_order_flagged' | 'weno5_all' | 'weno5_flagged'."""
 
     def __init__(self, k=3, r=1, n_diff=None, flux="upwind", nv=1, precision="fp64", limiter="none",
                  gamma=1.4, adv=(1.0, 1.0, 0.0)):
-        need = max(r, k - r - 2, 2 if limiter in ("eno3_all", "eno3_flagged") else 1)
+        need = max(r, k - r - 2, 2 if limiter in ("eno3_all", "eno3_flagged", "weno5_all", "weno5_flagged") else 1)
         self.k, self.r = k, r
         self.n_diff = need if n_diff is None else n_diff
         self.flux, self.nv, self.precision, self.limiter = flux, nv, precision, limiter

@@ -159,7 +159,9 @@ template <class T> dolinc_status upload(dolinc_mesh *m, const std::vector<T> &v,
 int needed_order(const dolinc_scheme &s)
 {
     int need = s.r > s.k - s.r - 2 ? s.r : s.k - s.r - 2;
-    if ((s.limiter == DOLINC_LIMIT_ENO3_ALL || s.limiter == DOLINC_LIMIT_ENO3_FLAGGED) && need < 2) need = 2;
+    if ((s.limiter == DOLINC_LIMIT_ENO3_ALL || s.limiter == DOLINC_LIMIT_ENO3_FLAGGED ||
+         s.limiter == DOLINC_LIMIT_WENO5_ALL || s.limiter == DOLINC_LIMIT_WENO5_FLAGGED) && need < 2)
+        need = 2;
     return need < 1 ? 1 : need;
 }
 
@@ -186,7 +188,7 @@ dolinc_status check_scheme_shape(const dolinc_mesh *m, const dolinc_scheme *s)
         return fail(DOLINC_ERR_INVALID_ARG, "stencil (k, r) / limiter needs more differential orders than n_diff");
     if (s->precision < DOLINC_FP64 || s->precision > DOLINC_FP32_BF16)
         return fail(DOLINC_ERR_INVALID_ARG, "unknown precision");
-    if (s->limiter < DOLINC_LIMIT_NONE || s->limiter > DOLINC_LIMIT_FIRST_ORDER_FLAGGED)
+    if (s->limiter < DOLINC_LIMIT_NONE || s->limiter > DOLINC_LIMIT_WENO5_FLAGGED)
         return fail(DOLINC_ERR_INVALID_ARG, "unknown limiter");
     const int dim = m->h.dim;
     if (s->flux == DOLINC_FLUX_UPWIND || s->flux == DOLINC_FLUX_BURGERS) {
@@ -197,7 +199,8 @@ dolinc_status check_scheme_shape(const dolinc_mesh *m, const dolinc_scheme *s)
     } else {
         return fail(DOLINC_ERR_INVALID_ARG, "unknown flux");
     }
-    if ((s->limiter == DOLINC_LIMIT_ENO3_FLAGGED || s->limiter == DOLINC_LIMIT_FIRST_ORDER_FLAGGED) && !m->flags)
+    if ((s->limiter == DOLINC_LIMIT_ENO3_FLAGGED || s->limiter == DOLINC_LIMIT_FIRST_ORDER_FLAGGED ||
+         s->limiter == DOLINC_LIMIT_WENO5_FLAGGED) && !m->flags)
         return fail(DOLINC_ERR_INVALID_ARG, "flagged limiter without flags (dolinc_set_flags)");
     return DOLINC_OK;
 }
@@ -268,10 +271,13 @@ StageArgs base_args(const dolinc_mesh *m, const dolinc_scheme *s, void *ws, cons
     a.flux = s->flux;
     a.gamma = s->gamma;
     for (int i = 0; i < 3; ++i) a.adv[i] = s->adv[i];
-    const bool flagged = s->limiter == DOLINC_LIMIT_ENO3_FLAGGED || s->limiter == DOLINC_LIMIT_FIRST_ORDER_FLAGGED;
+    const bool flagged = s->limiter == DOLINC_LIMIT_ENO3_FLAGGED || s->limiter == DOLINC_LIMIT_FIRST_ORDER_FLAGGED ||
+                         s->limiter == DOLINC_LIMIT_WENO5_FLAGGED;
     a.flags = flagged ? m->flags : nullptr;
-    a.eno_all = s->limiter == DOLINC_LIMIT_ENO3_ALL;
-    a.flag_mode = s->limiter == DOLINC_LIMIT_FIRST_ORDER_FLAGGED ? LIM_FIRST_ORDER : LIM_ENO3;
+    a.all_mode = s->limiter == DOLINC_LIMIT_ENO3_ALL ? LIM_ENO3 : s->limiter == DOLINC_LIMIT_WENO5_ALL ? LIM_WENO5 : LIM_NONE;
+    a.flag_mode = s->limiter == DOLINC_LIMIT_FIRST_ORDER_FLAGGED ? LIM_FIRST_ORDER
+                : s->limiter == DOLINC_LIMIT_WENO5_FLAGGED       ? LIM_WENO5
+                                                                 : LIM_ENO3;
     a.face_flux = B(ws, L.flux);
     return a;
 }

@@ -212,16 +212,17 @@ struct StageArgs {
     int k, r, mode, flux;
     double gamma, adv[3];
     const uint8_t *flags;        // faces touching a flagged cell are limited (null: none)
-    int eno_all;                 // ENO3 on every face
-    int flag_mode;               // limit of flagged faces: LIM_ENO3 or LIM_FIRST_ORDER
+    int all_mode;                // limit of every face: LIM_NONE, LIM_ENO3 or LIM_WENO5
+    int flag_mode;               // limit of flagged faces: LIM_ENO3, LIM_FIRST_ORDER or LIM_WENO5
 };
 
-// Face limit: none, ENO3-DOLINC, or first-order upwind (each side's own cell average)
-enum { LIM_NONE = 0, LIM_ENO3 = 1, LIM_FIRST_ORDER = 2 };
+// Face limit: none, ENO3-DOLINC, first-order upwind (each side's own cell average),
+// or WENO5-DOLINC
+enum { LIM_NONE = 0, LIM_ENO3 = 1, LIM_FIRST_ORDER = 2, LIM_WENO5 = 3 };
 
 __device__ __forceinline__ int face_limit(const StageArgs &a, bool flagged)
 {
-    return a.eno_all ? LIM_ENO3 : (flagged ? a.flag_mode : LIM_NONE);
+    return a.all_mode != LIM_NONE ? a.all_mode : (flagged ? a.flag_mode : LIM_NONE);
 }
 
 // Where a kernel reads cell records and face records from.  GlobalSrc: device memory
@@ -333,6 +334,52 @@ __device__ __forceinline__ R eno3_value(R g, const R *p0, const R *p1)
                                  ((R)3 * g2 * g + (R)4 * g2 + (R)3 * g + (R)1) * p0[0]) / (G2 * G3);
 }
 
+// WENO5-DOLINC value of one variable (Sec 2.4: the fixed DOLINC stencils plus stencil
+// weights).  The three 3-cell candidates on the geometric cells (closed forms of Eq
+// coeff) are weighted by a_r = d_r / (1e-6 + beta_r)^2 (Jiang-Shu), with linear
+// weights d_r that reproduce the 5-cell stencil (5,2):
+//   d_2 = g^6 / (H G5),  d_0 = G3 / (H G5),  d_1 = g^2 G2 G3 / (H G5),
+// G_n = 1 + g + .. + g^(n-1), H = 1 + g^2, and smoothness
+//   beta_r = b_r^2 - b_r c_r + (4/3) c_r^2,
+// b_r, c_r the slope at the upwind face and the curvature of the candidate's quadratic
+// (the derivative of the cubic through its primitive) in units of the upwind cell,
+// linear in the candidate's three values.  g = 1 gives the classical WENO5.
+template <int NS, class R>
+__device__ __forceinline__ R weno5_value(R g, const R *p0, const R *p1)
+{
+    static_assert(NS >= 2, "WENO5 needs second-order differentials");
+    R gi = (R)1 / g;
+    // far values phi_{-1}, phi_{-2}, phi_2 by Eq diffDLC (as for ENO3)
+    R m1 = gi * (p1[0] - p0[1] - ((R)1 - g) * p0[0]);
+    R m1_1 = gi * (p1[1] - p0[2] - ((R)1 - g) * p0[1]);
+    R m2 = gi * (p0[0] - gi * m1_1 - ((R)1 - g) * m1);
+    R q2f = g * p0[0] + g * p1[1] + ((R)1 - g) * p1[0];
+    const R f0 = p0[0], f1 = p1[0];
+    const R g2 = g * g, g3 = g2 * g;
+    const R G2 = (R)1 + g, G3 = (R)1 + g + g2;
+    const R D = G2 * G3, iD = (R)1 / D, iG3 = (R)1 / G3;
+    // candidates (cells i..i+2, i-1..i+1, i-2..i)
+    const R c0 = g2 * f0 * iG3 + ((g2 + (R)2 * g + (R)2) * f1 - q2f) * iD;
+    const R c1 = (-g3 * m1 + g * ((R)1 + (R)2 * g + (R)2 * g2) * f0) * iD + f1 * iG3;
+    const R c2 = g3 * m2 * iG3 + (-g * (g3 + (R)3 * g2 + (R)2 * g + (R)1) * m1 + ((R)3 * g3 + (R)4 * g2 + (R)3 * g + (R)1) * f0) * iD;
+    // smoothness
+    const R b0 = (R)2 * iD * (-g * (g + (R)2) * f0 + (g3 + (R)2 * g2 + g - (R)1) * gi * f1 - (g - (R)1) * gi * q2f);
+    const R k0 = (R)6 * iD * (f0 - G2 * gi * f1 + gi * q2f);
+    const R b1 = (R)2 * iD * (-g2 * (g - (R)1) * m1 + (g3 - g2 - (R)2 * g - (R)1) * f0 + ((R)2 * g + (R)1) * f1);
+    const R k1 = (R)6 * g * iD * (g * m1 - G2 * f0 + f1);
+    const R b2 = (R)2 * g * iD * (g2 * ((R)2 * g + (R)1) * m2 - ((R)2 * g3 + (R)4 * g2 + (R)2 * g + (R)1) * m1 +
+                                  ((R)3 * g2 + (R)2 * g + (R)1) * f0);
+    const R k2 = (R)6 * g3 * iD * (g * m2 - G2 * m1 + f0);
+    const R be0 = b0 * b0 - b0 * k0 + (R)(4.0 / 3.0) * k0 * k0;
+    const R be1 = b1 * b1 - b1 * k1 + (R)(4.0 / 3.0) * k1 * k1;
+    const R be2 = b2 * b2 - b2 * k2 + (R)(4.0 / 3.0) * k2 * k2;
+    // linear weights (common factor 1 / (H G5) cancels in the normalisation)
+    const R d0 = G3, d1 = g2 * G2 * G3, d2 = g3 * g3;
+    const R e0 = (R)1e-6 + be0, e1 = (R)1e-6 + be1, e2 = (R)1e-6 + be2;
+    const R a0 = d0 / (e0 * e0), a1 = d1 / (e1 * e1), a2 = d2 / (e2 * e2);
+    return (a0 * c0 + a1 * c1 + a2 * c2) / (a0 + a1 + a2);
+}
+
 // Both face states (or the upwind one only for linear advection) of face record fr.
 template <int DIM, int NV, int NS, int PREC, bool UPWIND_ONLY, class Src>
 __device__ __forceinline__ void face_states(const StageArgs &a, const Src &src, const typename PrecT<PREC>::R *fr,
@@ -362,6 +409,17 @@ __device__ __forceinline__ void face_states(const StageArgs &a, const Src &src, 
                 for (int m = 0; m < 3; ++m) { q0[m] = (m & 1) ? -phN[v][m] : phN[v][m]; q1[m] = (m & 1) ? -phP[v][m] : phP[v][m]; }
                 if (!UPWIND_ONLY || want_left) UL[v] = eno3_value<NS, R>(g, phP[v], phN[v]);
                 if (!UPWIND_ONLY || !want_left) UR[v] = eno3_value<NS, R>(rcp_bulk(g), q0, q1);
+            }
+            return;
+        }
+        if (lim == LIM_WENO5) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                R q0[3], q1[3];
+#pragma unroll
+                for (int m = 0; m < 3; ++m) { q0[m] = (m & 1) ? -phN[v][m] : phN[v][m]; q1[m] = (m & 1) ? -phP[v][m] : phP[v][m]; }
+                if (!UPWIND_ONLY || want_left) UL[v] = weno5_value<NS, R>(g, phP[v], phN[v]);
+                if (!UPWIND_ONLY || !want_left) UR[v] = weno5_value<NS, R>((R)1 / g, q0, q1);
             }
             return;
         }

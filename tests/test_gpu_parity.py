@@ -340,7 +340,7 @@ def test_renumbering_does_not_change_results(renumber):
 
 # ---------------------------------------------------------------------------- ENO3 limiter
 
-@pytest.mark.parametrize("mode", ["eno3_all", "eno3_flagged", "first_order_flagged"])
+@pytest.mark.parametrize("mode", ["eno3_all", "eno3_flagged", "first_order_flagged", "weno5_all", "weno5_flagged"])
 @pytest.mark.parametrize("name,nv", [("tri", 1), ("tri_bnd", 4), ("tet", 5)])
 def test_eno3_limiter_fp64(mode, name, nv):
     m, O = mesh(name)
@@ -356,12 +356,54 @@ def test_eno3_limiter_fp64(mode, name, nv):
     Rg = torch.zeros((nv, M.n_cells), dtype=torch.float64, device="cuda")
     dg.dolinc_residual(M, sch, to_dev(M, u), Rg, ws)
     got = M.from_lib(Rg.cpu().numpy())
-    eno = {"eno3_all": 1, "eno3_flagged": 2, "first_order_flagged": 3}[mode]
-    osch = oracle.Scheme(k=3, r=1, n_diff=2, nv=nv, eno=eno, troubled=flags if eno > 1 else None, **fx)
+    eno = {"eno3_all": 1, "eno3_flagged": 2, "first_order_flagged": 3, "weno5_all": 4, "weno5_flagged": 5}[mode]
+    osch = oracle.Scheme(k=3, r=1, n_diff=2, nv=nv, eno=eno, troubled=flags if eno in (2, 3, 5) else None, **fx)
     want = O.residual(u, osch)
     # stencil choices are taken in FP64 on both sides; smooth random data has no ties
     assert rel(got, want) < 1e-12
     dg.dolinc_set_flags(M, None)
+
+
+@pytest.mark.parametrize("name,nv", [("tri", 1), ("tri_bnd", 4), ("tet", 5), ("strip", 1)])
+def test_weno5_fp32_step(name, nv):
+    """WENO5-DOLINC in the FP32 bulk path: one SSP-RK3 step against the oracle (the
+    nonlinear weights are smooth functions of the data, so FP32 stays close)."""
+    m, O = mesh(name)
+    M = gpu_mesh(m)
+    u = field(m, nv, seed=71)
+    fx = euler_ok(nv) if nv > 1 else dict(flux="upwind", adv=(1.0, 0.5, 0.3))
+    sch = dg.Scheme(k=3, r=1, n_diff=2, nv=nv, precision="fp32", limiter="weno5_all", **fx)
+    ws = dg.workspace(M, sch)
+    x = to_dev(M, u)
+    dt = 1e-3
+    dg.dolinc_rk_step(M, sch, dt, x, ws)
+    dg.dolinc_sync_status(M, ws)
+    got = M.from_lib(x.cpu().numpy())
+    want = O.rk3_step(u, oracle.Scheme(k=3, r=1, n_diff=2, nv=nv, eno=4, **fx), dt)
+    assert rel(got - u, want - u) < 2e-4
+
+
+def test_weno5_reproduces_the_papers_sine_errors():
+    """Sec 3.2, Table orderHOScheme, WENO5 column: one period of sine advection on 20
+    and 40 uniform cells through the GPU step, FP64, within 6% of the printed errors."""
+    import os
+    rows = [r.split() for r in open(os.path.join(os.path.dirname(__file__), "golden", "paper_l2_1d_sine.txt"))
+            if r.strip() and not r.startswith("#")]
+    for row in rows[1:3]:
+        n, want = int(row[0]), float(row[4])
+        m = synth.strip_mesh(np.full(n, 1.0 / n))
+        M = gpu_mesh(m)
+        u0 = synth.cell_average(m, lambda p: np.sin(2 * np.pi * p[:, 0]), q=6)[None]
+        sch = dg.Scheme(k=3, r=1, n_diff=2, nv=1, precision="fp64", limiter="weno5_all", flux="upwind",
+                        adv=(1.0, 0.0))
+        ws = dg.workspace(M, sch)
+        x = to_dev(M, u0)
+        steps = int(np.ceil(1.0 / (0.05 / n)))
+        for _ in range(steps):
+            dg.dolinc_rk_step(M, sch, 1.0 / steps, x, ws)
+        dg.dolinc_sync_status(M, ws)
+        e = np.sqrt(np.mean((M.from_lib(x.cpu().numpy()) - u0) ** 2))
+        assert abs(e / want - 1) < 0.06, (n, e, want)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
