@@ -270,14 +270,18 @@ def run_dolinc(args):
         minimal = max(r0, k0 - r0 - 2, 1)     # differentials the stencil itself reads
         for prec, order, nd, tag in (("fp32_bf16", o0, o0 - 1, ""), (args.precision, o0, minimal, "_minimal"),
                                      ("fp64", o0, minimal, "_minimal"), (args.precision, 2, 1, ""),
-                                     (args.precision, 4, 3, ""), ("fp64", 2, 1, ""), ("fp64", 4, 3, "")):
+                                     (args.precision, 4, 3, ""), ("fp64", 2, 1, ""), ("fp64", 4, 3, ""),
+                                     (args.precision, o0, 2, "_weno5"), ("fp64", o0, 2, "_weno5")):
             k, r = synth.STENCIL_OF_ORDER[order]
             kw = dict(w["scheme"], k=k, r=r, n_diff=nd)
+            if tag == "_weno5":
+                kw["limiter"] = "weno5_all"
             vr = timed_run(prec, kw, args.steps, False)
-            v = {"precision": prec, "scheme_order": order, "stencil_k_r": [k, r], "n_diff": nd,
+            v = {"precision": prec, "scheme_order": 5 if tag == "_weno5" else order,
+                 "stencil_k_r": [k, r] if tag != "_weno5" else "WENO5-DOLINC on every face", "n_diff": nd,
                  "value": M.n_cells * world * 3 * args.steps / (vr["ms"] / 1e3),
                  "ms_per_step": vr["ms"] / args.steps, "finite_after_steps": vr["finite"]}
-            if order == o0 and "fp64" in results:
+            if order == o0 and tag != "_weno5" and "fp64" in results:
                 a = vr["state"].double().cpu().numpy()
                 b = results["fp64"]["state"].cpu().numpy()
                 v["l2_rel_vs_fp64_after_steps"] = _l2_rel(a, b)
