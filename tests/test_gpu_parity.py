@@ -359,8 +359,10 @@ def test_eno3_limiter_fp64(mode, name, nv):
     eno = {"eno3_all": 1, "eno3_flagged": 2, "first_order_flagged": 3, "weno5_all": 4, "weno5_flagged": 5}[mode]
     osch = oracle.Scheme(k=3, r=1, n_diff=2, nv=nv, eno=eno, troubled=flags if eno in (2, 3, 5) else None, **fx)
     want = O.residual(u, osch)
-    # stencil choices are taken in FP64 on both sides; smooth random data has no ties
-    assert rel(got, want) < 1e-12
+    # stencil choices are taken in FP64 on both sides; smooth random data has no ties.
+    # WENO5 combines values built from second-order differentials (N_s = 2): the
+    # FP64 bound 1e-12 * 4^N_s of the tolerance rule
+    assert rel(got, want) < (1.6e-11 if eno in (4, 5) else 1e-12)
     dg.dolinc_set_flags(M, None)
 
 
