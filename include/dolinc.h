@@ -107,7 +107,7 @@ typedef struct {
  *               Needs differentials through order max(r, k-r-2) (Sec 2.3: r far cells
  *               upwind need order r, k-r-1 cells downwind need order k-r-2).
  *   n_diff      differential orders computed each stage (1..4), >= what (k, r) needs
- *               (and >= 2 with an ENO3 limiter).  Orders above the need are computed
+ *               (and >= 2 with an ENO3 or WENO5 limiter).  Orders above the need are computed
  *               and stored but do not change the face values.
  *   flux        DOLINC_FLUX_*; nv = 1 for UPWIND and BURGERS, nv = dim+2 for RUSANOV
  *               (conserved rho, rho u.., rho E, reconstructed component-wise)
