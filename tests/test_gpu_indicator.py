@@ -146,3 +146,42 @@ def test_training_reduces_loss():
     net.forward(xd, None, fl)
     acc = (fl.cpu().numpy() == y).mean()
     assert acc > 0.95, acc
+
+
+def test_trained_network_keeps_a_riemann_run_finite():
+    """What the learned indicator gains over the method without it: trained on the
+    criterion's labels of four seeded Riemann runs, the network switches the
+    first-order fallback on a held-out problem whose unlimited run breaks down at
+    once; the network-switched run stays finite with positive density and lands
+    close to the criterion-switched run, and its flags agree with the criterion's."""
+    from paper_2404_08952_gb300 import indicator as ind
+    mk = lambda sd: synth.workload("euler2d_riemann", size=48, order=sd, q=2)
+    Xs, Ys = [], []
+    for x, y in ind.riemann_runs(mk, range(4), 30, 2, precision="fp32"):
+        Xs.append(x)
+        Ys.append(y)
+    X, Y = torch.cat(Xs), torch.cat(Ys)
+    net = dg.MLP(seed=4)
+    hist, _ = ind.train(net, X, Y, epochs=25, batch=4096, lr=2e-3)
+    assert hist[-1] < hist[0]
+    w = mk(1000)
+    steps = 40
+    st_none, fin_none, _, _ = ind.run_with(w, "none", steps, precision="fp32")
+    st_crit, fin_crit, _, fl_crit = ind.run_with(w, "criterion", steps, precision="fp32")
+    st_net, fin_net, _, fl_net = ind.run_with(w, "network", steps, precision="fp32", net=net)
+    assert not fin_none
+    assert fin_crit and fin_net
+    assert st_net[0].min() > 0
+    assert np.abs(st_net - st_crit).sum() / np.abs(st_crit).sum() < 1e-2
+    # held-out agreement of the network's flags with the criterion's
+    M = dg.Mesh(w["mesh"])
+    sch = dg.Scheme(precision="fp32", **w["scheme"])
+    ws = dg.workspace(M, sch)
+    u = torch.from_numpy(M.to_lib(st_crit)).cuda()
+    fc = torch.zeros(M.n_cells, dtype=torch.uint8, device="cuda")
+    dg.dolinc_criterion(M, sch, u, fc, ws)
+    xf = torch.zeros((M.n_cells, 24), dtype=torch.float32, device="cuda")
+    dg.dolinc_indicator_features(M, sch, u, xf, ws)
+    fn = torch.zeros_like(fc)
+    net.forward(xf, None, fn)
+    assert (fn.cpu().numpy() == fc.cpu().numpy()).mean() > 0.9
