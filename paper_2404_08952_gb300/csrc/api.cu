@@ -87,6 +87,9 @@ struct dolinc_mesh {
     std::vector<cudaEvent_t> pool;
     double prof_ms[DOLINC_KERNEL_COUNT] = {0};
     int64_t prof_n[DOLINC_KERNEL_COUNT] = {0};
+    // side stream for the differential passes a stage does not read (see run_diffs_split)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     ~dolinc_mesh()
     {
         for (auto &r : recs) pool.push_back(r.a), pool.push_back(r.b);
@@ -94,6 +97,9 @@ struct dolinc_mesh {
         int cur = 0;
         cudaGetDevice(&cur);
         cudaSetDevice(device);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
         for (void *p : allocs) cudaFree(p);
         cudaSetDevice(cur);
     }
@@ -335,6 +341,42 @@ void run_diffs(dolinc_mesh *m, const PathFns *p, void *ws, const WsLayout &L, si
                     reinterpret_cast<unsigned *>(B(ws, L.status)), st);
             if (mm == 1) p->bnd_grad(m->d, B(ws, o0off), B(ws, L.ord[1]), st);
         });
+}
+
+// Differential passes of one stage.  The passes the stencil reads (through
+// needed_order) run on `st`; the higher orders the scheme also computes are read by
+// nothing in the stage, so they run on the mesh's side stream, overlapping the stage.
+// Returns true when the side stream holds work the caller must join (m->ev_join)
+// before the next pass rewrites the records those passes read.
+bool run_diffs_split(dolinc_mesh *m, const PathFns *p, void *ws, const WsLayout &L, size_t o0off,
+                     const dolinc_scheme *s, const Tune &t, cudaStream_t st)
+{
+    const int need = needed_order(*s);
+    if (s->n_diff > need && !m->side) {
+        if (cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            if (m->side) cudaStreamDestroy(m->side);
+            if (m->ev_fork) cudaEventDestroy(m->ev_fork);
+            m->side = nullptr;
+            m->ev_fork = m->ev_join = nullptr;
+        }
+    }
+    if (s->n_diff <= need || !m->side) {
+        run_diffs(m, p, ws, L, o0off, s->n_diff, t, st);
+        return false;
+    }
+    run_diffs(m, p, ws, L, o0off, need, t, st);
+    cudaEventRecord(m->ev_fork, st);
+    cudaStreamWaitEvent(m->side, m->ev_fork, 0);
+    for (int mm = need + 1; mm <= s->n_diff; ++mm)
+        timed(m, mm, m->side, [&] {
+            p->diff(m->d, mm, B(ws, L.ord[mm - 1]), B(ws, L.ord[mm]), t, reinterpret_cast<unsigned *>(B(ws, L.status)),
+                    m->side);
+        });
+    cudaEventRecord(m->ev_join, m->side);
+    return true;
 }
 
 dolinc_status launch_check()
@@ -678,10 +720,16 @@ dolinc_status dolinc_rk_step(dolinc_mesh *m, const dolinc_scheme *s, double dt, 
     double *ust = reinterpret_cast<double *>(B(ws, L.ustage));
     const Tune tn = tune_for(m, s);
     timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, u, B(ws, L.o0[0]), cs); });
+    bool pending = false;
+    auto join = [&] {
+        if (pending) cudaStreamWaitEvent(cs, m->ev_join, 0);
+        pending = false;
+    };
     if (s->precision != DOLINC_FP64) {
         // increment form: stage k reads record o0[k], writes o0[k+1] and the accumulator
         for (int sg = 0; sg < 3; ++sg) {
-            run_diffs(m, p, ws, L, L.o0[sg], s->n_diff, tn, cs);
+            join();
+            pending = run_diffs_split(m, p, ws, L, L.o0[sg], s, tn, cs);
             StageArgs a = base_args(m, s, ws, L, L.o0[sg]);
             a.mode = 2;
             a.rk = sg;
@@ -693,11 +741,13 @@ dolinc_status dolinc_rk_step(dolinc_mesh *m, const dolinc_scheme *s, double dt, 
             a.o0_next = sg == 2 ? nullptr : B(ws, L.o0[sg + 1]);
             timed(m, DOLINC_KERNEL_STAGE, cs, [&] { p->stage(m->d, a, tn, cs); });
         }
+        join();
         return launch_check();
     }
     int cur = 0;
     for (int sg = 0; sg < 3; ++sg) {
-        run_diffs(m, p, ws, L, L.o0[cur], s->n_diff, tn, cs);
+        join();
+        pending = run_diffs_split(m, p, ws, L, L.o0[cur], s, tn, cs);
         StageArgs a = base_args(m, s, ws, L, L.o0[cur]);
         a.mode = 1;
         a.u0 = u;
@@ -710,6 +760,7 @@ dolinc_status dolinc_rk_step(dolinc_mesh *m, const dolinc_scheme *s, double dt, 
         timed(m, DOLINC_KERNEL_STAGE, cs, [&] { p->stage(m->d, a, tune_for(m, s), cs); });
         cur = 1 - cur;
     }
+    join();
     return launch_check();
 }
 
