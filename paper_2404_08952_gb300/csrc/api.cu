@@ -485,6 +485,12 @@ dolinc_status upload_mesh(dolinc_mesh *m)
     d.n_slots = (int)ns;
     for (int ti = 0; ti < 3; ++ti) d.max_tile_faces[ti] = mtf[ti];
     d.max_slots = m->max_faces;
+    d.uniform_slots = m->max_faces;
+    for (int64_t c = 0; c < nc; ++c)
+        if (h.off[c + 1] - h.off[c] != m->max_faces) {
+            d.uniform_slots = 0;
+            break;
+        }
     // Dirichlet / Neumann faces: index, kind, normal distance, and the cells holding them
     std::vector<int32_t> bidx(nf, -1), bcell, bcell_off(1, 0), bcell_face;
     std::vector<int8_t> bkind;

@@ -21,6 +21,7 @@ struct DevMesh {
     const int32_t *fown;         // [n_cells+1] first internal face owned by each cell
     int max_tile_faces[3];       // most faces owned by a tile of 64 / 128 / 256 cells
     int max_slots;               // most slots of one cell
+    int uniform_slots;           // slots of every cell when all cells have the same number, else 0
     // Dirichlet / Neumann boundary faces (Sec 2.6), n_bv of them
     int n_bv;
     const int32_t *bidx;         // [n_faces] index of the face among them, -1 otherwise (null: none)

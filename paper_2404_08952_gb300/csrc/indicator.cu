@@ -44,7 +44,8 @@ __global__ void __launch_bounds__(128) k_criterion(DevMesh mesh, StageArgs a, fl
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= mesh.n_cells) return;
     bool trouble = false;
-    const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+    int s0, s1;
+    slot_range(mesh, c, s0, s1);
     for (int s = s0; s < s1; ++s) {
         const int2 sw = __ldg(mesh.slot2 + s);
         const unsigned word = (unsigned)sw.y;
@@ -126,7 +127,8 @@ __global__ void __launch_bounds__(128) k_own_features(DevMesh mesh, StageArgs a,
     load_rec<T1, NV * C1, ord_stride<DIM, NV, 1, PREC>(), R>(static_cast<const T1 *>(a.ord[1]), c, p1);
     load_rec<T2, NV * C2, ord_stride<DIM, NV, 2, PREC>(), R>(static_cast<const T2 *>(a.ord[2]), c, p2);
     R mx[6] = {0, 0, 0, 0, 0, 0};
-    const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+    int s0, s1;
+    slot_range(mesh, c, s0, s1);
     for (int s = s0; s < s1; ++s) {
         const int f = (int)((unsigned)__ldg(mesh.slot2 + s).y >> 2);
         R d0, d1, d2, gg;
@@ -181,7 +183,8 @@ __global__ void __launch_bounds__(128) k_gather24(DevMesh mesh, const float *__r
     if (c >= mesh.n_cells) return;
     float top[3][6];
     int have = 0;
-    const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+    int s0, s1;
+    slot_range(mesh, c, s0, s1);
     for (int s = s0; s < s1; ++s) {
         const int nb = __ldg(mesh.slot2 + s).x;
         float f[6];

@@ -49,6 +49,19 @@ template <> struct Geo<float> {
     static __device__ __forceinline__ const float *bdelta(const DevMesh &m) { return m.bdelta32; }
 };
 
+// Slot range [s0, s1) of cell c: a fixed stride when every cell has the same number of
+// slots (tetrahedra, hexahedra, triangles, quads), else the CSR offsets.
+__device__ __forceinline__ void slot_range(const DevMesh &mesh, int c, int &s0, int &s1)
+{
+    if (mesh.uniform_slots > 0) {
+        s0 = c * mesh.uniform_slots;
+        s1 = s0 + mesh.uniform_slots;
+    } else {
+        s0 = __ldg(mesh.off + c);
+        s1 = __ldg(mesh.off + c + 1);
+    }
+}
+
 // State on boundary face f of a cell whose state is U (Sec 2.6): a Dirichlet face
 // takes its prescribed value, a Neumann face U + q delta (q the outward normal
 // gradient, delta the centroid-to-face normal distance); other faces keep U.
@@ -120,21 +133,20 @@ __global__ void __launch_bounds__(256) k_diff(DevMesh mesh, const void *__restri
 #pragma unroll
     for (int i = 0; i < P; ++i) acc[i] = (R)0;
     if (valid) {
-        R x[NV * CI];
-        if (l == 0) {
-            R wx, wy, wz, iv;
-            ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, wx, wy, wz, iv);
-            load_rec<TI, NV * CI, SI, R>(in, c, x);
-            poly_mul_acc<DIM, NV, M, R>(acc, x, wx, wy, wz);
-        }
-        const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
-        // slots in batches of UB: all slot records, then all neighbour records of the
-        // batch are requested before the first is used (the sums keep slot order)
+        int s0, s1;
+        slot_range(mesh, c, s0, s1);
+        // Slots in batches of UB, whose neighbour records are all requested before the
+        // first is used.  The slot records of the first batch are requested before the
+        // cell's own term is summed; with batches of one or two slots (large records,
+        // few registers to spare for a batch) those of the next batch are requested
+        // before the current batch is summed.  The sums keep the order own term, then
+        // slots in order.
         constexpr int UB = diff_batch(NV * CI);
-        for (int s = s0 + l; s < s1; s += LPC * UB) {
-            R kx[UB], ky[UB], kz[UB];
-            int nbv[UB];
-            bool ok[UB];
+        constexpr bool PREFETCH = UB <= 2;
+        R kx[UB], ky[UB], kz[UB];
+        int nbv[UB];
+        bool ok[UB];
+        auto load_k = [&](int s) {
 #pragma unroll
             for (int u = 0; u < UB; ++u) {
                 const int su = s + u * LPC;
@@ -144,13 +156,29 @@ __global__ void __launch_bounds__(256) k_diff(DevMesh mesh, const void *__restri
                 if (ok[u]) ld4<R>(Geo<R>::slotk(mesh) + 4ll * su, kx[u], ky[u], kz[u], kb);
                 nbv[u] = Geo<R>::nb_of(kb);
             }
+        };
+        load_k(s0 + l);
+        if (l == 0) {
+            R x[NV * CI];
+            R wx, wy, wz, iv;
+            ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, wx, wy, wz, iv);
+            load_rec<TI, NV * CI, SI, R>(in, c, x);
+            poly_mul_acc<DIM, NV, M, R>(acc, x, wx, wy, wz);
+        }
+        for (int s = s0 + l; s < s1; s += LPC * UB) {
             R xs[UB][NV * CI];
 #pragma unroll
             for (int u = 0; u < UB; ++u)
                 if (ok[u]) load_rec<TI, NV * CI, SI, R>(in, nbv[u], xs[u]);
+            R cx[UB], cy[UB], cz[UB];
+            bool cok[UB];
+#pragma unroll
+            for (int u = 0; u < UB; ++u) cx[u] = kx[u], cy[u] = ky[u], cz[u] = kz[u], cok[u] = ok[u];
+            if constexpr (PREFETCH) load_k(s + LPC * UB);
 #pragma unroll
             for (int u = 0; u < UB; ++u)
-                if (ok[u]) poly_mul_acc<DIM, NV, M, R>(acc, xs[u], kx[u], ky[u], kz[u]);
+                if (cok[u]) poly_mul_acc<DIM, NV, M, R>(acc, xs[u], cx[u], cy[u], cz[u]);
+            if constexpr (!PREFETCH) load_k(s + LPC * UB);
         }
     }
     if constexpr (LPC == 1) {
@@ -601,7 +629,8 @@ __global__ void __launch_bounds__(256, (PREC != PREC_F64 && NS <= 1) ? 4 : 1) k_
 #pragma unroll
     for (int v = 0; v < P; ++v) res[v] = (R)0;
     if (valid) {
-        const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+        int s0, s1;
+        slot_range(mesh, c, s0, s1);
         const bool own_flag = a.flags && a.flags[c];
         GlobalSrc<DIM, NV, PREC> src{a, mesh};
 #pragma unroll 2
@@ -765,7 +794,8 @@ __global__ void __launch_bounds__(256) k_gather(DevMesh mesh, StageArgs a)
     R res[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) res[v] = (R)0;
-    const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+    int s0, s1;
+    slot_range(mesh, c, s0, s1);
     for (int s = s0; s < s1; ++s) {
         const int2 sw = __ldg(mesh.slot2 + s);
         const long long f = (long long)((unsigned)sw.y >> 2);
@@ -844,7 +874,8 @@ __global__ void __launch_bounds__(TILE) k_stage_tile(DevMesh mesh, StageArgs a)
     R res[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) res[v] = (R)0;
-    const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+    int s0, s1;
+    slot_range(mesh, c, s0, s1);
     const bool own_flag = a.flags && a.flags[c];
     for (int s = s0; s < s1; ++s) {
         R F[NV];
@@ -883,7 +914,8 @@ __global__ void __launch_bounds__(TILE) k_diff_tile(DevMesh mesh, const void *__
         ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, wx, wy, wz, iv);
         load_rec<TI, NV * CI, SI, R, false>(tin, threadIdx.x, x);
         poly_mul_acc<DIM, NV, M, R>(acc, x, wx, wy, wz);
-        const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+        int s0, s1;
+        slot_range(mesh, c, s0, s1);
         constexpr int UB = diff_batch(NV * CI);
         for (int s = s0; s < s1; s += UB) {
             R kx[UB], ky[UB], kz[UB];
@@ -987,7 +1019,8 @@ __device__ __forceinline__ void diff_cell(const DevMesh &mesh, const void *in_v,
     ld4<R>(Geo<R>::cellk(mesh) + 4ll * c, wx, wy, wz, iv);
     load_rec<TI, NV * CI, SI, R, false>(in, c, x);
     poly_mul_acc<DIM, NV, M, R>(acc, x, wx, wy, wz);
-    const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+    int s0, s1;
+    slot_range(mesh, c, s0, s1);
     for (int s = s0; s < s1; ++s) {
         R kx, ky, kz, kb;
         ld4<R>(Geo<R>::slotk(mesh) + 4ll * s, kx, ky, kz, kb);
@@ -1050,7 +1083,8 @@ __global__ void __launch_bounds__(256) k_batch_stage(DevMesh mesh, StageArgs a, 
         R res[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) res[v] = (R)0;
-        const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+        int s0, s1;
+        slot_range(mesh, c, s0, s1);
         const bool own_flag = a.flags && a.flags[c];
         for (int s = s0; s < s1; ++s) {
             R F[NV];

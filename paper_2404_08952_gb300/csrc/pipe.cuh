@@ -110,7 +110,8 @@ __global__ void __launch_bounds__(NT) k_diff_pipe(DevMesh mesh, const void *__re
                 else load_rec<TI, NV * CI, SI, R>(in, c, x);
                 poly_mul_acc<DIM, NV, M, R>(acc, x, wx, wy, wz);
             }
-            const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+            int s0, s1;
+            slot_range(mesh, c, s0, s1);
             for (int s = s0 + l; s < s1; s += LPC) {
                 R kx, ky, kz, kb;
                 ld4<R, false>(tslot + 4 * (s - s_base), kx, ky, kz, kb);
@@ -262,7 +263,8 @@ __global__ void __launch_bounds__(NT) k_stage_pipe(DevMesh mesh, StageArgs a, in
             const int ci = threadIdx.x / LN, l = threadIdx.x % LN;
             if (ci < nt) {
                 const int c = t0 + ci;
-                const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+                int s0, s1;
+                slot_range(mesh, c, s0, s1);
                 const bool own_flag = a.flags && a.flags[c];
                 for (int s = s0 + l; s < s1; s += LN) {
                     const int2 sw = ts[s - a_lo];
@@ -283,7 +285,8 @@ __global__ void __launch_bounds__(NT) k_stage_pipe(DevMesh mesh, StageArgs a, in
         // phase B: each cell sums its signed fluxes in slot order
         if ((int)threadIdx.x < nt) {
             const int c = t0 + threadIdx.x;
-            const int s0 = __ldg(mesh.off + c), s1 = __ldg(mesh.off + c + 1);
+            int s0, s1;
+            slot_range(mesh, c, s0, s1);
             R res[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) res[v] = (R)0;
