@@ -369,22 +369,20 @@ def run_dolinc(args):
         line["fp64_gpu"] = {"value": v64, "ms_per_step": f["ms"] / args.steps,
                             "speedup_mixed_vs_fp64": value / v64,
                             "l2_rel_mixed_vs_fp64_after_steps": l2, "steps_compared": args.steps + args.warmup}
-    # e2e: the public call with host buffers, copies inside the timed region
+    # e2e: the public call with a host state (pinned): every step moves the state from
+    # host memory into the step's first kernel and the new state back to host memory
+    # from its last one, inside the timed region
     sch = main["sch"]
     ws = main["ws"]
     uh = torch.from_numpy(M.to_lib(u0)).pin_memory()
     ud = torch.empty_like(uh, device="cuda")
     for _ in range(2):
-        ud.copy_(uh, non_blocking=True)
-        dg.dolinc_rk_step(M, sch, dt, ud, ws)
-        uh.copy_(ud, non_blocking=True)
+        dg.dolinc_rk_step_host(M, sch, dt, uh, ud, ws)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        ud.copy_(uh, non_blocking=True)
-        dg.dolinc_rk_step(M, sch, dt, ud, ws)
-        uh.copy_(ud, non_blocking=True)
+        dg.dolinc_rk_step_host(M, sch, dt, uh, ud, ws)
     e1.record(stream)
     torch.cuda.synchronize()
     ems = reduce_max(e0.elapsed_time(e1), dist)

@@ -214,6 +214,22 @@ dolinc_status dolinc_rk_stage(dolinc_mesh *mesh, const dolinc_scheme *scheme, do
 dolinc_status dolinc_rk_step(dolinc_mesh *mesh, const dolinc_scheme *scheme, double dt, double *u_dev,
                              void *ws_dev, size_t ws_bytes, dolinc_stream stream);
 
+/* One SSP-RK3 step (Sec 3), computed as dolinc_rk_step computes it, of a state held
+ * in host memory: u_host (FP64 [v][c], library order) holds the step's input and
+ * receives the new state.  When u_host is page-locked and mapped into the device
+ * address space (cudaHostAlloc / cudaMallocHost / cudaHostRegister memory, as pinned
+ * tensors are), the step's first kernel reads it in place over the host link, keeping
+ * a device copy of the start state in u_dev, and the last stage writes the new state
+ * to it in place: the transfers are part of the step's own kernels.  Other host
+ * memory is copied to u_dev and back with cudaMemcpyAsync on the stream.
+ * u_dev: caller-owned device scratch of nv * n_cells doubles, contents afterwards
+ * unspecified.  Like every call here the step is asynchronous: u_host and u_dev must
+ * stay valid and untouched until the stream has completed it.  Errors as
+ * dolinc_rk_step; DOLINC_ERR_INVALID_ARG when u_dev is not device memory or aliases
+ * u_host. */
+dolinc_status dolinc_rk_step_host(dolinc_mesh *mesh, const dolinc_scheme *scheme, double dt, double *u_host,
+                                  double *u_dev, void *ws_dev, size_t ws_bytes, dolinc_stream stream);
+
 /* One SSP-RK3 step, like dolinc_rk_step, without a caller workspace and without any
  * allocation: for callers that hold only the field's device pointer and cannot obtain
  * device memory themselves (for example a plugin that a host application hands its

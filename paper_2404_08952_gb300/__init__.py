@@ -26,7 +26,7 @@ ABI_SYMBOLS = (
     "dolinc_mesh_create", "dolinc_mesh_destroy", "dolinc_mesh_get_info", "dolinc_mesh_permutation",
     "dolinc_mesh_geometry", "dolinc_workspace_size", "dolinc_workspace_init", "dolinc_diff_layout",
     "dolinc_differentials", "dolinc_reconstruct_faces", "dolinc_residual", "dolinc_rk_stage",
-    "dolinc_rk_step", "dolinc_set_flags", "dolinc_set_boundary_values", "dolinc_sync_status", "dolinc_profile_enable",
+    "dolinc_rk_step", "dolinc_rk_step_host", "dolinc_set_flags", "dolinc_set_boundary_values", "dolinc_sync_status", "dolinc_profile_enable",
     "dolinc_profile_read", "dolinc_rk_step_noalloc", "dolinc_autotune", "dolinc_set_tuning",
     "dolinc_criterion", "dolinc_indicator_features", "dolinc_mlp_create", "dolinc_mlp_destroy",
     "dolinc_mlp_get_params", "dolinc_mlp_set_params", "dolinc_mlp_forward", "dolinc_mlp_loss_grad",
@@ -82,7 +82,7 @@ def load(path=LIB_PATH):
             "dolinc_reconstruct_faces": [P, P, P, P, P, P, S, P],
             "dolinc_residual": [P, P, P, P, P, S, P],
             "dolinc_rk_stage": [P, P, D, I, P, P, P, P, S, P],
-            "dolinc_rk_step": [P, P, D, P, P, S, P],
+            "dolinc_rk_step": [P, P, D, P, P, S, P], "dolinc_rk_step_host": [P, P, D, P, P, P, S, P],
             "dolinc_set_flags": [P, P], "dolinc_set_boundary_values": [P, C.c_int, P],
             "dolinc_sync_status": [P, P, P], "dolinc_last_error": [],
             "dolinc_profile_enable": [P, I], "dolinc_profile_read": [P, P, P],
@@ -281,6 +281,15 @@ def dolinc_rk_step(mesh, scheme, dt, u, ws, stream=None):
     s = scheme.c()
     _check(load().dolinc_rk_step(mesh.handle, C.byref(s), float(dt), _ptr(u), _ptr(ws), ws.numel(),
                                  _stream(stream)))
+
+
+def dolinc_rk_step_host(mesh, scheme, dt, u_host, u_dev, ws, stream=None):
+    """One SSP-RK3 step of the FP64 state u_host (a CPU tensor or array, updated in
+    place; pinned memory is read and written by the step's kernels directly), with
+    u_dev a device scratch tensor of the same size.  Asynchronous on the stream."""
+    s = scheme.c()
+    _check(load().dolinc_rk_step_host(mesh.handle, C.byref(s), float(dt), _ptr(u_host), _ptr(u_dev), _ptr(ws),
+                                      ws.numel(), _stream(stream)))
 
 
 def dolinc_rk_step_noalloc(mesh, scheme, dt, u, stream=None):

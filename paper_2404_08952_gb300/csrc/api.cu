@@ -630,7 +630,7 @@ dolinc_status dolinc_differentials(dolinc_mesh *m, const dolinc_scheme *s, const
     const PathFns *p = path_for(m, s, needed_order(*s));
     if (!p) return fail(DOLINC_ERR_UNSUPPORTED, "no kernel for this (dim, nv, order, precision)");
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
-    timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, u, B(ws, L.o0[0]), cs); });
+    timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, u, B(ws, L.o0[0]), nullptr, cs); });
     size_t o = 0;
     const void *prev = B(ws, L.o0[0]);
     for (int mm = 1; mm <= order; ++mm) {
@@ -656,7 +656,7 @@ dolinc_status dolinc_reconstruct_faces(dolinc_mesh *m, const dolinc_scheme *s, c
     const PathFns *p = path_for(m, s, needed_order(*s));
     if (!p) return fail(DOLINC_ERR_UNSUPPORTED, "no kernel for this (dim, nv, order, precision)");
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
-    timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, u, B(ws, L.o0[0]), cs); });
+    timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, u, B(ws, L.o0[0]), nullptr, cs); });
     run_diffs(m, p, ws, L, L.o0[0], s->n_diff, tune_for(m, s), cs);
     StageArgs a = base_args(m, s, ws, L, L.o0[0]);
     timed(m, DOLINC_KERNEL_FACES, cs, [&] { p->faces(m->d, a, fL, fR, cs); });
@@ -674,7 +674,7 @@ dolinc_status dolinc_residual(dolinc_mesh *m, const dolinc_scheme *s, const doub
     const PathFns *p = path_for(m, s, needed_order(*s));
     if (!p) return fail(DOLINC_ERR_UNSUPPORTED, "no kernel for this (dim, nv, order, precision)");
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
-    timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, u, B(ws, L.o0[0]), cs); });
+    timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, u, B(ws, L.o0[0]), nullptr, cs); });
     run_diffs(m, p, ws, L, L.o0[0], s->n_diff, tune_for(m, s), cs);
     StageArgs a = base_args(m, s, ws, L, L.o0[0]);
     a.mode = 0;
@@ -696,7 +696,7 @@ dolinc_status dolinc_rk_stage(dolinc_mesh *m, const dolinc_scheme *s, double dt,
     const PathFns *p = path_for(m, s, needed_order(*s));
     if (!p) return fail(DOLINC_ERR_UNSUPPORTED, "no kernel for this (dim, nv, order, precision)");
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
-    timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, us, B(ws, L.o0[0]), cs); });
+    timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, us, B(ws, L.o0[0]), nullptr, cs); });
     run_diffs(m, p, ws, L, L.o0[0], s->n_diff, tune_for(m, s), cs);
     StageArgs a = base_args(m, s, ws, L, L.o0[0]);
     a.mode = 1;
@@ -711,21 +711,24 @@ dolinc_status dolinc_rk_stage(dolinc_mesh *m, const dolinc_scheme *s, double dt,
     return launch_check();
 }
 
-dolinc_status dolinc_rk_step(dolinc_mesh *m, const dolinc_scheme *s, double dt, double *u, void *ws,
-                             size_t ws_bytes, dolinc_stream stream)
+}  // extern "C"
+
+namespace {
+
+// One SSP-RK3 step.  The first kernel reads the step's state from u_in and, when
+// u_dev differs from it, also writes it to u_dev; the stages read the step's start
+// state from u_dev; the last stage writes the new state to u_out.  dolinc_rk_step
+// passes one device buffer for all three.
+dolinc_status rk_step_impl(dolinc_mesh *m, const dolinc_scheme *s, double dt, const double *u_in, double *u_dev,
+                           double *u_out, void *ws, const WsLayout &L, cudaStream_t cs)
 {
     static const double A[3] = {0.0, 0.75, 1.0 / 3.0}, Bc[3] = {1.0, 0.25, 2.0 / 3.0};
-    dolinc_status st = check_scheme(m, s);
-    if (st) return st;
-    WsLayout L;
-    if ((st = check_ws(m, s, ws, ws_bytes, L))) return st;
-    if (!u) return fail(DOLINC_ERR_INVALID_ARG, "null field");
     const PathFns *p = path_for(m, s, needed_order(*s));
     if (!p) return fail(DOLINC_ERR_UNSUPPORTED, "no kernel for this (dim, nv, order, precision)");
-    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     double *ust = reinterpret_cast<double *>(B(ws, L.ustage));
     const Tune tn = tune_for(m, s);
-    timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, u, B(ws, L.o0[0]), cs); });
+    timed(m, DOLINC_KERNEL_PACK, cs,
+          [&] { p->pack(m->d, u_in, B(ws, L.o0[0]), u_dev != u_in ? u_dev : nullptr, cs); });
     bool pending = false;
     auto join = [&] {
         if (pending) cudaStreamWaitEvent(cs, m->ev_join, 0);
@@ -739,8 +742,8 @@ dolinc_status dolinc_rk_step(dolinc_mesh *m, const dolinc_scheme *s, double dt, 
             StageArgs a = base_args(m, s, ws, L, L.o0[sg]);
             a.mode = 2;
             a.rk = sg;
-            a.u0 = u;
-            a.out = u;
+            a.u0 = u_dev;
+            a.out = u_out;
             a.dt = dt;
             a.dacc = reinterpret_cast<float *>(B(ws, L.dacc));
             a.rec_start = B(ws, L.o0[0]);
@@ -756,18 +759,64 @@ dolinc_status dolinc_rk_step(dolinc_mesh *m, const dolinc_scheme *s, double dt, 
         pending = run_diffs_split(m, p, ws, L, L.o0[cur], s, tn, cs);
         StageArgs a = base_args(m, s, ws, L, L.o0[cur]);
         a.mode = 1;
-        a.u0 = u;
-        a.us = sg == 0 ? u : ust;
-        a.out = sg == 2 ? u : ust;
+        a.u0 = u_dev;
+        a.us = sg == 0 ? u_dev : ust;
+        a.out = sg == 2 ? u_out : ust;
         a.A = A[sg];
         a.B = Bc[sg];
         a.dt = dt;
         a.o0_next = sg == 2 ? nullptr : B(ws, L.o0[1 - cur]);
-        timed(m, DOLINC_KERNEL_STAGE, cs, [&] { p->stage(m->d, a, tune_for(m, s), cs); });
+        timed(m, DOLINC_KERNEL_STAGE, cs, [&] { p->stage(m->d, a, tn, cs); });
         cur = 1 - cur;
     }
     join();
     return launch_check();
+}
+
+}  // namespace
+
+extern "C" {
+
+dolinc_status dolinc_rk_step(dolinc_mesh *m, const dolinc_scheme *s, double dt, double *u, void *ws,
+                             size_t ws_bytes, dolinc_stream stream)
+{
+    dolinc_status st = check_scheme(m, s);
+    if (st) return st;
+    WsLayout L;
+    if ((st = check_ws(m, s, ws, ws_bytes, L))) return st;
+    if (!u) return fail(DOLINC_ERR_INVALID_ARG, "null field");
+    return rk_step_impl(m, s, dt, u, u, u, ws, L, reinterpret_cast<cudaStream_t>(stream));
+}
+
+dolinc_status dolinc_rk_step_host(dolinc_mesh *m, const dolinc_scheme *s, double dt, double *u_host, double *u_dev,
+                                  void *ws, size_t ws_bytes, dolinc_stream stream)
+{
+    dolinc_status st = check_scheme(m, s);
+    if (st) return st;
+    WsLayout L;
+    if ((st = check_ws(m, s, ws, ws_bytes, L))) return st;
+    if (!u_host || !u_dev) return fail(DOLINC_ERR_INVALID_ARG, "null field");
+    if (u_host == u_dev) return fail(DOLINC_ERR_INVALID_ARG, "u_host and u_dev must be different buffers");
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, u_dev) != cudaSuccess ||
+        (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        return fail(DOLINC_ERR_INVALID_ARG, "u_dev must be device memory");
+    }
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    // page-locked, mapped host memory: the kernels read and write it in place
+    void *mapped = nullptr;
+    if (cudaHostGetDevicePointer(&mapped, u_host, 0) == cudaSuccess && mapped) {
+        double *uh = static_cast<double *>(mapped);
+        return rk_step_impl(m, s, dt, uh, u_dev, uh, ws, L, cs);
+    }
+    cudaGetLastError();
+    // other host memory: copied in and out on the stream
+    const size_t bytes = (size_t)m->h.n_cells * s->nv * sizeof(double);
+    CU(cudaMemcpyAsync(u_dev, u_host, bytes, cudaMemcpyHostToDevice, cs));
+    if ((st = rk_step_impl(m, s, dt, u_dev, u_dev, u_dev, ws, L, cs))) return st;
+    CU(cudaMemcpyAsync(u_host, u_dev, bytes, cudaMemcpyDeviceToHost, cs));
+    return DOLINC_OK;
 }
 
 dolinc_status dolinc_profile_enable(dolinc_mesh *m, int enable)
@@ -834,7 +883,7 @@ dolinc_status dolinc_autotune(dolinc_mesh *m, const dolinc_scheme *s, const doub
     if (!cached) {
         const bool prof = m->prof;
         m->prof = false;
-        p->pack(m->d, u, B(ws, L.o0[0]), cs);
+        p->pack(m->d, u, B(ws, L.o0[0]), nullptr, cs);
         cudaEvent_t e0, e1;
         CU(cudaEventCreate(&e0));
         CU(cudaEventCreate(&e1));
@@ -932,7 +981,7 @@ dolinc_status indicator_prep(dolinc_mesh *m, const dolinc_scheme *s, const doubl
     const int nsr = needed_order(*s) > 2 ? needed_order(*s) : 2;
     *fi = &g_ind[indicator_index(m->h.dim, nsr, s->precision)];
     if (!(*fi)->criterion) return fail(DOLINC_ERR_UNSUPPORTED, "no indicator kernel for this scheme");
-    timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, u, B(ws, L.o0[0]), cs); });
+    timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, u, B(ws, L.o0[0]), nullptr, cs); });
     run_diffs(m, p, ws, L, L.o0[0], s->n_diff, tune_for(m, s), cs);
     return DOLINC_OK;
 }

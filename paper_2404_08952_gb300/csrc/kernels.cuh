@@ -94,15 +94,25 @@ template <class R, bool LDG = true> __device__ __forceinline__ void ld4(const R 
 }
 
 // ------------------------------------------------------------------ pack
+// copy (may be null): also written with u, e.g. a device copy of a state that u reads
+// from mapped host memory
 template <int NV, int PREC>
-__global__ void __launch_bounds__(256) k_pack(int n, const double *__restrict__ u, typename PrecT<PREC>::T0 *o0)
+__global__ void __launch_bounds__(256) k_pack(int n, const double *__restrict__ u, typename PrecT<PREC>::T0 *o0,
+                                              double *__restrict__ copy)
 {
     using R = typename PrecT<PREC>::R;
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
+    double x[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) x[i] = u[(long long)i * n + c];
+    if (copy) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) copy[(long long)i * n + c] = x[i];
+    }
     R v[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] = (R)u[(long long)i * n + c];
+    for (int i = 0; i < NV; ++i) v[i] = (R)x[i];
     store_rec<typename PrecT<PREC>::T0, NV, rec_stride(NV, (int)sizeof(typename PrecT<PREC>::T0))>(o0, c, v);
 }
 

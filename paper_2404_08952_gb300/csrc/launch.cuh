@@ -35,7 +35,7 @@ inline int persistent_grid(const void *kernel, int threads, size_t smem)
 }
 
 struct PathFns {
-    void (*pack)(const DevMesh &, const double *, void *, cudaStream_t);
+    void (*pack)(const DevMesh &, const double *, void *, double *copy, cudaStream_t);
     void (*diff)(const DevMesh &, int M, const void *, void *, const Tune &, unsigned *, cudaStream_t);
     void (*stage)(const DevMesh &, const StageArgs &, const Tune &, cudaStream_t);
     void (*faces)(const DevMesh &, const StageArgs &, double *, double *, cudaStream_t);
@@ -46,10 +46,10 @@ inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 constexpr size_t kMaxSmem = 200 * 1024;   // dynamic shared memory a tiled block may use
 
 template <int DIM, int NV, int NS, int PREC> struct Path {
-    static void pack(const DevMesh &m, const double *u, void *o0, cudaStream_t s)
+    static void pack(const DevMesh &m, const double *u, void *o0, double *copy, cudaStream_t s)
     {
         k_pack<NV, PREC><<<nblk(m.n_cells, 256), 256, 0, s>>>(m.n_cells, u,
-                                                              static_cast<typename PrecT<PREC>::T0 *>(o0));
+                                                              static_cast<typename PrecT<PREC>::T0 *>(o0), copy);
     }
     // bytes of one output record of order MM, and the shared memory a block of bs
     // threads (one cell each) needs to stage its output records for the bulk store
