@@ -3,7 +3,10 @@
  * features (TEST INFRASTRUCTURE ONLY; see dolinc_oracle.c).
  *
  * The paper has no troubled-cell criterion; this one is built only from quantities
- * the paper defines (reading stated in the design notes, parity unpinned by the paper):
+ * the paper defines (reading stated in the design notes).  The paper cannot pin it;
+ * its computation is pinned by closed forms in the tests (equal indicators of
+ * quadratics on geometric strips, positivity of uniform states, the inputs of linear
+ * fields on un-jittered triangles, the neighbour choice by brute force):
  * cell c is troubled if, at any of its faces,
  *   (i)  a reconstructed face state (either orientation, the scheme's fixed stencil)
  *        has density <= 0 or pressure <= 0, or

@@ -468,3 +468,126 @@ def test_weno5_exact_for_quadratics_on_geometric_strips(g):
     assert ok.sum() >= 6
     np.testing.assert_allclose(L[0][ok], exact[ok], rtol=0, atol=1e-10)
     np.testing.assert_allclose(R[0][ok], exact[ok], rtol=0, atol=1e-10)
+
+
+# ------------------------------------------------------------------ troubled-cell criterion and network inputs
+# The paper has no troubled-cell criterion; the one built here (from the paper's ENO3
+# indicators, Sec 2.4) is pinned by what its ingredients must give in closed form.
+
+def _strip_quadratic(widths):
+    """Transmissive strip of the given widths with quadratic rho and rho E (cell
+    averages in closed form) and constant momentum, 2D Euler (rho, rho u, rho v, rho E)."""
+    m = synth.strip_mesh(widths, height=0.05, boundary="transmissive")
+    xs = np.concatenate([[0.0], np.cumsum(widths)])
+    a, b = xs[:-1], xs[1:]
+
+    def avg(c0, c1, c2):
+        return c0 + c1 * (a + b) / 2 + c2 * (a * a + a * b + b * b) / 3
+    n = len(widths)
+    u = np.stack([avg(1.0, 0.3, 0.2), np.full(n, 0.1), np.zeros(n), avg(2.5, 0.1, -0.15)])
+    return m, u
+
+
+@pytest.mark.parametrize("growth", [1.1, 1.0 / 1.15, 1.0])
+def test_criterion_indicators_are_equal_for_quadratics_on_geometric_strips(growth):
+    """On a geometric strip the three g-scaled second differences D_L, D_C, D_R of a
+    quadratic's cell averages are equal (they are the same multiple of its second
+    derivative), and the DOLINC inversion of the far values is exact there.  So with
+    kappa just above 1 no interior cell is flagged, and with kappa just below 1 every
+    interior cell is: a wrong power of g, a swapped side or a wrong sign in one of the
+    indicators breaks the equality and fails one of the two."""
+    widths = 0.05 * growth ** np.arange(23)
+    m, u = _strip_quadratic(widths)
+    O = oracle.Oracle(m)
+    sch = oracle.Scheme(k=3, r=1, n_diff=2, nv=4, flux="rusanov", gamma=1.4)
+    inner = slice(3, -3)                  # cells whose two-cell neighbourhoods avoid the ends
+    above = O.criterion(u, sch, kappa=1 + 1e-6, eps=1e-10)
+    below = O.criterion(u, sch, kappa=1 - 1e-6, eps=1e-10)
+    assert not above[inner].any()
+    assert below[inner].all()
+    # the relative threshold: with eps above |D_C| / (|phi_0| + |phi_1|) nothing is flagged
+    assert not O.criterion(u, sch, kappa=1 - 1e-6, eps=1.0)[inner].any()
+
+
+def test_criterion_positivity_special_cases():
+    """A uniform state: every face state equals it (constants are reconstructed
+    exactly), the indicators vanish, so only the positivity test can flag: all cells
+    when the pressure or the density is not positive, none otherwise."""
+    m = synth.tri_mesh(6, 5, jitter=0.2, seed=4)
+    O = oracle.Oracle(m)
+    sch = oracle.Scheme(k=3, r=1, n_diff=2, nv=4, flux="rusanov", gamma=1.4)
+    n = O.n_cells
+
+    def state(rho, mu, E):
+        return np.stack([np.full(n, rho), np.full(n, mu), np.full(n, 0.0), np.full(n, E)])
+    assert not O.criterion(state(1.0, 0.3, 2.5), sch).any()
+    assert O.criterion(state(1.0, 2.0, 1.0), sch).all()          # p = 0.4 (1 - 2) < 0
+    assert O.criterion(state(-0.5, 0.0, 1.0), sch).all()         # rho < 0, p > 0
+    assert O.criterion(state(1.0, 0.0, 0.0), sch).all()          # p = 0
+
+
+def test_network_inputs_of_linear_fields_on_uniform_triangles():
+    """On un-jittered split quads the Gauss gradient of a linear field is exact
+    (pinned above), so a cell's first-order inputs are log(1 + max_f |2 a.d_f| / s)
+    over its faces (a the field's gradient, d_f the centroid-to-centroid vector, s the
+    cell's rho, |rho E| or sqrt(rho |rho E|), the momentum taken as the norm of its
+    components' differentials), and its second-order inputs vanish wherever the
+    first-order differentials of its neighbours are exact."""
+    m = synth.tri_mesh(8, 8, jitter=0.0, boundary="transmissive")
+    O = oracle.Oracle(m)
+    sch = oracle.Scheme(k=3, r=1, n_diff=2, nv=4, flux="rusanov", gamma=1.4)
+    grads = np.array([[0.4, -0.3], [0.2, 0.1], [-0.1, 0.25], [0.5, 0.35]])
+    base = np.array([2.0, 0.3, -0.2, 4.0])
+    x = O.xc[:, :2]
+    u = np.stack([x @ grads[v] + base[v] for v in range(4)])
+    tiny = 1e-6
+    own, _ = O.features(u, sch, tiny=tiny)
+    bnd = np.zeros(O.n_cells, bool)
+    bnd[O.owner[O.neigh < 0]] = True
+    nbr = [[] for _ in range(O.n_cells)]
+    for f in range(len(O.owner)):
+        P, Q = O.owner[f], O.neigh[f]
+        if Q >= 0:
+            nbr[P].append((Q, O.d[f, :2]))
+            nbr[Q].append((P, -O.d[f, :2]))
+    inner = [c for c in range(O.n_cells) if not bnd[c]]
+    deep = [c for c in inner if all(not bnd[q] for q, _ in nbr[c])]
+    assert len(deep) > 20
+    for c in deep:
+        ds = np.array([d for _, d in nbr[c]])
+        rho, E = u[0, c], abs(u[3, c])
+        r = np.abs(2 * ds @ grads[0]).max()
+        e = np.abs(2 * ds @ grads[3]).max()
+        mo = np.sqrt((2 * ds @ grads[1]) ** 2 + (2 * ds @ grads[2]) ** 2).max()
+        want = np.log1p([r / (rho + tiny), e / (E + tiny), mo / (np.sqrt(rho * E) + tiny)])
+        np.testing.assert_allclose(own[c, :3], want, rtol=1e-10)
+    # the order-2 differential of c is the Gauss gradient of the (exact, constant)
+    # first-order ones of c and its neighbours, none of which touches the boundary
+    np.testing.assert_allclose(own[deep, 3:], 0.0, atol=1e-10)
+
+
+def test_network_input_neighbours_by_brute_force():
+    """The 24 inputs of a cell: its own 6, then the 6 of three face neighbours (the
+    cell itself across a boundary face), the largest three in lexicographic order of
+    their 6 inputs, largest first.  Checked against sorting all of them."""
+    m = synth.tri_mesh(7, 6, jitter=0.2, seed=8, boundary="transmissive")
+    O = oracle.Oracle(m)
+    sch = oracle.Scheme(k=3, r=1, n_diff=2, nv=4, flux="rusanov", gamma=1.4)
+    rng = np.random.default_rng(3)
+    x = O.xc[:, :2]
+    u = np.stack([1.0 + 0.2 * np.sin(6 * x[:, 0] + 1) * np.cos(5 * x[:, 1]),
+                  0.3 * np.sin(4 * x[:, 1]), 0.2 * np.cos(3 * x[:, 0]),
+                  2.5 + 0.3 * np.cos(7 * x[:, 0] - 2 * x[:, 1])]) + 1e-3 * rng.standard_normal((4, O.n_cells))
+    own, x24 = O.features(u, sch)
+    cand = [[] for _ in range(O.n_cells)]
+    for f in range(len(O.owner)):
+        P, Q = O.owner[f], O.neigh[f]
+        if Q >= 0:
+            cand[P].append(Q)
+            cand[Q].append(P)
+        else:
+            cand[P].append(P)
+    for c in range(O.n_cells):
+        rows = sorted((tuple(own[q]) for q in cand[c]), reverse=True)[:3]
+        np.testing.assert_array_equal(x24[c, :6], own[c])
+        np.testing.assert_array_equal(x24[c, 6:], np.concatenate(rows))
