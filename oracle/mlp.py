@@ -6,6 +6,9 @@ vector in the order W1 [64x24], b1 [64], W2 [64x64], b2, W3 [64x64], b3, W4 [1x6
 b4 [1] (row-major, W[out][in]).  The weights the network computes with are the
 bfloat16 roundings (round to nearest even) of the master values.
 Loss: binary cross-entropy on the logit with a weight on positive labels.
+Pinned in the tests by central differences of the loss (gradient), hand-computable
+networks (forward), torch's float32 -> bfloat16 conversion (rounding) and the
+first-step property of bias-corrected Adam.
 """
 import numpy as np
 

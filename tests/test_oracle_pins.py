@@ -591,3 +591,75 @@ def test_network_input_neighbours_by_brute_force():
         rows = sorted((tuple(own[q]) for q in cand[c]), reverse=True)[:3]
         np.testing.assert_array_equal(x24[c, :6], own[c])
         np.testing.assert_array_equal(x24[c, 6:], np.concatenate(rows))
+
+
+# ------------------------------------------------------------------ indicator network reference
+
+def test_network_gradient_matches_central_differences():
+    """The reference backward pass against central differences of its own loss, in
+    FP64 with unrounded weights (every hidden unit kept away from its ReLU kink)."""
+    from oracle import mlp
+    rng = np.random.default_rng(5)
+    theta = mlp.init(3).astype(np.float64)
+    theta[mlp.N_PARAMS - 1] = 0.2
+    X = rng.standard_normal((7, 24))
+    y = (rng.random(7) < 0.4).astype(np.float64)
+    _, A = mlp.forward(theta, X, weights_bf16=False)
+    for H in A[1:-1]:
+        assert np.abs(H[H > 0]).min() > 1e-6 or (H > 0).sum() == 0
+    L, G = mlp.loss_and_grad(theta, X, y, pos_weight=2.5, weights_bf16=False)
+    idx = np.concatenate([rng.choice(mlp.N_PARAMS - 200, 40, replace=False), np.arange(mlp.N_PARAMS - 65, mlp.N_PARAMS)])
+    h = 1e-6
+    for i in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (mlp.loss_and_grad(tp, X, y, 2.5, False)[0] - mlp.loss_and_grad(tm, X, y, 2.5, False)[0]) / (2 * h)
+        assert abs(fd - G[i]) < 1e-7 + 1e-5 * abs(fd)
+
+
+def test_network_forward_special_cases():
+    """All weights zero: the logit is the last bias for every input.  One unit per
+    layer on the identity path (exact in bfloat16): the logit is relu(x_0) plus the
+    bias.  All parameters zero: the logit is 0 and the loss of either label is log 2."""
+    from oracle import mlp
+    X = np.array([[0.75] + [0.3] * 23, [-1.5] + [2.0] * 23])
+    theta = np.zeros(mlp.N_PARAMS)
+    theta[-1] = -0.625
+    z, _ = mlp.forward(theta, X)
+    np.testing.assert_array_equal(z, [-0.625, -0.625])
+    o = 0
+    for (n_out, n_in) in mlp.SIZES:
+        theta[o] = 1.0                        # W[0][0]
+        o += n_out * n_in + n_out
+    z, _ = mlp.forward(theta, X)
+    np.testing.assert_array_equal(z, [0.75 - 0.625, -0.625])
+    L, _ = mlp.loss_and_grad(np.zeros(mlp.N_PARAMS), X, np.array([1.0, 0.0]), pos_weight=1.0)
+    assert abs(L - np.log(2.0)) < 1e-15
+
+
+def test_bfloat16_rounding_is_round_to_nearest_even():
+    """Against torch's float32 -> bfloat16 conversion (round to nearest even), on
+    halfway cases, near-halfway cases and random values."""
+    torch = pytest.importorskip("torch")
+    from oracle import mlp
+    one = np.float32(1.0)
+    ulp = np.float32(2.0 ** -7)
+    x = np.array([one + ulp / 2, one + 3 * ulp / 2, one + ulp / 2 + np.float32(2.0 ** -20), -(one + ulp / 2),
+                  np.float32(3.0e-39), np.float32(65504.0)], dtype=np.float32)
+    x = np.concatenate([x, np.random.default_rng(0).standard_normal(1000).astype(np.float32) * 10])
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(mlp.bf16(x), want)
+    assert mlp.bf16(np.float32(1.0 + 2.0 ** -8)) == 1.0                   # tie to even (down)
+    assert mlp.bf16(np.float32(1.0 + 3 * 2.0 ** -8)) == 1.0 + 2.0 ** -6    # tie to even (up)
+
+
+def test_adam_first_step_moves_each_parameter_by_the_learning_rate():
+    """Bias-corrected Adam from zero moments: the first update is lr g / (|g| + eps),
+    i.e. lr times the sign of the gradient for gradients far above eps."""
+    from oracle import mlp
+    g = np.array([3.0, -0.02, 1e-3, -40.0])
+    th, m, v = mlp.adam(np.zeros(4), np.zeros(4), np.zeros(4), g, 1, lr=0.01)
+    np.testing.assert_allclose(th, -0.01 * np.sign(g), rtol=1e-5)
+    np.testing.assert_allclose(m, 0.1 * g)
+    np.testing.assert_allclose(v, 0.001 * g * g)
