@@ -1,16 +1,22 @@
-// DOLINC stage kernels for sm_103a.  One thread per cell; each cell gathers over its
-// own face slots, so no kernel uses atomics on field data.
+// DOLINC stage kernels for sm_103a.  Each cell gathers over its own face slots, so no
+// kernel uses atomics on field data.
 //
-//   k_pack   FP64 cell averages [v][c]  ->  order-0 record (bulk precision, per cell)
-//   k_diff   order m-1 -> order m differential (Sec 2.3), the Gauss step on the
-//            polynomial coefficients:  p_m = w_c (S.d) p_{m-1,c} + sum_f k_f (S.d) p_{m-1,nb}
-//   k_stage  per face: contract both cells' differentials with d, invert + reconstruct
-//            both orientations (Secs 2.3-2.4), numerical flux (Sec 3), residual,
-//            then the SSP-RK3 combination in FP64 and the next order-0 record.
-//            A face is evaluated identically from its two cells (canonical
-//            owner -> neighbour orientation, same operands, same order), so the two
-//            contributions cancel exactly in the sum over cells.
-//   k_faces  face states written in the caller's face order (diagnostic entry point)
+//   k_pack    FP64 cell averages [v][c]  ->  order-0 record (bulk precision, per cell)
+//   k_diff    order m-1 -> order m differential (Sec 2.3), the Gauss step on the
+//             polynomial coefficients:  p_m = w_c (S.d) p_{m-1,c} + sum_f k_f (S.d) p_{m-1,nb}
+//   k_bnd_grad  Dirichlet / Neumann faces' correction of the first-order record (Sec 2.6)
+//   k_stage   per cell and face: contract both cells' differentials with d, invert +
+//             reconstruct both orientations (Secs 2.3-2.4), numerical flux (Sec 3),
+//             residual, then the stage epilogue: the SSP-RK3 combination in FP64, or
+//             below FP64 the increment form, and the next order-0 record.
+//             A face is evaluated identically from its two cells (canonical
+//             owner -> neighbour orientation, same operands, same order), so the two
+//             contributions cancel exactly in the sum over cells.
+//   k_flux + k_gather  the same stage face-centric: every face evaluated once into a
+//             flux array, then each cell sums its signed fluxes in slot order
+//   k_stage_tile / k_diff_tile  block-tiled variants (records staged in shared memory)
+//   k_batch_stage  one cooperative launch per stage over many concatenated meshes
+//   k_faces   face states written in the caller's face order (diagnostic entry point)
 #pragma once
 #include "common.cuh"
 #include "device_mesh.hpp"

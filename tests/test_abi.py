@@ -86,6 +86,12 @@ def test_host_validation_rejects_bad_meshes(lib):
     st, h = _create(lib, d)
     assert st == 2 and b"closed" in lib.dolinc_last_error() or b"volume" in lib.dolinc_last_error()
     assert lib.dolinc_mesh_create(None, C.byref(h)) == 1
+    # empty meshes: no cells, no faces
+    for field in ("n_cells", "n_faces"):
+        d, keep = _desc_from(m)
+        setattr(d, field, 0)
+        st, h = _create(lib, d)
+        assert st == 2 and b"empty" in lib.dolinc_last_error()
 
 
 def test_oracle_and_library_share_no_code():
