@@ -815,12 +815,20 @@ def run_reference(args):
     value = cells * args.steps / t
     sample = ("one SSP-RK3 stage per step on the %s family at %d^3 hexes x 5 (%d cells), "
               "FP64 C oracle, single thread" % (args.workload, args.ref_size, cells))
+    # the workload the other arm times (its config), of which each step here is a sample
+    config = {"workload": args.workload, "cells": cells, "scheme_order": w["info"].get("order"),
+              "precision": args.precision}
+    if args.workload == "euler3d_tet64":
+        n = args.size or 64
+        config = {"workload": args.workload, "cells": 5 * n ** 3, "faces": 10 * n ** 3,
+                  "scheme_order": args.order, "stencil_k_r": list(synth.STENCIL_OF_ORDER[args.order]),
+                  "n_diff": w["scheme"]["n_diff"], "precision": args.precision, "flux": w["scheme"]["flux"],
+                  "stages_per_step": 3, "parallelism": "single GPU"}
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "cells": cells, "scheme_order": w["info"].get("order"),
-                   "precision": "fp64"},
+        "config": config,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
