@@ -122,6 +122,50 @@ __device__ __forceinline__ void store_rec(T *__restrict__ base, long long cell, 
     }
 }
 
+DOL_HD constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+
+// store_rec into shared memory whose records (one per thread t, S * sizeof(T) bytes, a
+// multiple of 16) are contiguous, as a bulk copy to global memory wants them.  A
+// straight store would have the 8 threads of each 16-byte-per-thread store wavefront
+// write records 2^k x 16 bytes apart, i.e. into the same banks; here thread t writes
+// its 16-byte chunks in an order rotated by r_t, chosen so that those 8 threads always
+// hit 8 distinct groups of 4 banks.  The bytes written are those of store_rec.
+template <class T, int N, int S, class R>
+__device__ __forceinline__ void store_rec_smem(unsigned char *base, int t, const R *in)
+{
+    constexpr int B = S * (int)sizeof(T);
+    static_assert(B % 16 == 0, "records of whole 16-byte chunks");
+    constexpr int NCH = B / 16, V = 16 / (int)sizeof(T), G = gcd_c(NCH, 8);
+    uint4 q[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        T *e = reinterpret_cast<T *>(&q[c]);
+#pragma unroll
+        for (int j = 0; j < V; ++j) e[j] = (c * V + j < N) ? to_store<T, R>(in[c * V + j]) : to_store<T, R>((R)0);
+    }
+    // chunk slot (t * NCH + p) lands in bank group (t * NCH + p) mod 8: with
+    // p = (j + r_t) mod NCH and r_t = (t / (8 / G)) mod NCH those are distinct over
+    // any 8 consecutive t for every j
+    const int r = (t / (8 / G)) % NCH;
+    // rotate: q[j] <- q[(j + r) mod NCH], by the binary digits of r
+#pragma unroll
+    for (int b = 1; b < NCH; b <<= 1) {
+        uint4 u[NCH];
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) u[j] = q[(j + b) % NCH];
+        const bool on = (r & b) != 0;
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) q[j] = on ? u[j] : q[j];
+    }
+    uint4 *rec = reinterpret_cast<uint4 *>(base + (size_t)t * B);
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) {
+        int p = j + r;
+        p = p >= NCH ? p - NCH : p;
+        rec[p] = q[j];
+    }
+}
+
 // ------------------------------------------------------------------ polynomial algebra
 // acc (degree m, NVAR blocks of ncoef(DIM,m)) += (s . d) * in (degree m-1)
 template <int DIM, int NVAR, int M, class R>

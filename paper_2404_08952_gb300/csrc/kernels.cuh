@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) k_diff(DevMesh mesh, const void *__restri
             // the block's records are contiguous: stage them in shared memory and write
             // them with one bulk copy
             extern __shared__ __align__(16) unsigned char smo[];
-            if (valid) store_rec<TO, NV * CO, SO, R>(reinterpret_cast<TO *>(smo), threadIdx.x, acc);
+            if (valid) store_rec_smem<TO, NV * CO, SO, R>(smo, threadIdx.x, acc);
             fence_proxy_async_smem();
             __syncthreads();
             const long long c0 = (long long)blockIdx.x * blockDim.x;
@@ -961,7 +961,7 @@ __global__ void __launch_bounds__(TILE) k_diff_tile(DevMesh mesh, const void *__
     if constexpr (RBO % 16 == 0) {
         // the tile's output records are contiguous: one bulk copy from shared memory
         unsigned char *so = sm + r16((unsigned)TILE * SI * (unsigned)sizeof(TI));
-        if (valid) store_rec<TO, NV * CO, SO, R>(reinterpret_cast<TO *>(so), threadIdx.x, acc);
+        if (valid) store_rec_smem<TO, NV * CO, SO, R>(so, threadIdx.x, acc);
         fence_proxy_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) bulk_s2g_wait(out + (long long)t0 * SO, so, (unsigned)nt * RBO);
