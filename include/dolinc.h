@@ -182,7 +182,8 @@ dolinc_status dolinc_diff_layout(const dolinc_mesh *mesh, const dolinc_scheme *s
                                  int64_t *offset, int *stride, int *elem_bytes, int64_t *total_bytes);
 
 /* Differentials of orders 1..order (Sec 2.3) of the FP64 cell averages u_dev, in the
- * scheme's precision, written to diff_dev with the dolinc_diff_layout layout. */
+ * scheme's precision, written to diff_dev (256-byte aligned, total_bytes of
+ * dolinc_diff_layout; DOLINC_ERR_INVALID_ARG otherwise) with that layout. */
 dolinc_status dolinc_differentials(dolinc_mesh *mesh, const dolinc_scheme *scheme, const double *u_dev,
                                    int order, void *diff_dev, void *ws_dev, size_t ws_bytes,
                                    dolinc_stream stream);

@@ -627,6 +627,7 @@ dolinc_status dolinc_differentials(dolinc_mesh *m, const dolinc_scheme *s, const
     if ((st = check_ws(m, s, ws, ws_bytes, L))) return st;
     if (!u || !diff) return fail(DOLINC_ERR_INVALID_ARG, "null field");
     if (order < 1 || order > s->n_diff) return fail(DOLINC_ERR_INVALID_ARG, "order must be in 1..n_diff");
+    if (((uintptr_t)diff & 255) != 0) return fail(DOLINC_ERR_INVALID_ARG, "diff_dev must be 256-byte aligned");
     const PathFns *p = path_for(m, s, needed_order(*s));
     if (!p) return fail(DOLINC_ERR_UNSUPPORTED, "no kernel for this (dim, nv, order, precision)");
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);

@@ -67,12 +67,34 @@ template <bool LDG, class V> __device__ __forceinline__ V ldv(const V *p)
     else return *p;
 }
 
+// 32 bytes at a 32-byte aligned global address through the read-only path (one
+// 256-bit load)
+__device__ __forceinline__ void ldg32(const void *p, unsigned *w)
+{
+    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+        : "l"(p));
+}
+
 template <class T, int N, int S, class R, bool LDG = true>
 __device__ __forceinline__ void load_rec(const T *__restrict__ base, long long cell, R *out)
 {
     const T *p = base + cell * (long long)S;
     constexpr int B = S * (int)sizeof(T);
-    if constexpr (B % 16 == 0) {
+    if constexpr (LDG && B % 32 == 0) {
+        // records of whole 32-byte chunks (record arrays start 256-byte aligned)
+        constexpr int V = 32 / (int)sizeof(T);
+        constexpr int NV = (N + V - 1) / V;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            unsigned w[8];
+            ldg32(p + i * V, w);
+            const T *e = reinterpret_cast<const T *>(w);
+#pragma unroll
+            for (int j = 0; j < V; ++j)
+                if (i * V + j < N) out[i * V + j] = cvt<R>(e[j]);
+        }
+    } else if constexpr (B % 16 == 0) {
         constexpr int V = 16 / (int)sizeof(T);
         constexpr int NV = (N + V - 1) / V;
 #pragma unroll

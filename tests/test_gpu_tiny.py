@@ -53,3 +53,20 @@ def test_tiny_meshes_every_launch_shape(name, nv, prec, shape):
         assert rel(got, want) < 1e-12
     else:
         assert rel(got - u, want - u) < 1e-4
+
+
+def test_misaligned_differential_buffer_is_rejected():
+    """The differential records are read with 16- and 32-byte vector loads and written
+    by bulk copies: a caller buffer that is not 256-byte aligned is refused on the
+    host, before any launch."""
+    m = TINY["tri3"]()
+    M = dg.Mesh(m)
+    sch = dg.Scheme(k=3, r=1, n_diff=2, nv=1, precision="fp32", flux="upwind", adv=(1.0, 0.5, 0.3))
+    ws = dg.workspace(M, sch)
+    _, _, _, tot = dg.dolinc_diff_layout(M, sch, 2)
+    buf = torch.zeros(tot + 256, dtype=torch.uint8, device="cuda")
+    u = torch.zeros(M.n_cells, dtype=torch.float64, device="cuda")
+    with pytest.raises(dg.DolincError, match="256-byte aligned"):
+        dg.dolinc_differentials(M, sch, u, 2, buf[16:], ws)
+    dg.dolinc_differentials(M, sch, u, 2, buf[:tot], ws)
+    torch.cuda.synchronize()
