@@ -87,6 +87,9 @@ __device__ __forceinline__ void boundary_state(const DevMesh &mesh, int f, R *U)
     }
 }
 
+// 8 values of a 32-byte aligned record: 256-bit loads from global memory, else two ld4
+template <class R, bool LDG = true> __device__ __forceinline__ void ld8(const R *p, R *x);
+
 template <class R, bool LDG = true> __device__ __forceinline__ void ld4(const R *p, R &a, R &b, R &c, R &d)
 {
     if constexpr (sizeof(R) == 4) {
@@ -96,6 +99,23 @@ template <class R, bool LDG = true> __device__ __forceinline__ void ld4(const R 
         double2 v0 = ldv<LDG>(reinterpret_cast<const double2 *>(p));
         double2 v1 = ldv<LDG>(reinterpret_cast<const double2 *>(p) + 1);
         a = v0.x, b = v0.y, c = v1.x, d = v1.y;
+    }
+}
+
+template <class R, bool LDG> __device__ __forceinline__ void ld8(const R *p, R *x)
+{
+    if constexpr (LDG) {
+        unsigned w[8];
+#pragma unroll
+        for (int h = 0; h < (int)sizeof(R); h += 4) {
+            ldg32(p + 8 * h / (int)sizeof(R), w);
+            const R *e = reinterpret_cast<const R *>(w);
+#pragma unroll
+            for (int j = 0; j < 32 / (int)sizeof(R); ++j) x[8 * h / (int)sizeof(R) + j] = e[j];
+        }
+    } else {
+        ld4<R, false>(p, x[0], x[1], x[2], x[3]);
+        ld4<R, false>(p + 4, x[4], x[5], x[6], x[7]);
     }
 }
 
@@ -163,15 +183,36 @@ __global__ void __launch_bounds__(256) k_diff(DevMesh mesh, const void *__restri
         int nbv[UB];
         bool ok[UB];
         auto load_k = [&](int s) {
+            R kb[UB];
 #pragma unroll
             for (int u = 0; u < UB; ++u) {
-                const int su = s + u * LPC;
-                ok[u] = su < s1;
-                R kb = (R)0;
-                kx[u] = ky[u] = kz[u] = (R)0;
-                if (ok[u]) ld4<R>(Geo<R>::slotk(mesh) + 4ll * su, kx[u], ky[u], kz[u], kb);
-                nbv[u] = Geo<R>::nb_of(kb);
+                ok[u] = s + u * LPC < s1;
+                kb[u] = kx[u] = ky[u] = kz[u] = (R)0;
             }
+            if constexpr (LPC == 1 && UB >= 4 && UB % 2 == 0 && sizeof(R) == 4) {
+                // two consecutive 16-byte slot records starting at an even slot are one
+                // aligned 32-byte load
+#pragma unroll
+                for (int u = 0; u < UB; u += 2) {
+                    const int su = s + u;
+                    if (ok[u + 1] && (su & 1) == 0) {
+                        R k8[8];
+                        ld8<R>(Geo<R>::slotk(mesh) + 4ll * su, k8);
+                        kx[u] = k8[0], ky[u] = k8[1], kz[u] = k8[2], kb[u] = k8[3];
+                        kx[u + 1] = k8[4], ky[u + 1] = k8[5], kz[u + 1] = k8[6], kb[u + 1] = k8[7];
+                    } else {
+                        if (ok[u]) ld4<R>(Geo<R>::slotk(mesh) + 4ll * su, kx[u], ky[u], kz[u], kb[u]);
+                        if (ok[u + 1])
+                            ld4<R>(Geo<R>::slotk(mesh) + 4ll * (su + 1), kx[u + 1], ky[u + 1], kz[u + 1], kb[u + 1]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < UB; ++u)
+                    if (ok[u]) ld4<R>(Geo<R>::slotk(mesh) + 4ll * (s + u * LPC), kx[u], ky[u], kz[u], kb[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < UB; ++u) nbv[u] = Geo<R>::nb_of(kb[u]);
         };
         load_k(s0 + l);
         if (l == 0) {
@@ -523,11 +564,7 @@ __device__ __forceinline__ void canon_flux(const StageArgs &a, const Src &src, i
     const int f = (int)(word >> 2);
     const int side = word & 1;
     R fr[8];
-    {
-        const R *p = src.face(f);
-        ld4<R, Src::LDG>(p, fr[0], fr[1], fr[2], fr[3]);
-        ld4<R, Src::LDG>(p + 4, fr[4], fr[5], fr[6], fr[7]);
-    }
+    ld8<R, Src::LDG>(src.face(f), fr);
     if (word & 2) {
         // zero-gradient boundary (Sec 2.6): the auxiliary cell mirrors the cell value
         R U[NV];
@@ -631,6 +668,39 @@ __device__ __forceinline__ bool incr_update(const StageArgs &a, int c, int v, lo
     return nonfinite64(o);
 }
 
+// The same increment-form update for all NV variables of cell c (r[v] = R_c), with
+// the step's start record read, and the next stage's record written, whole.
+template <int NV, class R, class T0, int S0>
+__device__ __forceinline__ bool incr_update_cell(const StageArgs &a, int c, long long n, const R *r, R dtr, T0 *nxt)
+{
+    bool bad = false;
+    if (a.rk <= 1) {
+        R u0[NV], nx[NV];
+        load_rec<T0, NV, S0, R>(static_cast<const T0 *>(a.rec_start), c, u0);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const long long i = v * n + c;
+            const R d = mul_rn(r[v], dtr);
+            const R D = a.rk == 0 ? d : mul_rn((R)0.25, add_rn((R)a.dacc[i], d));
+            a.dacc[i] = (float)D;
+            nx[v] = add_rn(u0[v], D);
+            bad |= nonfinite32(D);
+        }
+        store_rec<T0, NV, S0, R>(nxt, c, nx);
+        return bad;
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const long long i = v * n + c;
+        const R d = mul_rn(r[v], dtr);
+        const R D = mul_rn((R)(2.0 / 3.0), add_rn((R)a.dacc[i], d));
+        const double o = __dadd_rn(a.u0[i], (double)D);
+        a.out[i] = o;
+        bad |= nonfinite64(o);
+    }
+    return bad;
+}
+
 // LPC lanes per cell: lane l evaluates slots l, l+LPC, ...; the group sums the signed
 // fluxes by recursive halving and lane l then updates variables [l*B, (l+1)*B).
 template <int DIM, int NV, int NS, int PREC, int LPC>
@@ -713,8 +783,10 @@ __device__ __forceinline__ void cell_epilogue(const DevMesh &mesh, const StageAr
     const R dtr = (R)a.dt;
     if constexpr (PREC != PREC_F64) {
         if (a.mode == 2) {
+            R r[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) bad |= incr_update<R, T0, S0>(a, c, v, n, res[v] * iv, dtr, nxt);
+            for (int v = 0; v < NV; ++v) r[v] = res[v] * iv;
+            bad = incr_update_cell<NV, R, T0, S0>(a, c, n, r, dtr, nxt);
             if (bad) atomicOr(a.status, 1u);
             return;
         }
@@ -812,15 +884,23 @@ __global__ void __launch_bounds__(256) k_gather(DevMesh mesh, StageArgs a)
     for (int v = 0; v < NV; ++v) res[v] = (R)0;
     int s0, s1;
     slot_range(mesh, c, s0, s1);
-    for (int s = s0; s < s1; ++s) {
-        const int2 sw = __ldg(mesh.slot2 + s);
-        const long long f = (long long)((unsigned)sw.y >> 2);
-        const bool side = sw.y & 1;
+    auto slot = [&](unsigned word) {
+        const long long f = (long long)(word >> 2);
+        const bool side = word & 1;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const R F = __ldg(flux + v * nf + f);
             res[v] += side ? F : -F;
         }
+    };
+    if (s1 - s0 == 4 && (s0 & 3) == 0) {
+        // the four (neighbour, word) pairs of a tetrahedron: one aligned 32-byte load
+        unsigned w[8];
+        ldg32(mesh.slot2 + s0, w);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) slot(w[2 * j + 1]);
+    } else {
+        for (int s = s0; s < s1; ++s) slot((unsigned)__ldg(mesh.slot2 + s).y);
     }
     cell_epilogue<DIM, NV, PREC>(mesh, a, c, res);
 }
