@@ -122,13 +122,32 @@ __device__ __forceinline__ void load_rec(const T *__restrict__ base, long long c
     }
 }
 
-// Stores N elements (padding lanes written as zero) of a record of stride S.
+// 32 bytes to a 32-byte aligned global address (one 256-bit store)
+__device__ __forceinline__ void stg32(void *p, const unsigned *w)
+{
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(w[0]), "r"(w[1]),
+                 "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+
+// Stores N elements (padding lanes written as zero) of a record of stride S to global
+// memory (record arrays start 256-byte aligned).
 template <class T, int N, int S, class R>
 __device__ __forceinline__ void store_rec(T *__restrict__ base, long long cell, const R *in)
 {
     T *p = base + cell * (long long)S;
     constexpr int B = S * (int)sizeof(T);
-    if constexpr (B % 16 == 0) {
+    if constexpr (B % 32 == 0) {
+        constexpr int V = 32 / (int)sizeof(T);
+#pragma unroll
+        for (int i = 0; i < S / V; ++i) {
+            unsigned w[8];
+            T *e = reinterpret_cast<T *>(w);
+#pragma unroll
+            for (int j = 0; j < V; ++j) e[j] = (i * V + j < N) ? to_store<T, R>(in[i * V + j]) : to_store<T, R>((R)0);
+            stg32(p + i * V, w);
+        }
+    } else if constexpr (B % 16 == 0) {
         constexpr int V = 16 / (int)sizeof(T);
 #pragma unroll
         for (int i = 0; i < S / V; ++i) {
