@@ -894,7 +894,8 @@ __global__ void __launch_bounds__(256) k_gather(DevMesh mesh, StageArgs a)
         }
     };
     if (s1 - s0 == 4 && (s0 & 3) == 0) {
-        // the four (neighbour, word) pairs of a tetrahedron: one aligned 32-byte load
+        // the four (neighbour, word) pairs of a four-slot cell (tetrahedron, quad): one
+        // aligned 32-byte load
         unsigned w[8];
         ldg32(mesh.slot2 + s0, w);
 #pragma unroll
