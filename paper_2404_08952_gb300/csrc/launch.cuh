@@ -215,7 +215,7 @@ template <int DIM, int NV, int NS, int PREC> struct Path {
     static void stage(const DevMesh &m, const StageArgs &a, const Tune &t, cudaStream_t s)
     {
         if (t.stage_lpc == -2) {                    // face-centric pair
-            k_flux<DIM, NV, NS, PREC><<<nblk(m.n_faces, 256), 256, 0, s>>>(m, a);
+            k_flux<DIM, NV, NS, PREC><<<nblk(m.n_faces, 128), 128, 0, s>>>(m, a);
             k_gather<DIM, NV, PREC><<<nblk(m.n_cells, t.stage_block), t.stage_block, 0, s>>>(m, a);
             return;
         }
