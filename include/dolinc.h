@@ -222,10 +222,12 @@ dolinc_status dolinc_rk_step(dolinc_mesh *mesh, const dolinc_scheme *scheme, dou
  * tensors are), the step's first kernel reads it in place over the host link, keeping
  * a device copy of the start state in u_dev, and the last stage writes the new state
  * to it in place: the transfers are part of the step's own kernels.  Other host
- * memory is copied to u_dev and back with cudaMemcpyAsync on the stream.
+ * memory is copied to u_dev and back with cudaMemcpyAsync on the stream (which, for
+ * pageable memory, returns only once the copy back has completed).
  * u_dev: caller-owned device scratch of nv * n_cells doubles, contents afterwards
- * unspecified.  Like every call here the step is asynchronous: u_host and u_dev must
- * stay valid and untouched until the stream has completed it.  Errors as
+ * unspecified.  With pinned memory the step is asynchronous like every call here:
+ * u_host and u_dev must stay valid and untouched until the stream has completed it.
+ * Errors as
  * dolinc_rk_step; DOLINC_ERR_INVALID_ARG when u_dev is not device memory or aliases
  * u_host. */
 dolinc_status dolinc_rk_step_host(dolinc_mesh *mesh, const dolinc_scheme *scheme, double dt, double *u_host,
