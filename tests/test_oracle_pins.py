@@ -663,3 +663,29 @@ def test_adam_first_step_moves_each_parameter_by_the_learning_rate():
     np.testing.assert_allclose(th, -0.01 * np.sign(g), rtol=1e-5)
     np.testing.assert_allclose(m, 0.1 * g)
     np.testing.assert_allclose(v, 0.001 * g * g)
+
+
+# ------------------------------------------------------------------ Burgers flux
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_burgers_flux_is_textbook_upwind_on_a_strip(sign):
+    """Scalar Burgers (flux u^2/2 along (1,1)) with every cell on the first-order
+    fallback: each face takes the state of its upwind side by the sign of the
+    average speed, so on a 1D strip with one-signed data the residual is the textbook
+    upwind difference -(u_i^2 - u_{i-1}^2) / (2 dx_i) (u > 0), or with the right
+    neighbour for u < 0; the strip's y-faces join a cell to itself and cancel."""
+    rng = np.random.default_rng(12)
+    n = 12
+    widths = rng.uniform(0.5, 1.5, n)
+    widths /= widths.sum()
+    m = synth.strip_mesh(widths)
+    O = oracle.Oracle(m)
+    assert np.all(np.argsort(O.xc[:, 0]) == np.arange(n))
+    u = sign * rng.uniform(0.5, 1.5, size=(1, n))
+    flagged = np.ones(n, dtype=np.uint8)
+    R = O.residual(u, oracle.Scheme(k=3, r=1, n_diff=2, flux="burgers", eno=3, troubled=flagged))
+    f = 0.5 * u[0] ** 2
+    for i in range(n):                          # periodic strip
+        up = (i - 1) % n if sign > 0 else (i + 1) % n
+        want = -(f[i] - f[up]) / widths[i] if sign > 0 else -(f[up] - f[i]) / widths[i]
+        assert abs(R[0, i] - want) < 1e-12 * max(1.0, abs(want))
