@@ -74,6 +74,8 @@ def _declare(L):
     L.or_rk3_step.argtypes = [P, P, P, C.c_double, P]
     L.or_rk3_stage.argtypes = [P, P, P, C.c_double, C.c_int, P, P, P]
     L.or_face_weights.argtypes = [P, P, P, P, P]
+    L.or_weno5_parts.argtypes = [C.c_double, P, P, P, P]
+    L.or_num_flux.argtypes = [C.c_int, P, P, P, P, P]
     L.or_criterion.argtypes = [P, P, P, P, C.c_double, C.c_double, P]
     L.or_indicator_features.argtypes = [P, P, P, P, C.c_double, P, P]
 
@@ -98,6 +100,31 @@ def phantoms(N, g, phi0, phi1):
     if lib().or_phantoms(N, float(g), _ptr(phi0), _ptr(phi1), _ptr(out)) != 0:
         raise ValueError("bad order")
     return out
+
+
+def weno5_parts(g, ph):
+    """WENO5-DOLINC pieces at growth rate g from the five values ph = phi_n, n = -2..2:
+    (q, d, beta), each [3] over the candidates r = 0, 1, 2 (cells i-r .. i-r+2):
+    candidate face values, linear weights, smoothness measures."""
+    ph = np.ascontiguousarray(ph, dtype=np.float64)
+    assert ph.shape == (5,)
+    q, d, beta = np.zeros(3), np.zeros(3), np.zeros(3)
+    if lib().or_weno5_parts(float(g), _ptr(ph), _ptr(q), _ptr(d), _ptr(beta)) != 0:
+        raise ValueError("g must be positive")
+    return q, d, beta
+
+
+def num_flux(dim, scheme, UL, UR, S):
+    """The oracle's numerical flux through the area vector S (owner -> neighbour) from
+    the two reconstructed states (scheme gives flux, gamma, adv, nv)."""
+    UL = np.ascontiguousarray(UL, dtype=np.float64)
+    UR = np.ascontiguousarray(UR, dtype=np.float64)
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    F = np.zeros(scheme.nv)
+    s = scheme._c()
+    if lib().or_num_flux(int(dim), C.byref(s), _ptr(UL), _ptr(UR), _ptr(S), _ptr(F)) != 0:
+        raise ValueError("bad dimension or variable count")
+    return F
 
 
 class Scheme:

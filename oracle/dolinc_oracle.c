@@ -382,10 +382,13 @@ static int eno3_choose(double g, const double *ph)
  * quadratic p_r on the upwind cell, in units of that cell's width:
  *   beta_r = int_cell (p_r')^2 + (p_r'')^2 dx,
  * p_r the derivative of the cubic interpolating the primitive at the candidate's four
- * faces.  On uniform cells this is the classical WENO5.  ph[n+2] = phi_n, n = -2..2. */
-static double weno5_value(double g, const double *ph)
+ * faces.  On uniform cells this is the classical WENO5.  ph[n+2] = phi_n, n = -2..2.
+ * or_weno5_parts returns the candidate values q[r], the linear weights d[r] and the
+ * smoothness beta[r] (r = 0, 1, 2); weno5_value combines them. */
+int or_weno5_parts(double g, const double *ph, double *q, double *d, double *beta)
 {
-    double c5[5], c3[3], q[3], d[3], beta[3];
+    double c5[5], c3[3];
+    if (!(g > 0.0)) return -1;
     or_coeff(5, 2, g, c5);
     for (int r = 0; r < 3; ++r) {
         or_coeff(3, r, g, c3);
@@ -420,6 +423,15 @@ static double weno5_value(double g, const double *ph)
         beta[r] = (b * b - b * cc + cc * cc / 3.0) + cc * cc;   /* int_{-1}^{0} (b + cc x)^2 dx + cc^2 */
     }
     d[1] = 1.0 - d[0] - d[2];
+    return 0;
+}
+
+/* The WENO5-DOLINC face value: the candidates q_r weighted by the normalised
+ * a_r = d_r / (1e-6 + beta_r)^2 (parts from or_weno5_parts). */
+static double weno5_value(double g, const double *ph)
+{
+    double q[3], d[3], beta[3];
+    or_weno5_parts(g, ph, q, d, beta);
     double a[3], sa = 0.0;
     for (int r = 0; r < 3; ++r) { a[r] = d[r] / ((1e-6 + beta[r]) * (1e-6 + beta[r])); sa += a[r]; }
     return (a[0] * q[0] + a[1] * q[1] + a[2] * q[2]) / sa;
@@ -528,6 +540,17 @@ static void num_flux(int D, const or_scheme *s, const double *UL, const double *
         double Sn = sqrt(vdot(S, S));
         for (int v = 0; v < D + 2; ++v) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * a * Sn * (UR[v] - UL[v]);
     }
+}
+
+/* num_flux for a caller: dimension D, scheme s (flux, gamma, adv), states UL, UR of
+ * s->nv variables and the face area vector S (owner -> neighbour); F gets s->nv values. */
+int or_num_flux(int D, const or_scheme *s, const double *UL, const double *UR, const double *S, double *F)
+{
+    if (D < 1 || D > OR_MAXD || s->nv < 1 || s->nv > OR_MAXV) return -1;
+    double S3[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < D; ++k) S3[k] = S[k];
+    num_flux(D, s, UL, UR, S3, F);
+    return 0;
 }
 
 /* Reconstructed face states of every face: [v][f] for L (owner upwind) and R. */

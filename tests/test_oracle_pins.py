@@ -470,6 +470,119 @@ def test_weno5_exact_for_quadratics_on_geometric_strips(g):
     np.testing.assert_allclose(R[0][ok], exact[ok], rtol=0, atol=1e-10)
 
 
+@pytest.mark.parametrize("g", [0.7, 1.0, 1.3, 1.9])
+def test_weno5_linear_weights_give_the_five_cell_stencil(g):
+    """The linear weights d_r of WENO5-DOLINC (Sec 2.4) combine the three 3-cell
+    candidates into the 5-cell stencil (5, 2) of Eq coeff.  The oracle derives d_r
+    from the two END coefficients only (cell i-2 appears in candidate r = 2 alone,
+    cell i+2 in r = 0 alone), so the three middle coefficients are an independent
+    check: a wrong power of g in any d_r fails them.  At g = 1 the weights are the
+    textbook (3/10, 6/10, 1/10) of Jiang and Shu."""
+    _, d, _ = oracle.weno5_parts(g, np.arange(5.0))
+    c5 = oracle.coeff(5, 2, g)
+    combo = np.zeros(5)
+    for r in range(3):
+        c3 = oracle.coeff(3, r, g)
+        for j in range(3):
+            combo[j + 2 - r] += d[r] * c3[j]          # candidate r covers cells i-r .. i-r+2
+    np.testing.assert_allclose(combo, c5, rtol=0, atol=1e-13)
+    assert np.all(d > 0) and abs(d.sum() - 1.0) < 1e-15
+    if g == 1.0:
+        np.testing.assert_allclose(d, [0.3, 0.6, 0.1], rtol=0, atol=1e-15)
+
+
+def _geometric_cells(g):
+    """Faces of cells i-2 .. i+2 on a strip growing by g, in units of cell i = [-1, 0]."""
+    left = [-1.0 - 1.0 / g - 1.0 / g ** 2, -1.0 - 1.0 / g, -1.0]
+    right = [0.0, g, g + g * g]
+    return np.array(left + right)
+
+
+@pytest.mark.parametrize("g", [0.7, 1.3, 1.9])
+def test_weno5_smoothness_of_quadratics_on_geometric_strips(g):
+    """Each WENO5 candidate reproduces a quadratic exactly, so its smoothness measure
+    must be that of the quadratic itself: for q(x) = a + b x + c x^2 over the upwind
+    cell [-1, 0] (units of that cell's width),
+        int_{-1}^{0} (q')^2 + (q'')^2 dx = b^2 - 2 b c + (4/3) c^2 + 4 c^2,
+    for all three candidates.  The cell averages come from the primitive of q on the
+    geometric cells; a smoothness measure taken over the wrong cell, in the wrong
+    units or with a wrong power of g in the faces fails it."""
+    rng = np.random.default_rng(int(g * 100))
+    X = _geometric_cells(g)
+    for _ in range(5):
+        a, b, c = rng.uniform(-2, 2, 3)
+        Q = lambda x: a * x + b * x * x / 2 + c * x ** 3 / 3      # primitive of q
+        ph = (Q(X[1:]) - Q(X[:-1])) / (X[1:] - X[:-1])
+        qv, _, beta = oracle.weno5_parts(g, ph)
+        want = b * b - 2 * b * c + 4.0 / 3.0 * c * c + 4 * c * c
+        np.testing.assert_allclose(beta, want, rtol=1e-11, atol=1e-12)
+        np.testing.assert_allclose(qv, a, rtol=0, atol=1e-12)      # q(0): the face x_{i+1/2}
+
+
+def test_weno5_smoothness_is_jiang_shu_on_uniform_cells():
+    """At g = 1 the smoothness measures are the classical Jiang-Shu closed forms for
+    arbitrary (non-polynomial) data f_{i-2} .. f_{i+2}."""
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        f = rng.normal(size=5)
+        fm2, fm1, f0, f1, f2 = f
+        want = [13 / 12 * (f0 - 2 * f1 + f2) ** 2 + 0.25 * (3 * f0 - 4 * f1 + f2) ** 2,      # r = 0: i .. i+2
+                13 / 12 * (fm1 - 2 * f0 + f1) ** 2 + 0.25 * (fm1 - f1) ** 2,                # r = 1
+                13 / 12 * (fm2 - 2 * fm1 + f0) ** 2 + 0.25 * (fm2 - 4 * fm1 + 3 * f0) ** 2]  # r = 2
+        _, _, beta = oracle.weno5_parts(1.0, f)
+        np.testing.assert_allclose(beta, want, rtol=1e-12, atol=1e-14)
+
+
+# ------------------------------------------------------------------ Rusanov (local Lax-Friedrichs) flux
+# Sec 3 names the local Lax-Friedrichs flux for the Euler cases.  Each case below is
+# worked by hand (gamma = 1.4; pressures chosen so that c = sqrt(gamma p / rho) = 1):
+# F = (F(U_L) + F(U_R)).S / 2 - alpha |S| (U_R - U_L) / 2, alpha = max over both sides
+# of |u.n| + c.  A dropped sound speed, a wave speed from one side only, or a factor
+# of 2 on the dissipation changes every case.
+
+_G = 1.4
+_RUSANOV_CASES = [
+    # 2D, S = (2, 0); both at rest; rho 1 / 0.5, p = rho / gamma: alpha = 1, |S| = 2.
+    # F(U_L).S = (0, 2/1.4, 0, 0), F(U_R).S = (0, 1/1.4, 0, 0); dissipation 1 * (U_R - U_L)
+    (2, [2.0, 0.0], [1.0, 0.0, 0.0, (1 / 1.4) / 0.4], [0.5, 0.0, 0.0, (0.5 / 1.4) / 0.4],
+     [0.5, 1.0714285714285714, 0.0, 0.8928571428571429]),
+    # 3D, S = (1.5, 2, 0) (|S| = 2.5, n = (0.6, 0.8, 0)); u_L = 0.5 n, u_R = -0.5 n,
+    # rho 1 / 2, p = rho / gamma: |u.n| + c = 1.5 on both sides; dissipation 1.875 (U_R - U_L)
+    (3, [1.5, 2.0, 0.0], [1.0, 0.3, 0.4, 0.0, (1 / 1.4) / 0.4 + 0.125], [2.0, -0.6, -0.8, 0.0, (2 / 1.4) / 0.4 + 0.25],
+     [-2.5, 3.857142857142857, 5.142857142857143, 0.0, -5.223214285714286]),
+    # 2D, S = (0, 3); u_L = (0.2, 0) (|u.n| + c = 1), u_R = (0, 2) (= 3): alpha = 3 from
+    # the right side; rho 1, p = 1/gamma; dissipation 4.5 (U_R - U_L)
+    (2, [0.0, 3.0], [1.0, 0.2, 0.0, (1 / 1.4) / 0.4 + 0.02], [1.0, 0.0, 2.0, (1 / 1.4) / 0.4 + 2.0],
+     [3.0, 0.9, -0.857142857142858, 4.59]),
+]
+
+
+@pytest.mark.parametrize("case", range(len(_RUSANOV_CASES)))
+def test_rusanov_flux_matches_hand_computed_cases(case):
+    D, S, UL, UR, want = _RUSANOV_CASES[case]
+    s = oracle.Scheme(flux="rusanov", nv=D + 2, gamma=_G)
+    F = oracle.num_flux(D, s, UL, UR, S)
+    np.testing.assert_allclose(F, want, rtol=1e-13, atol=1e-13)
+
+
+def test_rusanov_flux_is_consistent_and_conservative():
+    """F(U, U) carries no dissipation (it is the physical flux of U, which is
+    linear in S), and swapping the sides with S -> -S negates the flux."""
+    rng = np.random.default_rng(8)
+    s = oracle.Scheme(flux="rusanov", nv=5, gamma=_G)
+    for _ in range(10):
+        rho, p = rng.uniform(0.5, 2, 2)
+        vel = rng.uniform(-1, 1, 3)
+        U = np.array([rho, *(rho * vel), p / 0.4 + 0.5 * rho * vel @ vel])
+        V = U * rng.uniform(0.8, 1.2, 5)
+        S = rng.normal(size=3)
+        F1 = oracle.num_flux(3, s, U, U, S)
+        np.testing.assert_allclose(oracle.num_flux(3, s, U, U, 2.5 * S), 2.5 * F1, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(F1[0], rho * vel @ S, rtol=1e-12)       # mass flux
+        np.testing.assert_allclose(oracle.num_flux(3, s, U, V, S), -oracle.num_flux(3, s, V, U, -S),
+                                   rtol=1e-12, atol=1e-12)
+
+
 # ------------------------------------------------------------------ troubled-cell criterion and network inputs
 # The paper has no troubled-cell criterion; the one built here (from the paper's ENO3
 # indicators, Sec 2.4) is pinned by what its ingredients must give in closed form.
