@@ -133,26 +133,44 @@ def _widths(sch):
     return sg, sb
 
 
-def alg_bytes(kind, M, sch):
+def stage_orders(sch):
+    """Differential orders the stage reads: the stencil's own need (max(r, k-r-2),
+    at least 1), 2 under the ENO3 / WENO5 limiters, never more than are computed."""
+    k, r = getattr(sch, "k", 3), getattr(sch, "r", 1)
+    need = max(r, k - r - 2, 1)
+    if getattr(sch, "limiter", "none") in ("eno3_all", "eno3_flagged", "weno5_all", "weno5_flagged"):
+        need = max(need, 2)
+    return min(need, sch.n_diff)
+
+
+def alg_bytes(kind, M, sch, basis="stored"):
     """Algorithmic bytes of one launch, per cell as the scope table's measurement
     section defines them (B_alg), times the cells:
       diff m:  nv (s_{m-1} c_{m-1} + s_m c_m) + Gp
-      stage:   nv sum_{m<=N_d} s_m c_m + Gr + nv (16 + 8 + s_0)
-      Gp = nfc 8 + (nfc/2)(D 8 + 8) + 12,  Gr = Gp + (nfc/2) D 8
+      stage:   nv sum_{m<=N} s_m c_m + Gr + nv (16 + 8 + s_0)
+      Gp = nfc 8 + (nfc/2)(D s_g + s_g) + (s_g + 4),  Gr = Gp + (nfc/2) D s_g
     (c_m components of order m, s_m its stored width, nfc slots per cell, D the
-    dimension; geometry counted in FP64, the state as FP64 reads of u^n and u^(k), an
-    FP64 write and a bulk-precision copy).  pack (not in B_alg): nv (8 + s_0)."""
+    dimension; per slot the neighbour and face indices, per face S_f and omega, per
+    cell 1/V and a CSR offset, per face of the stage d_f; the state as FP64 reads of
+    u^n and u^(k), an FP64 write and a bulk-precision copy).
+    basis "stored" (the roofline's): the widths the build stores (geometry s_g = 4 B
+    below FP64) and, in the stage, the orders N the stencil reads (stage_orders).
+    basis "table": the scope table's own evaluation, geometry at FP64 widths and the
+    stage reading every computed order N = N_d.  pack (not in B_alg): nv (8 + s_0)."""
     nc, nv, dim = M.n_cells, sch.nv, M.dim
-    _, sb = _widths(sch)
+    sg, sb = _widths(sch)
+    if basis == "table":
+        sg = 8
     nfc = M.n_slots / nc
-    gp = nfc * 8 + (nfc / 2) * (dim * 8 + 8) + 12
-    gr = gp + (nfc / 2) * dim * 8
+    gp = nfc * 8 + (nfc / 2) * (dim * sg + sg) + (sg + 4)
+    gr = gp + (nfc / 2) * dim * sg
     if kind == "pack":
         return nc * nv * (8 + sb(0))
     if kind.startswith("diff"):
         m = int(kind[4:])
         return nc * (nv * (_ncoef(dim, m - 1) * sb(m - 1) + _ncoef(dim, m) * sb(m)) + gp)
-    return nc * (nv * sum(_ncoef(dim, m) * sb(m) for m in range(sch.n_diff + 1)) + gr + nv * (16 + 8 + sb(0)))
+    top = sch.n_diff if basis == "table" else stage_orders(sch)
+    return nc * (nv * sum(_ncoef(dim, m) * sb(m) for m in range(top + 1)) + gr + nv * (16 + 8 + sb(0)))
 
 
 def kernel_bytes(kind, M, sch):
@@ -185,11 +203,16 @@ KINDS = ["pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces"]
 
 def _stage_roofline(M, sch, ms_stage, peak):
     """B_alg of one whole RK stage (all differential passes + the fused stage) per
-    cell, and the achieved GB/s and fraction of the measured peak at ms_stage."""
+    cell, and the achieved GB/s and fraction of the measured peak at ms_stage (stored
+    basis; the scope table's FP64-width all-orders figure beside it)."""
     b = sum(alg_bytes("diff%d" % m, M, sch) for m in range(1, sch.n_diff + 1)) + alg_bytes("stage", M, sch)
+    bt = sum(alg_bytes("diff%d" % m, M, sch, "table") for m in range(1, sch.n_diff + 1)) + \
+        alg_bytes("stage", M, sch, "table")
     gbs = b / (ms_stage / 1e3) / 1e9
     return {"alg_bytes_per_cell": round(b / M.n_cells, 1), "ms_per_stage": round(ms_stage, 5),
-            "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4)}
+            "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+            "table_basis_bytes_per_cell": round(bt / M.n_cells, 1),
+            "table_basis_frac": round(bt / (ms_stage / 1e3) / 1e9 / peak, 4)}
 
 
 def _l2_rel(a, b):
@@ -313,6 +336,7 @@ def run_dolinc(args):
         per_launch_ms = per(KINDS[top])
         unit_name = KINDS[top]
     bytes_alg = sum(alg_bytes(kd, M, sch_m) for kd in unit)
+    bytes_table = sum(alg_bytes(kd, M, sch_m, "table") for kd in unit)
     achieved = bytes_alg / (per_launch_ms / 1e3) / 1e9
     bytes_kern = sum(kernel_bytes(kd, M, sch_m) for kd in unit)
     traffic = None
@@ -347,6 +371,10 @@ def run_dolinc(args):
         "roofline": {"bound": "hbm", "kernel": unit_name, "achieved": round(achieved, 1), "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "alg_bytes_per_launch": int(bytes_alg),
+                     "alg_basis": "stored widths (FP32 geometry below FP64), stage reads orders 0..%d" % stage_orders(
+                         sch_m),
+                     "table_basis_bytes_per_launch": int(bytes_table),
+                     "table_basis_frac": round(bytes_table / (per_launch_ms / 1e3) / 1e9 / peak, 4),
                      "kernel_bytes_per_launch": int(bytes_kern),
                      "kernel_bytes_frac": round(bytes_kern / (per_launch_ms / 1e3) / 1e9 / peak, 4),
                      "ms_per_launch": round(per_launch_ms, 5)},

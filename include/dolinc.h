@@ -242,12 +242,17 @@ dolinc_status dolinc_rk_step_host(dolinc_mesh *mesh, const dolinc_scheme *scheme
  * (32 MiB, held on every GPU that loads the library until the process exits).
  * Meshes/schemes whose dolinc_workspace_size exceeds it are rejected with
  * DOLINC_ERR_INVALID_ARG and a message; nothing is allocated, ever.
- * The first call on a device looks the array's address up and clears it (with that
- * device current); make that first call before any stream capture.
+ * Every call looks the array's address up on the current device (the first call on a
+ * device also loads the library's device code there: make that first call before any
+ * stream capture) and clears its first 1024 bytes (status and barrier words) on the
+ * stream, as dolinc_workspace_init does for a caller workspace.
  * All calls on a device share the one array, which keeps the last call's contents:
  * calls that overlap on the GPU (different streams, threads or meshes at once) race
- * and must be serialised by the caller.  Non-finite results are not reported here
- * (the status word is cleared at every call). */
+ * and must be serialised by the caller.  Device-side errors are NOT reported by this
+ * entry point: neither a non-finite result nor a bounded wait of a pipelined kernel
+ * that gave up (the status word lives in the array, which the caller cannot read, and
+ * the next call clears it).  Callers that need those checks use dolinc_rk_step with a
+ * workspace of their own and dolinc_sync_status. */
 #define DOLINC_NOALLOC_MAX_BYTES ((size_t)32 << 20)
 dolinc_status dolinc_rk_step_noalloc(dolinc_mesh *mesh, const dolinc_scheme *scheme, double dt, double *u_dev,
                                      dolinc_stream stream);

@@ -3,7 +3,6 @@
 // itself allocates nothing.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "../../include/dolinc.h"
@@ -20,40 +19,18 @@ constexpr size_t kNoAllocBytes = DOLINC_NOALLOC_MAX_BYTES;
 // stand-in for the device array: its device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_ws[kNoAllocBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_addr[kMaxDevices] = {nullptr};
-
-// Device address of the array on the current device, resolved once per device (with
-// that device current) and its status word cleared.  Returns null and sets *err on failure.
+// Device address of the array on the current device.  Looked up at every call (it
+// is a table lookup once the module is loaded), so a module reloaded after
+// cudaDeviceReset is picked up too.  Returns null and sets *err on failure.
 void *device_scratch(std::string *err)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        *err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_ws);
+    if (e != cudaSuccess || !p) {
+        *err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
         return nullptr;
     }
-    if (dev < 0 || dev >= kMaxDevices) {
-        *err = "device index out of range for the no-alloc workspace table";
-        return nullptr;
-    }
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_ws);
-        if (e != cudaSuccess || !p) {
-            *err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-            return nullptr;
-        }
-        e = cudaMemset(p, 0, 256);
-        if (e != cudaSuccess) {
-            *err = std::string("cudaMemset: ") + cudaGetErrorString(e);
-            return nullptr;
-        }
-        g_addr[dev] = p;
-    }
-    return g_addr[dev];
+    return p;
 }
 
 }  // namespace
@@ -72,8 +49,8 @@ extern "C" dolinc_status dolinc_rk_step_noalloc(dolinc_mesh *mesh, const dolinc_
     std::string err;
     void *ws = device_scratch(&err);
     if (!ws) return dol::report_error(DOLINC_ERR_CUDA, "dolinc_rk_step_noalloc: " + err);
-    cudaError_t e = cudaMemsetAsync(ws, 0, 256, reinterpret_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess)
-        return dol::report_error(DOLINC_ERR_CUDA, std::string("dolinc_rk_step_noalloc: ") + cudaGetErrorString(e));
+    // a fresh workspace, as every other path starts from: the status and barrier words
+    st = dolinc_workspace_init(ws, kNoAllocBytes, stream);
+    if (st != DOLINC_OK) return st;
     return dolinc_rk_step(mesh, scheme, dt, u_dev, ws, kNoAllocBytes, stream);
 }

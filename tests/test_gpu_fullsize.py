@@ -19,6 +19,7 @@ import pytest
 
 import oracle
 import synth
+from _tol import increment_ok
 
 torch = pytest.importorskip("torch")
 dg = pytest.importorskip("paper_2404_08952_gb300")
@@ -49,12 +50,12 @@ def tet64():
     w = synth.workload("euler3d_tet64", q=2)
     O = oracle.Oracle(w["mesh"])
     want = O.rk3_stage(w["u0"], w["u0"], oracle.Scheme(**w["scheme"]), w["dt"], 0)
-    return w, want
+    return w, want, O
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_euler3d_tet64_full_stage(tet64, prec):
-    w, want = tet64
+    w, want, O = tet64
     M = dg.Mesh(w["mesh"])
     sch = dg.Scheme(precision=prec, **w["scheme"])
     ws = dg.workspace(M, sch)
@@ -68,8 +69,12 @@ def test_euler3d_tet64_full_stage(tet64, prec):
     if prec == "fp64":
         assert rel(got, want) < 1e-13 and rel(inc, inc_ref) < 1e-11
     else:
-        # FP32 bulk: the stage increment (dt * residual) to 1e-5 of the flux scale
-        assert rel(inc, inc_ref) < 2e-4
+        # FP32 bulk: every cell's stage increment (dt * residual) within dt times the
+        # per-cell bound: 1e-5 of max|u| per face value (N_s = 1), carried through
+        # |S_f| * wave speed / V_c
+        fx = {k: v for k, v in w["scheme"].items() if k in ("flux", "adv")}
+        ok, worst = increment_ok(O, inc, inc_ref, w["u0"], w["dt"], "fp32", 1, fx, 3)
+        assert ok, worst
         assert rel(got, want) < 1e-6
 
 
