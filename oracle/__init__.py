@@ -15,24 +15,34 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SRC = [os.path.join(_HERE, "dolinc_oracle.c"), os.path.join(_HERE, "indicator_oracle.c")]
 _LIB = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 FLUX = {"upwind": 0, "burgers": 1, "rusanov": 2}
 
 
-def build(force=False):
-    """Compile the oracle shared library (plain C, -O2, no machine-specific flags)."""
-    os.makedirs(_BUILD, exist_ok=True)
+def _compile(out, extra, force):
     srcs = [s for s in _SRC if os.path.exists(s)]
-    stale = force or not os.path.exists(_LIB) or any(
-        os.path.getmtime(s) > os.path.getmtime(_LIB) for s in srcs)
+    stale = force or not os.path.exists(out) or any(os.path.getmtime(s) > os.path.getmtime(out) for s in srcs)
     if stale:
-        tmp = _LIB + ".%d.tmp" % os.getpid()
-        cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"]
+        tmp = out + ".%d.tmp" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared"] + extra + ["-o", tmp] + srcs + ["-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, out)
+    return out
+
+
+def build(force=False):
+    """Compile the oracle shared library (plain C, -O2, no machine-specific flags) and
+    its OpenMP build (the same source with -fopenmp: face fluxes on every thread)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    try:
+        _compile(_LIB_OMP, ["-fopenmp"], force)
+    except (subprocess.CalledProcessError, OSError) as e:     # no OpenMP: the plain build still serves
+        print("oracle: OpenMP build failed (%s)" % e)
+    return _compile(_LIB, [], force)
 
 
 def lib():
@@ -42,6 +52,22 @@ def lib():
             _lib = C.CDLL(build())
             _declare(_lib)
     return _lib
+
+
+def lib_omp():
+    """The OpenMP build (threads from OMP_NUM_THREADS, default all cores)."""
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            os.makedirs(_BUILD, exist_ok=True)
+            _lib_omp = C.CDLL(_compile(_LIB_OMP, ["-fopenmp"], False))
+            _declare(_lib_omp)
+    return _lib_omp
+
+
+def threads(parallel=True):
+    """Threads the (OpenMP) oracle computes face fluxes on."""
+    return int((lib_omp() if parallel else lib()).or_threads())
 
 
 class _Mesh(C.Structure):
@@ -76,6 +102,7 @@ def _declare(L):
     L.or_face_weights.argtypes = [P, P, P, P, P]
     L.or_weno5_parts.argtypes = [C.c_double, P, P, P, P]
     L.or_num_flux.argtypes = [C.c_int, P, P, P, P, P]
+    L.or_threads.argtypes = []
     L.or_criterion.argtypes = [P, P, P, P, C.c_double, C.c_double, P]
     L.or_indicator_features.argtypes = [P, P, P, P, C.c_double, P, P]
 
@@ -166,9 +193,11 @@ class Scheme:
 
 
 class Oracle:
-    """Geometry plus the stage operators of one mesh (dict from `synth`)."""
+    """Geometry plus the stage operators of one mesh (dict from `synth`).
+    parallel=True uses the OpenMP build (same results, face fluxes on every thread)."""
 
-    def __init__(self, mesh):
+    def __init__(self, mesh, parallel=False):
+        self._L = lib_omp() if parallel else lib()
         self.dim = int(mesh["dim"])
         self._keep = {}
         for key, dt in (("nodes", np.float64), ("face_node_offsets", np.int64), ("face_nodes", np.int64),
@@ -194,7 +223,7 @@ class Oracle:
         g = _Geom()
         g.V, g.xc, g.S, g.xf, g.w, g.d = (_ptr(a) for a in (self.V, self.xc, self.S, self.xf, self.w, self.d))
         self._g = g
-        if lib().or_geometry(C.byref(m), C.byref(g)) != 0:
+        if self._L.or_geometry(C.byref(m), C.byref(g)) != 0:
             raise MemoryError("oracle geometry")
         self.owner = k["face_owner"]
         self.neigh = k["face_neighbour"]
@@ -208,10 +237,10 @@ class Oracle:
         sizes = [nv * self.n_cells * D ** m for m in range(N + 1)]
         T = np.zeros(sum(sizes))
         if scheme is not None and scheme.bkind is not None:
-            lib().or_differentials_bc(C.byref(self._m), C.byref(self._g), nv, N, _ptr(u), _ptr(scheme.bkind),
+            self._L.or_differentials_bc(C.byref(self._m), C.byref(self._g), nv, N, _ptr(u), _ptr(scheme.bkind),
                                       _ptr(scheme.bval), _ptr(T))
         else:
-            lib().or_differentials(C.byref(self._m), C.byref(self._g), nv, N, _ptr(u), _ptr(T))
+            self._L.or_differentials(C.byref(self._m), C.byref(self._g), nv, N, _ptr(u), _ptr(T))
         out, o = [], 0
         for m in range(N + 1):
             out.append(T[o:o + sizes[m]].reshape(nv, self.n_cells, D ** m))
@@ -228,7 +257,7 @@ class Oracle:
         rL = np.zeros((nv, self.n_faces), dtype=np.int32)
         rR = np.zeros((nv, self.n_faces), dtype=np.int32)
         s = scheme._c()
-        lib().or_face_values(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(T), _ptr(L), _ptr(R),
+        self._L.or_face_values(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(T), _ptr(L), _ptr(R),
                              _ptr(rL), _ptr(rR))
         return L, R, rL, rR
 
@@ -239,7 +268,7 @@ class Oracle:
         WL = np.zeros((self.n_faces, nw))
         WR = np.zeros((self.n_faces, nw))
         s = scheme._c()
-        lib().or_face_weights(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(WL), _ptr(WR))
+        self._L.or_face_weights(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(WL), _ptr(WR))
         return WL.reshape(self.n_faces, 2, -1), WR.reshape(self.n_faces, 2, -1)
 
     def criterion(self, u, scheme, kappa=4.0, eps=1e-3):
@@ -247,7 +276,7 @@ class Oracle:
         _, T = self.differentials(u, scheme.n_diff, scheme=scheme)
         flags = np.zeros(self.n_cells, dtype=np.uint8)
         s = scheme._c()
-        if lib().or_criterion(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(T), float(kappa), float(eps),
+        if self._L.or_criterion(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(T), float(kappa), float(eps),
                               _ptr(flags)) != 0:
             raise ValueError("criterion needs Euler with n_diff >= 2")
         return flags
@@ -258,7 +287,7 @@ class Oracle:
         own = np.zeros((self.n_cells, 6))
         x = np.zeros((self.n_cells, 24))
         s = scheme._c()
-        if lib().or_indicator_features(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(T), float(tiny),
+        if self._L.or_indicator_features(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(T), float(tiny),
                                        _ptr(own), _ptr(x)) != 0:
             raise MemoryError
         return own, x
@@ -267,14 +296,14 @@ class Oracle:
         u = np.ascontiguousarray(np.atleast_2d(u), dtype=np.float64)
         R = np.zeros_like(u)
         s = scheme._c()
-        if lib().or_residual(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(u), _ptr(R)) != 0:
+        if self._L.or_residual(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(u), _ptr(R)) != 0:
             raise MemoryError
         return R
 
     def rk3_step(self, u, scheme, dt):
         u = np.array(np.atleast_2d(u), dtype=np.float64, order="C")
         s = scheme._c()
-        if lib().or_rk3_step(C.byref(self._m), C.byref(self._g), C.byref(s), float(dt), _ptr(u)) != 0:
+        if self._L.or_rk3_step(C.byref(self._m), C.byref(self._g), C.byref(s), float(dt), _ptr(u)) != 0:
             raise MemoryError
         return u
 
@@ -283,7 +312,7 @@ class Oracle:
         us = np.ascontiguousarray(np.atleast_2d(us), dtype=np.float64)
         out = np.zeros_like(us)
         s = scheme._c()
-        if lib().or_rk3_stage(C.byref(self._m), C.byref(self._g), C.byref(s), float(dt), int(stage),
+        if self._L.or_rk3_stage(C.byref(self._m), C.byref(self._g), C.byref(s), float(dt), int(stage),
                               _ptr(u0), _ptr(us), _ptr(out)) != 0:
             raise MemoryError
         return out

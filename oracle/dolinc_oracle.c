@@ -31,6 +31,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_MAXD 3
 #define OR_MAXN 4      /* highest differential order */
@@ -571,22 +574,34 @@ int or_face_values(const or_mesh *m, const or_geom *g, const or_scheme *s, const
     return 0;
 }
 
-/* Residual R_c = -(1/V_c) sum_f (+-) F_f from differentials T (Sec 3). */
+/* Residual R_c = -(1/V_c) sum_f (+-) F_f from differentials T (Sec 3): every face's
+ * flux first, then the sums over faces in face order.  The face fluxes are
+ * independent of one another; a build with OpenMP (-fopenmp) computes them on all
+ * threads, with the same results (the sums stay sequential). */
 int or_residual_T(const or_mesh *m, const or_geom *g, const or_scheme *s, const double *T, double *R)
 {
     const int D = m->dim, nv = s->nv;
-    const long nc = m->n_cells;
-    memset(R, 0, sizeof(double) * (size_t)nv * (size_t)nc);
-    for (long f = 0; f < m->n_faces; ++f) {
-        long P = m->owner[f], Q = m->neigh[f];
-        double UL[OR_MAXV], UR[OR_MAXV], F[OR_MAXV];
+    const long nc = m->n_cells, nf = m->n_faces;
+    double *Ff = malloc(sizeof(double) * (size_t)nv * (size_t)(nf > 0 ? nf : 1));
+    if (!Ff) return -1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4096)
+#endif
+    for (long f = 0; f < nf; ++f) {
+        double UL[OR_MAXV], UR[OR_MAXV];
         face_states(m, g, s, T, f, UL, UR, NULL, NULL);
-        num_flux(D, s, UL, UR, &g->S[3*f], F);
+        num_flux(D, s, UL, UR, &g->S[3*f], &Ff[f * nv]);
+    }
+    memset(R, 0, sizeof(double) * (size_t)nv * (size_t)nc);
+    for (long f = 0; f < nf; ++f) {
+        long P = m->owner[f], Q = m->neigh[f];
+        const double *F = &Ff[f * nv];
         for (int v = 0; v < nv; ++v) {
             R[(long)v * nc + P] -= F[v] / g->V[P];
             if (Q >= 0) R[(long)v * nc + Q] += F[v] / g->V[Q];
         }
     }
+    free(Ff);
     return 0;
 }
 
@@ -597,9 +612,19 @@ int or_residual(const or_mesh *m, const or_geom *g, const or_scheme *s, const do
     double *T = malloc(sizeof(double) * (size_t)tsize(m->dim, s->nv, m->n_cells, s->n_diff));
     if (!T) return -1;
     or_differentials_bc(m, g, s->nv, s->n_diff, u, s->bkind, s->bval, T);
-    or_residual_T(m, g, s, T, R);
+    int rc = or_residual_T(m, g, s, T, R);
     free(T);
-    return 0;
+    return rc;
+}
+
+/* Threads the build computes face fluxes on: 1 without OpenMP. */
+int or_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* One step of the third-order TVD (SSP) Runge-Kutta scheme (Sec 3):
@@ -609,14 +634,14 @@ int or_rk3_step(const or_mesh *m, const or_geom *g, const or_scheme *s, double d
     const long n = (long)s->nv * m->n_cells;
     double *u1 = malloc(sizeof(double) * (size_t)n), *R = malloc(sizeof(double) * (size_t)n);
     if (!u1 || !R) return -1;
-    or_residual(m, g, s, u, R);
+    int rc = or_residual(m, g, s, u, R);
     for (long i = 0; i < n; ++i) u1[i] = u[i] + dt * R[i];
-    or_residual(m, g, s, u1, R);
+    rc |= or_residual(m, g, s, u1, R);
     for (long i = 0; i < n; ++i) u1[i] = 0.75 * u[i] + 0.25 * (u1[i] + dt * R[i]);
-    or_residual(m, g, s, u1, R);
+    rc |= or_residual(m, g, s, u1, R);
     for (long i = 0; i < n; ++i) u[i] = u[i] / 3.0 + 2.0 / 3.0 * (u1[i] + dt * R[i]);
     free(u1); free(R);
-    return 0;
+    return rc ? -1 : 0;
 }
 
 /* One stage as the fused GPU stage computes it: given the step's start u0 and the
@@ -628,10 +653,10 @@ int or_rk3_stage(const or_mesh *m, const or_geom *g, const or_scheme *s, double 
     const long n = (long)s->nv * m->n_cells;
     double *R = malloc(sizeof(double) * (size_t)n);
     if (!R || stage < 0 || stage > 2) { free(R); return -1; }
-    or_residual(m, g, s, us, R);
+    int rc = or_residual(m, g, s, us, R);
     for (long i = 0; i < n; ++i) out[i] = A[stage] * u0[i] + B[stage] * (us[i] + dt * R[i]);
     free(R);
-    return 0;
+    return rc;
 }
 
 /* Conditioning of each face value: the weights W0[m], W1[m] (m = 0..N) of the DOLINC
