@@ -409,6 +409,92 @@ enum { DOLINC_KERNEL_PACK = 0, DOLINC_KERNEL_DIFF1 = 1, DOLINC_KERNEL_DIFF2 = 2,
 dolinc_status dolinc_profile_enable(dolinc_mesh *mesh, int enable);
 dolinc_status dolinc_profile_read(dolinc_mesh *mesh, double *ms, int64_t *launches);
 
+/* ---------------------------------------------------------------- partitioned meshes
+ * Halo-exchanged parts of one mesh, one part per GPU (Sec 2.6: a coupled boundary
+ * exchanges only the adjacent cells' data plus their differentials).  A part holds
+ * its own cells and a depth-1 layer of ghost cells (cells of other parts sharing a
+ * face with an own cell).  Each differential pass reads only face neighbours and the
+ * reconstruction only the two face cells' records (Secs 2.3-2.4), so before each pass
+ * a part needs its ghosts' records of the order that pass reads, and before the stage
+ * the ghosts' records of every order the stage reads: one exchange per order, of
+ * depth 1.  A part keeps the whole mesh's library cell order and face order and
+ * orientation, and copies the whole mesh's geometry, so its own cells compute exactly
+ * what the whole mesh computes for them (the same operands in the same order). */
+
+/* Space-filling-curve partition: cells in Morton order of their centroids (the
+ * library order of DOLINC_RENUMBER_MORTON) cut into n_parts contiguous ranges of
+ * equal size (+-1).  part_of_cell[n_cells] (host) gets each caller cell's part.
+ * Host only; no GPU needed.  Errors: INVALID_ARG (null pointers, n_parts < 1 or
+ * above n_cells), MESH as dolinc_mesh_create. */
+dolinc_status dolinc_partition(const dolinc_mesh_desc *desc, int n_parts, int32_t *part_of_cell);
+
+typedef struct {
+    int64_t n_local;        /* own + ghost cells of the part */
+    int64_t n_owned;
+    int64_t n_faces;        /* faces of the own cells */
+    int32_t n_peers;        /* parts this part exchanges with */
+    int64_t n_send;         /* records sent per exchange (all peers) */
+    int64_t n_recv;         /* records received per exchange (all peers) */
+} dolinc_part_sizes;
+
+/* The plan of part `part` of the mesh under part_of_cell (caller cell order, values
+ * 0..n_parts-1; any assignment, e.g. dolinc_partition's).  Host only; no GPU needed.
+ * Call with NULL arrays to get `sizes`, then with arrays of those sizes (host):
+ *   local_cells [n_local]  caller cell id of each local cell, in the part's order
+ *                          (the whole mesh's library order restricted to the part);
+ *                          a part mesh's fields are [v * n_local + j] in this order
+ *   owned       [n_local]  1 own cell, 0 ghost
+ *   peers       [n_peers]  the other parts, ascending
+ *   send_off, recv_off [n_peers + 1]   offsets into send_cells / recv_cells per peer
+ *   send_cells  [n_send]   local indices of own cells peer q holds as ghosts
+ *   recv_cells  [n_recv]   local indices of the ghosts peer q owns
+ * Each list is in ascending library order, so part p's send list to q names the same
+ * cells, in the same order, as q's recv list from p.  Errors: INVALID_ARG (bad part,
+ * part_of_cell entry out of range, a part with no cell), MESH as dolinc_mesh_create. */
+dolinc_status dolinc_part_plan(const dolinc_mesh_desc *desc, const int32_t *part_of_cell, int n_parts, int part,
+                               dolinc_part_sizes *sizes, int64_t *local_cells, uint8_t *owned, int32_t *peers,
+                               int64_t *send_off, int64_t *send_cells, int64_t *recv_off, int64_t *recv_cells);
+
+/* Device mesh of part `part` (arguments as dolinc_part_plan; desc->renumber chooses
+ * the library order, as for the whole mesh).  Its cells are the plan's local cells,
+ * in that order (the permutation is the identity); its faces are the own cells'
+ * faces; its workspace (dolinc_workspace_size) also holds the exchange buffers.
+ * Destroy with dolinc_mesh_destroy.  Every other entry point accepts it; the ghosts'
+ * results of those are meaningless.  Errors as dolinc_part_plan, plus OOM / CUDA. */
+dolinc_status dolinc_mesh_create_part(const dolinc_mesh_desc *desc, const int32_t *part_of_cell, int n_parts,
+                                      int part, dolinc_mesh **out);
+
+dolinc_status dolinc_mesh_part_sizes(const dolinc_mesh *mesh, dolinc_part_sizes *sizes);
+
+/* A pending halo exchange of a partitioned step.  When pending = 1 the caller moves,
+ * for every peer q (in the plan's order), the record_bytes * (send_off[q+1] -
+ * send_off[q]) bytes at send_dev + record_bytes * send_off[q] to peer q, and fills
+ * recv_dev + record_bytes * recv_off[q] with what q sends (both device buffers inside
+ * the workspace; e.g. NCCL send/recv on `stream`), then calls dolinc_part_step_continue.
+ * order: the differential order being exchanged (0 = the stage's cell averages). */
+typedef struct {
+    int pending;
+    int order;
+    size_t record_bytes;
+    void *send_dev;
+    void *recv_dev;
+} dolinc_halo;
+
+/* One SSP-RK3 step of a part mesh, with a halo exchange before each differential
+ * pass and before the stage kernel of each of the three stages (orders 0 ..
+ * max(n_diff - 1, stencil order) per stage).  dolinc_part_step_begin packs u (the
+ * part's FP64 state, own cells and ghosts, [v * n_local + j]; the ghosts' values are
+ * not read) and stops at the first exchange with *halo filled; each
+ * dolinc_part_step_continue takes the received records into the ghosts and runs to the
+ * next exchange, or to the end of the step (halo->pending = 0; u then holds the own
+ * cells' new state; the ghosts' entries are meaningless).  All launches on `stream`;
+ * the exchange must be ordered on it too.  Errors: INVALID_ARG (not a part mesh,
+ * continue without a step in progress, workspace), as dolinc_rk_step otherwise. */
+dolinc_status dolinc_part_step_begin(dolinc_mesh *mesh, const dolinc_scheme *scheme, double dt, double *u_dev,
+                                     void *ws_dev, size_t ws_bytes, dolinc_stream stream, dolinc_halo *halo);
+dolinc_status dolinc_part_step_continue(dolinc_mesh *mesh, const dolinc_scheme *scheme, void *ws_dev,
+                                        size_t ws_bytes, dolinc_stream stream, dolinc_halo *halo);
+
 /* Message of the calling thread's last failing call ("" if none). */
 const char *dolinc_last_error(void);
 

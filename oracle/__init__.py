@@ -92,6 +92,7 @@ def _declare(L):
     L.or_geometry.argtypes = [P, P]
     L.or_differentials.argtypes = [P, P, C.c_int, C.c_int, P, P]
     L.or_differentials_bc.argtypes = [P, P, C.c_int, C.c_int, P, P, P, P]
+    L.or_gauss_pass.argtypes = [P, P, C.c_int, C.c_int, P, P, P, P]
     L.or_coeff.argtypes = [C.c_int, C.c_int, C.c_double, P]
     L.or_phantoms.argtypes = [C.c_int, C.c_double, P, P, P]
     L.or_face_values.argtypes = [P, P, P, P, P, P, P, P]
@@ -227,6 +228,59 @@ class Oracle:
             raise MemoryError("oracle geometry")
         self.owner = k["face_owner"]
         self.neigh = k["face_neighbour"]
+
+    @classmethod
+    def from_geometry(cls, dim, owner, neigh, shift, V, xc, S, xf, w, d, parallel=False):
+        """An oracle over given topology and geometry (no geometry computed): faces
+        owner -> neigh (-1 boundary) with periodic translations shift [n_faces][dim]
+        (or None), and the per-cell / per-face arrays of another Oracle's geometry.
+        Only the stage operators that take geometry from these arrays are meaningful."""
+        self = cls.__new__(cls)
+        self._L = lib_omp() if parallel else lib()
+        self.dim = int(dim)
+        nc, nf = int(np.asarray(V).shape[0]), int(np.asarray(owner).shape[0])
+        self.n_cells, self.n_faces = nc, nf
+        k = {"face_owner": np.ascontiguousarray(owner, dtype=np.int64),
+             "face_neighbour": np.ascontiguousarray(neigh, dtype=np.int64),
+             "face_periodic_shift": (np.ascontiguousarray(shift, dtype=np.float64) if shift is not None
+                                     else np.zeros((nf, dim))),
+             "nodes": np.zeros((1, dim)), "face_node_offsets": np.zeros(nf + 1, dtype=np.int64),
+             "face_nodes": np.zeros(1, dtype=np.int64)}
+        self._keep = k
+        m = _Mesh()
+        m.dim, m.n_nodes, m.n_cells, m.n_faces = self.dim, 1, nc, nf
+        m.nodes, m.face_node_off, m.face_nodes = _ptr(k["nodes"]), _ptr(k["face_node_offsets"]), _ptr(k["face_nodes"])
+        m.owner, m.neigh, m.shift = _ptr(k["face_owner"]), _ptr(k["face_neighbour"]), _ptr(k["face_periodic_shift"])
+        self._m = m
+        self.V, self.xc, self.S, self.xf, self.w, self.d = (np.ascontiguousarray(a, dtype=np.float64).copy()
+                                                            for a in (V, xc, S, xf, w, d))
+        g = _Geom()
+        g.V, g.xc, g.S, g.xf, g.w, g.d = (_ptr(a) for a in (self.V, self.xc, self.S, self.xf, self.w, self.d))
+        self._g = g
+        self.owner, self.neigh = k["face_owner"], k["face_neighbour"]
+        return self
+
+    def gauss_pass(self, T_prev, m, scheme=None):
+        """Order m (>= 1) full tensors [nv, n_cells, dim**m] from order m-1 [nv, n_cells, dim**(m-1)]
+        (one pass of the differentials; scheme supplies the boundary conditions)."""
+        T_prev = np.ascontiguousarray(T_prev, dtype=np.float64)
+        nv = T_prev.shape[0]
+        out = np.zeros((nv, self.n_cells, self.dim ** m))
+        bk = _ptr(scheme.bkind) if scheme is not None and scheme.bkind is not None else None
+        bv = _ptr(scheme.bval) if scheme is not None and scheme.bval is not None else None
+        if self._L.or_gauss_pass(C.byref(self._m), C.byref(self._g), nv, int(m), _ptr(T_prev), _ptr(out), bk, bv):
+            raise ValueError("bad order")
+        return out
+
+    def residual_T(self, T, scheme):
+        """Residual from given differentials T (list over orders 0..n_diff of [nv, n_cells, dim**m])."""
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(t, dtype=np.float64).ravel() for t in T]))
+        nv = scheme.nv
+        R = np.zeros((nv, self.n_cells))
+        s = scheme._c()
+        if self._L.or_residual_T(C.byref(self._m), C.byref(self._g), C.byref(s), _ptr(flat), _ptr(R)) != 0:
+            raise MemoryError
+        return R
 
     # differentials: list of arrays, order m -> [nv, n_cells, dim**m]
     def differentials(self, u, N, nv=None, scheme=None):

@@ -256,33 +256,42 @@ int or_differentials(const or_mesh *m, const or_geom *g, int nv, int N, const do
     return or_differentials_bc(m, g, nv, N, u, NULL, NULL, T);
 }
 
+/* One Gauss pass: order mm (>= 1) from order mm-1, full tensors [v][c][D^(mm-1)] ->
+ * [v][c][D^mm]; boundary faces as in or_differentials_bc. */
+int or_gauss_pass(const or_mesh *m, const or_geom *g, int nv, int mm, const double *Ti, double *To, const int *bkind,
+                  const double *bval)
+{
+    const int D = m->dim;
+    const long nc = m->n_cells;
+    if (mm < 1 || mm > OR_MAXN) return -1;
+    const int Ain = ipow(D, mm - 1), Aout = ipow(D, mm);
+    memset(To, 0, sizeof(double) * (size_t)nv * (size_t)nc * (size_t)Aout);
+    for (long f = 0; f < m->n_faces; ++f) {
+        long P = m->owner[f], Q = m->neigh[f];
+        const double *S = &g->S[3*f];
+        double w = g->w[f];
+        for (int v = 0; v < nv; ++v)
+            for (int a = 0; a < Ain; ++a) {
+                double tP = Ti[((long)v * nc + P) * Ain + a];
+                double tf = Q >= 0 ? w * tP + (1.0 - w) * Ti[((long)v * nc + Q) * Ain + a]
+                                   : (mm == 1 ? boundary_value(g, bkind, bval, m->n_faces, f, P, v, tP) : tP);
+                for (int k = 0; k < D; ++k) {
+                    To[((long)v * nc + P) * Aout + k * Ain + a] += S[k] * tf / g->V[P];
+                    if (Q >= 0) To[((long)v * nc + Q) * Aout + k * Ain + a] -= S[k] * tf / g->V[Q];
+                }
+            }
+    }
+    return 0;
+}
+
 int or_differentials_bc(const or_mesh *m, const or_geom *g, int nv, int N, const double *u, const int *bkind,
                         const double *bval, double *T)
 {
     const int D = m->dim;
     const long nc = m->n_cells;
     memcpy(T, u, sizeof(double) * (size_t)nv * (size_t)nc);
-    for (int mm = 1; mm <= N; ++mm) {
-        const int Ain = ipow(D, mm - 1), Aout = ipow(D, mm);
-        const double *Ti = T + toff(D, nv, nc, mm - 1);
-        double *To = T + toff(D, nv, nc, mm);
-        memset(To, 0, sizeof(double) * (size_t)nv * (size_t)nc * (size_t)Aout);
-        for (long f = 0; f < m->n_faces; ++f) {
-            long P = m->owner[f], Q = m->neigh[f];
-            const double *S = &g->S[3*f];
-            double w = g->w[f];
-            for (int v = 0; v < nv; ++v)
-                for (int a = 0; a < Ain; ++a) {
-                    double tP = Ti[((long)v * nc + P) * Ain + a];
-                    double tf = Q >= 0 ? w * tP + (1.0 - w) * Ti[((long)v * nc + Q) * Ain + a]
-                                       : (mm == 1 ? boundary_value(g, bkind, bval, m->n_faces, f, P, v, tP) : tP);
-                    for (int k = 0; k < D; ++k) {
-                        To[((long)v * nc + P) * Aout + k * Ain + a] += S[k] * tf / g->V[P];
-                        if (Q >= 0) To[((long)v * nc + Q) * Aout + k * Ain + a] -= S[k] * tf / g->V[Q];
-                    }
-                }
-        }
-    }
+    for (int mm = 1; mm <= N; ++mm)
+        or_gauss_pass(m, g, nv, mm, T + toff(D, nv, nc, mm - 1), T + toff(D, nv, nc, mm), bkind, bval);
     return 0;
 }
 

@@ -32,7 +32,8 @@ ABI_SYMBOLS = (
     "dolinc_mlp_get_params", "dolinc_mlp_set_params", "dolinc_mlp_forward", "dolinc_mlp_loss_grad",
     "dolinc_mlp_train_step", "dolinc_indicator_infer", "dolinc_batch_create", "dolinc_batch_destroy",
     "dolinc_batch_info", "dolinc_batch_set_spin_limit", "dolinc_batch_workspace_size", "dolinc_batch_rk_step",
-    "dolinc_batch_autotune", "dolinc_last_error",
+    "dolinc_batch_autotune", "dolinc_partition", "dolinc_part_plan", "dolinc_mesh_create_part",
+    "dolinc_mesh_part_sizes", "dolinc_part_step_begin", "dolinc_part_step_continue", "dolinc_last_error",
 )
 KERNEL_KINDS = ("pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces")
 
@@ -100,6 +101,11 @@ def load(path=LIB_PATH):
             "dolinc_batch_set_spin_limit": [P, C.c_uint], "dolinc_batch_workspace_size": [P, P, P],
             "dolinc_batch_rk_step": [P, P, P, P, P, S, I, P],
             "dolinc_batch_autotune": [P, P, P, P, P, S, P, P, P, P],
+            "dolinc_partition": [P, I, P],
+            "dolinc_part_plan": [P, P, I, I, P, P, P, P, P, P, P, P],
+            "dolinc_mesh_create_part": [P, P, I, I, P], "dolinc_mesh_part_sizes": [P, P],
+            "dolinc_part_step_begin": [P, P, D, P, P, S, P, P],
+            "dolinc_part_step_continue": [P, P, P, S, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -158,37 +164,94 @@ class _Tuning(C.Structure):
                 ("stage_ms", C.c_double)]
 
 
-class Mesh:
-    """A library mesh handle built from a mesh dict (see synth.meshes)."""
+def _make_desc(m, renumber):
+    """dolinc_mesh_desc of a mesh dict, and the arrays it points to (keep them alive)."""
+    a = {}
+    for key, dt in (("nodes", np.float64), ("cell_face_offsets", np.int64), ("cell_faces", np.int64),
+                    ("face_node_offsets", np.int64), ("face_nodes", np.int64), ("face_owner", np.int64),
+                    ("face_neighbour", np.int64), ("face_periodic_shift", np.float64),
+                    ("boundary_kind", np.int32)):
+        if key in m and m[key] is not None:
+            a[key] = np.ascontiguousarray(m[key], dtype=dt)
+    d = _Desc()
+    d.dim = int(m["dim"])
+    d.n_nodes = a["nodes"].shape[0]
+    d.nodes = _ptr(a["nodes"])
+    d.n_cells = a["cell_face_offsets"].shape[0] - 1
+    d.cell_face_offsets = _ptr(a.get("cell_face_offsets"))
+    d.cell_faces = _ptr(a.get("cell_faces"))
+    d.n_faces = a["face_owner"].shape[0]
+    d.face_node_offsets = _ptr(a["face_node_offsets"])
+    d.face_nodes = _ptr(a["face_nodes"])
+    d.face_owner = _ptr(a["face_owner"])
+    d.face_neighbour = _ptr(a["face_neighbour"])
+    d.face_periodic_shift = _ptr(a.get("face_periodic_shift"))
+    d.boundary_kind = _ptr(a.get("boundary_kind"))
+    d.renumber = RENUMBER[renumber] if isinstance(renumber, str) else int(renumber)
+    return d, a
 
-    def __init__(self, m, renumber="morton"):
+
+class _PartSizes(C.Structure):
+    _fields_ = [("n_local", C.c_int64), ("n_owned", C.c_int64), ("n_faces", C.c_int64), ("n_peers", C.c_int32),
+                ("n_send", C.c_int64), ("n_recv", C.c_int64)]
+
+
+class _Halo(C.Structure):
+    _fields_ = [("pending", C.c_int), ("order", C.c_int), ("record_bytes", C.c_size_t), ("send_dev", C.c_void_p),
+                ("recv_dev", C.c_void_p)]
+
+
+def dolinc_partition(m, n_parts):
+    """Space-filling-curve partition of a mesh dict: the part of every caller cell."""
+    d, keep = _make_desc(m, "morton")
+    out = np.zeros(d.n_cells, dtype=np.int32)
+    _check(load().dolinc_partition(C.byref(d), int(n_parts), _ptr(out)))
+    return out
+
+
+def dolinc_part_plan(m, part_of_cell, n_parts, part, renumber="morton"):
+    """Host plan of one part: local cells (caller ids), own flags, peers and the
+    per-peer send / receive lists (local indices)."""
+    d, keep = _make_desc(m, renumber)
+    pc = np.ascontiguousarray(part_of_cell, dtype=np.int32)
+    z = _PartSizes()
+    L = load()
+    _check(L.dolinc_part_plan(C.byref(d), _ptr(pc), int(n_parts), int(part), C.byref(z), *([None] * 7)))
+    out = dict(local_cells=np.zeros(z.n_local, dtype=np.int64), owned=np.zeros(z.n_local, dtype=np.uint8),
+               peers=np.zeros(z.n_peers, dtype=np.int32), send_off=np.zeros(z.n_peers + 1, dtype=np.int64),
+               send_cells=np.zeros(z.n_send, dtype=np.int64), recv_off=np.zeros(z.n_peers + 1, dtype=np.int64),
+               recv_cells=np.zeros(z.n_recv, dtype=np.int64))
+    _check(L.dolinc_part_plan(C.byref(d), _ptr(pc), int(n_parts), int(part), C.byref(z), _ptr(out["local_cells"]),
+                              _ptr(out["owned"]), _ptr(out["peers"]), _ptr(out["send_off"]), _ptr(out["send_cells"]),
+                              _ptr(out["recv_off"]), _ptr(out["recv_cells"])))
+    out["n_faces"] = z.n_faces
+    return out
+
+
+class Mesh:
+    """A library mesh handle built from a mesh dict (see synth.meshes).
+    part=(part_of_cell, n_parts, p) builds part p of a partitioned mesh instead
+    (dolinc_mesh_create_part): its cells are the plan's local cells (self.plan), in
+    that order."""
+
+    def __init__(self, m, renumber="morton", part=None):
         L = load()
-        self._arrays = {}
-        for key, dt in (("nodes", np.float64), ("cell_face_offsets", np.int64), ("cell_faces", np.int64),
-                        ("face_node_offsets", np.int64), ("face_nodes", np.int64), ("face_owner", np.int64),
-                        ("face_neighbour", np.int64), ("face_periodic_shift", np.float64),
-                        ("boundary_kind", np.int32)):
-            if key in m and m[key] is not None:
-                self._arrays[key] = np.ascontiguousarray(m[key], dtype=dt)
-        a = self._arrays
-        d = _Desc()
-        d.dim = int(m["dim"])
-        d.n_nodes = a["nodes"].shape[0]
-        d.nodes = _ptr(a["nodes"])
-        d.n_cells = a["cell_face_offsets"].shape[0] - 1
-        d.cell_face_offsets = _ptr(a.get("cell_face_offsets"))
-        d.cell_faces = _ptr(a.get("cell_faces"))
-        d.n_faces = a["face_owner"].shape[0]
-        d.face_node_offsets = _ptr(a["face_node_offsets"])
-        d.face_nodes = _ptr(a["face_nodes"])
-        d.face_owner = _ptr(a["face_owner"])
-        d.face_neighbour = _ptr(a["face_neighbour"])
-        d.face_periodic_shift = _ptr(a.get("face_periodic_shift"))
-        d.boundary_kind = _ptr(a.get("boundary_kind"))
-        d.renumber = RENUMBER[renumber] if isinstance(renumber, str) else int(renumber)
+        d, self._arrays = _make_desc(m, renumber)
         h = C.c_void_p()
-        _check(L.dolinc_mesh_create(C.byref(d), C.byref(h)))
+        self.plan = None
+        if part is None:
+            _check(L.dolinc_mesh_create(C.byref(d), C.byref(h)))
+        else:
+            pc, n_parts, p = part
+            pc = np.ascontiguousarray(pc, dtype=np.int32)
+            _check(L.dolinc_mesh_create_part(C.byref(d), _ptr(pc), int(n_parts), int(p), C.byref(h)))
+            self.plan = dolinc_part_plan(m, pc, n_parts, p, renumber)
         self.handle = h
+        self._finish()
+
+    def _finish(self):
+        L = load()
+        h = self.handle
         info = _Info()
         _check(L.dolinc_mesh_get_info(h, C.byref(info)))
         self.dim, self.n_cells, self.n_faces = info.dim, info.n_cells, info.n_faces
@@ -487,3 +550,63 @@ class Batch:
         _check(load().dolinc_batch_autotune(self.handle, C.byref(s), _ptr(dt), _ptr(u), _ptr(ws), ws.numel(),
                                             _stream(stream), C.byref(b), C.byref(g), C.byref(ms)))
         return dict(block=b.value, grid=g.value, ms_per_step=ms.value)
+
+
+class Halo:
+    """A pending exchange of a partitioned step (dolinc_halo)."""
+
+    def __init__(self, h):
+        self.pending, self.order, self.record_bytes = h.pending, h.order, h.record_bytes
+        self.send_dev, self.recv_dev = h.send_dev or 0, h.recv_dev or 0
+
+    def views(self, ws, plan):
+        """Per peer: (peer, send bytes, receive bytes) as uint8 views of the workspace ws."""
+        rb = self.record_bytes
+        s0, r0 = self.send_dev - ws.data_ptr(), self.recv_dev - ws.data_ptr()
+        out = []
+        for i, q in enumerate(plan["peers"]):
+            a, b = int(plan["send_off"][i]) * rb, int(plan["send_off"][i + 1]) * rb
+            c, d = int(plan["recv_off"][i]) * rb, int(plan["recv_off"][i + 1]) * rb
+            out.append((int(q), ws[s0 + a:s0 + b], ws[r0 + c:r0 + d]))
+        return out
+
+
+def dolinc_part_step_begin(mesh, scheme, dt, u, ws, stream=None):
+    h = _Halo()
+    s = scheme.c()
+    _check(load().dolinc_part_step_begin(mesh.handle, C.byref(s), float(dt), _ptr(u), _ptr(ws), ws.numel(),
+                                         _stream(stream), C.byref(h)))
+    return Halo(h)
+
+
+def dolinc_part_step_continue(mesh, scheme, ws, stream=None):
+    h = _Halo()
+    s = scheme.c()
+    _check(load().dolinc_part_step_continue(mesh.handle, C.byref(s), _ptr(ws), ws.numel(), _stream(stream),
+                                            C.byref(h)))
+    return Halo(h)
+
+
+def part_rk_step(mesh, scheme, dt, u, ws, exchange, stream=None):
+    """One SSP-RK3 step of a part mesh; exchange(halo) moves each pending halo's
+    records between the parts (e.g. exchange_collective)."""
+    h = dolinc_part_step_begin(mesh, scheme, dt, u, ws, stream)
+    while h.pending:
+        exchange(h)
+        h = dolinc_part_step_continue(mesh, scheme, ws, stream)
+
+
+def exchange_collective(dist, mesh, ws):
+    """An exchange over torch.distributed point-to-point (NCCL: on the current stream):
+    this rank is part dist.get_rank() of the partition."""
+    def run(h):
+        ops = []
+        for q, snd, rcv in h.views(ws, mesh.plan):
+            if snd.numel():
+                ops.append(dist.P2POp(dist.isend, snd, q))
+            if rcv.numel():
+                ops.append(dist.P2POp(dist.irecv, rcv, q))
+        if ops:
+            for r in dist.batch_isend_irecv(ops):
+                r.wait()
+    return run

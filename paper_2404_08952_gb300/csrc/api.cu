@@ -7,6 +7,7 @@
 #include <chrono>
 #include <fstream>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <sstream>
 #include <string>
@@ -67,9 +68,23 @@ namespace dol {
 dolinc_status report_error(dolinc_status s, const std::string &msg) { return fail(s, msg); }
 }  // namespace dol
 
+// A part of a partitioned mesh: its plan, the device copies of its exchange lists and
+// the progress of the step in flight (dolinc_part_step_begin / _continue).
+struct PartState {
+    PartPlan plan;
+    const int32_t *send_dev = nullptr, *recv_dev = nullptr;   // local cell indices
+    bool active = false;     // a step is in progress
+    int stage = 0;           // its SSP-RK3 stage
+    int cur = 0;             // FP64 path: the order-0 record buffer the stage reads
+    int order = -1;          // order of the exchange in flight
+    double dt = 0;
+    double *u = nullptr;
+};
+
 struct dolinc_mesh {
     HostMesh h;
     DevMesh d{};
+    std::unique_ptr<PartState> part;
     int device = 0;
     std::vector<void *> allocs;
     const uint8_t *flags = nullptr;
@@ -216,7 +231,7 @@ int ncoef_h(int dim, int m) { return dim == 2 ? m + 1 : (m + 1) * (m + 2) / 2; }
 int stride_h(int dim, int nv, int m, int prec) { return rec_stride(nv * ncoef_h(dim, m), elem_bytes(prec, m)); }
 
 struct WsLayout {
-    size_t status, o0[3], ord[MAXN + 1], ustage, dacc, flux, total;
+    size_t status, o0[3], ord[MAXN + 1], ustage, dacc, flux, hsend, hrecv, total;
 };
 
 WsLayout ws_layout(const dolinc_mesh *m, const dolinc_scheme *s)
@@ -244,6 +259,16 @@ WsLayout ws_layout(const dolinc_mesh *m, const dolinc_scheme *s)
     if (s->precision != DOLINC_FP64) o += al256(nc * s->nv * sizeof(float));
     L.flux = o;                                 // per-face fluxes of the face-centric stage
     o += al256((size_t)m->h.n_faces * s->nv * (s->precision == DOLINC_FP64 ? sizeof(double) : sizeof(float)));
+    // part meshes: the halo exchange buffers, sized for the largest record exchanged
+    L.hsend = L.hrecv = o;
+    if (m->part) {
+        size_t rb = 0;
+        for (int mm = 0; mm <= s->n_diff; ++mm)
+            rb = std::max(rb, (size_t)stride_h(m->h.dim, s->nv, mm, s->precision) * elem_bytes(s->precision, mm));
+        o += al256(rb * m->part->plan.send_cells.size());
+        L.hrecv = o;
+        o += al256(rb * m->part->plan.recv_cells.size());
+    }
     L.total = o;
     return L;
 }
@@ -1504,6 +1529,300 @@ dolinc_status dolinc_sync_status(dolinc_mesh *m, void *ws, dolinc_stream stream)
     if (h & 2u) return fail(DOLINC_ERR_DEVICE_TIMEOUT, "a device-side wait gave up");
     if (h & 1u) return fail(DOLINC_ERR_NONFINITE, "a stage produced NaN or Inf");
     return DOLINC_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ partitioned meshes
+namespace {
+
+// Record rows of `n` cells: gather (dst row i = src row idx[i]) or scatter (dst row
+// idx[i] = src row i), moved in words of wbytes (a divisor of the record size; rows
+// and buffers start at multiples of it).
+__global__ void __launch_bounds__(256) k_halo_copy(const unsigned char *__restrict__ src, unsigned char *__restrict__ dst,
+                                                   const int32_t *__restrict__ idx, long long n, int words,
+                                                   int wbytes, int gather)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * words) return;
+    const long long i = t / words;
+    const int w = (int)(t % words);
+    const long long a = gather ? (long long)idx[i] : i, b = gather ? i : (long long)idx[i];
+    const size_t rb = (size_t)words * wbytes;
+    const unsigned char *ps = src + a * rb;
+    unsigned char *pd = dst + b * rb;
+    switch (wbytes) {
+    case 16: reinterpret_cast<uint4 *>(pd)[w] = reinterpret_cast<const uint4 *>(ps)[w]; break;
+    case 8: reinterpret_cast<uint2 *>(pd)[w] = reinterpret_cast<const uint2 *>(ps)[w]; break;
+    case 4: reinterpret_cast<unsigned *>(pd)[w] = reinterpret_cast<const unsigned *>(ps)[w]; break;
+    case 2: reinterpret_cast<unsigned short *>(pd)[w] = reinterpret_cast<const unsigned short *>(ps)[w]; break;
+    default: pd[w] = ps[w]; break;
+    }
+}
+
+size_t rec_bytes(const dolinc_mesh *m, const dolinc_scheme *s, int order)
+{
+    return (size_t)stride_h(m->h.dim, s->nv, order, s->precision) * elem_bytes(s->precision, order);
+}
+
+void halo_copy(const void *src, void *dst, const int32_t *idx, size_t n, size_t rb, bool gather, cudaStream_t cs)
+{
+    if (n == 0) return;
+    int wb = 16;
+    while (rb % wb) wb /= 2;
+    const int words = (int)(rb / wb);
+    const long long tot = (long long)n * words;
+    k_halo_copy<<<(int)((tot + 255) / 256), 256, 0, cs>>>(static_cast<const unsigned char *>(src),
+                                                          static_cast<unsigned char *>(dst), idx, (long long)n,
+                                                          words, wb, gather ? 1 : 0);
+}
+
+// Offset of the record buffer of `order` that the current stage reads.
+size_t part_rec_off(const dolinc_mesh *m, const dolinc_scheme *s, const WsLayout &L, int order)
+{
+    const PartState &P = *m->part;
+    if (order > 0) return L.ord[order];
+    return s->precision != DOLINC_FP64 ? L.o0[P.stage] : L.o0[P.cur];
+}
+
+// Packs the own cells' records of `order` for the peers and describes the exchange.
+void part_request(dolinc_mesh *m, const dolinc_scheme *s, void *ws, const WsLayout &L, int order, cudaStream_t cs,
+                  dolinc_halo *h)
+{
+    PartState &P = *m->part;
+    const size_t rb = rec_bytes(m, s, order);
+    halo_copy(B(ws, part_rec_off(m, s, L, order)), B(ws, L.hsend), P.send_dev, P.plan.send_cells.size(), rb, true,
+              cs);
+    P.order = order;
+    h->pending = 1;
+    h->order = order;
+    h->record_bytes = rb;
+    h->send_dev = B(ws, L.hsend);
+    h->recv_dev = B(ws, L.hrecv);
+}
+
+// Highest order exchanged per stage: each pass's input, and every order the stage reads.
+int part_top_order(const dolinc_scheme *s)
+{
+    const int need = needed_order(*s);
+    return std::max(s->n_diff - 1, need);
+}
+
+// Runs the step from just after the exchange of P.order to the next exchange point
+// (or the end of the step).
+dolinc_status part_advance(dolinc_mesh *m, const dolinc_scheme *s, void *ws, const WsLayout &L, cudaStream_t cs,
+                           dolinc_halo *h)
+{
+    static const double A[3] = {0.0, 0.75, 1.0 / 3.0}, Bc[3] = {1.0, 0.25, 2.0 / 3.0};
+    PartState &P = *m->part;
+    const PathFns *p = path_for(m, s, needed_order(*s));
+    if (!p) return fail(DOLINC_ERR_UNSUPPORTED, "no kernel for this (dim, nv, order, precision)");
+    const Tune tn = tune_for(m, s);
+    const int top = part_top_order(s);
+    const size_t o0off = part_rec_off(m, s, L, 0);
+    for (int mm = P.order + 1; mm <= s->n_diff; ++mm) {
+        timed(m, mm, cs, [&] {
+            p->diff(m->d, mm, B(ws, mm == 1 ? o0off : L.ord[mm - 1]), B(ws, L.ord[mm]), tn,
+                    reinterpret_cast<unsigned *>(B(ws, L.status)), cs);
+            if (mm == 1) p->bnd_grad(m->d, B(ws, o0off), B(ws, L.ord[1]), cs);
+        });
+        if (mm <= top) {
+            part_request(m, s, ws, L, mm, cs, h);
+            return launch_check();
+        }
+    }
+    // every order the stage reads is in place on the ghosts: the stage kernel
+    const int sg = P.stage;
+    StageArgs a = base_args(m, s, ws, L, o0off);
+    a.dt = P.dt;
+    a.u0 = P.u;
+    if (s->precision != DOLINC_FP64) {
+        a.mode = 2;
+        a.rk = sg;
+        a.out = P.u;
+        a.dacc = reinterpret_cast<float *>(B(ws, L.dacc));
+        a.rec_start = B(ws, L.o0[0]);
+        a.o0_next = sg == 2 ? nullptr : B(ws, L.o0[sg + 1]);
+    } else {
+        double *ust = reinterpret_cast<double *>(B(ws, L.ustage));
+        a.mode = 1;
+        a.us = sg == 0 ? P.u : ust;
+        a.out = sg == 2 ? P.u : ust;
+        a.A = A[sg];
+        a.B = Bc[sg];
+        a.o0_next = sg == 2 ? nullptr : B(ws, L.o0[1 - P.cur]);
+    }
+    timed(m, DOLINC_KERNEL_STAGE, cs, [&] { p->stage(m->d, a, tn, cs); });
+    if (sg < 2) {
+        P.stage = sg + 1;
+        P.cur = 1 - P.cur;
+        part_request(m, s, ws, L, 0, cs, h);
+        return launch_check();
+    }
+    P.active = false;
+    P.order = -1;
+    h->pending = 0;
+    h->order = -1;
+    h->record_bytes = 0;
+    h->send_dev = h->recv_dev = nullptr;
+    return launch_check();
+}
+
+dolinc_status plan_from_desc(const dolinc_mesh_desc *desc, const int32_t *part_of_cell, int n_parts, int part,
+                             HostMesh &g, PartPlan &plan)
+{
+    if (!desc || !part_of_cell) return fail(DOLINC_ERR_INVALID_ARG, "null descriptor or part_of_cell");
+    std::string err;
+    try {
+        err = build_host_mesh(*desc, g);
+    } catch (const std::bad_alloc &) {
+        return fail(DOLINC_ERR_OOM, "host allocation while building the mesh");
+    }
+    if (!err.empty()) return fail(DOLINC_ERR_MESH, err);
+    std::vector<int32_t> part_lib(g.n_cells);
+    for (int64_t c = 0; c < g.n_cells; ++c) part_lib[g.perm[c]] = part_of_cell[c];
+    err = plan_part(g, part_lib, n_parts, part, plan);
+    if (!err.empty()) return fail(DOLINC_ERR_INVALID_ARG, err);
+    return DOLINC_OK;
+}
+
+void fill_sizes(const PartPlan &p, dolinc_part_sizes *z)
+{
+    z->n_local = (int64_t)p.cells.size();
+    z->n_owned = 0;
+    for (uint8_t o : p.owned) z->n_owned += o;
+    z->n_faces = (int64_t)p.faces.size();
+    z->n_peers = (int32_t)p.peers.size();
+    z->n_send = (int64_t)p.send_cells.size();
+    z->n_recv = (int64_t)p.recv_cells.size();
+}
+
+}  // namespace
+
+extern "C" {
+
+dolinc_status dolinc_partition(const dolinc_mesh_desc *desc, int n_parts, int32_t *part_of_cell)
+{
+    if (!desc || !part_of_cell) return fail(DOLINC_ERR_INVALID_ARG, "null argument");
+    if (n_parts < 1 || n_parts > desc->n_cells) return fail(DOLINC_ERR_INVALID_ARG, "n_parts must be in 1..n_cells");
+    dolinc_mesh_desc d = *desc;
+    d.renumber = DOLINC_RENUMBER_MORTON;
+    HostMesh g;
+    std::string err;
+    try {
+        err = build_host_mesh(d, g);
+    } catch (const std::bad_alloc &) {
+        return fail(DOLINC_ERR_OOM, "host allocation while building the mesh");
+    }
+    if (!err.empty()) return fail(DOLINC_ERR_MESH, err);
+    for (int64_t c = 0; c < g.n_cells; ++c) part_of_cell[c] = (int32_t)((g.perm[c] * (int64_t)n_parts) / g.n_cells);
+    return DOLINC_OK;
+}
+
+dolinc_status dolinc_part_plan(const dolinc_mesh_desc *desc, const int32_t *part_of_cell, int n_parts, int part,
+                               dolinc_part_sizes *sizes, int64_t *local_cells, uint8_t *owned, int32_t *peers,
+                               int64_t *send_off, int64_t *send_cells, int64_t *recv_off, int64_t *recv_cells)
+{
+    if (!sizes) return fail(DOLINC_ERR_INVALID_ARG, "null sizes");
+    HostMesh g;
+    PartPlan p;
+    dolinc_status st = plan_from_desc(desc, part_of_cell, n_parts, part, g, p);
+    if (st) return st;
+    fill_sizes(p, sizes);
+    if (local_cells) {
+        std::vector<int64_t> old_of_new(g.n_cells);
+        for (int64_t c = 0; c < g.n_cells; ++c) old_of_new[g.perm[c]] = c;
+        for (size_t j = 0; j < p.cells.size(); ++j) local_cells[j] = old_of_new[p.cells[j]];
+    }
+    if (owned) std::memcpy(owned, p.owned.data(), p.owned.size());
+    if (peers) std::memcpy(peers, p.peers.data(), sizeof(int32_t) * p.peers.size());
+    if (send_off) std::memcpy(send_off, p.send_off.data(), sizeof(int64_t) * p.send_off.size());
+    if (recv_off) std::memcpy(recv_off, p.recv_off.data(), sizeof(int64_t) * p.recv_off.size());
+    if (send_cells) std::memcpy(send_cells, p.send_cells.data(), sizeof(int64_t) * p.send_cells.size());
+    if (recv_cells) std::memcpy(recv_cells, p.recv_cells.data(), sizeof(int64_t) * p.recv_cells.size());
+    return DOLINC_OK;
+}
+
+dolinc_status dolinc_mesh_create_part(const dolinc_mesh_desc *desc, const int32_t *part_of_cell, int n_parts,
+                                      int part, dolinc_mesh **out)
+{
+    if (!out) return fail(DOLINC_ERR_INVALID_ARG, "null output handle");
+    *out = nullptr;
+    HostMesh g;
+    auto ps = std::unique_ptr<PartState>(new (std::nothrow) PartState());
+    if (!ps) return fail(DOLINC_ERR_OOM, "host allocation");
+    dolinc_status st = plan_from_desc(desc, part_of_cell, n_parts, part, g, ps->plan);
+    if (st) return st;
+    dolinc_mesh *m = new (std::nothrow) dolinc_mesh();
+    if (!m) return fail(DOLINC_ERR_OOM, "host allocation");
+    try {
+        slice_host_mesh(g, ps->plan, m->h);
+    } catch (const std::bad_alloc &) {
+        delete m;
+        return fail(DOLINC_ERR_OOM, "host allocation while slicing the part");
+    }
+    if ((st = upload_mesh(m))) {
+        delete m;
+        return st;
+    }
+    std::vector<int32_t> sc(ps->plan.send_cells.begin(), ps->plan.send_cells.end());
+    std::vector<int32_t> rc(ps->plan.recv_cells.begin(), ps->plan.recv_cells.end());
+    sc.push_back(0);                            // never empty
+    rc.push_back(0);
+    if ((st = upload(m, sc, &ps->send_dev)) || (st = upload(m, rc, &ps->recv_dev))) {
+        delete m;
+        return st;
+    }
+    m->part = std::move(ps);
+    *out = m;
+    return DOLINC_OK;
+}
+
+dolinc_status dolinc_mesh_part_sizes(const dolinc_mesh *m, dolinc_part_sizes *sizes)
+{
+    if (!m || !sizes) return fail(DOLINC_ERR_INVALID_ARG, "null argument");
+    if (!m->part) return fail(DOLINC_ERR_INVALID_ARG, "not a part mesh");
+    fill_sizes(m->part->plan, sizes);
+    return DOLINC_OK;
+}
+
+dolinc_status dolinc_part_step_begin(dolinc_mesh *m, const dolinc_scheme *s, double dt, double *u, void *ws,
+                                     size_t ws_bytes, dolinc_stream stream, dolinc_halo *h)
+{
+    dolinc_status st = check_scheme(m, s);
+    if (st) return st;
+    if (!m->part) return fail(DOLINC_ERR_INVALID_ARG, "not a part mesh (dolinc_mesh_create_part)");
+    if (!h || !u) return fail(DOLINC_ERR_INVALID_ARG, "null field or halo");
+    WsLayout L;
+    if ((st = check_ws(m, s, ws, ws_bytes, L))) return st;
+    const PathFns *p = path_for(m, s, needed_order(*s));
+    if (!p) return fail(DOLINC_ERR_UNSUPPORTED, "no kernel for this (dim, nv, order, precision)");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    PartState &P = *m->part;
+    P.active = true;
+    P.stage = 0;
+    P.cur = 0;
+    P.dt = dt;
+    P.u = u;
+    timed(m, DOLINC_KERNEL_PACK, cs, [&] { p->pack(m->d, u, B(ws, L.o0[0]), nullptr, cs); });
+    part_request(m, s, ws, L, 0, cs, h);
+    return launch_check();
+}
+
+dolinc_status dolinc_part_step_continue(dolinc_mesh *m, const dolinc_scheme *s, void *ws, size_t ws_bytes,
+                                        dolinc_stream stream, dolinc_halo *h)
+{
+    dolinc_status st = check_scheme(m, s);
+    if (st) return st;
+    if (!m->part || !m->part->active) return fail(DOLINC_ERR_INVALID_ARG, "no partitioned step in progress");
+    if (!h) return fail(DOLINC_ERR_INVALID_ARG, "null halo");
+    WsLayout L;
+    if ((st = check_ws(m, s, ws, ws_bytes, L))) return st;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    PartState &P = *m->part;
+    halo_copy(B(ws, L.hrecv), B(ws, part_rec_off(m, s, L, P.order)), P.recv_dev, P.plan.recv_cells.size(),
+              rec_bytes(m, s, P.order), false, cs);
+    return part_advance(m, s, ws, L, cs, h);
 }
 
 }  // extern "C"

@@ -96,6 +96,53 @@ uint64_t spread2(uint64_t v)   // 31 bits -> every second bit
 
 }  // namespace
 
+// Cell -> face slot tables from the internal faces (fo, fn, fS, fw) and volumes:
+// a cell's slots follow the internal face order.
+void build_slots(HostMesh &m)
+{
+    const int64_t nc = m.n_cells, nf = m.n_faces;
+    m.off.assign(nc + 1, 0);
+    for (int64_t i = 0; i < nf; ++i) {
+        m.off[m.fo[i] + 1]++;
+        if (m.fn[i] >= 0) m.off[m.fn[i] + 1]++;
+    }
+    for (int64_t c = 0; c < nc; ++c) m.off[c + 1] += m.off[c];
+    m.n_slots = m.off[nc];
+    m.snb.resize(m.n_slots);
+    m.sword.resize(m.n_slots);
+    m.ss.assign(3 * m.n_slots, 0.0);
+    m.cw.assign(4 * nc, 0.0);
+    std::vector<int32_t> fill(m.off.begin(), m.off.end() - 1);
+    // slots of a cell follow the internal face order
+    for (int64_t i = 0; i < nf; ++i) {
+        const int64_t P = m.fo[i], N = m.fn[i];
+        const V3 s{m.fS[3 * i], m.fS[3 * i + 1], m.fS[3 * i + 2]};
+        const double w = m.fw[i];
+        {
+            int64_t sl = fill[P]++;
+            m.snb[sl] = (int32_t)(N >= 0 ? N : P);
+            m.sword[sl] = slot_word(i, N < 0, 0);
+            double iv = 1.0 / m.V[P];
+            // weight of P at the face: w (boundary: w = 1, face value = cell value)
+            V3 k = ((1.0 - w) * iv) * s;
+            m.ss[3 * sl] = k.x, m.ss[3 * sl + 1] = k.y, m.ss[3 * sl + 2] = k.z;
+            m.cw[4 * P] += w * iv * s.x, m.cw[4 * P + 1] += w * iv * s.y, m.cw[4 * P + 2] += w * iv * s.z;
+        }
+        if (N >= 0) {
+            int64_t sl = fill[N]++;
+            m.snb[sl] = (int32_t)P;
+            m.sword[sl] = slot_word(i, false, 1);
+            double iv = 1.0 / m.V[N];
+            // N sees -S with weight 1-w; its neighbour P gets weight w
+            V3 k = (-w * iv) * s;
+            m.ss[3 * sl] = k.x, m.ss[3 * sl + 1] = k.y, m.ss[3 * sl + 2] = k.z;
+            double wn = (1.0 - w) * iv;
+            m.cw[4 * N] -= wn * s.x, m.cw[4 * N + 1] -= wn * s.y, m.cw[4 * N + 2] -= wn * s.z;
+        }
+    }
+    for (int64_t c = 0; c < nc; ++c) m.cw[4 * c + 3] = 1.0 / m.V[c];
+}
+
 std::string build_host_mesh(const dolinc_mesh_desc &d, HostMesh &m)
 {
     // ---------------------------------------------------------------- validation
@@ -314,48 +361,8 @@ std::string build_host_mesh(const dolinc_mesh_desc &d, HostMesh &m)
         }
     }
     if (m.g_max == 0) m.g_min = m.g_max = 1.0;
-    // ---------------------------------------------------------------- slots
-    m.off.assign(nc + 1, 0);
-    for (int64_t i = 0; i < nf; ++i) {
-        m.off[m.fo[i] + 1]++;
-        if (m.fn[i] >= 0) m.off[m.fn[i] + 1]++;
-    }
-    for (int64_t c = 0; c < nc; ++c) m.off[c + 1] += m.off[c];
-    m.n_slots = m.off[nc];
-    m.snb.resize(m.n_slots);
-    m.sword.resize(m.n_slots);
-    m.ss.assign(3 * m.n_slots, 0.0);
-    m.cw.assign(4 * nc, 0.0);
-    std::vector<int32_t> fill(m.off.begin(), m.off.end() - 1);
-    // slots of a cell follow the internal face order
-    for (int64_t i = 0; i < nf; ++i) {
-        const int64_t P = m.fo[i], N = m.fn[i];
-        const V3 s{m.fS[3 * i], m.fS[3 * i + 1], m.fS[3 * i + 2]};
-        const double w = m.fw[i];
-        {
-            int64_t sl = fill[P]++;
-            m.snb[sl] = (int32_t)(N >= 0 ? N : P);
-            m.sword[sl] = slot_word(i, N < 0, 0);
-            double iv = 1.0 / m.V[P];
-            // weight of P at the face: w (boundary: w = 1, face value = cell value)
-            V3 k = ((1.0 - w) * iv) * s;
-            m.ss[3 * sl] = k.x, m.ss[3 * sl + 1] = k.y, m.ss[3 * sl + 2] = k.z;
-            m.cw[4 * P] += w * iv * s.x, m.cw[4 * P + 1] += w * iv * s.y, m.cw[4 * P + 2] += w * iv * s.z;
-        }
-        if (N >= 0) {
-            int64_t sl = fill[N]++;
-            m.snb[sl] = (int32_t)P;
-            m.sword[sl] = slot_word(i, false, 1);
-            double iv = 1.0 / m.V[N];
-            // N sees -S with weight 1-w; its neighbour P gets weight w
-            V3 k = (-w * iv) * s;
-            m.ss[3 * sl] = k.x, m.ss[3 * sl + 1] = k.y, m.ss[3 * sl + 2] = k.z;
-            double wn = (1.0 - w) * iv;
-            m.cw[4 * N] -= wn * s.x, m.cw[4 * N + 1] -= wn * s.y, m.cw[4 * N + 2] -= wn * s.z;
-        }
-    }
+    build_slots(m);
     m.h_min = 1e300;
-    for (int64_t c = 0; c < nc; ++c) m.cw[4 * c + 3] = 1.0 / m.V[c];
     for (int64_t c = 0; c < nc; ++c) m.h_min = std::min(m.h_min, V[c] / std::max(amax[c], 1e-300));
     return "";
 }

@@ -38,4 +38,33 @@ struct HostMesh {
 // Builds the host mesh; returns an empty string on success, else the error message.
 std::string build_host_mesh(const dolinc_mesh_desc &d, HostMesh &m);
 
+// Cell -> face slot tables (off, snb, sword, ss, cw) from the internal faces and the
+// volumes: a cell's slots follow the internal face order.
+void build_slots(HostMesh &m);
+
+// One part of a partition of a mesh (Sec 2.6: a coupled boundary exchanges only the
+// adjacent cells' data and their differentials).  Local cells are the part's own
+// cells and its ghosts (cells of other parts that share a face with an own cell),
+// in the whole mesh's library order; local faces are the faces of the own cells, in
+// the whole mesh's internal face order.  So every own cell sees the same faces, in
+// the same order and orientation, with the same geometry as in the whole mesh.
+struct PartPlan {
+    int part = 0, n_parts = 0;
+    std::vector<int64_t> cells;          // library index (whole mesh) of each local cell, ascending
+    std::vector<uint8_t> owned;          // 1: an own cell, 0: a ghost
+    std::vector<int64_t> faces;          // internal face index (whole mesh) of each local face, ascending
+    std::vector<int32_t> peers;          // parts this part exchanges with, ascending
+    // per peer (offsets into the lists, n_peers + 1): own cells the peer holds as
+    // ghosts, and ghosts the peer owns; local indices, each list in ascending library
+    // order, so a sender's list to q and q's list from the sender name the same cells
+    // in the same order
+    std::vector<int64_t> send_off, send_cells, recv_off, recv_cells;
+};
+
+// Plans part `part` of whole mesh g; part_lib[c] is the part of library cell c.
+std::string plan_part(const HostMesh &g, const std::vector<int32_t> &part_lib, int n_parts, int part, PartPlan &p);
+
+// The part's local host mesh: geometry and face tables copied from g, slots rebuilt.
+void slice_host_mesh(const HostMesh &g, const PartPlan &p, HostMesh &out);
+
 }  // namespace dol

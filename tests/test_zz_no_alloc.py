@@ -23,7 +23,7 @@ def _dirty_the_array():
     accumulators, face fluxes)."""
     for m, sch in ((synth.tri_mesh(23, 19, 0.2, 7),
                     dg.Scheme(k=4, r=1, n_diff=3, flux="upwind", nv=1, adv=(1.0, 0.4, 0.0), precision="fp32")),
-                   (synth.tet_mesh(7, 0.15, 8),
+                   (synth.tet_mesh(8, 0.15, 8),
                     dg.Scheme(k=5, r=2, n_diff=2, flux="rusanov", nv=5, gamma=1.4, precision="fp64"))):
         M = dg.Mesh(m)
         u = torch.rand((sch.nv, M.n_cells), dtype=torch.float64, device="cuda") + 1.0
