@@ -409,6 +409,24 @@ enum { DOLINC_KERNEL_PACK = 0, DOLINC_KERNEL_DIFF1 = 1, DOLINC_KERNEL_DIFF2 = 2,
 dolinc_status dolinc_profile_enable(dolinc_mesh *mesh, int enable);
 dolinc_status dolinc_profile_read(dolinc_mesh *mesh, double *ms, int64_t *launches);
 
+/* Skewness correction (no counterpart in the paper's method: the paper names the low
+ * accuracy of its inversion on tetrahedral and hybrid grids as future work, Sec 4).
+ * The Eq 3 interpolation and the DOLINC reconstruction along d give a face the value
+ * of the point x*_f = x_P + (1 - w) d of the centroid line, which on a skewed mesh is
+ * not the face centroid x_f.  With the correction on:
+ *   - every differential pass applies, per cell, M_c^-1 to the new gradient index,
+ *     M_c = (1/V_c) sum_f S_{c,f} (x) (x*_f - x_c) (the identity when every x*_f = x_f,
+ *     as on geometric strips and stretched hexahedra, where the scheme is unchanged);
+ *     it is folded into the mesh's weight tables, so the passes cost the same;
+ *   - each face state adds (x_f - x*_f) . T^(1) of its upwind cell (not on faces of
+ *     the first-order fallback).
+ * Both together reproduce linear fields exactly at face centroids on meshes with
+ * planar faces.  Boundary faces count as unskewed (x*_f = x_f).  A mesh option: every
+ * scheme on the mesh uses it.  Synchronises the device (call between steps).  Errors:
+ * UNSUPPORTED on a mesh with Dirichlet/Neumann faces, MESH if some M_c is singular
+ * (the correction then stays off).  Batches take no mesh with the correction on. */
+dolinc_status dolinc_mesh_set_skew_correction(dolinc_mesh *mesh, int enable);
+
 /* ---------------------------------------------------------------- partitioned meshes
  * Halo-exchanged parts of one mesh, one part per GPU (Sec 2.6: a coupled boundary
  * exchanges only the adjacent cells' data plus their differentials).  A part holds

@@ -78,7 +78,7 @@ class _Mesh(C.Structure):
 
 class _Geom(C.Structure):
     _fields_ = [("V", C.c_void_p), ("xc", C.c_void_p), ("S", C.c_void_p), ("xf", C.c_void_p),
-                ("w", C.c_void_p), ("d", C.c_void_p)]
+                ("w", C.c_void_p), ("d", C.c_void_p), ("Minv", C.c_void_p), ("sdelta", C.c_void_p)]
 
 
 class _Scheme(C.Structure):
@@ -93,6 +93,7 @@ def _declare(L):
     L.or_differentials.argtypes = [P, P, C.c_int, C.c_int, P, P]
     L.or_differentials_bc.argtypes = [P, P, C.c_int, C.c_int, P, P, P, P]
     L.or_gauss_pass.argtypes = [P, P, C.c_int, C.c_int, P, P, P, P]
+    L.or_skew_geometry.argtypes = [P, P]
     L.or_coeff.argtypes = [C.c_int, C.c_int, C.c_double, P]
     L.or_phantoms.argtypes = [C.c_int, C.c_double, P, P, P]
     L.or_face_values.argtypes = [P, P, P, P, P, P, P, P]
@@ -195,9 +196,10 @@ class Scheme:
 
 class Oracle:
     """Geometry plus the stage operators of one mesh (dict from `synth`).
-    parallel=True uses the OpenMP build (same results, face fluxes on every thread)."""
+    parallel=True uses the OpenMP build (same results, face fluxes on every thread).
+    skew=True applies the skewness correction (or_skew_geometry) in every operator."""
 
-    def __init__(self, mesh, parallel=False):
+    def __init__(self, mesh, parallel=False, skew=False):
         self._L = lib_omp() if parallel else lib()
         self.dim = int(mesh["dim"])
         self._keep = {}
@@ -226,8 +228,18 @@ class Oracle:
         self._g = g
         if self._L.or_geometry(C.byref(m), C.byref(g)) != 0:
             raise MemoryError("oracle geometry")
+        self.Minv = self.sdelta = None
+        if skew:
+            self._skew()
         self.owner = k["face_owner"]
         self.neigh = k["face_neighbour"]
+
+    def _skew(self):
+        self.Minv = np.zeros((self.n_cells, 3, 3))
+        self.sdelta = np.zeros((self.n_faces, 3))
+        self._g.Minv, self._g.sdelta = _ptr(self.Minv), _ptr(self.sdelta)
+        if self._L.or_skew_geometry(C.byref(self._m), C.byref(self._g)) != 0:
+            raise ValueError("singular skewness matrix")
 
     @classmethod
     def from_geometry(cls, dim, owner, neigh, shift, V, xc, S, xf, w, d, parallel=False):
@@ -257,6 +269,7 @@ class Oracle:
         g = _Geom()
         g.V, g.xc, g.S, g.xf, g.w, g.d = (_ptr(a) for a in (self.V, self.xc, self.S, self.xf, self.w, self.d))
         self._g = g
+        self.Minv = self.sdelta = None
         self.owner, self.neigh = k["face_owner"], k["face_neighbour"]
         return self
 

@@ -57,6 +57,9 @@ typedef struct {
     double *xf;   /* [n_faces][3]        face centroid (owner side) */
     double *w;    /* [n_faces]           Eq 3 weight of the owner */
     double *d;    /* [n_faces][3]        Eq 2 centre distance, owner -> neighbour */
+    /* skewness correction (NULL: the plain scheme), from or_skew_geometry */
+    double *Minv; /* [n_cells][3][3]     inverse of the cell's skewness matrix M_c */
+    double *sdelta; /* [n_faces][3]      face centroid minus the reconstruction point x* */
 } or_geom;
 
 typedef struct {
@@ -215,6 +218,53 @@ int or_geometry(const or_mesh *m, or_geom *g)
     return 0;
 }
 
+/* Skewness correction (the paper names the low accuracy of its inversion on
+ * tetrahedral and hybrid grids as future work, Sec 4; this correction is this
+ * library's).  The linear interpolation of Eq 3 gives the face the value of a linear
+ * field at x*_f = x_P + (1 - w) d, the point of the centroid line that divides it like
+ * the face, and the DOLINC reconstruction along d is likewise a value at x*_f; on a
+ * skewed mesh x*_f is not the face centroid x_f.  For a linear field the Gauss sum of
+ * such face values is M_c grad(phi) with
+ *   M_c = (1/V_c) sum_f S_{c,f} (x) (x*_f - x_c)      (M_c = I when every x*_f = x_f),
+ * so the corrected pass applies M_c^-1 to the new (gradient) index of every order, and
+ * the face value gets the shift (x_f - x*_f) . T^(1) of its upwind cell.  Both are
+ * exact for linear fields on meshes with planar faces.  Boundary faces count as
+ * unskewed (x*_f = x_f).  Fills g->Minv and g->sdelta (allocated by the caller);
+ * returns -1 if some M_c is singular. */
+int or_skew_geometry(const or_mesh *m, or_geom *g)
+{
+    const int D = m->dim;
+    const long nc = m->n_cells;
+    double *M = calloc((size_t)nc * 9, sizeof(double));
+    if (!M) return -1;
+    for (long f = 0; f < m->n_faces; ++f) {
+        long P = m->owner[f], N = m->neigh[f];
+        const double *S = &g->S[3*f], *xf = &g->xf[3*f];
+        double xs[3], sh[3];
+        shift3(m, f, sh);
+        for (int k = 0; k < 3; ++k)
+            xs[k] = N >= 0 ? g->xc[3*P + k] + (1.0 - g->w[f]) * g->d[3*f + k] : xf[k];
+        for (int k = 0; k < 3; ++k) g->sdelta[3*f + k] = xf[k] - xs[k];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                M[9*P + 3*i + j] += S[i] * (xs[j] - g->xc[3*P + j]) / g->V[P];
+                if (N >= 0) M[9*N + 3*i + j] -= S[i] * (xs[j] - sh[j] - g->xc[3*N + j]) / g->V[N];
+            }
+    }
+    for (long c = 0; c < nc; ++c) {
+        double *a = &M[9*c], *b = &g->Minv[9*c];
+        if (D == 2) { a[2] = a[5] = a[6] = a[7] = 0.0; a[8] = 1.0; }
+        /* inverse by cofactors */
+        double det = a[0] * (a[4]*a[8] - a[5]*a[7]) - a[1] * (a[3]*a[8] - a[5]*a[6]) + a[2] * (a[3]*a[7] - a[4]*a[6]);
+        if (!(fabs(det) > 1e-12)) { free(M); return -1; }
+        b[0] = (a[4]*a[8] - a[5]*a[7]) / det; b[1] = (a[2]*a[7] - a[1]*a[8]) / det; b[2] = (a[1]*a[5] - a[2]*a[4]) / det;
+        b[3] = (a[5]*a[6] - a[3]*a[8]) / det; b[4] = (a[0]*a[8] - a[2]*a[6]) / det; b[5] = (a[2]*a[3] - a[0]*a[5]) / det;
+        b[6] = (a[3]*a[7] - a[4]*a[6]) / det; b[7] = (a[1]*a[6] - a[0]*a[7]) / det; b[8] = (a[0]*a[4] - a[1]*a[3]) / det;
+    }
+    free(M);
+    return 0;
+}
+
 /* offset of differential order mm in the concatenated full-tensor buffer */
 static long toff(int D, int nv, long nc, int mm)
 {
@@ -280,6 +330,19 @@ int or_gauss_pass(const or_mesh *m, const or_geom *g, int nv, int mm, const doub
                     if (Q >= 0) To[((long)v * nc + Q) * Aout + k * Ain + a] -= S[k] * tf / g->V[Q];
                 }
             }
+    }
+    if (g->Minv) {              /* skewness correction: M_c^-1 on the new index */
+        for (int v = 0; v < nv; ++v)
+            for (long c = 0; c < nc; ++c)
+                for (int a = 0; a < Ain; ++a) {
+                    double t[3] = {0.0, 0.0, 0.0}, o[3];
+                    for (int k = 0; k < D; ++k) t[k] = To[((long)v * nc + c) * Aout + k * Ain + a];
+                    for (int k = 0; k < D; ++k) {
+                        o[k] = 0.0;
+                        for (int j = 0; j < D; ++j) o[k] += g->Minv[9*c + 3*k + j] * t[j];
+                    }
+                    for (int k = 0; k < D; ++k) To[((long)v * nc + c) * Aout + k * Ain + a] = o[k];
+                }
     }
     return 0;
 }
@@ -515,6 +578,13 @@ static void face_states(const or_mesh *m, const or_geom *g, const or_scheme *s, 
         }
         UL[v] = reconstruct(s, N, gL, pP, pQ, eno, rL ? &rL[v] : NULL);
         UR[v] = reconstruct(s, N, gR, qQ, qP, eno, rR ? &rR[v] : NULL);
+        if (g->sdelta) {        /* skewness correction: from x*_f to the face centroid */
+            const double *T1 = T + toff(D, nv, nc, 1), *dl = &g->sdelta[3*f];
+            for (int k = 0; k < D; ++k) {
+                UL[v] += dl[k] * T1[((long)v * nc + P) * D + k];
+                UR[v] += dl[k] * T1[((long)v * nc + Q) * D + k];
+            }
+        }
     }
 }
 

@@ -33,7 +33,8 @@ ABI_SYMBOLS = (
     "dolinc_mlp_train_step", "dolinc_indicator_infer", "dolinc_batch_create", "dolinc_batch_destroy",
     "dolinc_batch_info", "dolinc_batch_set_spin_limit", "dolinc_batch_workspace_size", "dolinc_batch_rk_step",
     "dolinc_batch_autotune", "dolinc_partition", "dolinc_part_plan", "dolinc_mesh_create_part",
-    "dolinc_mesh_part_sizes", "dolinc_part_step_begin", "dolinc_part_step_continue", "dolinc_last_error",
+    "dolinc_mesh_part_sizes", "dolinc_part_step_begin", "dolinc_part_step_continue",
+    "dolinc_mesh_set_skew_correction", "dolinc_last_error",
 )
 KERNEL_KINDS = ("pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces")
 
@@ -106,6 +107,7 @@ def load(path=LIB_PATH):
             "dolinc_mesh_create_part": [P, P, I, I, P], "dolinc_mesh_part_sizes": [P, P],
             "dolinc_part_step_begin": [P, P, D, P, P, S, P, P],
             "dolinc_part_step_continue": [P, P, P, S, P, P],
+            "dolinc_mesh_set_skew_correction": [P, I],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -285,6 +287,11 @@ class Mesh:
         d = np.zeros((self.n_faces, 3))
         _check(load().dolinc_mesh_geometry(self.handle, _ptr(V), _ptr(xc), _ptr(S), _ptr(w), _ptr(d)))
         return dict(V=V, xc=xc, S=S, w=w, d=d)
+
+
+def dolinc_mesh_set_skew_correction(mesh, enable=True):
+    """Skewness correction of the mesh on or off (every scheme on the mesh)."""
+    _check(load().dolinc_mesh_set_skew_correction(mesh.handle, 1 if enable else 0))
 
 
 def dolinc_workspace_size(mesh, scheme):

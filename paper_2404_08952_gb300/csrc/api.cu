@@ -448,17 +448,17 @@ dolinc_status dolinc_mesh_create(const dolinc_mesh_desc *desc, dolinc_mesh **out
 
 }  // extern "C"
 
-// Copies the host tables of m->h to the device (FP64 and FP32 derived tables).
-dolinc_status upload_mesh(dolinc_mesh *m)
+// Gauss weight tables of the differential passes: per slot ((1-w_c) S / V_c, the
+// neighbour id bits), per cell (sum w_c S / V_c, 1 / V_c), FP64 and FP32.
+void weight_tables(const HostMesh &h, std::vector<double> &sk64, std::vector<float> &sk32, std::vector<double> &ck64,
+                   std::vector<float> &ck32)
 {
-    cudaGetDevice(&m->device);
-    const HostMesh &h = m->h;
-    const int64_t nc = h.n_cells, nf = h.n_faces, ns = h.n_slots;
-    std::vector<int2> slot2(ns + 2, make_int2(0, 0));   // two spare entries: bulk copies round to 16 bytes
-    std::vector<double> sk64(4 * ns), ck64(4 * nc), f64(8 * nf);
-    std::vector<float> sk32(4 * ns), ck32(4 * nc), f32(8 * nf);
+    const int64_t nc = h.n_cells, ns = h.n_slots;
+    sk64.assign(4 * ns, 0.0);
+    sk32.assign(4 * ns, 0.0f);
+    ck64.assign(4 * nc, 0.0);
+    ck32.assign(4 * nc, 0.0f);
     for (int64_t s = 0; s < ns; ++s) {
-        slot2[s] = make_int2(h.snb[s], (int)h.sword[s]);
         for (int k = 0; k < 3; ++k) {
             sk64[4 * s + k] = h.ss[3 * s + k];
             sk32[4 * s + k] = (float)h.ss[3 * s + k];
@@ -473,6 +473,19 @@ dolinc_status upload_mesh(dolinc_mesh *m)
             ck64[4 * c + k] = h.cw[4 * c + k];
             ck32[4 * c + k] = (float)h.cw[4 * c + k];
         }
+}
+
+// Copies the host tables of m->h to the device (FP64 and FP32 derived tables).
+dolinc_status upload_mesh(dolinc_mesh *m)
+{
+    cudaGetDevice(&m->device);
+    const HostMesh &h = m->h;
+    const int64_t nc = h.n_cells, nf = h.n_faces, ns = h.n_slots;
+    std::vector<int2> slot2(ns + 2, make_int2(0, 0));   // two spare entries: bulk copies round to 16 bytes
+    std::vector<double> sk64, ck64, f64(8 * nf);
+    std::vector<float> sk32, ck32, f32(8 * nf);
+    for (int64_t s = 0; s < ns; ++s) slot2[s] = make_int2(h.snb[s], (int)h.sword[s]);
+    weight_tables(h, sk64, sk32, ck64, ck32);
     std::vector<int32_t> fo(nf), fn(nf), fe(nf);
     std::vector<int8_t> ff(nf);
     for (int64_t f = 0; f < nf; ++f) {
@@ -1193,6 +1206,9 @@ dolinc_status dolinc_indicator_infer(dolinc_mesh *me, const dolinc_scheme *s, do
 // ------------------------------------------------------------------ batches
 dolinc_status dolinc_batch_create(dolinc_mesh *const *meshes, int n, dolinc_batch **out)
 {
+    for (int b = 0; meshes && b < n; ++b)
+        if (meshes[b] && !meshes[b]->h.minv.empty())
+            return fail(DOLINC_ERR_UNSUPPORTED, "batches take no mesh with the skewness correction on");
     if (!out) return fail(DOLINC_ERR_INVALID_ARG, "null output handle");
     *out = nullptr;
     if (!meshes || n <= 0) return fail(DOLINC_ERR_INVALID_ARG, "empty batch");
@@ -1823,6 +1839,66 @@ dolinc_status dolinc_part_step_continue(dolinc_mesh *m, const dolinc_scheme *s, 
     halo_copy(B(ws, L.hrecv), B(ws, part_rec_off(m, s, L, P.order)), P.recv_dev, P.plan.recv_cells.size(),
               rec_bytes(m, s, P.order), false, cs);
     return part_advance(m, s, ws, L, cs, h);
+}
+
+}  // extern "C"
+
+extern "C" {
+
+dolinc_status dolinc_mesh_set_skew_correction(dolinc_mesh *m, int enable)
+{
+    if (!m) return fail(DOLINC_ERR_INVALID_ARG, "null mesh");
+    if (enable && m->d.n_bv > 0)
+        return fail(DOLINC_ERR_UNSUPPORTED, "the skewness correction takes no Dirichlet/Neumann faces");
+    std::vector<uint8_t> ghost;
+    if (m->part) {
+        ghost.resize(m->h.n_cells);
+        for (size_t j = 0; j < ghost.size(); ++j) ghost[j] = m->part->plan.owned[j] ? 0 : 1;
+    }
+    std::string err;
+    try {
+        err = apply_skew(m->h, enable != 0, m->part ? &ghost : nullptr);
+    } catch (const std::bad_alloc &) {
+        return fail(DOLINC_ERR_OOM, "host allocation");
+    }
+    if (!err.empty()) {
+        apply_skew(m->h, false, nullptr);
+        return fail(DOLINC_ERR_MESH, err);
+    }
+    std::vector<double> sk64, ck64;
+    std::vector<float> sk32, ck32;
+    weight_tables(m->h, sk64, sk32, ck64, ck32);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    CU(cudaSetDevice(m->device));
+    CU(cudaDeviceSynchronize());
+    auto put = [&](const void *dst, const void *src, size_t bytes) {
+        return cudaMemcpy(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice);
+    };
+    CU(put(m->d.slotk64, sk64.data(), sizeof(double) * sk64.size()));
+    CU(put(m->d.slotk32, sk32.data(), sizeof(float) * sk32.size()));
+    CU(put(m->d.cellk64, ck64.data(), sizeof(double) * ck64.size()));
+    CU(put(m->d.cellk32, ck32.data(), sizeof(float) * ck32.size()));
+    if (enable) {
+        const int64_t nf = m->h.n_faces;
+        std::vector<double> d64(4 * nf, 0.0);
+        std::vector<float> d32(4 * nf, 0.0f);
+        for (int64_t f = 0; f < nf; ++f)
+            for (int k = 0; k < 3; ++k) {
+                d64[4 * f + k] = m->h.sdelta[3 * f + k];
+                d32[4 * f + k] = (float)m->h.sdelta[3 * f + k];
+            }
+        dolinc_status st;
+        if ((st = upload(m, d64, &m->d.fdelta64)) || (st = upload(m, d32, &m->d.fdelta32))) {
+            cudaSetDevice(cur);
+            return st;
+        }
+    } else {
+        m->d.fdelta64 = nullptr;
+        m->d.fdelta32 = nullptr;
+    }
+    CU(cudaSetDevice(cur));
+    return DOLINC_OK;
 }
 
 }  // extern "C"

@@ -32,6 +32,9 @@ struct DevMesh {
     const float *bval32;         //   (Neumann), set by dolinc_set_boundary_values (null until then)
     int n_bcell;                 // cells with such faces, and their faces (CSR)
     const int32_t *bcell, *bcell_off, *bcell_face;
+    // skewness correction (null: off): per internal face x_f - x*_f, padded to 4 values
+    const double *fdelta64;
+    const float *fdelta32;
 };
 
 }  // namespace dol

@@ -45,6 +45,7 @@ template <> struct Geo<double> {
     static __device__ __forceinline__ int nb_of(double w) { return (int)__double_as_longlong(w); }
     static __device__ __forceinline__ const double *bval(const DevMesh &m) { return m.bval64; }
     static __device__ __forceinline__ const double *bdelta(const DevMesh &m) { return m.bdelta64; }
+    static __device__ __forceinline__ const double *fdelta(const DevMesh &m) { return m.fdelta64; }
 };
 template <> struct Geo<float> {
     static __device__ __forceinline__ const float *slotk(const DevMesh &m) { return m.slotk32; }
@@ -53,6 +54,7 @@ template <> struct Geo<float> {
     static __device__ __forceinline__ int nb_of(float w) { return __float_as_int(w); }
     static __device__ __forceinline__ const float *bval(const DevMesh &m) { return m.bval32; }
     static __device__ __forceinline__ const float *bdelta(const DevMesh &m) { return m.bdelta32; }
+    static __device__ __forceinline__ const float *fdelta(const DevMesh &m) { return m.fdelta32; }
 };
 
 // Slot range [s0, s1) of cell c: a fixed stride when every cell has the same number of
@@ -467,9 +469,10 @@ __device__ __forceinline__ R weno5_value(R g, const R *p0, const R *p1)
 
 // Both face states (or the upwind one only for linear advection) of face record fr.
 template <int DIM, int NV, int NS, int PREC, bool UPWIND_ONLY, class Src>
-__device__ __forceinline__ void face_states(const StageArgs &a, const Src &src, const typename PrecT<PREC>::R *fr,
-                                            int P, int N, int lim, typename PrecT<PREC>::R *UL,
-                                            typename PrecT<PREC>::R *UR, bool want_left)
+__device__ __forceinline__ void face_states_dolinc(const StageArgs &a, const Src &src,
+                                                   const typename PrecT<PREC>::R *fr, int P, int N, int lim,
+                                                   typename PrecT<PREC>::R *UL, typename PrecT<PREC>::R *UR,
+                                                   bool want_left)
 {
     using R = typename PrecT<PREC>::R;
     if (lim == LIM_FIRST_ORDER) {
@@ -536,6 +539,45 @@ __device__ __forceinline__ void face_states(const StageArgs &a, const Src &src, 
     }
 }
 
+// Skewness correction of the face states (mesh.fdelta non-null): the DOLINC value is
+// that of the point x*_f of the centroid line; each orientation adds
+// (x_f - x*_f) . T^(1) of its upwind cell to reach the face centroid.
+template <int DIM, int NV, int PREC, class Src>
+__device__ __forceinline__ void skew_shift(const Src &src, int f, int P, int N, typename PrecT<PREC>::R *UL,
+                                           typename PrecT<PREC>::R *UR, bool doL, bool doR)
+{
+    using R = typename PrecT<PREC>::R;
+    using T1 = typename OrdT<PREC, 1>::T;
+    constexpr int C1 = ncoef(DIM, 1), S1 = ord_stride<DIM, NV, 1, PREC>();
+    R dl[4];
+    ld4<R>(Geo<R>::fdelta(src.mesh) + 4ll * f, dl[0], dl[1], dl[2], dl[3]);
+    auto shift = [&](int X, R *U) {
+        R r[NV * C1];
+        load_rec<T1, NV * C1, S1, R, Src::LDG>(src.template rec<1>(X), 0, r);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            R t = U[v];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) t = fma(dl[k], r[v * C1 + k], t);
+            U[v] = t;
+        }
+    };
+    if (doL) shift(P, UL);
+    if (doR) shift(N, UR);
+}
+
+// Face states of internal face f (face record fr): the DOLINC values, with the
+// skewness correction when the mesh has it on (not on first-order fallback faces).
+template <int DIM, int NV, int NS, int PREC, bool UPWIND_ONLY, class Src>
+__device__ __forceinline__ void face_states(const StageArgs &a, const Src &src, const typename PrecT<PREC>::R *fr,
+                                            int f, int P, int N, int lim, typename PrecT<PREC>::R *UL,
+                                            typename PrecT<PREC>::R *UR, bool want_left)
+{
+    face_states_dolinc<DIM, NV, NS, PREC, UPWIND_ONLY>(a, src, fr, P, N, lim, UL, UR, want_left);
+    if (Geo<typename PrecT<PREC>::R>::fdelta(src.mesh) && lim != LIM_FIRST_ORDER)
+        skew_shift<DIM, NV, PREC>(src, f, P, N, UL, UR, !UPWIND_ONLY || want_left, !UPWIND_ONLY || !want_left);
+}
+
 template <int DIM, int NV, class R>
 __device__ __forceinline__ void phys_flux(const StageArgs &a, const R *U, const R *fr, R *F)
 {
@@ -580,17 +622,17 @@ __device__ __forceinline__ void canon_flux(const StageArgs &a, const Src &src, i
             if (a.flux == 0) {
                 R an = (R)a.adv[0] * fr[4] + (R)a.adv[1] * fr[5] + (DIM == 3 ? (R)a.adv[2] * fr[6] : (R)0);
                 bool left = an >= (R)0;
-                face_states<DIM, NV, NS, PREC, true>(a, src, fr, P, N, lim, UL, UR, left);
+                face_states<DIM, NV, NS, PREC, true>(a, src, fr, f, P, N, lim, UL, UR, left);
                 F[0] = an * (left ? UL[0] : UR[0]);
             } else {
-                face_states<DIM, NV, NS, PREC, false>(a, src, fr, P, N, lim, UL, UR, true);
+                face_states<DIM, NV, NS, PREC, false>(a, src, fr, f, P, N, lim, UL, UR, true);
                 R sg = fr[4] + fr[5] + (DIM == 3 ? fr[6] : (R)0);
                 R lam = (R)0.5 * (UL[0] + UR[0]) * sg;       // Roe speed of u^2/2 (1,..,1)
                 R uu = lam >= (R)0 ? UL[0] : UR[0];
                 F[0] = (R)0.5 * uu * uu * sg;
             }
         } else {
-            face_states<DIM, NV, NS, PREC, false>(a, src, fr, P, N, lim, UL, UR, true);
+            face_states<DIM, NV, NS, PREC, false>(a, src, fr, f, P, N, lim, UL, UR, true);
             rusanov<DIM, R>((R)a.gamma, UL, UR, fr[4], fr[5], fr[6], fr[7], F);
         }
     }
@@ -1233,7 +1275,7 @@ __global__ void __launch_bounds__(128) k_faces(DevMesh mesh, StageArgs a, double
     } else {
         const int lim = face_limit(a, a.flags && (a.flags[P] || a.flags[N]));
         GlobalSrc<DIM, NV, PREC> src{a, mesh};
-        face_states<DIM, NV, NS, PREC, false>(a, src, fr, P, N, lim, UL, UR, true);
+        face_states<DIM, NV, NS, PREC, false>(a, src, fr, i, P, N, lim, UL, UR, true);
     }
     const long long nf = mesh.n_faces;
 #pragma unroll

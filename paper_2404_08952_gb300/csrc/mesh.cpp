@@ -114,11 +114,20 @@ void build_slots(HostMesh &m)
     m.cw.assign(4 * nc, 0.0);
     std::vector<int32_t> fill(m.off.begin(), m.off.end() - 1);
     // slots of a cell follow the internal face order
+    const bool skew = !m.minv.empty();
+    // M_c^-1 S (skewness correction) or S
+    auto corr = [&](int64_t c, V3 s) {
+        if (!skew) return s;
+        const double *a = &m.minv[9 * c];
+        return V3{a[0] * s.x + a[1] * s.y + a[2] * s.z, a[3] * s.x + a[4] * s.y + a[5] * s.z,
+                  a[6] * s.x + a[7] * s.y + a[8] * s.z};
+    };
     for (int64_t i = 0; i < nf; ++i) {
         const int64_t P = m.fo[i], N = m.fn[i];
-        const V3 s{m.fS[3 * i], m.fS[3 * i + 1], m.fS[3 * i + 2]};
+        const V3 s0{m.fS[3 * i], m.fS[3 * i + 1], m.fS[3 * i + 2]};
         const double w = m.fw[i];
         {
+            const V3 s = corr(P, s0);
             int64_t sl = fill[P]++;
             m.snb[sl] = (int32_t)(N >= 0 ? N : P);
             m.sword[sl] = slot_word(i, N < 0, 0);
@@ -129,6 +138,7 @@ void build_slots(HostMesh &m)
             m.cw[4 * P] += w * iv * s.x, m.cw[4 * P + 1] += w * iv * s.y, m.cw[4 * P + 2] += w * iv * s.z;
         }
         if (N >= 0) {
+            const V3 s = corr(N, s0);
             int64_t sl = fill[N]++;
             m.snb[sl] = (int32_t)P;
             m.sword[sl] = slot_word(i, false, 1);
@@ -141,6 +151,61 @@ void build_slots(HostMesh &m)
         }
     }
     for (int64_t c = 0; c < nc; ++c) m.cw[4 * c + 3] = 1.0 / m.V[c];
+}
+
+std::string apply_skew(HostMesh &m, bool on, const std::vector<uint8_t> *keep_identity)
+{
+    const int64_t nc = m.n_cells, nf = m.n_faces;
+    if (!on) {
+        m.minv.clear();
+        m.sdelta.clear();
+        build_slots(m);
+        return "";
+    }
+    // M_c = (1/V_c) sum_f S_{c,f} (x) (x*_f - x_c): from the owner x*_f - x_P = (1-w) d,
+    // from the neighbour (its own frame) x*_f - x_N = -w d; boundary faces x*_f = x_f
+    std::vector<double> M(9 * nc, 0.0), sd(3 * nf, 0.0);
+    for (int64_t i = 0; i < nf; ++i) {
+        const int64_t P = m.fo[i], N = m.fn[i];
+        const V3 s{m.fS[3 * i], m.fS[3 * i + 1], m.fS[3 * i + 2]};
+        const V3 xf{m.fxf[3 * i], m.fxf[3 * i + 1], m.fxf[3 * i + 2]};
+        const V3 xP{m.xc[3 * P], m.xc[3 * P + 1], m.xc[3 * P + 2]};
+        const V3 dd{m.fd[3 * i], m.fd[3 * i + 1], m.fd[3 * i + 2]};
+        const double w = m.fw[i];
+        const V3 rP = N >= 0 ? (1.0 - w) * dd : xf - xP;
+        const double sv[3] = {s.x, s.y, s.z}, rp[3] = {rP.x, rP.y, rP.z};
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) M[9 * P + 3 * a + b] += sv[a] * rp[b] / m.V[P];
+        if (N >= 0) {
+            const double rn[3] = {-w * dd.x, -w * dd.y, -w * dd.z};
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) M[9 * N + 3 * a + b] -= sv[a] * rn[b] / m.V[N];
+            const V3 del = xf - (xP + rP);
+            sd[3 * i] = del.x, sd[3 * i + 1] = del.y, sd[3 * i + 2] = del.z;
+        }
+    }
+    std::vector<double> inv(9 * nc);
+    for (int64_t c = 0; c < nc; ++c) {
+        double *a = &M[9 * c], *b = &inv[9 * c];
+        if (m.dim == 2) a[2] = a[5] = a[6] = a[7] = 0.0, a[8] = 1.0;
+        const double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+                           a[2] * (a[3] * a[7] - a[4] * a[6]);
+        if ((keep_identity && (*keep_identity)[c]) || !(std::fabs(det) > 1e-12)) {
+            if (!(keep_identity && (*keep_identity)[c]))
+                return fmt("cell %lld: singular skewness matrix", c);
+            for (int k = 0; k < 9; ++k) b[k] = (k % 4 == 0) ? 1.0 : 0.0;
+            continue;
+        }
+        b[0] = (a[4] * a[8] - a[5] * a[7]) / det, b[1] = (a[2] * a[7] - a[1] * a[8]) / det;
+        b[2] = (a[1] * a[5] - a[2] * a[4]) / det, b[3] = (a[5] * a[6] - a[3] * a[8]) / det;
+        b[4] = (a[0] * a[8] - a[2] * a[6]) / det, b[5] = (a[2] * a[3] - a[0] * a[5]) / det;
+        b[6] = (a[3] * a[7] - a[4] * a[6]) / det, b[7] = (a[1] * a[6] - a[0] * a[7]) / det;
+        b[8] = (a[0] * a[4] - a[1] * a[3]) / det;
+    }
+    m.minv.swap(inv);
+    m.sdelta.swap(sd);
+    build_slots(m);
+    return "";
 }
 
 std::string build_host_mesh(const dolinc_mesh_desc &d, HostMesh &m)

@@ -33,14 +33,24 @@ struct HostMesh {
     std::vector<double> ss;             // [n_slots][3] (1-w_c) S_{c,f} / V_c
     std::vector<double> cw;             // [n_cells][4] (sum_f w_c S_{c,f} / V_c, 1/V_c)
     double g_min = 0, g_max = 0, h_min = 0, volume = 0;
+    // skewness correction (empty: off): per cell M_c^-1 [n_cells][9], which the slot
+    // and cell weights absorb; per internal face x_f - x*_f [n_faces][3]
+    std::vector<double> minv, sdelta;
 };
 
 // Builds the host mesh; returns an empty string on success, else the error message.
 std::string build_host_mesh(const dolinc_mesh_desc &d, HostMesh &m);
 
 // Cell -> face slot tables (off, snb, sword, ss, cw) from the internal faces and the
-// volumes: a cell's slots follow the internal face order.
+// volumes: a cell's slots follow the internal face order.  With the skewness
+// correction on, each cell's area vectors enter its weights as M_c^-1 S.
 void build_slots(HostMesh &m);
+
+// Turns the skewness correction on or off (minv, sdelta, then the slot tables).
+// keep_identity (may be null): cells whose M_c^-1 is taken as the identity (ghost
+// cells of a part, whose faces are not all present).  Returns an error message if
+// some other cell's M_c is singular.
+std::string apply_skew(HostMesh &m, bool on, const std::vector<uint8_t> *keep_identity);
 
 // One part of a partition of a mesh (Sec 2.6: a coupled boundary exchanges only the
 // adjacent cells' data and their differentials).  Local cells are the part's own
