@@ -346,6 +346,8 @@ def run_dolinc(args):
                 v["l2_rel_vs_fp64_after_steps"] = _l2_rel(a, b)
             variants["%s_order%d%s" % (prec, order, tag)] = v
             del vr
+    stability = _stability(args, w, M, dg, torch) if (not args.no_variants and args.workload == "euler3d_tet64") \
+        else None
     main = results[args.precision]
     cells = M.n_cells
     total_cells = reduce_sum(cells, dist)
@@ -418,6 +420,8 @@ def run_dolinc(args):
     }
     if variants:
         line["variants"] = variants
+    if stability:
+        line["stability"] = stability
     line["finite_after_steps"] = main["finite"]
     if "fp64" in results and args.precision != "fp64":
         f = results["fp64"]
@@ -481,6 +485,66 @@ def run_dolinc(args):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _stability(args, w, M, dg, torch):
+    """The workload's scheme run to t = args.stab_time on the full mesh, FP32 bulk:
+    unlimited (the timed configuration), with the skewness correction, and with the
+    troubled-cell criterion switching flagged faces to the first-order fallback
+    (criterion evaluated every step, inside the timing).  Each: whether the state
+    stayed finite with positive density, the first time it did not, and the
+    throughput of the whole run."""
+    import numpy as np
+    m, u0, dt = w["mesh"], w["u0"], w["dt"]
+    steps = int(np.ceil(args.stab_time / dt - 1e-9))
+    out = {}
+    Ms = None
+    for tag, skew, limiter in (("plain", False, "none"), ("skew_corrected", True, "none"),
+                               ("criterion_first_order", False, "first_order_flagged")):
+        if skew:
+            Ms = dg.Mesh(m, renumber="morton")
+            dg.dolinc_mesh_set_skew_correction(Ms, True)
+        X = Ms if skew else M
+        sch = dg.Scheme(precision=args.precision, limiter=limiter, **w["scheme"])
+        flags = None
+        if limiter != "none":
+            flags = torch.zeros(X.n_cells, dtype=torch.uint8, device="cuda")
+            dg.dolinc_set_flags(X, flags)
+        ws = dg.workspace(X, sch)
+        u = torch.from_numpy(X.to_lib(u0)).cuda()
+        dg.dolinc_autotune(X, sch, u, ws)
+        t_bad, done, ms = None, 0, 0.0
+        chunk = 50
+        while done < steps and t_bad is None:
+            n = min(chunk, steps - done)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(n):
+                if flags is not None:
+                    dg.dolinc_criterion(X, sch, u, flags, ws)
+                dg.dolinc_rk_step(X, sch, dt, u, ws)
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            done += n
+            ok = True
+            try:
+                dg.dolinc_sync_status(X, ws)
+            except dg.DolincError:
+                ok = False
+            rho_min = float(u[0].min().item())
+            if not ok or not np.isfinite(rho_min) or rho_min <= 0:
+                t_bad = done * dt
+        r = {"t_end": steps * dt, "steps_run": done, "finite_to_t_end": t_bad is None,
+             "first_failure_by_t": t_bad, "rho_min_end": float(u[0].min().item()) if t_bad is None else None,
+             "value": X.n_cells * 3 * done / (ms / 1e3), "ms_per_step": ms / done}
+        if flags is not None:
+            r["flagged_fraction_end"] = float(flags.float().mean().item())
+            dg.dolinc_set_flags(X, None)
+        out[tag] = r
+        del ws, u
+    del Ms
+    return out
 
 
 def _sync_cpu(t):
@@ -707,13 +771,15 @@ def run_hexprism(args):
             del ws, u
     del M
     conv = {}
-    for prec in ("fp32", "fp64"):
+    for prec, skew in (("fp32", False), ("fp64", False), ("fp32", True), ("fp64", True)):
         for order in orders:
             k, r = synth.STENCIL_OF_ORDER[order]
             row = []
             for n in sizes:
                 w, exact, _ = host[n]
                 Mn = dg.Mesh(w["mesh"], renumber="morton")
+                if skew:
+                    dg.dolinc_mesh_set_skew_correction(Mn, True)
                 sch = dg.Scheme(precision=prec, **dict(w["scheme"], k=k, r=r, n_diff=order - 1))
                 ws = dg.workspace(Mn, sch)
                 u = torch.from_numpy(Mn.to_lib(w["u0"])).cuda()
@@ -737,7 +803,7 @@ def run_hexprism(args):
             for a_, b_ in zip(row, row[1:]):
                 if a_["l2"] and b_["l2"]:
                     b_["order_vs_previous"] = float(np.log(a_["l2"] / b_["l2"]) / np.log(b_["lattice"] / a_["lattice"]))
-            conv["%s_order%d" % (prec, order)] = row
+            conv["%s_order%d%s" % (prec, order, "_skew" if skew else "")] = row
     main = thr["fp32_order5"]
     line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
@@ -924,6 +990,7 @@ def main():
     ap.add_argument("--hp-sizes", default="35,70,140", help="adv3d_hexprism convergence lattices")
     ap.add_argument("--hp-time", type=float, default=0.05, help="adv3d_hexprism convergence end time")
     ap.add_argument("--hp-quad", type=int, default=3, help="adv3d_hexprism quadrature points per direction")
+    ap.add_argument("--stab-time", type=float, default=0.4, help="euler3d_tet64 stability runs: end time")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
