@@ -146,10 +146,16 @@ def test_adv3d_hexprism_full_order5_properties(hexprism140):
     assert np.abs(r32 - r64).max() < 5e-3 * np.abs(r64).max()
 
 
-def test_burgers_batch_full_size():
+@pytest.fixture(scope="module")
+def burgers512():
     wl = synth.workload("burgers_batch", q=1)
+    meshes = [dg.Mesh(x["mesh"]) for x in wl["meshes"]]
+    return wl, meshes
+
+
+def test_burgers_batch_full_size(burgers512):
+    wl, meshes = burgers512
     ms_ = wl["meshes"]
-    meshes = [dg.Mesh(x["mesh"]) for x in ms_]
     bt = dg.Batch(meshes)
     s = dg.Scheme(precision="fp64", **wl["scheme"])
     ws = bt.workspace(s)
@@ -169,3 +175,40 @@ def test_burgers_batch_full_size():
         if i in pick:
             want = oracle.Oracle(x["mesh"]).rk3_step(x["u0"], oracle.Scheme(**wl["scheme"]), x["dt"])
             assert rel(g, want) < 1e-12, i
+
+
+def test_burgers_batch_full_size_fp32(burgers512):
+    """The ensemble's stated precision (FP32 bulk, FP64 update): the 512-mesh batch in
+    one launch per stage from a CUDA graph against the per-mesh FP32 step of every mesh
+    (the same arithmetic in another kernel: rounding-level agreement), and four meshes
+    against the FP64 oracle under the per-cell 1e-5 rule."""
+    wl, meshes = burgers512
+    ms_ = wl["meshes"]
+    bt = dg.Batch(meshes)
+    s = dg.Scheme(precision="fp32", **wl["scheme"])
+    ws = bt.workspace(s)
+    u = torch.from_numpy(bt.to_lib([x["u0"] for x in ms_])).cuda()
+    dt = torch.tensor([x["dt"] for x in ms_], dtype=torch.float64, device="cuda")
+    bt.autotune(s, dt, u, ws)
+    bt.rk_step(s, dt, u, ws, use_graph=True)
+    dg.dolinc_sync_status(meshes[0], ws)
+    got = bt.from_lib(u.cpu().numpy())
+    sizes = np.array([M.n_cells for M in meshes])
+    pick = {int(np.argmin(sizes)), int(np.argmax(sizes)), 7, 300}
+    fx = {"flux": wl["scheme"]["flux"]}
+    worst = 0.0
+    for i, (M, x, g) in enumerate(zip(meshes, ms_, got)):
+        w1 = dg.workspace(M, s)
+        ref = torch.from_numpy(M.to_lib(x["u0"])).cuda()
+        dg.dolinc_rk_step(M, s, x["dt"], ref, w1)
+        r = M.from_lib(ref.cpu().numpy())
+        # both FP32 increments round the same FP64 arithmetic: a few FP32 ulps of the step
+        inc = r - x["u0"]
+        assert np.abs(g - r).max() <= 1e-5 * np.abs(inc).max() + 1e-12, i
+        if i in pick:
+            O = oracle.Oracle(x["mesh"])
+            want = O.rk3_step(x["u0"], oracle.Scheme(**wl["scheme"]), x["dt"])
+            ok, ratio = increment_ok(O, g - x["u0"], want - x["u0"], x["u0"], x["dt"], "fp32", 1, fx, 2)
+            worst = max(worst, ratio)
+            assert ok, (i, ratio)
+    assert worst > 0

@@ -135,6 +135,10 @@ def test_launch_shapes_bit_identical_and_step_matches_oracle(prec):
     sch = dg.Scheme(k=3, r=1, n_diff=2, nv=5, precision=prec, **euler_ok(5))
     ws = dg.workspace(M, sch)
     out = {}
+    # the shapes whose sums run in the same order (one lane per cell: gather,
+    # pipelined gather; the stage cell-centric, face-centric pair, pipelined) are
+    # bit-identical; 4 lanes per cell sum in another order and are checked against
+    # the oracle only
     for shape in ((1, 128, 1, 128), (1, 64, -2, 128), (-1, 128, -1, 128), (4, 128, 4, 64)):
         dg.dolinc_set_tuning(M, sch, *shape)
         x = to_dev(M, u)
@@ -142,15 +146,16 @@ def test_launch_shapes_bit_identical_and_step_matches_oracle(prec):
         dg.dolinc_sync_status(M, ws)
         out[shape] = x.cpu().numpy()
     vals = list(out.values())
-    for v in vals[1:]:
+    for v in vals[1:3]:
         assert np.array_equal(v, vals[0])
-    got = M.from_lib(vals[0])
     want = O.rk3_step(u, oracle.Scheme(k=3, r=1, n_diff=2, nv=5, **euler_ok(5)), 1e-3)
-    if prec == "fp64":
-        assert rel(got - u, want - u) < 1e-11
-    else:
-        ok, worst = increment_ok(O, got - u, want - u, u, 1e-3, "fp32", 1, euler_ok(5) | {"flux": "rusanov"}, 3)
-        assert ok, worst
+    for v in (vals[0], vals[3]):
+        got = M.from_lib(v)
+        if prec == "fp64":
+            assert rel(got - u, want - u) < 1e-11
+        else:
+            ok, worst = increment_ok(O, got - u, want - u, u, 1e-3, "fp32", 1, euler_ok(5), 3)
+            assert ok, worst
 
 
 def test_turning_the_correction_off_restores_the_plain_scheme():
