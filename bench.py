@@ -444,6 +444,9 @@ def run_dolinc(args):
         line["variants"] = variants
     if stability:
         line["stability"] = stability
+    if rank == 0 and not args.no_variants and args.workload == "euler3d_tet64" and world == 1:
+        line["indicator"] = _indicator_summary(args)
+        line["batch"] = _batch_summary(args)
     line["finite_after_steps"] = main["finite"]
     if "fp64" in results and args.precision != "fp64":
         f = results["fp64"]
@@ -576,7 +579,28 @@ def _sync_cpu(t):
     return t.cpu().numpy()
 
 
-def run_indicator(args):
+def _indicator_summary(args):
+    """The learned indicator inside the default run, small but in the full
+    configuration: a network trained on a few criterion-labelled runs of a reduced mesh,
+    then the full 724^2 Riemann mesh advanced with the network switching flagged faces
+    to the first-order fallback (FP32) against the criterion doing it (FP32 and the
+    plain FP64 GPU method)."""
+    a = argparse.Namespace(**vars(args))
+    a.ind_runs, a.ind_eval_runs, a.ind_train_size, a.ind_train_steps, a.ind_epochs = 4, 1, 96, 40, 10
+    a.size, a.steps = None, 20
+    return run_indicator(a, emit=False, forms=("network_fp32", "criterion_fp32", "criterion_fp64"))
+
+
+def _batch_summary(args):
+    """The batched ensemble inside the default run: 64 meshes of the 512-mesh
+    distribution, one persistent launch per stage from a CUDA graph, FP32 bulk / FP64
+    update, against each mesh stepped by its own FP64 launches."""
+    a = argparse.Namespace(**vars(args))
+    a.batch_meshes, a.steps, a.warmup = 64, 10, 3
+    return run_batch(a, emit=False)
+
+
+def run_indicator(args, emit=True, forms=None):
     """Learned troubled-cell indicator on the four-quadrant Riemann workload.
 
     Trains the network on criterion labels of seeded runs (smaller mesh), measures its
@@ -625,6 +649,8 @@ def run_indicator(args):
                                     ("network_eno3_fp32", "network", "fp32", eno),
                                     ("criterion_eno3_fp64", "criterion", "fp64", eno),
                                     ("none_fp32", "none", "fp32", fo), ("eno3_all_fp32", "all", "fp32", fo)):
+        if forms is not None and name not in forms:
+            continue
         st, finite, sec, flagged = ind.run_with(w, switch, steps, precision=prec, net=net, flagged_limiter=lim)
         res[name] = dict(state=st, finite=finite, sec_per_step=sec, flagged=flagged,
                          value=cells * 3 / sec)
@@ -647,10 +673,13 @@ def run_indicator(args):
             "indicator": {"train_seconds": t_train, "epochs": args.ind_epochs, "final_loss": hist[-1],
                           "first_loss": hist[0], "pos_weight": pw, "heldout_vs_criterion": conf},
             "forms": out, "seconds_total": time.perf_counter() - t_all}
+    if not emit:
+        return {"config": line["config"], "indicator": {k: v for k, v in line["indicator"].items()},
+                "forms": out, "seconds_total": line["seconds_total"]}
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
+def run_batch(args, emit=True):
     """Batched ensemble of 2D Burgers meshes: one persistent cooperative launch per
     stage replayed from a CUDA graph (FP32 bulk, FP64 update), against the plain FP64
     GPU method (each mesh stepped by its own launches)."""
@@ -718,6 +747,8 @@ def run_batch(args):
                        "min_cells": int(min(M.n_cells for M in meshes)), "max_cells": int(max(M.n_cells for M in meshes)),
                        "stencil_k_r": [3, 1], "n_diff": 2, "flux": "burgers"},
             "forms": out, "seconds_total": time.perf_counter() - t_all}
+    if not emit:
+        return {"config": line["config"], "forms": out, "seconds_total": line["seconds_total"]}
     print(json.dumps(line), flush=True)
 
 

@@ -10,14 +10,19 @@
 // non-pipelined kernels, so results are bit-identical for the same lanes per cell.
 //
 // Every mbarrier wait is bounded; a wait that gives up sets status bit 1 (reported
-// as DOLINC_ERR_DEVICE_TIMEOUT), waits (bounded again) for the CTA's other copy in
-// flight and leaves the kernel without writing the tile.
+// as DOLINC_ERR_DEVICE_TIMEOUT).  Then, before the CTA leaves (without writing the
+// tile), every thread waits again for each bulk copy the CTA has in flight -- the
+// current tile's and the next tile's, both issued by thread 0 before its wait -- with
+// a longer bound (kPipeDrainLimit), so that no copy lands in the shared memory of a
+// CTA that has exited.  Only a GPU that stopped completing copies altogether gets
+// past both bounds; the kernel then returns rather than hang.
 #pragma once
 #include "kernels.cuh"
 
 namespace dol {
 
 constexpr unsigned kPipeWaitLimit = 1u << 22;   // try_wait polls before a wait gives up
+constexpr unsigned kPipeDrainLimit = 1u << 25;  // polls per in-flight copy on the give-up path
 
 DOL_HD constexpr unsigned al128(unsigned b) { return (b + 127u) & ~127u; }
 
@@ -83,8 +88,8 @@ __global__ void __launch_bounds__(NT) k_diff_pipe(DevMesh mesh, const void *__re
         const bool ok = mbar_wait(bar + b, (unsigned)(j >> 1) & 1u, kPipeWaitLimit);
         if (!__syncthreads_and(ok)) {
             if (threadIdx.x == 0) atomicOr(status, 2u);
-            if (!ok) mbar_wait(bar + b, (unsigned)(j >> 1) & 1u, kPipeWaitLimit);
-            if (next < n_tiles) mbar_wait(bar + (b ^ 1), (unsigned)((j + 1) >> 1) & 1u, kPipeWaitLimit);
+            if (!ok) mbar_wait(bar + b, (unsigned)(j >> 1) & 1u, kPipeDrainLimit);
+            if (next < n_tiles) mbar_wait(bar + (b ^ 1), (unsigned)((j + 1) >> 1) & 1u, kPipeDrainLimit);
             return;
         }
         const unsigned char *buf = sm + 128 + b * bb;
@@ -237,8 +242,8 @@ __global__ void __launch_bounds__(NT) k_stage_pipe(DevMesh mesh, StageArgs a, in
         const bool ok = mbar_wait(bar + b, (unsigned)(j >> 1) & 1u, kPipeWaitLimit);
         if (!__syncthreads_and(ok)) {
             if (threadIdx.x == 0) atomicOr(a.status, 2u);
-            if (!ok) mbar_wait(bar + b, (unsigned)(j >> 1) & 1u, kPipeWaitLimit);
-            if (next < n_tiles) mbar_wait(bar + (b ^ 1), (unsigned)((j + 1) >> 1) & 1u, kPipeWaitLimit);
+            if (!ok) mbar_wait(bar + b, (unsigned)(j >> 1) & 1u, kPipeDrainLimit);
+            if (next < n_tiles) mbar_wait(bar + (b ^ 1), (unsigned)((j + 1) >> 1) & 1u, kPipeDrainLimit);
             return;
         }
         const unsigned char *buf = sm + 128 + b * bb;

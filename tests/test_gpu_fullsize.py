@@ -179,9 +179,11 @@ def test_burgers_batch_full_size(burgers512):
 
 def test_burgers_batch_full_size_fp32(burgers512):
     """The ensemble's stated precision (FP32 bulk, FP64 update): the 512-mesh batch in
-    one launch per stage from a CUDA graph against the per-mesh FP32 step of every mesh
-    (the same arithmetic in another kernel: rounding-level agreement), and four meshes
-    against the FP64 oracle under the per-cell 1e-5 rule."""
+    one launch per stage from a CUDA graph against the per-mesh FP32 step of every mesh,
+    and four meshes against the FP64 oracle under the per-cell 1e-5 rule.  The batch
+    kernel forms each stage value by the FP64 Shu-Osher combination of an FP32
+    residual, the per-mesh step by the increment form; both round every stage input
+    to FP32, at different points, so they agree to a few FP32 ulps of the state."""
     wl, meshes = burgers512
     ms_ = wl["meshes"]
     bt = dg.Batch(meshes)
@@ -202,9 +204,7 @@ def test_burgers_batch_full_size_fp32(burgers512):
         ref = torch.from_numpy(M.to_lib(x["u0"])).cuda()
         dg.dolinc_rk_step(M, s, x["dt"], ref, w1)
         r = M.from_lib(ref.cpu().numpy())
-        # both FP32 increments round the same FP64 arithmetic: a few FP32 ulps of the step
-        inc = r - x["u0"]
-        assert np.abs(g - r).max() <= 1e-5 * np.abs(inc).max() + 1e-12, i
+        assert np.abs(g - r).max() <= 4 * 2.0 ** -23 * np.abs(r).max(), i
         if i in pick:
             O = oracle.Oracle(x["mesh"])
             want = O.rk3_step(x["u0"], oracle.Scheme(**wl["scheme"]), x["dt"])
