@@ -157,6 +157,8 @@ def alg_bytes(kind, M, sch, basis="stored"):
     below FP64) and, in the stage, the orders N the stencil reads (stage_orders).
     basis "table": the scope table's own evaluation, geometry at FP64 widths and the
     stage reading every computed order N = N_d.  pack (not in B_alg): nv (8 + s_0)."""
+    if kind == "diff_pair":         # one stage's order-2 pass with the next stage's order-1 pass
+        return alg_bytes("diff2", M, sch, basis) + alg_bytes("diff1", M, sch, basis)
     nc, nv, dim = M.n_cells, sch.nv, M.dim
     sg, sb = _widths(sch)
     if basis == "table":
@@ -183,6 +185,9 @@ def kernel_bytes(kind, M, sch):
     sg, sb = _widths(sch)
     if kind == "pack":
         return nc * nv * (8 + sb(0))
+    if kind == "diff_pair":         # the two passes' data, their geometry read once
+        geo = nc * (4 * sg + 4) + ns * 4 * sg
+        return kernel_bytes("diff2", M, sch) + kernel_bytes("diff1", M, sch) - geo
     if kind.startswith("diff"):
         m = int(kind[4:])
         data = nc * nv * (_ncoef(dim, m - 1) * sb(m - 1) + _ncoef(dim, m) * sb(m))
@@ -198,7 +203,7 @@ def kernel_bytes(kind, M, sch):
     return data + state + geo
 
 
-KINDS = ["pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces"]
+KINDS = ["pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces", "diff_pair"]
 
 
 def _stage_roofline(M, sch, ms_stage, peak):
@@ -385,7 +390,15 @@ def run_dolinc(args):
     sch_m = main["sch"]
     need = max(sch_m.r, sch_m.k - sch_m.r - 2, 1)
     per = lambda kind: kms[KINDS.index(kind)] / max(kn[KINDS.index(kind)], 1)
-    if sch_m.n_diff > need:
+    paired = (main["tune"] or {}).get("diff_lanes") == 2 and kn[KINDS.index("diff_pair")] > 0
+    if paired:
+        # paired schedule: no concurrent passes; the unit is the larger of the stage and
+        # the paired differential launch
+        top = max(("stage", "diff_pair"), key=lambda kd: kms[KINDS.index(kd)])
+        unit = [top]
+        per_launch_ms = per(top)
+        unit_name = top
+    elif sch_m.n_diff > need:
         unit = ["stage"] + ["diff%d" % mm for mm in range(need + 1, sch_m.n_diff + 1)]
         pack_share = kms[KINDS.index("pack")] / (3.0 * args.steps)
         per_launch_ms = ms_step / 3.0 - pack_share - sum(per("diff%d" % mm) for mm in range(1, need + 1))

@@ -284,7 +284,11 @@ dolinc_status dolinc_autotune(dolinc_mesh *mesh, const dolinc_scheme *scheme, co
                               size_t ws_bytes, const char *cache_path, dolinc_stream stream, dolinc_tuning *out);
 /* Sets the launch shape used for this mesh and scheme (lanes per cell 1, 4 or 8 with a
  * block of 32..256 threads, a multiple of 32; or lanes 0, tiled, with a block of 64,
- * 128 or 256; differential passes also lanes -1 or -4, pipelined, with 128 or 256;
+ * 128 or 256; differential passes also lanes -1 or -4, pipelined, with 128 or 256, or
+ * lanes 2: one thread per cell with the paired schedule, where a scheme computing one
+ * order above what its stencil reads (n_diff = 2, stencil order 1) runs that order of
+ * stage k in one launch with order 1 of stage k+1, both reading the Gauss weights once,
+ * with the same results as lanes 1;
  * the stage also lanes -1, pipelined, with tiles of 64 or 128 cells, or -2, the
  * face-centric pair, with 64, 128 or 256), e.g. a shape read back from an autotuning
  * cache. */
@@ -400,12 +404,15 @@ dolinc_status dolinc_sync_status(dolinc_mesh *mesh, void *ws_dev, dolinc_stream 
  * events around each of its kernel launches, on the call's stream.  Kernel kinds:
  * DOLINC_KERNEL_PACK (FP64 field -> order-0 record), DOLINC_KERNEL_DIFF1..DIFF4 (the
  * differential pass producing order m), DOLINC_KERNEL_STAGE (reconstruction + flux +
- * residual + update), DOLINC_KERNEL_FACES (dolinc_reconstruct_faces).
+ * residual + update), DOLINC_KERNEL_FACES (dolinc_reconstruct_faces),
+ * DOLINC_KERNEL_DIFF_PAIR (one stage's order-2 pass fused with the next stage's
+ * order-1 pass, under the paired schedule of dolinc_set_tuning's diff_lanes = 2).
  * dolinc_profile_enable resets the counters.  dolinc_profile_read waits for the
  * recorded events and fills ms[DOLINC_KERNEL_COUNT] (summed device time) and
  * launches[DOLINC_KERNEL_COUNT]; either pointer may be NULL. */
 enum { DOLINC_KERNEL_PACK = 0, DOLINC_KERNEL_DIFF1 = 1, DOLINC_KERNEL_DIFF2 = 2, DOLINC_KERNEL_DIFF3 = 3,
-       DOLINC_KERNEL_DIFF4 = 4, DOLINC_KERNEL_STAGE = 5, DOLINC_KERNEL_FACES = 6, DOLINC_KERNEL_COUNT = 7 };
+       DOLINC_KERNEL_DIFF4 = 4, DOLINC_KERNEL_STAGE = 5, DOLINC_KERNEL_FACES = 6, DOLINC_KERNEL_DIFF_PAIR = 7,
+       DOLINC_KERNEL_COUNT = 8 };
 dolinc_status dolinc_profile_enable(dolinc_mesh *mesh, int enable);
 dolinc_status dolinc_profile_read(dolinc_mesh *mesh, double *ms, int64_t *launches);
 

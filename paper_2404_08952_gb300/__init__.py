@@ -36,7 +36,7 @@ ABI_SYMBOLS = (
     "dolinc_mesh_part_sizes", "dolinc_part_step_begin", "dolinc_part_step_continue",
     "dolinc_mesh_set_skew_correction", "dolinc_last_error",
 )
-KERNEL_KINDS = ("pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces")
+KERNEL_KINDS = ("pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces", "diff_pair")
 
 
 class DolincError(RuntimeError):

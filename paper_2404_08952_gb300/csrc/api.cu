@@ -231,8 +231,11 @@ int ncoef_h(int dim, int m) { return dim == 2 ? m + 1 : (m + 1) * (m + 2) / 2; }
 int stride_h(int dim, int nv, int m, int prec) { return rec_stride(nv * ncoef_h(dim, m), elem_bytes(prec, m)); }
 
 struct WsLayout {
-    size_t status, o0[3], ord[MAXN + 1], ustage, dacc, flux, hsend, hrecv, total;
+    size_t status, o0[3], ord[MAXN + 1], ord1b, ustage, dacc, flux, hsend, hrecv, total;
 };
+
+// The paired schedule applies: one order above the stencil's (n_diff = 2, order 1 read).
+bool pair_scheme(const dolinc_scheme *s) { return s->n_diff == 2 && needed_order(*s) == 1; }
 
 WsLayout ws_layout(const dolinc_mesh *m, const dolinc_scheme *s)
 {
@@ -253,6 +256,8 @@ WsLayout ws_layout(const dolinc_mesh *m, const dolinc_scheme *s)
         L.ord[mm] = o;
         if (mm <= s->n_diff) o += al256(nc * stride_h(m->h.dim, s->nv, mm, s->precision) * elem_bytes(s->precision, mm));
     }
+    L.ord1b = o;                                // second order-1 buffer of the paired schedule
+    if (pair_scheme(s)) o += al256(nc * stride_h(m->h.dim, s->nv, 1, s->precision) * elem_bytes(s->precision, 1));
     L.ustage = o;
     o += al256(nc * s->nv * sizeof(double));
     L.dacc = o;                                 // increment accumulator (bulk precision below FP64)
@@ -773,12 +778,39 @@ dolinc_status rk_step_impl(dolinc_mesh *m, const dolinc_scheme *s, double dt, co
         if (pending) cudaStreamWaitEvent(cs, m->ev_join, 0);
         pending = false;
     };
+    // Paired schedule (diff lanes 2): order 1 of stage k goes to buffer k % 2; order 2 of
+    // stage k is computed with order 1 of stage k+1 in one launch, the last one after
+    // the last stage.  Returns the offset of the stage's order-1 buffer.
+    const bool paired = tn.diff_lpc == 2 && pair_scheme(s);
+    auto paired_diffs = [&](int sg, size_t o0off) -> size_t {
+        const size_t o1 = (sg & 1) ? L.ord1b : L.ord[1], o1prev = (sg & 1) ? L.ord[1] : L.ord1b;
+        unsigned *stw = reinterpret_cast<unsigned *>(B(ws, L.status));
+        bool done = false;
+        if (sg > 0)
+            timed(m, DOLINC_KERNEL_DIFF_PAIR, cs,
+                  [&] { done = p->diff_pair(m->d, B(ws, o1prev), B(ws, L.ord[2]), B(ws, o0off), B(ws, o1), cs); });
+        if (!done) {
+            if (sg > 0)
+                timed(m, 2, cs, [&] { p->diff(m->d, 2, B(ws, o1prev), B(ws, L.ord[2]), tn, stw, cs); });
+            timed(m, 1, cs, [&] { p->diff(m->d, 1, B(ws, o0off), B(ws, o1), tn, stw, cs); });
+        }
+        p->bnd_grad(m->d, B(ws, o0off), B(ws, o1), cs);
+        return o1;
+    };
+    auto paired_tail = [&] {            // order 2 of the last stage (its order 1 is in buffer 0)
+        timed(m, 2, cs, [&] {
+            p->diff(m->d, 2, B(ws, L.ord[1]), B(ws, L.ord[2]), tn, reinterpret_cast<unsigned *>(B(ws, L.status)), cs);
+        });
+    };
     if (s->precision != DOLINC_FP64) {
         // increment form: stage k reads record o0[k], writes o0[k+1] and the accumulator
         for (int sg = 0; sg < 3; ++sg) {
             join();
-            pending = run_diffs_split(m, p, ws, L, L.o0[sg], s, tn, cs);
+            size_t o1 = L.ord[1];
+            if (paired) o1 = paired_diffs(sg, L.o0[sg]);
+            else pending = run_diffs_split(m, p, ws, L, L.o0[sg], s, tn, cs);
             StageArgs a = base_args(m, s, ws, L, L.o0[sg]);
+            a.ord[1] = B(ws, o1);
             a.mode = 2;
             a.rk = sg;
             a.u0 = u_dev;
@@ -790,13 +822,17 @@ dolinc_status rk_step_impl(dolinc_mesh *m, const dolinc_scheme *s, double dt, co
             timed(m, DOLINC_KERNEL_STAGE, cs, [&] { p->stage(m->d, a, tn, cs); });
         }
         join();
+        if (paired) paired_tail();
         return launch_check();
     }
     int cur = 0;
     for (int sg = 0; sg < 3; ++sg) {
         join();
-        pending = run_diffs_split(m, p, ws, L, L.o0[cur], s, tn, cs);
+        size_t o1 = L.ord[1];
+        if (paired) o1 = paired_diffs(sg, L.o0[cur]);
+        else pending = run_diffs_split(m, p, ws, L, L.o0[cur], s, tn, cs);
         StageArgs a = base_args(m, s, ws, L, L.o0[cur]);
+        a.ord[1] = B(ws, o1);
         a.mode = 1;
         a.u0 = u_dev;
         a.us = sg == 0 ? u_dev : ust;
@@ -809,6 +845,7 @@ dolinc_status rk_step_impl(dolinc_mesh *m, const dolinc_scheme *s, double dt, co
         cur = 1 - cur;
     }
     join();
+    if (paired) paired_tail();
     return launch_check();
 }
 
@@ -978,6 +1015,15 @@ dolinc_status dolinc_autotune(dolinc_mesh *m, const dolinc_scheme *s, const doub
                 double tsg = time_it([&] { p->stage(m->d, a, t, cs); });
                 if (tsg < bs) bs = tsg, best.stage_lpc = t.stage_lpc, best.stage_block = t.stage_block;
             }
+        // the paired schedule (lanes 2): a stage's passes are one paired launch (order 2
+        // of the previous stage with its own order 1), against lanes 1's two passes
+        if (pair_scheme(s) && best.diff_lpc == 1) {
+            bool launched = true;
+            const double tp = time_it([&] {
+                launched = p->diff_pair(m->d, B(ws, L.ord[1]), B(ws, L.ord[2]), B(ws, L.o0[0]), B(ws, L.ord1b), cs);
+            });
+            if (launched && tp < bd) bd = tp, best.diff_lpc = 2;
+        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         m->prof = prof;
@@ -1471,13 +1517,15 @@ dolinc_status dolinc_set_tuning(dolinc_mesh *m, const dolinc_scheme *s, const do
         if (l == 0) return b == 64 || b == 128 || b == 256;
         return (l == 1 || l == 4 || l == 8) && b >= 32 && b <= 256 && b % 32 == 0;
     };
-    const bool diff_pipe = (t->diff_lanes == -1 || t->diff_lanes == -4) && (t->diff_block == 128 || t->diff_block == 256);
+    const bool diff_pipe = ((t->diff_lanes == -1 || t->diff_lanes == -4) && (t->diff_block == 128 || t->diff_block == 256)) ||
+                           (t->diff_lanes == 2 && t->diff_block >= 32 && t->diff_block <= 256 && t->diff_block % 32 == 0);
     const bool stage_pipe = (t->stage_lanes == -1 && (t->stage_block == 64 || t->stage_block == 128)) ||
                             (t->stage_lanes == -2 && (t->stage_block == 64 || t->stage_block == 128 || t->stage_block == 256));
     if (!(ok(t->diff_lanes, t->diff_block) || diff_pipe) || !(ok(t->stage_lanes, t->stage_block) || stage_pipe))
         return fail(DOLINC_ERR_INVALID_ARG,
                     "lanes 1, 4 or 8 with blocks a multiple of 32 in 32..256, or lanes 0 (tiled) with 64/128/256; "
-                    "differential passes also lanes -1 / -4 (persistent pipelined) with 128/256, the stage "
+                    "differential passes also lanes -1 / -4 (persistent pipelined) with 128/256 or lanes 2 (paired "
+                    "schedule) with blocks as lanes 1, the stage "
                     "lanes -1 (persistent pipelined) with tiles of 64/128 cells or -2 (face-centric) with 64/128/256");
     Tune x;
     x.diff_lpc = t->diff_lanes;

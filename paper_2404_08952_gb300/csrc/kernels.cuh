@@ -152,8 +152,12 @@ DOL_HD constexpr int round_up(int n, int q) { return ((n + q - 1) / q) * q; }
 // slots gathered per batch, by the size of the input record (registers held per slot)
 DOL_HD constexpr int diff_batch(int rec_values) { return rec_values <= 8 ? 4 : (rec_values <= 16 ? 2 : 1); }
 
+// One differential pass over a group of nt threads (thread t of the group, global
+// thread index gt of the pass; for LPC = 1 the group's cells start at c0 and its
+// output records are staged in smo and written by thread 0 with one bulk copy).
 template <int DIM, int NV, int M, int PREC, int LPC>
-__global__ void __launch_bounds__(256) k_diff(DevMesh mesh, const void *__restrict__ in_v, void *__restrict__ out_v)
+__device__ __forceinline__ void diff_cells(const DevMesh &mesh, const void *__restrict__ in_v, void *__restrict__ out_v,
+                                           long long gt, int t, int nt, long long c0, unsigned char *smo)
 {
     using R = typename PrecT<PREC>::R;
     using TI = typename OrdT<PREC, M - 1>::T;
@@ -162,7 +166,6 @@ __global__ void __launch_bounds__(256) k_diff(DevMesh mesh, const void *__restri
     constexpr int SI = ord_stride<DIM, NV, M - 1, PREC>(), SO = ord_stride<DIM, NV, M, PREC>();
     const TI *in = static_cast<const TI *>(in_v);
     TO *out = static_cast<TO *>(out_v);
-    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int c = (int)(gt / LPC), l = (int)(gt % LPC);
     const bool valid = c < mesh.n_cells;
     constexpr int VO = 16 / (int)sizeof(TO);
@@ -245,13 +248,11 @@ __global__ void __launch_bounds__(256) k_diff(DevMesh mesh, const void *__restri
         if constexpr (RBO % 16 == 0) {
             // the block's records are contiguous: stage them in shared memory and write
             // them with one bulk copy
-            extern __shared__ __align__(16) unsigned char smo[];
-            if (valid) store_rec_smem<TO, NV * CO, SO, R>(smo, threadIdx.x, acc);
+            if (valid) store_rec_smem<TO, NV * CO, SO, R>(smo, t, acc);
             fence_proxy_async_smem();
             __syncthreads();
-            const long long c0 = (long long)blockIdx.x * blockDim.x;
-            if (threadIdx.x == 0 && c0 < mesh.n_cells) {
-                const unsigned n = (unsigned)min((long long)blockDim.x, (long long)mesh.n_cells - c0);
+            if (t == 0 && c0 < mesh.n_cells) {
+                const unsigned n = (unsigned)min((long long)nt, (long long)mesh.n_cells - c0);
                 bulk_s2g_wait(out + c0 * SO, smo, n * RBO);
             }
         } else {
@@ -281,6 +282,40 @@ __global__ void __launch_bounds__(256) k_diff(DevMesh mesh, const void *__restri
                 if (e0 + i < NV * CO) rec[e0 + i] = to_store<TO, R>(acc[i]);
         }
     }
+}
+
+
+template <int DIM, int NV, int M, int PREC, int LPC>
+__global__ void __launch_bounds__(256) k_diff(DevMesh mesh, const void *__restrict__ in_v, void *__restrict__ out_v)
+{
+    extern __shared__ __align__(16) unsigned char smo[];
+    diff_cells<DIM, NV, M, PREC, LPC>(mesh, in_v, out_v, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                                      threadIdx.x, blockDim.x, (long long)blockIdx.x * blockDim.x, smo);
+}
+
+// Two differential passes in one launch over the same cells: the first CB threads of
+// a block gather order MA (inA -> outA), the next CB threads order 1 (inB -> outB),
+// for the block's CB cells.  Both halves read the cells' slot and cell weights, which
+// the second half finds in L1: one read of the Gauss weights for two passes (the order
+// a stage does not read, with the next stage's first order).  Each half is the
+// one-thread-per-cell pass (diff_cells), so every output is bit-identical to it.
+template <int DIM, int NV, int MA, int PREC, int CB>
+__global__ void __launch_bounds__(2 * CB) k_diff_dual(DevMesh mesh, const void *__restrict__ inA, void *__restrict__ outA,
+                                                      const void *__restrict__ inB, void *__restrict__ outB)
+{
+    // both halves stage their records for a bulk copy, i.e. pass one __syncthreads
+    static_assert((ord_stride<DIM, NV, MA, PREC>() * sizeof(typename OrdT<PREC, MA>::T)) % 16 == 0 &&
+                      (ord_stride<DIM, NV, 1, PREC>() * sizeof(typename OrdT<PREC, 1>::T)) % 16 == 0,
+                  "records of whole 16-byte chunks in both passes");
+    extern __shared__ __align__(16) unsigned char smo[];
+    const int t = threadIdx.x % CB;
+    const long long c0 = (long long)blockIdx.x * CB;
+    if (threadIdx.x < CB)
+        diff_cells<DIM, NV, MA, PREC, 1>(mesh, inA, outA, c0 + t, t, CB, c0, smo);
+    else
+        diff_cells<DIM, NV, 1, PREC, 1>(mesh, inB, outB, c0 + t, t, CB, c0,
+                                        smo + (size_t)CB * ord_stride<DIM, NV, MA, PREC>() *
+                                                  sizeof(typename OrdT<PREC, MA>::T));
 }
 
 // ------------------------------------------------------------------ stage

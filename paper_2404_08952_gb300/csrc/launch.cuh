@@ -37,6 +37,9 @@ inline int persistent_grid(const void *kernel, int threads, size_t smem)
 struct PathFns {
     void (*pack)(const DevMesh &, const double *, void *, double *copy, cudaStream_t);
     void (*diff)(const DevMesh &, int M, const void *, void *, const Tune &, unsigned *, cudaStream_t);
+    // order 2 (inA -> outA) and order 1 (inB -> outB) in one launch; false (nothing
+    // launched) where the records do not allow it
+    bool (*diff_pair)(const DevMesh &, const void *, void *, const void *, void *, cudaStream_t);
     void (*stage)(const DevMesh &, const StageArgs &, const Tune &, cudaStream_t);
     void (*faces)(const DevMesh &, const StageArgs &, double *, double *, cudaStream_t);
     void (*bnd_grad)(const DevMesh &, const void *, void *, cudaStream_t);
@@ -239,6 +242,18 @@ template <int DIM, int NV, int NS, int PREC> struct Path {
         default: k_stage<DIM, NV, NS, PREC, 1><<<nblk(m.n_cells, bs), bs, 0, s>>>(m, a); break;
         }
     }
+    static bool diff_pair(const DevMesh &m, const void *inA, void *outA, const void *inB, void *outB, cudaStream_t s)
+    {
+        constexpr unsigned ra = out_rec_bytes<2>(), rb = out_rec_bytes<1>();
+        if constexpr (ra % 16 != 0 || rb % 16 != 0) {
+            return false;
+        } else {
+            constexpr int CB = 64;
+            k_diff_dual<DIM, NV, 2, PREC, CB><<<nblk(m.n_cells, CB), 2 * CB, (size_t)CB * (ra + rb), s>>>(m, inA, outA,
+                                                                                                          inB, outB);
+            return true;
+        }
+    }
     static void faces(const DevMesh &m, const StageArgs &a, double *fL, double *fR, cudaStream_t s)
     {
         k_faces<DIM, NV, NS, PREC><<<nblk(m.n_faces, 128), 128, 0, s>>>(m, a, fL, fR);
@@ -247,7 +262,7 @@ template <int DIM, int NV, int NS, int PREC> struct Path {
     {
         if (m.n_bcell > 0) k_bnd_grad<DIM, NV, PREC><<<nblk(m.n_bcell, 128), 128, 0, s>>>(m, o0, o1);
     }
-    static PathFns fns() { return PathFns{&pack, &diff, &stage, &faces, &bnd_grad}; }
+    static PathFns fns() { return PathFns{&pack, &diff, &diff_pair, &stage, &faces, &bnd_grad}; }
 };
 
 // Persistent batched stage (k_batch_stage), launched cooperatively.

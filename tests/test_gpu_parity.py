@@ -536,3 +536,38 @@ def test_autotune_picks_a_valid_shape_and_keeps_parity(tmp_path):
     dg.dolinc_sync_status(M, ws)
     want = O.rk3_step(u, oracle.Scheme(k=3, r=1, n_diff=2, nv=5, **euler_ok(5)), dt)
     assert rel(M.from_lib(x.cpu().numpy()), want) < 1e-12
+
+
+@pytest.mark.parametrize("name,nv,prec", [("tet", 5, "fp32"), ("tet", 5, "fp64"), ("tet", 5, "fp32_bf16"),
+                                          ("tri", 4, "fp32"), ("tri", 1, "fp32"), ("hexprism", 1, "fp64")])
+@pytest.mark.parametrize("stage_shape", [(-2, 128), (1, 128)])
+def test_paired_schedule_is_bit_identical(name, nv, prec, stage_shape):
+    """Diff lanes 2 (the paired schedule: a stage's unread order-2 pass runs in one
+    launch with the next stage's order-1 pass, order 1 double-buffered) gives the
+    steps of lanes 1 bit for bit; where the records allow it (16-byte multiples) the
+    paired launch runs twice per step."""
+    m, O = mesh(name)
+    M = gpu_mesh(m)
+    u = field(m, nv, seed=61)
+    fx = euler_ok(nv) if nv > 1 else dict(flux="upwind", adv=(1.0, 0.5, 0.3))
+    sch = dg.Scheme(k=3, r=1, n_diff=2, nv=nv, precision=prec, **fx)
+    ws = dg.workspace(M, sch)
+    out = {}
+    for lanes in (1, 2):
+        dg.dolinc_set_tuning(M, sch, lanes, 64, *stage_shape)
+        x = to_dev(M, u)
+        dg.dolinc_profile_enable(M, True)
+        for _ in range(2):
+            dg.dolinc_rk_step(M, sch, 1e-3, x, ws)
+        kms, kn = dg.profile_read(M)
+        dg.dolinc_profile_enable(M, False)
+        dg.dolinc_sync_status(M, ws)
+        out[lanes] = (x.cpu().numpy(), kn[dg.KERNEL_KINDS.index("diff_pair")])
+    assert np.array_equal(out[1][0], out[2][0])
+    assert out[1][1] == 0
+    records_ok = not (name == "tri" and nv == 1 and prec != "fp64")      # 8-byte order-1 records
+    assert out[2][1] == (4 if records_ok else 0), out[2][1]
+    want = O.run(u, oracle.Scheme(k=3, r=1, n_diff=2, nv=nv, **fx), 1e-3, 2)
+    got = M.from_lib(out[2][0])
+    tol = {"fp64": 1e-12, "fp32": 1e-6, "fp32_bf16": 1e-5}[prec]
+    assert rel(got - u, want - u) < tol * 10 or rel(got, want) < tol
