@@ -4,7 +4,8 @@ Workload (default): euler3d_tet64 — 64^3 hexes x 5 tetrahedra (1,310,720 cells
 +-15% node jitter, periodic, isentropic vortex, Rusanov flux, scheme order 3
 (stencil (3,1) = USR3, differentials through order 2), FP32 differentials/reconstruction/
 flux with FP64 geometry master and FP64 state update.  A step is one SSP-RK3 time
-step (3 stages, each: differential passes + fused reconstruct/flux/residual/update).
+step (3 stages, each: differential passes + fused reconstruct/flux/residual/update);
+the timed K steps are one dolinc_rk_steps call (the state stays on the device).
 
 Metric: cell-updates per second per RK stage = cells * 3 * steps / time.
 The line also carries the FP64 GPU run of the same steps, the mixed-vs-FP64
@@ -314,8 +315,7 @@ def run_dolinc(args):
             tune = dict(diff_lanes=dl, diff_block=db, stage_lanes=sl, stage_block=sb, forced=True)
         else:
             tune = dg.dolinc_autotune(M, sch, u, ws) if not args.no_tune else None
-        for _ in range(args.warmup):
-            dg.dolinc_rk_step(M, sch, dt, u, ws)
+        dg.dolinc_rk_steps(M, sch, dt, args.warmup, u, ws)
         finite = True
         try:
             dg.dolinc_sync_status(M, ws)
@@ -328,8 +328,7 @@ def run_dolinc(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with Clocks(local if clocks else -1) as ck:
             e0.record(stream)
-            for _ in range(steps):
-                dg.dolinc_rk_step(M, sch, dt, u, ws)
+            dg.dolinc_rk_steps(M, sch, dt, steps, u, ws)       # the K steps in one call: state stays on device
             e1.record(stream)
             torch.cuda.synchronize()
         ms = reduce_max(e0.elapsed_time(e1), dist)
@@ -811,14 +810,12 @@ def run_hexprism(args):
             ws = dg.workspace(M, sch)
             u = torch.from_numpy(M.to_lib(w["u0"])).cuda()
             tune = dg.dolinc_autotune(M, sch, u, ws)
-            for _ in range(args.warmup):
-                dg.dolinc_rk_step(M, sch, w["dt"], u, ws)
+            dg.dolinc_rk_steps(M, sch, w["dt"], args.warmup, u, ws)
             dg.dolinc_profile_enable(M, True)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for _ in range(args.steps):
-                dg.dolinc_rk_step(M, sch, w["dt"], u, ws)
+            dg.dolinc_rk_steps(M, sch, w["dt"], args.steps, u, ws)
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)

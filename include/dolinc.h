@@ -215,6 +215,15 @@ dolinc_status dolinc_rk_stage(dolinc_mesh *mesh, const dolinc_scheme *scheme, do
 dolinc_status dolinc_rk_step(dolinc_mesh *mesh, const dolinc_scheme *scheme, double dt, double *u_dev,
                              void *ws_dev, size_t ws_bytes, dolinc_stream stream);
 
+/* n_steps SSP-RK3 steps of u_dev in one call: the same results, bit for bit, as
+ * n_steps calls of dolinc_rk_step.  The state stays on the device between the steps,
+ * so the last stage of each step also writes the next step's bulk-precision record
+ * (the first step alone converts u_dev), and under the paired schedule (diff lanes 2)
+ * the last order-2 pass of a step runs with the next step's first order-1 pass.
+ * Errors as dolinc_rk_step; INVALID_ARG for n_steps < 1. */
+dolinc_status dolinc_rk_steps(dolinc_mesh *mesh, const dolinc_scheme *scheme, double dt, int n_steps, double *u_dev,
+                              void *ws_dev, size_t ws_bytes, dolinc_stream stream);
+
 /* One SSP-RK3 step (Sec 3), computed as dolinc_rk_step computes it, of a state held
  * in host memory: u_host (FP64 [v][c], library order) holds the step's input and
  * receives the new state.  When u_host is page-locked and mapped into the device

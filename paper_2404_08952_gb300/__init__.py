@@ -26,7 +26,7 @@ ABI_SYMBOLS = (
     "dolinc_mesh_create", "dolinc_mesh_destroy", "dolinc_mesh_get_info", "dolinc_mesh_permutation",
     "dolinc_mesh_geometry", "dolinc_workspace_size", "dolinc_workspace_init", "dolinc_diff_layout",
     "dolinc_differentials", "dolinc_reconstruct_faces", "dolinc_residual", "dolinc_rk_stage",
-    "dolinc_rk_step", "dolinc_rk_step_host", "dolinc_set_flags", "dolinc_set_boundary_values", "dolinc_sync_status", "dolinc_profile_enable",
+    "dolinc_rk_step", "dolinc_rk_steps", "dolinc_rk_step_host", "dolinc_set_flags", "dolinc_set_boundary_values", "dolinc_sync_status", "dolinc_profile_enable",
     "dolinc_profile_read", "dolinc_rk_step_noalloc", "dolinc_autotune", "dolinc_set_tuning",
     "dolinc_criterion", "dolinc_indicator_features", "dolinc_mlp_create", "dolinc_mlp_destroy",
     "dolinc_mlp_get_params", "dolinc_mlp_set_params", "dolinc_mlp_forward", "dolinc_mlp_loss_grad",
@@ -85,6 +85,7 @@ def load(path=LIB_PATH):
             "dolinc_residual": [P, P, P, P, P, S, P],
             "dolinc_rk_stage": [P, P, D, I, P, P, P, P, S, P],
             "dolinc_rk_step": [P, P, D, P, P, S, P], "dolinc_rk_step_host": [P, P, D, P, P, P, S, P],
+            "dolinc_rk_steps": [P, P, D, I, P, P, S, P],
             "dolinc_set_flags": [P, P], "dolinc_set_boundary_values": [P, C.c_int, P],
             "dolinc_sync_status": [P, P, P], "dolinc_last_error": [],
             "dolinc_profile_enable": [P, I], "dolinc_profile_read": [P, P, P],
@@ -351,6 +352,13 @@ def dolinc_rk_step(mesh, scheme, dt, u, ws, stream=None):
     s = scheme.c()
     _check(load().dolinc_rk_step(mesh.handle, C.byref(s), float(dt), _ptr(u), _ptr(ws), ws.numel(),
                                  _stream(stream)))
+
+
+def dolinc_rk_steps(mesh, scheme, dt, n_steps, u, ws, stream=None):
+    """n_steps SSP-RK3 steps in one call (bit-identical to n_steps dolinc_rk_step calls)."""
+    s = scheme.c()
+    _check(load().dolinc_rk_steps(mesh.handle, C.byref(s), float(dt), int(n_steps), _ptr(u), _ptr(ws), ws.numel(),
+                                  _stream(stream)))
 
 
 def dolinc_rk_step_host(mesh, scheme, dt, u_host, u_dev, ws, stream=None):

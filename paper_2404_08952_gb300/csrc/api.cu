@@ -764,13 +764,16 @@ namespace {
 // state from u_dev; the last stage writes the new state to u_out.  dolinc_rk_step
 // passes one device buffer for all three.
 dolinc_status rk_step_impl(dolinc_mesh *m, const dolinc_scheme *s, double dt, const double *u_in, double *u_dev,
-                           double *u_out, void *ws, const WsLayout &L, cudaStream_t cs)
+                           double *u_out, void *ws, const WsLayout &L, cudaStream_t cs, int n_steps = 1)
 {
     static const double A[3] = {0.0, 0.75, 1.0 / 3.0}, Bc[3] = {1.0, 0.25, 2.0 / 3.0};
     const PathFns *p = path_for(m, s, needed_order(*s));
     if (!p) return fail(DOLINC_ERR_UNSUPPORTED, "no kernel for this (dim, nv, order, precision)");
     double *ust = reinterpret_cast<double *>(B(ws, L.ustage));
     const Tune tn = tune_for(m, s);
+    // Several steps in one call keep the state on the device: the last stage of a step
+    // also writes the next step's order-0 record (the bulk-precision rounding of the new
+    // FP64 state, as the pack would), so only the first step packs.
     timed(m, DOLINC_KERNEL_PACK, cs,
           [&] { p->pack(m->d, u_in, B(ws, L.o0[0]), u_dev != u_in ? u_dev : nullptr, cs); });
     bool pending = false;
@@ -778,74 +781,84 @@ dolinc_status rk_step_impl(dolinc_mesh *m, const dolinc_scheme *s, double dt, co
         if (pending) cudaStreamWaitEvent(cs, m->ev_join, 0);
         pending = false;
     };
-    // Paired schedule (diff lanes 2): order 1 of stage k goes to buffer k % 2; order 2 of
-    // stage k is computed with order 1 of stage k+1 in one launch, the last one after
-    // the last stage.  Returns the offset of the stage's order-1 buffer.
+    // Paired schedule (diff lanes 2): order 1 of stage t (counted over the call's steps)
+    // goes to buffer t % 2; order 2 of stage t is computed with order 1 of stage t+1 in
+    // one launch, the last one after the last stage.  Returns the offset of the stage's
+    // order-1 buffer.
     const bool paired = tn.diff_lpc == 2 && pair_scheme(s);
-    auto paired_diffs = [&](int sg, size_t o0off) -> size_t {
-        const size_t o1 = (sg & 1) ? L.ord1b : L.ord[1], o1prev = (sg & 1) ? L.ord[1] : L.ord1b;
+    auto o1buf = [&](int t) { return (t & 1) ? L.ord1b : L.ord[1]; };
+    auto paired_diffs = [&](int t, size_t o0off) -> size_t {
+        const size_t o1 = o1buf(t), o1prev = o1buf(t + 1);
         unsigned *stw = reinterpret_cast<unsigned *>(B(ws, L.status));
-        bool done = false;
-        if (sg > 0)
+        const bool done = t > 0 && p->diff_pair(m->d, nullptr, nullptr, nullptr, nullptr, cs, true);
+        if (done)
             timed(m, DOLINC_KERNEL_DIFF_PAIR, cs,
-                  [&] { done = p->diff_pair(m->d, B(ws, o1prev), B(ws, L.ord[2]), B(ws, o0off), B(ws, o1), cs); });
-        if (!done) {
-            if (sg > 0)
+                  [&] { p->diff_pair(m->d, B(ws, o1prev), B(ws, L.ord[2]), B(ws, o0off), B(ws, o1), cs, false); });
+        else {
+            if (t > 0)
                 timed(m, 2, cs, [&] { p->diff(m->d, 2, B(ws, o1prev), B(ws, L.ord[2]), tn, stw, cs); });
             timed(m, 1, cs, [&] { p->diff(m->d, 1, B(ws, o0off), B(ws, o1), tn, stw, cs); });
         }
         p->bnd_grad(m->d, B(ws, o0off), B(ws, o1), cs);
         return o1;
     };
-    auto paired_tail = [&] {            // order 2 of the last stage (its order 1 is in buffer 0)
+    auto paired_tail = [&](int t_last) {   // order 2 of the last stage
         timed(m, 2, cs, [&] {
-            p->diff(m->d, 2, B(ws, L.ord[1]), B(ws, L.ord[2]), tn, reinterpret_cast<unsigned *>(B(ws, L.status)), cs);
+            p->diff(m->d, 2, B(ws, o1buf(t_last)), B(ws, L.ord[2]), tn, reinterpret_cast<unsigned *>(B(ws, L.status)),
+                    cs);
         });
     };
+    int t = 0;
     if (s->precision != DOLINC_FP64) {
         // increment form: stage k reads record o0[k], writes o0[k+1] and the accumulator
-        for (int sg = 0; sg < 3; ++sg) {
-            join();
-            size_t o1 = L.ord[1];
-            if (paired) o1 = paired_diffs(sg, L.o0[sg]);
-            else pending = run_diffs_split(m, p, ws, L, L.o0[sg], s, tn, cs);
-            StageArgs a = base_args(m, s, ws, L, L.o0[sg]);
-            a.ord[1] = B(ws, o1);
-            a.mode = 2;
-            a.rk = sg;
-            a.u0 = u_dev;
-            a.out = u_out;
-            a.dt = dt;
-            a.dacc = reinterpret_cast<float *>(B(ws, L.dacc));
-            a.rec_start = B(ws, L.o0[0]);
-            a.o0_next = sg == 2 ? nullptr : B(ws, L.o0[sg + 1]);
-            timed(m, DOLINC_KERNEL_STAGE, cs, [&] { p->stage(m->d, a, tn, cs); });
+        for (int k = 0; k < n_steps; ++k) {
+            const bool last = k == n_steps - 1;
+            for (int sg = 0; sg < 3; ++sg, ++t) {
+                join();
+                size_t o1 = L.ord[1];
+                if (paired) o1 = paired_diffs(t, L.o0[sg]);
+                else pending = run_diffs_split(m, p, ws, L, L.o0[sg], s, tn, cs);
+                StageArgs a = base_args(m, s, ws, L, L.o0[sg]);
+                a.ord[1] = B(ws, o1);
+                a.mode = 2;
+                a.rk = sg;
+                a.u0 = u_dev;
+                a.out = last ? u_out : u_dev;
+                a.dt = dt;
+                a.dacc = reinterpret_cast<float *>(B(ws, L.dacc));
+                a.rec_start = B(ws, L.o0[0]);
+                a.o0_next = sg < 2 ? B(ws, L.o0[sg + 1]) : (last ? nullptr : B(ws, L.o0[0]));
+                timed(m, DOLINC_KERNEL_STAGE, cs, [&] { p->stage(m->d, a, tn, cs); });
+            }
         }
         join();
-        if (paired) paired_tail();
+        if (paired) paired_tail(t - 1);
         return launch_check();
     }
     int cur = 0;
-    for (int sg = 0; sg < 3; ++sg) {
-        join();
-        size_t o1 = L.ord[1];
-        if (paired) o1 = paired_diffs(sg, L.o0[cur]);
-        else pending = run_diffs_split(m, p, ws, L, L.o0[cur], s, tn, cs);
-        StageArgs a = base_args(m, s, ws, L, L.o0[cur]);
-        a.ord[1] = B(ws, o1);
-        a.mode = 1;
-        a.u0 = u_dev;
-        a.us = sg == 0 ? u_dev : ust;
-        a.out = sg == 2 ? u_out : ust;
-        a.A = A[sg];
-        a.B = Bc[sg];
-        a.dt = dt;
-        a.o0_next = sg == 2 ? nullptr : B(ws, L.o0[1 - cur]);
-        timed(m, DOLINC_KERNEL_STAGE, cs, [&] { p->stage(m->d, a, tn, cs); });
-        cur = 1 - cur;
+    for (int k = 0; k < n_steps; ++k) {
+        const bool last = k == n_steps - 1;
+        for (int sg = 0; sg < 3; ++sg, ++t) {
+            join();
+            size_t o1 = L.ord[1];
+            if (paired) o1 = paired_diffs(t, L.o0[cur]);
+            else pending = run_diffs_split(m, p, ws, L, L.o0[cur], s, tn, cs);
+            StageArgs a = base_args(m, s, ws, L, L.o0[cur]);
+            a.ord[1] = B(ws, o1);
+            a.mode = 1;
+            a.u0 = u_dev;
+            a.us = sg == 0 ? u_dev : ust;
+            a.out = sg < 2 ? ust : (last ? u_out : u_dev);
+            a.A = A[sg];
+            a.B = Bc[sg];
+            a.dt = dt;
+            a.o0_next = (sg == 2 && last) ? nullptr : B(ws, L.o0[1 - cur]);
+            timed(m, DOLINC_KERNEL_STAGE, cs, [&] { p->stage(m->d, a, tn, cs); });
+            cur = 1 - cur;
+        }
     }
     join();
-    if (paired) paired_tail();
+    if (paired) paired_tail(t - 1);
     return launch_check();
 }
 
@@ -862,6 +875,18 @@ dolinc_status dolinc_rk_step(dolinc_mesh *m, const dolinc_scheme *s, double dt, 
     if ((st = check_ws(m, s, ws, ws_bytes, L))) return st;
     if (!u) return fail(DOLINC_ERR_INVALID_ARG, "null field");
     return rk_step_impl(m, s, dt, u, u, u, ws, L, reinterpret_cast<cudaStream_t>(stream));
+}
+
+dolinc_status dolinc_rk_steps(dolinc_mesh *m, const dolinc_scheme *s, double dt, int n_steps, double *u, void *ws,
+                              size_t ws_bytes, dolinc_stream stream)
+{
+    dolinc_status st = check_scheme(m, s);
+    if (st) return st;
+    WsLayout L;
+    if ((st = check_ws(m, s, ws, ws_bytes, L))) return st;
+    if (!u) return fail(DOLINC_ERR_INVALID_ARG, "null field");
+    if (n_steps < 1) return fail(DOLINC_ERR_INVALID_ARG, "n_steps must be at least 1");
+    return rk_step_impl(m, s, dt, u, u, u, ws, L, reinterpret_cast<cudaStream_t>(stream), n_steps);
 }
 
 dolinc_status dolinc_rk_step_host(dolinc_mesh *m, const dolinc_scheme *s, double dt, double *u_host, double *u_dev,
@@ -1019,9 +1044,10 @@ dolinc_status dolinc_autotune(dolinc_mesh *m, const dolinc_scheme *s, const doub
         // of the previous stage with its own order 1), against lanes 1's two passes
         if (pair_scheme(s) && best.diff_lpc == 1) {
             bool launched = true;
-            const double tp = time_it([&] {
-                launched = p->diff_pair(m->d, B(ws, L.ord[1]), B(ws, L.ord[2]), B(ws, L.o0[0]), B(ws, L.ord1b), cs);
-            });
+            launched = p->diff_pair(m->d, nullptr, nullptr, nullptr, nullptr, cs, true);
+            const double tp = launched ? time_it([&] {
+                p->diff_pair(m->d, B(ws, L.ord[1]), B(ws, L.ord[2]), B(ws, L.o0[0]), B(ws, L.ord1b), cs, false);
+            }) : 1e30;
             if (launched && tp < bd) bd = tp, best.diff_lpc = 2;
         }
         cudaEventDestroy(e0);

@@ -742,6 +742,7 @@ __device__ __forceinline__ bool incr_update(const StageArgs &a, int c, int v, lo
     const R D = mul_rn((R)(2.0 / 3.0), add_rn((R)a.dacc[i], d));
     const double o = __dadd_rn(a.u0[i], (double)D);
     a.out[i] = o;
+    if (nxt) nxt[c * (long long)S0 + v] = (T0)(R)o;    // the next step's record (several steps per call)
     return nonfinite64(o);
 }
 
@@ -766,6 +767,7 @@ __device__ __forceinline__ bool incr_update_cell(const StageArgs &a, int c, long
         store_rec<T0, NV, S0, R>(nxt, c, nx);
         return bad;
     }
+    R nx[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         const long long i = v * n + c;
@@ -773,8 +775,10 @@ __device__ __forceinline__ bool incr_update_cell(const StageArgs &a, int c, long
         const R D = mul_rn((R)(2.0 / 3.0), add_rn((R)a.dacc[i], d));
         const double o = __dadd_rn(a.u0[i], (double)D);
         a.out[i] = o;
+        nx[v] = (R)o;
         bad |= nonfinite64(o);
     }
+    if (nxt) store_rec<T0, NV, S0, R>(nxt, c, nx);      // the next step's record (several steps per call)
     return bad;
 }
 

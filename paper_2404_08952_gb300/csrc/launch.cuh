@@ -38,8 +38,8 @@ struct PathFns {
     void (*pack)(const DevMesh &, const double *, void *, double *copy, cudaStream_t);
     void (*diff)(const DevMesh &, int M, const void *, void *, const Tune &, unsigned *, cudaStream_t);
     // order 2 (inA -> outA) and order 1 (inB -> outB) in one launch; false (nothing
-    // launched) where the records do not allow it
-    bool (*diff_pair)(const DevMesh &, const void *, void *, const void *, void *, cudaStream_t);
+    // launched) where the records do not allow it; dry: only answer whether they do
+    bool (*diff_pair)(const DevMesh &, const void *, void *, const void *, void *, cudaStream_t, bool dry);
     void (*stage)(const DevMesh &, const StageArgs &, const Tune &, cudaStream_t);
     void (*faces)(const DevMesh &, const StageArgs &, double *, double *, cudaStream_t);
     void (*bnd_grad)(const DevMesh &, const void *, void *, cudaStream_t);
@@ -242,12 +242,14 @@ template <int DIM, int NV, int NS, int PREC> struct Path {
         default: k_stage<DIM, NV, NS, PREC, 1><<<nblk(m.n_cells, bs), bs, 0, s>>>(m, a); break;
         }
     }
-    static bool diff_pair(const DevMesh &m, const void *inA, void *outA, const void *inB, void *outB, cudaStream_t s)
+    static bool diff_pair(const DevMesh &m, const void *inA, void *outA, const void *inB, void *outB, cudaStream_t s,
+                          bool dry)
     {
         constexpr unsigned ra = out_rec_bytes<2>(), rb = out_rec_bytes<1>();
         if constexpr (ra % 16 != 0 || rb % 16 != 0) {
             return false;
         } else {
+            if (dry) return true;
             constexpr int CB = 64;
             k_diff_dual<DIM, NV, 2, PREC, CB><<<nblk(m.n_cells, CB), 2 * CB, (size_t)CB * (ra + rb), s>>>(m, inA, outA,
                                                                                                           inB, outB);

@@ -571,3 +571,26 @@ def test_paired_schedule_is_bit_identical(name, nv, prec, stage_shape):
     got = M.from_lib(out[2][0])
     tol = {"fp64": 1e-12, "fp32": 1e-6, "fp32_bf16": 1e-5}[prec]
     assert rel(got - u, want - u) < tol * 10 or rel(got, want) < tol
+
+
+@pytest.mark.parametrize("name,nv,prec", [("tet", 5, "fp32"), ("tet", 5, "fp64"), ("tet", 5, "fp32_bf16"),
+                                          ("tri", 1, "fp32"), ("tri_bnd", 4, "fp64"), ("hexprism", 1, "fp32")])
+@pytest.mark.parametrize("shape", [(1, 64, -2, 128), (2, 64, -2, 128), (2, 128, 1, 128), (4, 128, 4, 64),
+                                   (-1, 128, -1, 128), (0, 128, 0, 64)])
+def test_several_steps_per_call_equal_single_steps(name, nv, prec, shape):
+    """dolinc_rk_steps(n) keeps the state on the device (the last stage writes the next
+    step's record, the paired schedule pairs across steps) and must give n calls of
+    dolinc_rk_step bit for bit, for every launch shape."""
+    m, O = mesh(name)
+    M = gpu_mesh(m)
+    u = field(m, nv, seed=62)
+    fx = euler_ok(nv) if nv > 1 else dict(flux="upwind", adv=(1.0, 0.5, 0.3))
+    sch = dg.Scheme(k=3, r=1, n_diff=2, nv=nv, precision=prec, **fx)
+    ws = dg.workspace(M, sch)
+    dg.dolinc_set_tuning(M, sch, *shape)
+    a, b = to_dev(M, u), to_dev(M, u)
+    for _ in range(3):
+        dg.dolinc_rk_step(M, sch, 1e-3, a, ws)
+    dg.dolinc_rk_steps(M, sch, 1e-3, 3, b, ws)
+    dg.dolinc_sync_status(M, ws)
+    assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
