@@ -279,6 +279,34 @@ def _increment_bound_ratio(O, inc, inc_ref, u0, dt, scheme):
     return float((np.abs(inc - inc_ref) / bound[None, :]).max())
 
 
+# GB300's FP64 peak from its unit counts and clock: 152 SMs x 2 FP64 FMA per clock per SM
+# x 2 FLOP x 2.07 GHz (the 1.25 TFLOP/s nominal figure)
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+
+
+def _fp64_roofline(args, w, M, f):
+    """The FP64 path's stage pair against the FP64 ALU peak: FP64 FLOP per face of the
+    pair (2 per DFMA, 1 per DADD / DMUL) from the instruction counters of one ncu
+    capture (profiles/fp64_flops.json, per face, the same scheme) times the faces, over
+    the pair's live per-launch time."""
+    pfile = os.path.join(ROOT, "profiles", "fp64_flops.json")
+    key = "%s/order%d" % (args.workload, w["info"].get("order", 0))
+    try:
+        per_face = float(json.load(open(pfile))[key])
+    except Exception:
+        return None
+    kms, kn = f["kms"], f["kn"]
+    i = KINDS.index("stage")
+    if kn[i] == 0:
+        return None
+    ms = kms[i] / kn[i]
+    gf = per_face * M.n_faces / (ms / 1e3) / 1e9
+    return {"bound": "alu", "kernel": "stage (k_flux + k_gather, FP64)", "achieved": round(gf, 1),
+            "peak": round(FP64_PEAK_GFLOPS, 1), "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",
+            "unit": "GFLOP/s", "frac": round(gf / FP64_PEAK_GFLOPS, 4), "flop_per_face": per_face,
+            "ms_per_launch": round(ms, 5)}
+
+
 def _l2_rel(a, b):
     """max over variables of ||a_v - b_v||_2 / ||b||_2 (all variables' norm, so a
     variable that is zero in the data, e.g. z-momentum, is measured against the state)."""
@@ -469,6 +497,9 @@ def run_dolinc(args):
         line["fp64_gpu"] = {"value": v64, "ms_per_step": f["ms"] / args.steps,
                             "speedup_mixed_vs_fp64": value / v64,
                             "l2_rel_mixed_vs_fp64_after_steps": l2, "steps_compared": args.steps + args.warmup}
+        fr = _fp64_roofline(args, w, M, f)
+        if fr:
+            line["fp64_gpu"]["roofline"] = fr
     # e2e: the public call with a host state (pinned): every step moves the state from
     # host memory into the step's first kernel and the new state back to host memory
     # from its last one, inside the timed region

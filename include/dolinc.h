@@ -350,8 +350,10 @@ dolinc_status dolinc_mlp_loss_grad(dolinc_mlp *mlp, const float *x_dev, const ui
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8) with learning rate lr on one batch. */
 dolinc_status dolinc_mlp_train_step(dolinc_mlp *mlp, const float *x_dev, const uint8_t *y_dev, int64_t n,
                                     float lr, float pos_weight, float *loss_dev, dolinc_stream stream);
-/* Features + network: flags_dev [n_cells] (and logits_dev, may be NULL); x24_dev is
- * caller scratch of n_cells x 24 floats. */
+/* Features + network: flags_dev [n_cells] (and logits_dev, may be NULL).  x24_dev:
+ * caller scratch of n_cells x 24 floats that receives the inputs, or NULL: the
+ * network kernel then gathers each cell's 24 inputs itself, without writing them out
+ * (the same flags). */
 dolinc_status dolinc_indicator_infer(dolinc_mesh *mesh, const dolinc_scheme *scheme, dolinc_mlp *mlp,
                                      const double *u_dev, float *x24_dev, uint8_t *flags_dev, float *logits_dev,
                                      void *ws_dev, size_t ws_bytes, dolinc_stream stream);

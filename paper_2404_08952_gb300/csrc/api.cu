@@ -490,6 +490,8 @@ dolinc_status upload_mesh(dolinc_mesh *m)
     std::vector<double> sk64, ck64, f64(8 * nf);
     std::vector<float> sk32, ck32, f32(8 * nf);
     for (int64_t s = 0; s < ns; ++s) slot2[s] = make_int2(h.snb[s], (int)h.sword[s]);
+    std::vector<uint32_t> sword(h.sword.begin(), h.sword.end());
+    sword.resize(ns + 4, 0u);                           // spare entries: 16-byte loads of 4 words
     weight_tables(h, sk64, sk32, ck64, ck32);
     std::vector<int32_t> fo(nf), fn(nf), fe(nf);
     std::vector<int8_t> ff(nf);
@@ -573,7 +575,8 @@ dolinc_status upload_mesh(dolinc_mesh *m)
     } else {
         d.bidx = nullptr;
     }
-    if ((st = upload(m, off, &d.off)) || (st = upload(m, slot2, &d.slot2)) || (st = upload(m, sk64, &d.slotk64)) ||
+    if ((st = upload(m, off, &d.off)) || (st = upload(m, slot2, &d.slot2)) || (st = upload(m, sword, &d.sword)) ||
+        (st = upload(m, sk64, &d.slotk64)) ||
         (st = upload(m, sk32, &d.slotk32)) || (st = upload(m, ck64, &d.cellk64)) ||
         (st = upload(m, ck32, &d.cellk32)) || (st = upload(m, f64, &d.face64)) || (st = upload(m, f32, &d.face32)) ||
         (st = upload(m, fo, &d.fo)) || (st = upload(m, fn, &d.fn)) || (st = upload(m, fe, &d.face_ext)) ||
@@ -1270,9 +1273,27 @@ dolinc_status dolinc_indicator_infer(dolinc_mesh *me, const dolinc_scheme *s, do
                                      float *x24, uint8_t *flags, float *logits, void *ws, size_t ws_bytes,
                                      dolinc_stream stream)
 {
-    dolinc_status st = dolinc_indicator_features(me, s, u, x24, ws, ws_bytes, stream);
+    if (x24) {
+        dolinc_status st = dolinc_indicator_features(me, s, u, x24, ws, ws_bytes, stream);
+        if (st) return st;
+        return dolinc_mlp_forward(net, x24, me->h.n_cells, logits, flags, stream);
+    }
+    // without an input buffer: the network gathers its inputs itself (no round trip)
+    if (!net || (!logits && !flags)) return fail(DOLINC_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    WsLayout L;
+    const IndicatorFns *fi = nullptr;
+    dolinc_status st = indicator_prep(me, s, u, ws, ws_bytes, cs, L, &fi);
     if (st) return st;
-    return dolinc_mlp_forward(net, x24, me->h.n_cells, logits, flags, stream);
+    StageArgs a = base_args(me, s, ws, L, L.o0[0]);
+    float *own = reinterpret_cast<float *>(B(ws, L.ustage));
+    fi->own_features(me->d, a, own, cs);
+    if (!net->frag_ok) {
+        launch_mlp_frags(net->theta, net->frag, cs);
+        net->frag_ok = true;
+    }
+    launch_mlp_infer_fused(net->frag, net->theta, me->d, own, logits, flags, cs);
+    return launch_check();
 }
 
 // ------------------------------------------------------------------ batches

@@ -9,6 +9,7 @@ struct DevMesh {
     int dim, n_cells, n_faces, n_slots;
     const int32_t *off;          // [n_cells+1] slot ranges
     const int2 *slot2;           // [n_slots] (neighbour cell, slot word)
+    const uint32_t *sword;       // [n_slots + 4] the slot words alone (16-byte aligned groups of 4)
     const double *slotk64;       // [n_slots][4] ((1-w_c) S_{c,f} / V_c, neighbour id bits)
     const float *slotk32;
     const double *cellk64;       // [n_cells][4] (sum_f w_c S_{c,f} / V_c, 1/V_c)

@@ -177,10 +177,8 @@ __device__ __forceinline__ bool lex_gt(const float *a, const float *b)
 
 // Network input of cell c: its own 6 features, then the 6 of the three largest face
 // neighbours in lexicographic order (itself across a boundary face).
-__global__ void __launch_bounds__(128) k_gather24(DevMesh mesh, const float *__restrict__ own, float *__restrict__ x)
+__device__ __forceinline__ void gather24_cell(const DevMesh &mesh, const float *__restrict__ own, int c, float *o)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= mesh.n_cells) return;
     float top[3][6];
     int have = 0;
     int s0, s1;
@@ -205,19 +203,28 @@ __global__ void __launch_bounds__(128) k_gather24(DevMesh mesh, const float *__r
     }
     float self[6];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) self[q] = own[6ll * c + q];
+    for (int q = 0; q < 6; ++q) self[q] = __ldg(own + 6ll * c + q);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
         if (a >= have)
 #pragma unroll
             for (int q = 0; q < 6; ++q) top[a][q] = self[q];
-    float *o = x + 24ll * c;
 #pragma unroll
     for (int q = 0; q < 6; ++q) o[q] = self[q];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int q = 0; q < 6; ++q) o[6 + 6 * a + q] = top[a][q];
+}
+
+__global__ void __launch_bounds__(128) k_gather24(DevMesh mesh, const float *__restrict__ own, float *__restrict__ x)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= mesh.n_cells) return;
+    float o[24];
+    gather24_cell(mesh, own, c, o);
+#pragma unroll
+    for (int q = 0; q < 24; ++q) x[24ll * c + q] = o[q];
 }
 
 // ------------------------------------------------------------------ tensor-core inference
@@ -256,10 +263,15 @@ __device__ __forceinline__ void mma_bf16(float *d, const uint32_t *a, uint2 b)
 
 // 16 cells per warp tile; activations stay in registers between layers (the f32
 // accumulator layout of two adjacent n-tiles is the bf16 A layout of one k-tile).
+// FUSED: the inputs are not read from x but gathered per tile (gather24_cell, lanes
+// 0-15 one cell each) into the warp's 16 x 24 shared-memory rows.
+template <bool FUSED>
 __global__ void __launch_bounds__(128) k_mlp_infer(const uint2 *__restrict__ frag, const float *__restrict__ theta,
                                                    const float *__restrict__ x, long long n,
-                                                   float *__restrict__ logits, uint8_t *__restrict__ flags)
+                                                   float *__restrict__ logits, uint8_t *__restrict__ flags,
+                                                   DevMesh mesh, const float *__restrict__ own)
 {
+    __shared__ float sx[FUSED ? 4 * 16 * MLP_IN : 1];
     __shared__ uint2 sfrag[N_FRAGS * 32];
     __shared__ float sbias[3 * MLP_H + 1];
     for (int i = threadIdx.x; i < N_FRAGS * 32; i += blockDim.x) sfrag[i] = frag[i];
@@ -275,9 +287,20 @@ __global__ void __launch_bounds__(128) k_mlp_infer(const uint2 *__restrict__ fra
     const long long w0 = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     for (long long tile = w0; tile * 16 < n; tile += warps) {
         const long long r0 = tile * 16 + g, r1 = r0 + 8;
+        float *wx = sx + (FUSED ? (threadIdx.x / 32) * 16 * MLP_IN : 0);
+        if constexpr (FUSED) {
+            __syncwarp();
+            const long long cr = tile * 16 + lane;
+            if (lane < 16 && cr < n) gather24_cell(mesh, own, (int)cr, wx + lane * MLP_IN);
+            __syncwarp();
+        }
         // layer 1 input: 24 features padded to 32 (two k-tiles)
         uint32_t A[4][4];
-        auto xv = [&](long long r, int col) { return (r < n && col < MLP_IN) ? __ldg(x + r * MLP_IN + col) : 0.0f; };
+        auto xv = [&](long long r, int col) {
+            if (r >= n || col >= MLP_IN) return 0.0f;
+            if constexpr (FUSED) return wx[(r - tile * 16) * MLP_IN + col];
+            else return __ldg(x + r * MLP_IN + col);
+        };
 #pragma unroll
         for (int kt = 0; kt < 2; ++kt) {
             const int c0 = 16 * kt + 2 * t;
@@ -446,7 +469,17 @@ void launch_mlp_infer(const uint2 *frag, const float *theta, const float *x, lon
     int blocks = (int)((tiles + 3) / 4);
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    k_mlp_infer<<<blocks, 128, 0, s>>>(frag, theta, x, n, logits, flags);
+    k_mlp_infer<false><<<blocks, 128, 0, s>>>(frag, theta, x, n, logits, flags, DevMesh{}, nullptr);
+}
+void launch_mlp_infer_fused(const uint2 *frag, const float *theta, const DevMesh &m, const float *own, float *logits,
+                            uint8_t *flags, cudaStream_t s)
+{
+    const long long n = m.n_cells;
+    long long tiles = (n + 15) / 16;
+    int blocks = (int)((tiles + 3) / 4);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_mlp_infer<true><<<blocks, 128, 0, s>>>(frag, theta, nullptr, n, logits, flags, m, own);
 }
 void launch_quantize(const float *theta, float *q, cudaStream_t s)
 {

@@ -32,6 +32,9 @@ void launch_gather24(const DevMesh &m, const float *own, float *x, cudaStream_t 
 void launch_mlp_frags(const float *theta, uint2 *frag, cudaStream_t s);
 void launch_mlp_infer(const uint2 *frag, const float *theta, const float *x, long long n, float *logits,
                       uint8_t *flags, cudaStream_t s);
+// the network on every cell of m, its inputs gathered from the own features inside the kernel
+void launch_mlp_infer_fused(const uint2 *frag, const float *theta, const DevMesh &m, const float *own, float *logits,
+                            uint8_t *flags, cudaStream_t s);
 void launch_quantize(const float *theta, float *theta_q, cudaStream_t s);
 void launch_dense_fwd(const float *A, int in_dim, const float *W, const float *b, int out_dim, long long n, float *Z,
                       bool relu, cudaStream_t s);

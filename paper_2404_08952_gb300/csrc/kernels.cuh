@@ -155,7 +155,7 @@ DOL_HD constexpr int diff_batch(int rec_values) { return rec_values <= 8 ? 4 : (
 // One differential pass over a group of nt threads (thread t of the group, global
 // thread index gt of the pass; for LPC = 1 the group's cells start at c0 and its
 // output records are staged in smo and written by thread 0 with one bulk copy).
-template <int DIM, int NV, int M, int PREC, int LPC>
+template <int DIM, int NV, int M, int PREC, int LPC, int UBF = 0>
 __device__ __forceinline__ void diff_cells(const DevMesh &mesh, const void *__restrict__ in_v, void *__restrict__ out_v,
                                            long long gt, int t, int nt, long long c0, unsigned char *smo)
 {
@@ -182,7 +182,7 @@ __device__ __forceinline__ void diff_cells(const DevMesh &mesh, const void *__re
         // few registers to spare for a batch) those of the next batch are requested
         // before the current batch is summed.  The sums keep the order own term, then
         // slots in order.
-        constexpr int UB = diff_batch(NV * CI);
+        constexpr int UB = UBF > 0 ? UBF : diff_batch(NV * CI);   // UBF: a batch size forced by the caller
         constexpr bool PREFETCH = UB <= 2;
         R kx[UB], ky[UB], kz[UB];
         int nbv[UB];
@@ -299,8 +299,8 @@ __global__ void __launch_bounds__(256) k_diff(DevMesh mesh, const void *__restri
 // the second half finds in L1: one read of the Gauss weights for two passes (the order
 // a stage does not read, with the next stage's first order).  Each half is the
 // one-thread-per-cell pass (diff_cells), so every output is bit-identical to it.
-template <int DIM, int NV, int MA, int PREC, int CB>
-__global__ void __launch_bounds__(2 * CB) k_diff_dual(DevMesh mesh, const void *__restrict__ inA, void *__restrict__ outA,
+template <int DIM, int NV, int MA, int PREC, int CB, int MINB = 1>
+__global__ void __launch_bounds__(2 * CB, MINB) k_diff_dual(DevMesh mesh, const void *__restrict__ inA, void *__restrict__ outA,
                                                       const void *__restrict__ inB, void *__restrict__ outB)
 {
     // both halves stage their records for a bulk copy, i.e. pass one __syncthreads
@@ -310,8 +310,10 @@ __global__ void __launch_bounds__(2 * CB) k_diff_dual(DevMesh mesh, const void *
     extern __shared__ __align__(16) unsigned char smo[];
     const int t = threadIdx.x % CB;
     const long long c0 = (long long)blockIdx.x * CB;
+    // the order-MA half gathers one slot per batch (the other half's loads are in flight
+    // meanwhile): fewer registers, the same sums in the same order
     if (threadIdx.x < CB)
-        diff_cells<DIM, NV, MA, PREC, 1>(mesh, inA, outA, c0 + t, t, CB, c0, smo);
+        diff_cells<DIM, NV, MA, PREC, 1, 1>(mesh, inA, outA, c0 + t, t, CB, c0, smo);
     else
         diff_cells<DIM, NV, 1, PREC, 1>(mesh, inB, outB, c0 + t, t, CB, c0,
                                         smo + (size_t)CB * ord_stride<DIM, NV, MA, PREC>() *
@@ -975,14 +977,15 @@ __global__ void __launch_bounds__(256) k_gather(DevMesh mesh, StageArgs a)
         }
     };
     if (s1 - s0 == 4 && (s0 & 3) == 0) {
-        // the four (neighbour, word) pairs of a four-slot cell (tetrahedron, quad): one
-        // aligned 32-byte load
-        unsigned w[8];
-        ldg32(mesh.slot2 + s0, w);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) slot(w[2 * j + 1]);
+        // the four slot words of a four-slot cell (tetrahedron, quad): one aligned
+        // 16-byte load
+        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(mesh.sword + s0));
+        slot(w.x);
+        slot(w.y);
+        slot(w.z);
+        slot(w.w);
     } else {
-        for (int s = s0; s < s1; ++s) slot((unsigned)__ldg(mesh.slot2 + s).y);
+        for (int s = s0; s < s1; ++s) slot(__ldg(mesh.sword + s));
     }
     cell_epilogue<DIM, NV, PREC>(mesh, a, c, res);
 }

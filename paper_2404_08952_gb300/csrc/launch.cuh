@@ -251,8 +251,10 @@ template <int DIM, int NV, int NS, int PREC> struct Path {
         } else {
             if (dry) return true;
             constexpr int CB = 64;
-            k_diff_dual<DIM, NV, 2, PREC, CB><<<nblk(m.n_cells, CB), 2 * CB, (size_t)CB * (ra + rb), s>>>(m, inA, outA,
-                                                                                                          inB, outB);
+            // bulk precisions fit 8 blocks per SM (64 registers, no spills); FP64 does not
+            constexpr int MINB = PREC == PREC_F64 ? 1 : 8;
+            k_diff_dual<DIM, NV, 2, PREC, CB, MINB><<<nblk(m.n_cells, CB), 2 * CB, (size_t)CB * (ra + rb), s>>>(
+                m, inA, outA, inB, outB);
             return true;
         }
     }

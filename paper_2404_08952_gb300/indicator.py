@@ -16,8 +16,8 @@ default here.
 """
 import numpy as np
 
-from . import (MLP, Mesh, Scheme, dolinc_criterion, dolinc_indicator_features, dolinc_rk_step, dolinc_set_flags,
-               dolinc_sync_status, workspace)
+from . import (MLP, Mesh, Scheme, dolinc_criterion, dolinc_indicator_features, dolinc_indicator_infer, dolinc_rk_step,
+               dolinc_set_flags, dolinc_sync_status, workspace)
 
 
 def riemann_runs(make_workload, seeds, steps, sample_every, precision="fp32", kappa=4.0, eps=1e-3,
@@ -92,7 +92,6 @@ def run_with(w, switch, steps, precision="fp32", net=None, kappa=4.0, eps=1e-3, 
         dolinc_set_flags(M, flags)
     ws = workspace(M, sch)
     u = torch.from_numpy(M.to_lib(w["u0"])).cuda()
-    x = torch.zeros((M.n_cells, 24), dtype=torch.float32, device="cuda") if switch == "network" else None
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     frac = 0.0
     torch.cuda.synchronize()
@@ -101,8 +100,7 @@ def run_with(w, switch, steps, precision="fp32", net=None, kappa=4.0, eps=1e-3, 
         if switch == "criterion":
             dolinc_criterion(M, sch, u, flags, ws, kappa, eps)
         elif switch == "network":
-            dolinc_indicator_features(M, sch, u, x, ws)
-            net.forward(x, None, flags)
+            dolinc_indicator_infer(M, sch, net, u, None, flags, ws)     # inputs gathered inside the network kernel
         dolinc_rk_step(M, sch, w["dt"], u, ws)
     e1.record()
     torch.cuda.synchronize()

@@ -92,6 +92,29 @@ def test_network_inputs(name, prec):
         assert abs(got[c, 6::6][:3].sum() - want[c, 6::6][:3].sum()) <= 3 * tol, c
 
 
+@pytest.mark.parametrize("name", ["riemann2d", "tet3d"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fused_inference_equals_features_then_network(name, prec):
+    """dolinc_indicator_infer without an input buffer gathers each cell's 24 inputs
+    inside the network kernel; logits and flags equal the features pass followed by
+    the network on the written inputs, bit for bit."""
+    w = case(name)
+    M = dg.Mesh(w["mesh"])
+    sch = dg.Scheme(precision=prec, **w["scheme"])
+    ws = dg.workspace(M, sch)
+    net = dg.MLP(seed=5)
+    u = dev(M, w["u0"])
+    x = torch.zeros((M.n_cells, 24), dtype=torch.float32, device="cuda")
+    out = []
+    for buf in (x, None):
+        lg = torch.zeros(M.n_cells, dtype=torch.float32, device="cuda")
+        fl = torch.zeros(M.n_cells, dtype=torch.uint8, device="cuda")
+        dg.dolinc_indicator_infer(M, sch, net, u, buf, fl, ws, logits=lg)
+        out.append((lg.cpu().numpy(), fl.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert 0 < out[0][1].sum() < M.n_cells or np.abs(out[0][0]).max() > 0
+
+
 def test_tensor_core_inference_matches_bf16_reference():
     rng = np.random.default_rng(3)
     theta = omlp.init(7)
