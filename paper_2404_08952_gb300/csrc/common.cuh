@@ -409,6 +409,55 @@ __device__ __forceinline__ void dolinc_weights(int k, int r, R g, R *W0, R *W1)
     for (int m = 0; m <= NS; ++m) { W0[m] = wt[NS][m]; W1[m] = wt[NS + 1][m]; }
 }
 
+// Both orientations' weights: (W0f, W1f) at g and (W0r, W1r) at 1/g (the neighbour-
+// upwind orientation).  For the closed-form stencils (2,1), (3,1), (4,1) the 1/g
+// weights are polynomials in g over the same denominator (multiplying Eq coeff's
+// closed forms through by g^(k-1) etc.), so one reciprocal serves both:
+//   (2,1): W0r = ((2g+1), g) iv,  W1r = (-g, 0) iv,                 iv = 1/G2
+//   (3,1): W0r = ((g^2+3g+1), g) iv,  W1r = (g(g^2+g-1), 0) iv,     iv = 1/(G2 G3)
+//   (4,1): W0r = ((-g^4+g^3+2g^2+3g+1), g) iv,
+//          W1r = ((g^5+3g^4+2g^3+g^2-g), -g^4) iv,                   iv = 1/(G3 G4)
+template <int NS, class R>
+__device__ __forceinline__ void dolinc_weights_both(int k, int r, R g, R *W0f, R *W1f, R *W0r, R *W1r)
+{
+    if (r == 1 && k >= 2 && k <= 4) {
+#pragma unroll
+        for (int m = 0; m <= NS; ++m) W0f[m] = W1f[m] = W0r[m] = W1r[m] = (R)0;
+        const R g2 = g * g;
+        if (k == 2) {
+            const R iv = rcp_bulk((R)1 + g);
+            W0f[0] = ((R)2 + g) * iv;
+            W0f[1] = iv;
+            W1f[0] = -iv;
+            W0r[0] = ((R)2 * g + (R)1) * iv;
+            W0r[1] = g * iv;
+            W1r[0] = -g * iv;
+        } else if (k == 3) {
+            const R iv = rcp_bulk(((R)1 + g) * ((R)1 + g + g2));
+            W0f[0] = g * ((R)1 + (R)3 * g + g2) * iv;
+            W0f[1] = g2 * iv;
+            W1f[0] = ((R)1 + g - g2) * iv;
+            W0r[0] = (g2 + (R)3 * g + (R)1) * iv;
+            W0r[1] = g * iv;
+            W1r[0] = g * (g2 + g - (R)1) * iv;
+        } else {
+            const R g3 = g2 * g, g4 = g2 * g2;
+            const R iv = rcp_bulk(((R)1 + g + g2) * ((R)1 + g + g2 + g3));
+            W0f[0] = (-g + g2 + (R)2 * g3 + (R)3 * g4 + g4 * g) * iv;
+            W0f[1] = g4 * iv;
+            W1f[0] = ((R)1 + (R)3 * g + (R)2 * g2 + g3 - g4) * iv;
+            W1f[1] = -g * iv;
+            W0r[0] = (-g4 + g3 + (R)2 * g2 + (R)3 * g + (R)1) * iv;
+            W0r[1] = g * iv;
+            W1r[0] = (g4 * g + (R)3 * g4 + (R)2 * g3 + g2 - g) * iv;
+            W1r[1] = -g4 * iv;
+        }
+        return;
+    }
+    dolinc_weights<NS, R>(k, r, g, W0f, W1f);
+    dolinc_weights<NS, R>(k, r, rcp_bulk(g), W0r, W1r);
+}
+
 // ------------------------------------------------------------------ lane groups
 // Sum of v[0..P) over the LPC lanes of an aligned group (LPC a power of two dividing
 // 32), by recursive halving: on return lane j of the group holds the total of

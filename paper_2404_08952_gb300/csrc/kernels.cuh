@@ -549,9 +549,11 @@ __device__ __forceinline__ void face_states_dolinc(const StageArgs &a, const Src
             return;
         }
     }
-    R W0[NS + 1], W1[NS + 1];
+    R W0[NS + 1], W1[NS + 1], V0[NS + 1], V1[NS + 1];
+    if constexpr (!UPWIND_ONLY)
+        dolinc_weights_both<NS, R>(a.k, a.r, g, W0, W1, V0, V1);     // both orientations, one reciprocal
     if (!UPWIND_ONLY || want_left) {
-        dolinc_weights<NS, R>(a.k, a.r, g, W0, W1);
+        if constexpr (UPWIND_ONLY) dolinc_weights<NS, R>(a.k, a.r, g, W0, W1);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             R s = (R)0;
@@ -562,13 +564,13 @@ __device__ __forceinline__ void face_states_dolinc(const StageArgs &a, const Src
     }
     if (!UPWIND_ONLY || !want_left) {
         // neighbour upwind: d -> -d, g -> 1/g, phi^(m) -> (-1)^m phi^(m)
-        dolinc_weights<NS, R>(a.k, a.r, rcp_bulk(g), W0, W1);
+        if constexpr (UPWIND_ONLY) dolinc_weights<NS, R>(a.k, a.r, rcp_bulk(g), V0, V1);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             R s = (R)0;
 #pragma unroll
             for (int m = 0; m <= NS; ++m) {
-                R t = fma(W0[m], phN[v][m], W1[m] * phP[v][m]);
+                R t = fma(V0[m], phN[v][m], V1[m] * phP[v][m]);
                 s = (m & 1) ? s - t : s + t;
             }
             UR[v] = s;
