@@ -198,3 +198,51 @@ def test_partitioned_residual_equals_whole_mesh(lib, name, world):
     assert sum(o[3] for o in out) == case(name)["u0"].shape[1]     # every cell owned once
     for rank, same, diff, _ in out:
         assert same, (rank, diff)
+
+
+def _collective_worker(rank, world, port, name, q):
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        m = CASES[name]()["mesh"]
+        pc = dg.dolinc_partition(m, world)
+        plan = dg.dolinc_part_plan(m, pc, world, rank)
+        lc = plan["local_cells"]
+        rb = 16                                        # a 16-byte record: the caller id, twice
+        ns, nr = len(plan["send_cells"]), len(plan["recv_cells"])
+        ws = torch.zeros(256 + rb * (ns + nr), dtype=torch.uint8)
+        send = ws[256:256 + rb * ns].view(torch.int64).view(ns, 2)
+        send[:, 0] = torch.from_numpy(lc[plan["send_cells"]])
+        send[:, 1] = -send[:, 0]
+        h = dg.Halo.__new__(dg.Halo)
+        h.pending, h.order, h.record_bytes = 1, 0, rb
+        h.send_dev, h.recv_dev = ws.data_ptr() + 256, ws.data_ptr() + 256 + rb * ns
+        holder = type("PartMesh", (), {"plan": plan})()
+        dg.exchange_collective(dist, holder, ws)(h)
+        got = ws[256 + rb * ns:].view(torch.int64).view(nr, 2).numpy()
+        want = lc[plan["recv_cells"]]
+        q.put((rank, bool(np.array_equal(got[:, 0], want) and np.array_equal(got[:, 1], -want))))
+    finally:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("name,world", [("tet_euler", 2), ("hexprism_order5", 3)])
+def test_exchange_collective_delivers_each_ghost_record(lib, name, world):
+    """The package's exchange (torch.distributed point-to-point, here over gloo on CPU
+    tensors) moves each peer's send region into this rank's receive region: every
+    ghost receives its owner's record, in the plan's order."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    qu = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_collective_worker, args=(r, world, port, name, qu)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = sorted(qu.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert all(ok for _, ok in out), out
