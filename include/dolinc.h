@@ -523,9 +523,11 @@ typedef struct {
  * not read) and stops at the first exchange with *halo filled; each
  * dolinc_part_step_continue takes the received records into the ghosts and runs to the
  * next exchange, or to the end of the step (halo->pending = 0; u then holds the own
- * cells' new state; the ghosts' entries are meaningless).  All launches on `stream`;
- * the exchange must be ordered on it too.  Errors: INVALID_ARG (not a part mesh,
- * continue without a step in progress, workspace), as dolinc_rk_step otherwise. */
+ * cells' new state; the ghosts' entries are meaningless, and must hold finite values
+ * when the step begins).  One step uses one scheme, workspace and stream from begin to
+ * its end; a begin abandons a step in progress.  All launches on `stream`; the
+ * exchange must be ordered on it too.  Errors: INVALID_ARG (not a part mesh, continue
+ * without a step in progress, workspace), as dolinc_rk_step otherwise. */
 dolinc_status dolinc_part_step_begin(dolinc_mesh *mesh, const dolinc_scheme *scheme, double dt, double *u_dev,
                                      void *ws_dev, size_t ws_bytes, dolinc_stream stream, dolinc_halo *halo);
 dolinc_status dolinc_part_step_continue(dolinc_mesh *mesh, const dolinc_scheme *scheme, void *ws_dev,
