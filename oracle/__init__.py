@@ -388,3 +388,71 @@ class Oracle:
         for _ in range(steps):
             u = self.rk3_step(u, scheme, dt)
         return u
+
+    # ------------------------------------------------------------ semi-implicit step
+    # Sec 2.4 (Eq USR3, Eq CSR4): a DOLINC face value splits into the weight part of the
+    # two face cells and a remainder,  phi_f = w_s phi_up + (1 - w_s) phi_down + c_r,
+    # w_s the weight of the upwind cell; under an implicit time integration the weight
+    # part enters the matrix and c_r (the inverted far-field data) stays explicit, a
+    # semi-implicit scheme.  Linear advection (flux "upwind", one variable) on meshes
+    # whose boundary faces are zero-gradient.
+
+    def _split_faces(self, scheme):
+        if scheme.flux != "upwind" or scheme.nv != 1:
+            raise ValueError("the semi-implicit step is for linear advection (flux 'upwind', nv = 1)")
+        if scheme.bkind is not None and np.any(np.isin(scheme.bkind[self.neigh < 0], (2, 3))):
+            raise ValueError("the semi-implicit step takes zero-gradient boundary faces only")
+        D = self.dim
+        an = self.S[:, :D] @ np.asarray(scheme.adv[:D], dtype=np.float64)     # a . S_f, owner -> neighbour
+        WL, WR = self.face_weights(scheme)
+        P, Q = self.owner, self.neigh
+        bnd = Q < 0
+        own_up = an >= 0.0
+        # weights of the owner's and the neighbour's averages in the upwind face value
+        cP = np.where(bnd, 1.0, np.where(own_up, WL[:, 0, 0], WR[:, 1, 0]))
+        cQ = np.where(bnd, 0.0, np.where(own_up, WL[:, 1, 0], WR[:, 0, 0]))
+        return an, P, np.where(bnd, P, Q), bnd, cP, cQ
+
+    def implicit_operator(self, scheme):
+        """K (scipy CSR, n_cells x n_cells): (K u)_c is the sum over the faces of c of
+        the outward flux a.S (w_s u_up + (1 - w_s) u_down), the weight part of every
+        face value (boundary faces: a.S u_c)."""
+        import scipy.sparse as sp
+        an, P, Q, bnd, cP, cQ = self._split_faces(scheme)
+        it = ~bnd
+        rows = np.concatenate([P, P, Q[it], Q[it]])
+        cols = np.concatenate([P, Q, P[it], Q[it]])
+        vals = np.concatenate([an * cP, an * cQ, -(an * cP)[it], -(an * cQ)[it]])
+        return sp.csr_matrix((vals, (rows, cols)), shape=(self.n_cells, self.n_cells))
+
+    def explicit_correction(self, u, scheme):
+        """C(u) (n_cells): the sum over the faces of c of the outward a.S c_r, with
+        c_r = phi_f - w_s u_up - (1 - w_s) u_down from the DOLINC face values of u."""
+        u = np.ascontiguousarray(np.atleast_2d(u), dtype=np.float64)
+        an, P, Q, bnd, cP, cQ = self._split_faces(scheme)
+        phiL, phiR, _, _ = self.face_values(u, scheme)
+        phi = np.where(an >= 0.0, phiL[0], phiR[0])
+        Fc = an * (phi - cP * u[0, P] - cQ * u[0, Q])
+        out = np.zeros(self.n_cells)
+        np.add.at(out, P, Fc)
+        np.add.at(out, Q[~bnd], -Fc[~bnd])
+        return out
+
+    def semi_implicit_step(self, u, scheme, dt, theta=1.0, n_outer=1):
+        """One theta-scheme step with the weight part implicit and c_r explicit:
+            V (u' - u) / dt = -theta K u' - (1 - theta) K u - C(u),
+        solved directly (sparse LU).  n_outer > 1 repeats the solve with the c_r of the
+        latest iterate taken at the new level,
+            V (u^(k+1) - u) / dt = -theta K u^(k+1) - (1 - theta) (K u + C(u)) - theta C(u^(k)),
+        whose fixed point is the theta scheme of the full DOLINC operator."""
+        import scipy.sparse as sp
+        import scipy.sparse.linalg as spl
+        u = np.array(np.atleast_2d(u), dtype=np.float64)
+        K = self.implicit_operator(scheme)
+        A = (sp.diags(self.V / dt) + theta * K).tocsc()
+        base = self.V / dt * u[0] - (1.0 - theta) * (K @ u[0] + self.explicit_correction(u, scheme))
+        uk = u
+        for _ in range(max(int(n_outer), 1)):
+            rhs = base - theta * self.explicit_correction(uk, scheme)
+            uk = spl.spsolve(A, rhs)[None, :]
+        return uk
