@@ -204,7 +204,7 @@ def kernel_bytes(kind, M, sch):
     return data + state + geo
 
 
-KINDS = ["pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces", "diff_pair"]
+KINDS = ["pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces", "diff_pair", "solve"]
 
 
 def _stage_roofline(M, sch, ms_stage, peak):
@@ -915,6 +915,144 @@ def run_hexprism(args):
     print(json.dumps(line), flush=True)
 
 
+def solve_alg_bytes(M, iterations, solves):
+    """Algorithmic bytes of the semi-implicit solve launches: per cell and BiCGSTAB
+    iteration the phases' FP64 vectors (A: r, p, v, rh read, p, v written; B: r, v read,
+    s, t written; C: x, p, s, t, rh read, x, r written) and the scaled rows read in A
+    and B (per slot an 8 B coefficient and a 4 B neighbour, per cell a 4 B offset); per
+    solve the set-up (R and the row scale read; x, r, rh, p, v written) and the final
+    u += x (x, u read, u written).  Neighbour re-reads are not counted."""
+    nc, ns = M.n_cells, M.n_slots
+    per_it = nc * 8 * (6 + 4 + 7) + 2 * (ns * 12 + nc * 4)
+    per_solve = nc * 8 * (2 + 5) + nc * 8 * 3
+    return iterations * per_it + solves * per_solve
+
+
+def run_implicit(args):
+    """Semi-implicit DOLINC steps (Sec 2.4: the weight part of every face value at the
+    new level, c_r explicit) of the Gaussian pulse on the mixed hex/prism mesh.
+
+    Throughput of one step (explicit residual + one BiCGSTAB solve in one cooperative
+    launch) at dt = imp_dt_factor times the explicit step, for backward Euler and
+    Crank-Nicolson (one and two outer iterations), FP32 and FP64 residuals, orders 3
+    and 5; the solve kernel's roofline; and, to t = imp_time, the L2 error against the
+    exact translated pulse beside SSP-RK3 at the explicit step, with each run's time."""
+    import synth
+    from synth import fields
+    t_all = time.perf_counter()
+    workers = max(1, min(16, os.cpu_count() or 1))
+    size = args.size or 140
+    w = synth.workload("adv3d_hexprism", order=3, size=size, q=args.hp_quad, workers=workers)
+    a = np.asarray(w["scheme"]["adv"], dtype=np.float64)
+    T = args.imp_time
+    c = tuple(0.5 + a[k] * T for k in range(3))
+    exact = fields.cell_average(w["mesh"], lambda p: fields.gaussian3d(p, centre=c), q=args.hp_quad, workers=workers)
+    t_host = time.perf_counter() - t_all
+    import torch
+    import paper_2404_08952_gb300 as dg
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    M = dg.Mesh(w["mesh"], renumber="morton")
+    cells = M.n_cells
+    V = M.from_lib(M.geometry()["V"])
+    peak, peak_src = _peaks()
+    dt_exp = w["dt"]
+    dt = args.imp_dt_factor * dt_exp
+    h = 1.0 / size
+    forms = [("fp32", 3, 1.0, 1), ("fp64", 3, 1.0, 1), ("fp32", 3, 0.5, 1), ("fp32", 3, 0.5, 2), ("fp32", 5, 1.0, 1),
+             ("fp32", 5, 0.5, 2)]
+
+    def l2(u):
+        e = M.from_lib(u.cpu().numpy())[0] - exact[0]
+        return float(np.sqrt((V * e * e).sum() / V.sum()))
+
+    def timed_steps(fn, n):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    out = {}
+    for prec, order, theta, n_outer in forms:
+        k, r = synth.STENCIL_OF_ORDER[order]
+        sch = dg.Scheme(precision=prec, **dict(w["scheme"], k=k, r=r, n_diff=order - 1))
+        ws = dg.workspace(M, sch)
+        S = dg.Implicit(M, sch, dt, theta)
+        S.set_solver(rel_tol=args.imp_tol, max_iter=500)
+        u = torch.from_numpy(M.to_lib(w["u0"])).cuda()
+        for _ in range(args.warmup):
+            S.step(u, ws, n_outer)
+        i0 = S.info()
+        dg.dolinc_profile_enable(M, True)
+        ms = timed_steps(lambda: S.step(u, ws, n_outer), args.steps)
+        i1 = S.info()
+        kms, kn = dg.profile_read(M)
+        dg.dolinc_profile_enable(M, False)
+        iters = i1["total_iterations"] - i0["total_iterations"]
+        solves = i1["total_solves"] - i0["total_solves"]
+        ks = KINDS.index("solve")
+        solve_ms = kms[ks] / max(kn[ks], 1)
+        ab = solve_alg_bytes(M, iters / max(solves, 1), 1)
+        gbs = ab / (solve_ms / 1e3) / 1e9
+        # accuracy to T: the implicit steps, dt rounded to divide T
+        nI = int(np.ceil(T / dt - 1e-9))
+        S2 = dg.Implicit(M, sch, T / nI, theta)
+        S2.set_solver(rel_tol=args.imp_tol, max_iter=500)
+        u = torch.from_numpy(M.to_lib(w["u0"])).cuda()
+        conv = True
+        its = []
+        for _ in range(nI):
+            S2.step(u, ws, n_outer)
+            inf = S2.info()
+            conv = conv and inf["converged"]
+            its.append(inf["iterations"])
+        u = torch.from_numpy(M.to_lib(w["u0"])).cuda()
+        ms_T = timed_steps(lambda: S2.step(u, ws, n_outer), nI)
+        name = "%s_order%d_theta%g_outer%d" % (prec, order, theta, n_outer)
+        out[name] = {
+            "value": cells * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+            "iterations_per_solve": iters / max(solves, 1), "solves": solves, "launches": int(sum(kn)),
+            "kernel_ms_share": {KINDS[i]: round(kms[i] / sum(kms), 4) for i in range(len(KINDS)) if kn[i]},
+            "solve_roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                               "frac": round(gbs / peak, 4), "alg_bytes_per_cell_iteration":
+                                   round(solve_alg_bytes(M, 1, 0) / cells, 1), "ms_per_solve": round(solve_ms, 4)},
+            "to_time": {"t": T, "steps": nI, "dt": T / nI, "l2": l2(u), "converged": conv,
+                        "iterations_per_step": its, "ms": round(ms_T, 3)}}
+        del ws, S, S2, u
+    # SSP-RK3 at the explicit step to the same time
+    expl = {}
+    for prec, order in (("fp32", 3), ("fp32", 5)):
+        k, r = synth.STENCIL_OF_ORDER[order]
+        sch = dg.Scheme(precision=prec, **dict(w["scheme"], k=k, r=r, n_diff=order - 1))
+        ws = dg.workspace(M, sch)
+        u = torch.from_numpy(M.to_lib(w["u0"])).cuda()
+        dg.dolinc_autotune(M, sch, u, ws)
+        nE = int(np.ceil(T / dt_exp - 1e-9))
+        dg.dolinc_rk_steps(M, sch, T / nE, 2, u, ws)
+        u = torch.from_numpy(M.to_lib(w["u0"])).cuda()
+        msE = timed_steps(lambda: dg.dolinc_rk_steps(M, sch, T / nE, nE, u, ws), 1)
+        expl["%s_order%d_rk3" % (prec, order)] = {"steps": nE, "dt": T / nE, "ms": round(msE, 3), "l2": l2(u)}
+        del ws, u
+    main = out["fp32_order3_theta1_outer1"]
+    line = {"metric": "cell-updates/s per semi-implicit step (residual + linear solve)", "value": main["value"],
+            "unit": "cell-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 residual, f64 solve", "data": "synthetic",
+            "config": {"workload": "adv3d_hexprism_implicit", "lattice": size, "cells": cells,
+                       "headline": "fp32_order3_theta1_outer1", "flux": "upwind", "adv": list(w["scheme"]["adv"]),
+                       "jitter": 0.2, "dt": dt, "dt_explicit": dt_exp, "cfl_sum": float(np.abs(a).sum() * dt / h),
+                       "rel_tol": args.imp_tol, "time": T, "quad": args.hp_quad, "peak_GBs": peak,
+                       "peak_source": peak_src, "l2_flush": "inputs larger than L2 (vectors and rows > 300 MB)"},
+            "roofline": main["solve_roofline"], "gpu_launches": main["launches"],
+            "forms": out, "explicit_rk3": expl, "host_input_seconds": round(t_host, 1),
+            "seconds_total": time.perf_counter() - t_all}
+    print(json.dumps(line), flush=True)
+
+
 def bl_mesh(growth, h0=0.002, ymax=0.3, nx=12, nz=3, x0=0.5, x1=1.0, dz=0.01):
     """Boundary-layer mesh: hexes over x in [x0, x1] (transmissive ends), wall-normal
     spacing h0 growing by `growth` up to ymax, nz cells of width dz across
@@ -1088,6 +1226,9 @@ def main():
     ap.add_argument("--hp-time", type=float, default=0.05, help="adv3d_hexprism convergence end time")
     ap.add_argument("--hp-quad", type=int, default=3, help="adv3d_hexprism quadrature points per direction")
     ap.add_argument("--stab-time", type=float, default=0.4, help="euler3d_tet64 stability runs: end time")
+    ap.add_argument("--imp-dt-factor", type=float, default=16.0, help="semi-implicit dt / explicit dt")
+    ap.add_argument("--imp-time", type=float, default=0.1, help="semi-implicit accuracy runs: end time")
+    ap.add_argument("--imp-tol", type=float, default=1e-8, help="semi-implicit solver relative tolerance")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -1099,6 +1240,8 @@ def main():
         run_batch(args)
     elif args.workload == "adv3d_hexprism":
         run_hexprism(args)
+    elif args.workload == "adv3d_hexprism_implicit":
+        run_implicit(args)
     elif args.workload == "blasius_bl":
         run_blasius(args)
     else:

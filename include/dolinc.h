@@ -417,13 +417,14 @@ dolinc_status dolinc_sync_status(dolinc_mesh *mesh, void *ws_dev, dolinc_stream 
  * differential pass producing order m), DOLINC_KERNEL_STAGE (reconstruction + flux +
  * residual + update), DOLINC_KERNEL_FACES (dolinc_reconstruct_faces),
  * DOLINC_KERNEL_DIFF_PAIR (one stage's order-2 pass fused with the next stage's
- * order-1 pass, under the paired schedule of dolinc_set_tuning's diff_lanes = 2).
+ * order-1 pass, under the paired schedule of dolinc_set_tuning's diff_lanes = 2),
+ * DOLINC_KERNEL_SOLVE (one linear solve of dolinc_implicit_step).
  * dolinc_profile_enable resets the counters.  dolinc_profile_read waits for the
  * recorded events and fills ms[DOLINC_KERNEL_COUNT] (summed device time) and
  * launches[DOLINC_KERNEL_COUNT]; either pointer may be NULL. */
 enum { DOLINC_KERNEL_PACK = 0, DOLINC_KERNEL_DIFF1 = 1, DOLINC_KERNEL_DIFF2 = 2, DOLINC_KERNEL_DIFF3 = 3,
        DOLINC_KERNEL_DIFF4 = 4, DOLINC_KERNEL_STAGE = 5, DOLINC_KERNEL_FACES = 6, DOLINC_KERNEL_DIFF_PAIR = 7,
-       DOLINC_KERNEL_COUNT = 8 };
+       DOLINC_KERNEL_SOLVE = 8, DOLINC_KERNEL_COUNT = 9 };
 dolinc_status dolinc_profile_enable(dolinc_mesh *mesh, int enable);
 dolinc_status dolinc_profile_read(dolinc_mesh *mesh, double *ms, int64_t *launches);
 
@@ -532,6 +533,73 @@ dolinc_status dolinc_part_step_begin(dolinc_mesh *mesh, const dolinc_scheme *sch
                                      void *ws_dev, size_t ws_bytes, dolinc_stream stream, dolinc_halo *halo);
 dolinc_status dolinc_part_step_continue(dolinc_mesh *mesh, const dolinc_scheme *scheme, void *ws_dev,
                                         size_t ws_bytes, dolinc_stream stream, dolinc_halo *halo);
+
+/* ------------------------------------------------------------ semi-implicit step
+ * Sec 2.4 (Eq USR3, Eq CSR4): a DOLINC face value is  w_s phi_up + (1 - w_s) phi_down
+ * + c_r,  the weights w_s, 1 - w_s of the two face cells' averages plus c_r, the part
+ * that carries the inverted far-field data.  The paper notes that under an implicit
+ * time integration this gives a semi-implicit scheme: the weight part is taken at the
+ * new time level, c_r stays explicit.  For linear advection (flux UPWIND, nv = 1) and
+ * theta in [0, 1] one step solves
+ *     V (u' - u) / dt = -theta K u' - (1 - theta) K u - C(u),
+ * (K x)_c = sum over the faces of c of a.S_{c,f} (w_s x_up + (1 - w_s) x_down), with
+ * a.S u_c on a zero-gradient boundary face, and C(u)_c the sum of a.S_{c,f} c_r.  In
+ * delta form  (V/dt + theta K) delta = V R(u),  R the explicit DOLINC residual of the
+ * scheme (dolinc_residual: differentials, reconstruction, flux; at the scheme's
+ * precision and with its limiter and the mesh's skewness correction), u' = u + delta.
+ * The rows are scaled by their diagonal and solved by BiCGSTAB in FP64, all iterations
+ * in one cooperative launch, to ||b - A delta|| <= rel_tol ||b|| on the scaled rows.
+ * theta = 0 is the explicit forward Euler step.
+ *
+ * n_outer > 1 repeats the solve with c_r of the latest iterate at the new level
+ * (deferred correction):
+ *     V (u^(k+1) - u) / dt = -theta K u^(k+1) - (1 - theta) (K u + C(u)) - theta C(u^(k));
+ * its fixed point is the theta scheme of the full DOLINC operator.
+ *
+ * dolinc_implicit_create assembles the rows on the mesh's device (the mesh must outlive
+ * the solver) and waits for them.  Errors: UNSUPPORTED for another flux, nv != 1,
+ * Dirichlet/Neumann faces or a part mesh; INVALID_ARG for dt <= 0 or theta outside
+ * [0, 1]; OOM. */
+typedef struct dolinc_implicit dolinc_implicit;
+dolinc_status dolinc_implicit_create(dolinc_mesh *mesh, const dolinc_scheme *scheme, double dt, double theta,
+                                     dolinc_implicit **out);
+void dolinc_implicit_destroy(dolinc_implicit *solver);
+
+/* Solver limits: relative tolerance (default 1e-10), iterations per solve (default
+ * 1000), and the polls a grid-barrier wait makes before it gives up (default 2^23). */
+dolinc_status dolinc_implicit_set_solver(dolinc_implicit *solver, double rel_tol, int max_iter,
+                                         unsigned spin_limit);
+
+/* One step on u_dev (FP64 [cell], library order, in place), n_outer >= 1 solves.  ws:
+ * a workspace of the mesh and scheme (dolinc_workspace_size), used for the residual.
+ * All launches on `stream`, asynchronous.  A solve that stops at max_iter or breaks
+ * down still applies its last iterate; dolinc_implicit_info reports it. */
+dolinc_status dolinc_implicit_step(dolinc_implicit *solver, double *u_dev, int n_outer, void *ws_dev,
+                                   size_t ws_bytes, dolinc_stream stream);
+
+/* The last step's solves: iterations summed over them, their number, whether all
+ * reached rel_tol, whether one broke down (a zero BiCGSTAB denominator), and the last
+ * solve's final ||b - A delta|| / ||b||; and the iterations and solves of every step
+ * since the solver was created.  Waits for the last step's stream.
+ * DOLINC_ERR_DEVICE_TIMEOUT if a grid-barrier wait gave up: that solve stopped in
+ * every block and the step's result is not valid. */
+typedef struct {
+    int iterations;
+    int solves;
+    int converged;
+    int breakdown;
+    double rel_residual;
+    int64_t total_iterations;
+    int64_t total_solves;
+} dolinc_solve_info;
+dolinc_status dolinc_implicit_info(dolinc_implicit *solver, dolinc_solve_info *info);
+
+/* Host copies of the assembled rows of V/dt + theta K, library order: row_offsets
+ * [n_cells + 1] (the mesh's face slots), nbr [n_slots] the neighbour of each slot,
+ * off [n_slots] its coefficient in the row (a cell can be its own neighbour across a
+ * periodic face), diag [n_cells]. */
+dolinc_status dolinc_implicit_rows(const dolinc_implicit *solver, int32_t *row_offsets, int32_t *nbr, double *off,
+                                   double *diag);
 
 /* Message of the calling thread's last failing call ("" if none). */
 const char *dolinc_last_error(void);

@@ -34,9 +34,11 @@ ABI_SYMBOLS = (
     "dolinc_batch_info", "dolinc_batch_set_spin_limit", "dolinc_batch_workspace_size", "dolinc_batch_rk_step",
     "dolinc_batch_autotune", "dolinc_partition", "dolinc_part_plan", "dolinc_mesh_create_part",
     "dolinc_mesh_part_sizes", "dolinc_part_step_begin", "dolinc_part_step_continue",
-    "dolinc_mesh_set_skew_correction", "dolinc_last_error",
+    "dolinc_mesh_set_skew_correction", "dolinc_implicit_create", "dolinc_implicit_destroy",
+    "dolinc_implicit_set_solver", "dolinc_implicit_step", "dolinc_implicit_info", "dolinc_implicit_rows",
+    "dolinc_last_error",
 )
-KERNEL_KINDS = ("pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces", "diff_pair")
+KERNEL_KINDS = ("pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces", "diff_pair", "solve")
 
 
 class DolincError(RuntimeError):
@@ -109,12 +111,16 @@ def load(path=LIB_PATH):
             "dolinc_part_step_begin": [P, P, D, P, P, S, P, P],
             "dolinc_part_step_continue": [P, P, P, S, P, P],
             "dolinc_mesh_set_skew_correction": [P, I],
+            "dolinc_implicit_create": [P, P, D, D, P], "dolinc_implicit_destroy": [P],
+            "dolinc_implicit_set_solver": [P, D, I, C.c_uint], "dolinc_implicit_step": [P, P, I, P, S, P],
+            "dolinc_implicit_info": [P, P], "dolinc_implicit_rows": [P, P, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = C.c_char_p if name == "dolinc_last_error" else (
-                None if name in ("dolinc_mesh_destroy", "dolinc_mlp_destroy", "dolinc_batch_destroy") else C.c_int)
+                None if name in ("dolinc_mesh_destroy", "dolinc_mlp_destroy", "dolinc_batch_destroy",
+                                "dolinc_implicit_destroy") else C.c_int)
         _lib = L
     return _lib
 
@@ -565,6 +571,65 @@ class Batch:
         _check(load().dolinc_batch_autotune(self.handle, C.byref(s), _ptr(dt), _ptr(u), _ptr(ws), ws.numel(),
                                             _stream(stream), C.byref(b), C.byref(g), C.byref(ms)))
         return dict(block=b.value, grid=g.value, ms_per_step=ms.value)
+
+
+class _SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("solves", C.c_int), ("converged", C.c_int), ("breakdown", C.c_int),
+                ("rel_residual", C.c_double), ("total_iterations", C.c_int64), ("total_solves", C.c_int64)]
+
+
+class Implicit:
+    """Semi-implicit DOLINC steps of linear advection on one mesh (dolinc_implicit_*):
+    the weight part of every face value at the new level, c_r explicit."""
+
+    def __init__(self, mesh, scheme, dt, theta=1.0):
+        h = C.c_void_p()
+        s = scheme.c()
+        _check(load().dolinc_implicit_create(mesh.handle, C.byref(s), float(dt), float(theta), C.byref(h)))
+        self.handle = h
+        self.mesh, self.scheme, self.dt, self.theta = mesh, scheme, float(dt), float(theta)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.dolinc_implicit_destroy(h)
+            self.handle = None
+
+    def set_solver(self, rel_tol=1e-10, max_iter=1000, spin_limit=1 << 23):
+        _check(load().dolinc_implicit_set_solver(self.handle, float(rel_tol), int(max_iter), int(spin_limit)))
+
+    def step(self, u, ws, n_outer=1, stream=None):
+        _check(load().dolinc_implicit_step(self.handle, _ptr(u), int(n_outer), _ptr(ws), ws.numel(),
+                                           _stream(stream)))
+
+    def info(self):
+        i = _SolveInfo()
+        _check(load().dolinc_implicit_info(self.handle, C.byref(i)))
+        return dict(iterations=i.iterations, solves=i.solves, converged=bool(i.converged),
+                    breakdown=bool(i.breakdown), rel_residual=i.rel_residual,
+                    total_iterations=i.total_iterations, total_solves=i.total_solves)
+
+    def rows(self):
+        """(row_offsets, nbr, off, diag) of V/dt + theta K in library order (host arrays)."""
+        nc, ns = self.mesh.n_cells, self.mesh.n_slots
+        ro = np.zeros(nc + 1, dtype=np.int32)
+        nb = np.zeros(ns, dtype=np.int32)
+        off = np.zeros(ns)
+        dg = np.zeros(nc)
+        _check(load().dolinc_implicit_rows(self.handle, _ptr(ro), _ptr(nb), _ptr(off), _ptr(dg)))
+        return ro, nb, off, dg
+
+
+def dolinc_implicit_create(mesh, scheme, dt, theta=1.0):
+    return Implicit(mesh, scheme, dt, theta)
+
+
+def dolinc_implicit_step(solver, u, ws, n_outer=1, stream=None):
+    solver.step(u, ws, n_outer, stream)
+
+
+def dolinc_implicit_info(solver):
+    return solver.info()
 
 
 class Halo:

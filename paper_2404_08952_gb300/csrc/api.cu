@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/dolinc.h"
+#include "implicit.cuh"
 #include "indicator.cuh"
 #include "launch.cuh"
 #include "mesh.hpp"
@@ -1993,6 +1994,213 @@ dolinc_status dolinc_mesh_set_skew_correction(dolinc_mesh *m, int enable)
         m->d.fdelta32 = nullptr;
     }
     CU(cudaSetDevice(cur));
+    return DOLINC_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ semi-implicit step
+struct dolinc_implicit {
+    dolinc_mesh *m = nullptr;
+    dolinc_scheme s{};
+    double dt = 0.0, theta = 1.0;
+    double rel_tol = 1e-10;
+    int max_iter = 1000;
+    unsigned spin_limit = 1u << 23;
+    int grid = 0, device = 0;
+    int64_t n = 0, ns = 0;
+    void *mem = nullptr;
+    int32_t *nbr = nullptr;
+    double *off = nullptr, *diag = nullptr, *bscale = nullptr;
+    double *vec[9] = {};                 // x r rh p0 p1 v0 v1 s t
+    double *R = nullptr, *Rn = nullptr, *un = nullptr;
+    double *part = nullptr;
+    double *scal = nullptr;              // ctrl block: scalars (256 B), then barrier words and status (512 B)
+    double *life = nullptr;              // [2] iterations and solves since creation (not reset per step)
+    unsigned *bar = nullptr;
+    cudaStream_t last = nullptr;
+    ~dolinc_implicit()
+    {
+        if (!mem) return;
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(device);
+        cudaFree(mem);
+        cudaSetDevice(cur);
+    }
+};
+
+namespace {
+constexpr size_t kImpCtrl = 768;     // scalars 256 B + barrier words [0], [32], [64] and status [96]
+}
+
+extern "C" {
+
+dolinc_status dolinc_implicit_create(dolinc_mesh *m, const dolinc_scheme *s, double dt, double theta,
+                                     dolinc_implicit **out)
+{
+    if (!out) return fail(DOLINC_ERR_INVALID_ARG, "null output");
+    *out = nullptr;
+    dolinc_status st = check_scheme(m, s);
+    if (st) return st;
+    if (s->flux != DOLINC_FLUX_UPWIND || s->nv != 1)
+        return fail(DOLINC_ERR_UNSUPPORTED, "the semi-implicit step is for linear advection (UPWIND flux, nv = 1)");
+    if (m->d.n_bv > 0)
+        return fail(DOLINC_ERR_UNSUPPORTED, "the semi-implicit step takes zero-gradient boundary faces only");
+    if (m->part) return fail(DOLINC_ERR_UNSUPPORTED, "the semi-implicit step solves over a whole mesh, not a part");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DOLINC_ERR_INVALID_ARG, "dt must be positive and finite");
+    if (!(theta >= 0.0 && theta <= 1.0)) return fail(DOLINC_ERR_INVALID_ARG, "theta must be in [0, 1]");
+    std::unique_ptr<dolinc_implicit> imp(new dolinc_implicit);
+    imp->m = m;
+    imp->s = *s;
+    imp->dt = dt;
+    imp->theta = theta;
+    imp->device = m->device;
+    imp->n = m->h.n_cells;
+    imp->ns = m->h.n_slots;
+    int cur = 0;
+    CU(cudaGetDevice(&cur));
+    CU(cudaSetDevice(m->device));
+    int sms = 0;
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+    const int64_t need = (imp->n + IMP_BLOCK - 1) / IMP_BLOCK;
+    const int64_t cap = (int64_t)sms * (int64_t)std::max(imp_solve_blocks_per_sm(), 1);
+    imp->grid = (int)std::max<int64_t>(1, std::min(need, cap));
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t n8 = al(8 * (size_t)std::max<int64_t>(imp->n, 1)), s8 = al(8 * (size_t)std::max<int64_t>(imp->ns, 1));
+    const size_t s4 = al(4 * (size_t)std::max<int64_t>(imp->ns, 1)), pb = al(16 * (size_t)imp->grid);
+    const size_t total = s4 + s8 + 14 * n8 + pb + kImpCtrl + 256;
+    cudaError_t e = cudaMalloc(&imp->mem, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaSetDevice(cur);
+        return fail(DOLINC_ERR_OOM, std::string("implicit solver memory: ") + cudaGetErrorString(e));
+    }
+    char *q = static_cast<char *>(imp->mem);
+    auto take = [&](size_t b) { char *r = q; q += b; return r; };
+    imp->nbr = reinterpret_cast<int32_t *>(take(s4));
+    imp->off = reinterpret_cast<double *>(take(s8));
+    imp->diag = reinterpret_cast<double *>(take(n8));
+    imp->bscale = reinterpret_cast<double *>(take(n8));
+    for (auto &v : imp->vec) v = reinterpret_cast<double *>(take(n8));
+    imp->R = reinterpret_cast<double *>(take(n8));
+    imp->Rn = reinterpret_cast<double *>(take(n8));
+    imp->un = reinterpret_cast<double *>(take(n8));
+    imp->part = reinterpret_cast<double *>(take(pb));
+    imp->scal = reinterpret_cast<double *>(take(kImpCtrl));
+    imp->bar = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(imp->scal) + 256);
+    imp->life = reinterpret_cast<double *>(take(256));
+    CU(cudaMemset(imp->mem, 0, total));
+    launch_imp_assemble(m->d, needed_order(*s), s->k, s->r, s->adv[0], s->adv[1], s->adv[2], dt, theta, imp->nbr,
+                        imp->off, imp->diag, imp->bscale, nullptr);
+    if ((st = launch_check())) {
+        cudaSetDevice(cur);
+        return st;
+    }
+    CU(cudaDeviceSynchronize());
+    CU(cudaSetDevice(cur));
+    *out = imp.release();
+    return DOLINC_OK;
+}
+
+void dolinc_implicit_destroy(dolinc_implicit *imp) { delete imp; }
+
+dolinc_status dolinc_implicit_set_solver(dolinc_implicit *imp, double rel_tol, int max_iter, unsigned spin_limit)
+{
+    if (!imp) return fail(DOLINC_ERR_INVALID_ARG, "null solver");
+    if (!(rel_tol >= 0.0) || !std::isfinite(rel_tol)) return fail(DOLINC_ERR_INVALID_ARG, "rel_tol must be >= 0");
+    if (max_iter < 1) return fail(DOLINC_ERR_INVALID_ARG, "max_iter must be >= 1");
+    imp->rel_tol = rel_tol;
+    imp->max_iter = max_iter;
+    imp->spin_limit = spin_limit;
+    return DOLINC_OK;
+}
+
+dolinc_status dolinc_implicit_step(dolinc_implicit *imp, double *u, int n_outer, void *ws, size_t ws_bytes,
+                                   dolinc_stream stream)
+{
+    if (!imp || !u) return fail(DOLINC_ERR_INVALID_ARG, "null solver or field");
+    if (n_outer < 1) return fail(DOLINC_ERR_INVALID_ARG, "n_outer must be >= 1");
+    dolinc_mesh *m = imp->m;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    CU(cudaMemsetAsync(imp->scal, 0, kImpCtrl, cs));
+    if (n_outer > 1) CU(cudaMemcpyAsync(imp->un, u, 8 * (size_t)imp->n, cudaMemcpyDeviceToDevice, cs));
+    ImpSolve a{};
+    a.n = (int)imp->n;
+    a.row = m->d.off;
+    a.nbr = imp->nbr;
+    a.off = imp->off;
+    a.bscale = imp->bscale;
+    a.inv_dt = 1.0 / imp->dt;
+    a.theta = imp->theta;
+    a.u = u;
+    a.x = imp->vec[0];
+    a.r = imp->vec[1];
+    a.rh = imp->vec[2];
+    a.p[0] = imp->vec[3];
+    a.p[1] = imp->vec[4];
+    a.v[0] = imp->vec[5];
+    a.v[1] = imp->vec[6];
+    a.s = imp->vec[7];
+    a.t = imp->vec[8];
+    a.part = imp->part;
+    a.scal = imp->scal;
+    a.life = imp->life;
+    a.bar = imp->bar;
+    a.status = imp->bar + 96;
+    a.tol2 = imp->rel_tol * imp->rel_tol;
+    a.max_iter = imp->max_iter;
+    a.spin_limit = imp->spin_limit;
+    for (int k = 0; k < n_outer; ++k) {
+        double *Rk = k == 0 ? imp->Rn : imp->R;
+        dolinc_status st = dolinc_residual(m, &imp->s, u, Rk, ws, ws_bytes, stream);
+        if (st) return st;
+        a.R = Rk;
+        a.Rn = k == 0 ? nullptr : imp->Rn;
+        a.un = k == 0 ? nullptr : imp->un;
+        cudaError_t e = cudaSuccess;
+        timed(m, DOLINC_KERNEL_SOLVE, cs, [&] { e = launch_imp_solve(a, imp->grid, cs); });
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(DOLINC_ERR_CUDA, std::string("cooperative launch: ") + cudaGetErrorString(e));
+        }
+    }
+    imp->last = cs;
+    return launch_check();
+}
+
+dolinc_status dolinc_implicit_info(dolinc_implicit *imp, dolinc_solve_info *info)
+{
+    if (!imp || !info) return fail(DOLINC_ERR_INVALID_ARG, "null argument");
+    double sc[SC_COUNT], life[2];
+    unsigned status = 0;
+    CU(cudaStreamSynchronize(imp->last));
+    CU(cudaMemcpy(sc, imp->scal, sizeof sc, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(life, imp->life, sizeof life, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(&status, imp->bar + 96, sizeof status, cudaMemcpyDeviceToHost));
+    info->iterations = (int)sc[SC_ITERS];
+    info->solves = (int)sc[SC_SOLVES];
+    info->breakdown = (status & 4u) ? 1 : 0;
+    info->converged = (status & (2u | 4u | 8u)) ? 0 : 1;
+    info->rel_residual = sc[SC_BB] > 0.0 ? std::sqrt(sc[SC_RR] / sc[SC_BB]) : 0.0;
+    info->total_iterations = (int64_t)life[0];
+    info->total_solves = (int64_t)life[1];
+    if (status & 2u) return fail(DOLINC_ERR_DEVICE_TIMEOUT, "a device-side wait gave up");
+    return DOLINC_OK;
+}
+
+dolinc_status dolinc_implicit_rows(const dolinc_implicit *imp, int32_t *row_offsets, int32_t *nbr, double *off,
+                                   double *diag)
+{
+    if (!imp || !row_offsets || !nbr || !off || !diag) return fail(DOLINC_ERR_INVALID_ARG, "null argument");
+    const dolinc_mesh *m = imp->m;
+    CU(cudaDeviceSynchronize());
+    std::memcpy(row_offsets, m->h.off.data(), sizeof(int32_t) * (size_t)(imp->n + 1));
+    CU(cudaMemcpy(nbr, imp->nbr, 4 * (size_t)imp->ns, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(off, imp->off, 8 * (size_t)imp->ns, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(diag, imp->diag, 8 * (size_t)imp->n, cudaMemcpyDeviceToHost));
+    for (int64_t c = 0; c < imp->n; ++c)
+        for (int32_t k = row_offsets[c]; k < row_offsets[c + 1]; ++k) off[k] *= diag[c];
     return DOLINC_OK;
 }
 

@@ -1,0 +1,317 @@
+// Semi-implicit DOLINC step for linear advection (Sec 2.4): matrix rows from the
+// DOLINC weights, and one persistent cooperative launch per linear solve.
+//
+// k_imp_assemble  one thread per cell: for each face slot the flux speed a.S and the
+//                 weights of the upwind and downwind averages in the face value
+//                 (W0[0], W1[0] of the DOLINC representation, the same routine the
+//                 stage kernels use), summed into the diagonal or stored against the
+//                 neighbour; then every row is scaled by its diagonal.
+// k_imp_solve     BiCGSTAB on the scaled rows, all iterations in one launch.  Each
+//                 iteration is three grid-stride phases separated by a grid barrier
+//                 that also reduces the phase's dot products:
+//                   A  p = r + beta (p - omega v) on the fly for the cell and its
+//                      neighbours; v = A p;                   sum rh.v
+//                   B  s = r - alpha v likewise; t = A s;     sum t.s, t.t
+//                   C  x += alpha p + omega s; r = s - omega t;   sum rh.r, r.r
+//                 The block that arrives last at a barrier sums the per-block partials
+//                 in block order (the result does not depend on arrival order),
+//                 computes the next scalars and releases the grid.  A wait polls at
+//                 most spin_limit times; one that gives up sets status bit 1 and an
+//                 abort word that ends the solve in every block.  The launch is
+//                 cooperative, so all blocks are resident and the waits end.
+//                 Vectors written inside the launch are read with ld.global.cg (L2),
+//                 never through the incoherent L1.
+#include "common.cuh"
+#include "implicit.cuh"
+
+namespace dol {
+
+// ----------------------------------------------------------------------------- assembly
+template <int NS>
+__global__ void __launch_bounds__(256) k_imp_assemble(DevMesh m, int k, int r, double ax, double ay, double az,
+                                                      double inv_dt, double theta, int32_t *nbr, double *off,
+                                                      double *diag, double *bscale)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m.n_cells) return;
+    const double V = 1.0 / m.cellk64[4ll * c + 3];
+    double dsum = 0.0;
+    const int s0 = m.off[c], s1 = m.off[c + 1];
+    for (int s = s0; s < s1; ++s) {
+        const int2 sw = m.slot2[s];
+        const unsigned word = (unsigned)sw.y;
+        const int f = (int)(word >> 2);
+        const bool bnd = (word & 2u) != 0;
+        const int side = (int)(word & 1u);
+        const double *fr = m.face64 + 8ll * f;
+        // a.S of the face in its internal owner -> neighbour orientation
+        const double an = ax * fr[4] + ay * fr[5] + (m.dim == 3 ? az * fr[6] : 0.0);
+        nbr[s] = sw.x;
+        if (bnd) {            // zero-gradient face: the flux of the cell's own value
+            dsum += theta * an;
+            off[s] = 0.0;
+            continue;
+        }
+        // weights of the owner's (cP) and the neighbour's (cN) averages in the upwind value
+        double W0[NS + 1], W1[NS + 1], cP, cN;
+        if (an >= 0.0) {
+            dolinc_weights<NS, double>(k, r, fr[3], W0, W1);
+            cP = W0[0];
+            cN = W1[0];
+        } else {
+            dolinc_weights<NS, double>(k, r, rcp_bulk(fr[3]), W0, W1);
+            cP = W1[0];
+            cN = W0[0];
+        }
+        // the flux an (cP u_P + cN u_N) leaves the owner and enters the neighbour
+        if (side == 0) {
+            dsum += theta * an * cP;
+            off[s] = theta * an * cN;
+        } else {
+            dsum -= theta * an * cN;
+            off[s] = -theta * an * cP;
+        }
+    }
+    const double D = V * inv_dt + dsum;
+    const double iD = 1.0 / D;
+    for (int s = s0; s < s1; ++s) off[s] *= iD;
+    diag[c] = D;
+    bscale[c] = V * iD;
+}
+
+void launch_imp_assemble(const DevMesh &m, int ns, int k, int r, double ax, double ay, double az, double dt,
+                         double theta, int32_t *nbr, double *off, double *diag, double *bscale, cudaStream_t s)
+{
+    const int grid = (m.n_cells + 255) / 256;
+    if (grid == 0) return;
+    const double idt = 1.0 / dt;
+    switch (ns) {
+    case 1: k_imp_assemble<1><<<grid, 256, 0, s>>>(m, k, r, ax, ay, az, idt, theta, nbr, off, diag, bscale); break;
+    case 2: k_imp_assemble<2><<<grid, 256, 0, s>>>(m, k, r, ax, ay, az, idt, theta, nbr, off, diag, bscale); break;
+    case 3: k_imp_assemble<3><<<grid, 256, 0, s>>>(m, k, r, ax, ay, az, idt, theta, nbr, off, diag, bscale); break;
+    default: k_imp_assemble<4><<<grid, 256, 0, s>>>(m, k, r, ax, ay, az, idt, theta, nbr, off, diag, bscale); break;
+    }
+}
+
+// -------------------------------------------------------------------------------- solve
+// Sum over the block of two values, in a fixed order; the result is in thread 0.
+__device__ __forceinline__ void block_sum2(double &a, double &b, double (*sh)[IMP_BLOCK / 32])
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { sh[0][w] = a; sh[1][w] = b; }
+    __syncthreads();
+    if (w == 0) {
+        a = l < IMP_BLOCK / 32 ? sh[0][l] : 0.0;
+        b = l < IMP_BLOCK / 32 ? sh[1][l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ void stcg(double *p, double v) { __stcg(p, v); }
+
+// Grid barrier that reduces (v0, v1) over all threads of the grid.  The last block to
+// arrive sums the per-block partials in block order and calls fin(sum0, sum1) in its
+// thread 0 (fin writes the next scalars) before the others are released.  Returns
+// false when the solve was aborted (a wait gave up here or in an earlier barrier).
+template <class Fin>
+__device__ __forceinline__ bool reduce_barrier(const ImpSolve &a, double v0, double v1, Fin fin)
+{
+    __shared__ double sh[2][IMP_BLOCK / 32];
+    __shared__ int last, ok;
+    block_sum2(v0, v1, sh);
+    volatile unsigned *gen = a.bar + 32, *abort = a.bar + 64;
+    unsigned g = 0;
+    if (threadIdx.x == 0) {
+        a.part[2 * blockIdx.x] = v0;
+        a.part[2 * blockIdx.x + 1] = v1;
+        g = *gen;
+        __threadfence();
+        last = atomicAdd(a.bar, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        double t0 = 0.0, t1 = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += IMP_BLOCK) {
+            t0 += ldcg(a.part + 2 * b);
+            t1 += ldcg(a.part + 2 * b + 1);
+        }
+        block_sum2(t0, t1, sh);
+        if (threadIdx.x == 0) {
+            fin(t0, t1);
+            atomicExch(a.bar, 0u);
+            __threadfence();
+            atomicAdd(const_cast<unsigned *>(gen), 1u);
+        }
+    } else if (threadIdx.x == 0) {
+        unsigned it = 0;
+        while (*gen == g && !*abort) {
+            if (++it > a.spin_limit) {
+                atomicOr(a.status, 2u);
+                atomicExch(const_cast<unsigned *>(abort), 1u);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+    }
+    if (threadIdx.x == 0) ok = !*abort;
+    __syncthreads();
+    return ok;
+}
+
+__global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
+{
+    const int n = a.n;
+    const int nth = gridDim.x * IMP_BLOCK;
+    const int t0 = blockIdx.x * IMP_BLOCK + threadIdx.x;
+    double *sc = a.scal;
+
+    // b = bscale * rhs; x = 0; r = rh = b; p = v = 0 (so the first p is r)
+    double bb = 0.0;
+    for (int c = t0; c < n; c += nth) {
+        double rhs = a.R[c];
+        if (a.Rn) rhs = (a.un[c] - a.u[c]) * a.inv_dt + a.theta * rhs + (1.0 - a.theta) * a.Rn[c];
+        const double b = a.bscale[c] * rhs;
+        a.x[c] = 0.0;
+        a.r[c] = b;
+        a.rh[c] = b;
+        a.p[0][c] = 0.0;
+        a.v[0][c] = 0.0;
+        bb = fma(b, b, bb);
+    }
+    bool ok = reduce_barrier(a, bb, 0.0, [&](double s0, double) {
+        stcg(sc + SC_RHO, s0);
+        stcg(sc + SC_BB, s0);
+        stcg(sc + SC_RR, s0);
+        stcg(sc + SC_BETA, 0.0);
+        stcg(sc + SC_OMEGA, 0.0);
+        stcg(sc + SC_SOLVES, ldcg(sc + SC_SOLVES) + 1.0);
+        stcg(a.life + 1, ldcg(a.life + 1) + 1.0);
+        stcg(sc + SC_DONE, (s0 == 0.0) ? 1.0 : 0.0);
+    });
+
+    for (int it = 0; ok && ldcg(sc + SC_DONE) == 0.0; ++it) {
+        const double *pold = a.p[it & 1], *vold = a.v[it & 1];
+        double *pnew = a.p[(it + 1) & 1], *vnew = a.v[(it + 1) & 1];
+        // A: p = r + beta (p - omega v); v = A p
+        {
+            const double beta = ldcg(sc + SC_BETA), om = ldcg(sc + SC_OMEGA);
+            double dot = 0.0;
+            for (int c = t0; c < n; c += nth) {
+                const double pc = fma(beta, ldcg(pold + c) - om * ldcg(vold + c), ldcg(a.r + c));
+                double acc = pc;
+                const int s0 = __ldg(a.row + c), s1 = __ldg(a.row + c + 1);
+                for (int s = s0; s < s1; ++s) {
+                    const int j = __ldg(a.nbr + s);
+                    const double pj = fma(beta, ldcg(pold + j) - om * ldcg(vold + j), ldcg(a.r + j));
+                    acc = fma(__ldg(a.off + s), pj, acc);
+                }
+                pnew[c] = pc;
+                vnew[c] = acc;
+                dot = fma(ldcg(a.rh + c), acc, dot);
+            }
+            ok = reduce_barrier(a, dot, 0.0, [&](double rv, double) {
+                const double rho = ldcg(sc + SC_RHO);
+                if (rv == 0.0 || !isfinite(rv)) {
+                    atomicOr(a.status, 4u);
+                    stcg(sc + SC_DONE, 1.0);
+                    stcg(sc + SC_ALPHA, 0.0);
+                } else {
+                    stcg(sc + SC_ALPHA, rho / rv);
+                }
+            });
+            if (!ok || ldcg(sc + SC_DONE) != 0.0) break;
+        }
+        // B: s = r - alpha v; t = A s
+        {
+            const double al = ldcg(sc + SC_ALPHA);
+            double ts = 0.0, tt = 0.0;
+            for (int c = t0; c < n; c += nth) {
+                const double scv = fma(-al, ldcg(vnew + c), ldcg(a.r + c));
+                double acc = scv;
+                const int s0 = __ldg(a.row + c), s1 = __ldg(a.row + c + 1);
+                for (int s = s0; s < s1; ++s) {
+                    const int j = __ldg(a.nbr + s);
+                    acc = fma(__ldg(a.off + s), fma(-al, ldcg(vnew + j), ldcg(a.r + j)), acc);
+                }
+                a.s[c] = scv;
+                a.t[c] = acc;
+                ts = fma(acc, scv, ts);
+                tt = fma(acc, acc, tt);
+            }
+            ok = reduce_barrier(a, ts, tt, [&](double sts, double stt) {
+                stcg(sc + SC_OMEGA, stt > 0.0 ? sts / stt : 0.0);
+            });
+            if (!ok) break;
+        }
+        // C: x += alpha p + omega s; r = s - omega t
+        {
+            const double al = ldcg(sc + SC_ALPHA), om = ldcg(sc + SC_OMEGA);
+            double rr0 = 0.0, rr = 0.0;
+            for (int c = t0; c < n; c += nth) {
+                const double sv = ldcg(a.s + c);
+                a.x[c] = fma(om, sv, fma(al, ldcg(pnew + c), ldcg(a.x + c)));
+                const double rv = fma(-om, ldcg(a.t + c), sv);
+                a.r[c] = rv;
+                rr0 = fma(ldcg(a.rh + c), rv, rr0);
+                rr = fma(rv, rv, rr);
+            }
+            ok = reduce_barrier(a, rr0, rr, [&](double rho1, double rr1) {
+                stcg(sc + SC_RR, rr1);
+                stcg(sc + SC_ITERS, ldcg(sc + SC_ITERS) + 1.0);
+                stcg(a.life, ldcg(a.life) + 1.0);
+                const double om = ldcg(sc + SC_OMEGA);
+                if (rr1 <= a.tol2 * ldcg(sc + SC_BB)) {
+                    stcg(sc + SC_DONE, 1.0);
+                } else if (om == 0.0 || rho1 == 0.0 || !isfinite(rr1)) {
+                    atomicOr(a.status, 4u);
+                    stcg(sc + SC_DONE, 1.0);
+                } else if (it + 1 >= a.max_iter) {
+                    atomicOr(a.status, 8u);
+                    stcg(sc + SC_DONE, 1.0);
+                } else {
+                    stcg(sc + SC_BETA, (rho1 / ldcg(sc + SC_RHO)) * (ldcg(sc + SC_ALPHA) / om));
+                    stcg(sc + SC_RHO, rho1);
+                }
+            });
+        }
+    }
+    if (!ok) return;
+    // u += delta
+    for (int c = t0; c < n; c += nth) a.u[c] += ldcg(a.x + c);
+}
+
+cudaError_t launch_imp_solve(const ImpSolve &a, int grid, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(IMP_BLOCK);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_imp_solve, a);
+}
+
+int imp_solve_blocks_per_sm()
+{
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_imp_solve, IMP_BLOCK, 0);
+    return n;
+}
+
+}  // namespace dol
