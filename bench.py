@@ -962,8 +962,10 @@ def run_implicit(args):
     forms = [("fp32", 3, 1.0, 1), ("fp64", 3, 1.0, 1), ("fp32", 3, 0.5, 1), ("fp32", 3, 0.5, 2), ("fp32", 5, 1.0, 1),
              ("fp32", 5, 0.5, 2)]
 
+    exact = np.asarray(exact, dtype=np.float64).reshape(-1)
+
     def l2(u):
-        e = M.from_lib(u.cpu().numpy())[0] - exact[0]
+        e = M.from_lib(u.cpu().numpy())[0] - exact
         return float(np.sqrt((V * e * e).sum() / V.sum()))
 
     def timed_steps(fn, n):

@@ -20,7 +20,8 @@
 //                 abort word that ends the solve in every block.  The launch is
 //                 cooperative, so all blocks are resident and the waits end.
 //                 Vectors written inside the launch are read with ld.global.cg (L2),
-//                 never through the incoherent L1.
+//                 never through the incoherent L1.  40 registers: 6 blocks of 256
+//                 threads per SM.
 #include "common.cuh"
 #include "implicit.cuh"
 
@@ -171,7 +172,7 @@ __device__ __forceinline__ bool reduce_barrier(const ImpSolve &a, double v0, dou
     return ok;
 }
 
-__global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
+__global__ void __launch_bounds__(IMP_BLOCK, 6) k_imp_solve(ImpSolve a)
 {
     const int n = a.n;
     const int nth = gridDim.x * IMP_BLOCK;
