@@ -959,8 +959,9 @@ def run_implicit(args):
     dt_exp = w["dt"]
     dt = args.imp_dt_factor * dt_exp
     h = 1.0 / size
-    forms = [("fp32", 3, 1.0, 1), ("fp64", 3, 1.0, 1), ("fp32", 3, 0.5, 1), ("fp32", 3, 0.5, 2), ("fp32", 5, 1.0, 1),
-             ("fp32", 5, 0.5, 2)]
+    forms = [("fp32", 3, 1.0, 1, False), ("fp32", 3, 1.0, 1, True), ("fp64", 3, 1.0, 1, False),
+             ("fp32", 3, 0.5, 1, False), ("fp32", 3, 0.5, 1, True), ("fp32", 3, 0.5, 2, False),
+             ("fp32", 5, 1.0, 1, False), ("fp32", 5, 0.5, 2, False)]
 
     exact = np.asarray(exact, dtype=np.float64).reshape(-1)
 
@@ -979,12 +980,12 @@ def run_implicit(args):
         return e0.elapsed_time(e1)
 
     out = {}
-    for prec, order, theta, n_outer in forms:
+    for prec, order, theta, n_outer, warm in forms:
         k, r = synth.STENCIL_OF_ORDER[order]
         sch = dg.Scheme(precision=prec, **dict(w["scheme"], k=k, r=r, n_diff=order - 1))
         ws = dg.workspace(M, sch)
         S = dg.Implicit(M, sch, dt, theta)
-        S.set_solver(rel_tol=args.imp_tol, max_iter=500)
+        S.set_solver(rel_tol=args.imp_tol, max_iter=500, warm_start=warm)
         u = torch.from_numpy(M.to_lib(w["u0"])).cuda()
         for _ in range(args.warmup):
             S.step(u, ws, n_outer)
@@ -1003,7 +1004,7 @@ def run_implicit(args):
         # accuracy to T: the implicit steps, dt rounded to divide T
         nI = int(np.ceil(T / dt - 1e-9))
         S2 = dg.Implicit(M, sch, T / nI, theta)
-        S2.set_solver(rel_tol=args.imp_tol, max_iter=500)
+        S2.set_solver(rel_tol=args.imp_tol, max_iter=500, warm_start=warm)
         u = torch.from_numpy(M.to_lib(w["u0"])).cuda()
         conv = True
         its = []
@@ -1013,8 +1014,9 @@ def run_implicit(args):
             conv = conv and inf["converged"]
             its.append(inf["iterations"])
         u = torch.from_numpy(M.to_lib(w["u0"])).cuda()
+        S2.set_solver(rel_tol=args.imp_tol, max_iter=500, warm_start=warm)
         ms_T = timed_steps(lambda: S2.step(u, ws, n_outer), nI)
-        name = "%s_order%d_theta%g_outer%d" % (prec, order, theta, n_outer)
+        name = "%s_order%d_theta%g_outer%d%s" % (prec, order, theta, n_outer, "_warm" if warm else "")
         out[name] = {
             "value": cells * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
             "iterations_per_solve": iters / max(solves, 1), "solves": solves, "launches": int(sum(kn)),

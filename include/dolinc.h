@@ -565,10 +565,14 @@ dolinc_status dolinc_implicit_create(dolinc_mesh *mesh, const dolinc_scheme *sch
                                      dolinc_implicit **out);
 void dolinc_implicit_destroy(dolinc_implicit *solver);
 
-/* Solver limits: relative tolerance (default 1e-10), iterations per solve (default
- * 1000), and the polls a grid-barrier wait makes before it gives up (default 2^23). */
+/* Solver settings: relative tolerance (default 1e-10), iterations per solve (default
+ * 1000), the polls a grid-barrier wait makes before it gives up (default 2^23), and
+ * warm_start (default 0): 1 starts the first solve of each step from the previous
+ * step's first solution instead of 0 (the outer corrections start from 0).  The call
+ * waits for the device and resets the kept solution to 0.  INVALID_ARG for
+ * rel_tol < 0, max_iter < 1 or warm_start not 0/1. */
 dolinc_status dolinc_implicit_set_solver(dolinc_implicit *solver, double rel_tol, int max_iter,
-                                         unsigned spin_limit);
+                                         unsigned spin_limit, int warm_start);
 
 /* One step on u_dev (FP64 [cell], library order, in place), n_outer >= 1 solves.  ws:
  * a workspace of the mesh and scheme (dolinc_workspace_size), used for the residual.

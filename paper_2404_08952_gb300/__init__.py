@@ -112,7 +112,7 @@ def load(path=LIB_PATH):
             "dolinc_part_step_continue": [P, P, P, S, P, P],
             "dolinc_mesh_set_skew_correction": [P, I],
             "dolinc_implicit_create": [P, P, D, D, P], "dolinc_implicit_destroy": [P],
-            "dolinc_implicit_set_solver": [P, D, I, C.c_uint], "dolinc_implicit_step": [P, P, I, P, S, P],
+            "dolinc_implicit_set_solver": [P, D, I, C.c_uint, I], "dolinc_implicit_step": [P, P, I, P, S, P],
             "dolinc_implicit_info": [P, P], "dolinc_implicit_rows": [P, P, P, P, P],
         }
         for name, args in sig.items():
@@ -595,8 +595,9 @@ class Implicit:
             _lib.dolinc_implicit_destroy(h)
             self.handle = None
 
-    def set_solver(self, rel_tol=1e-10, max_iter=1000, spin_limit=1 << 23):
-        _check(load().dolinc_implicit_set_solver(self.handle, float(rel_tol), int(max_iter), int(spin_limit)))
+    def set_solver(self, rel_tol=1e-10, max_iter=1000, spin_limit=1 << 23, warm_start=False):
+        _check(load().dolinc_implicit_set_solver(self.handle, float(rel_tol), int(max_iter), int(spin_limit),
+                                                 1 if warm_start else 0))
 
     def step(self, u, ws, n_outer=1, stream=None):
         _check(load().dolinc_implicit_step(self.handle, _ptr(u), int(n_outer), _ptr(ws), ws.numel(),

@@ -2007,6 +2007,7 @@ struct dolinc_implicit {
     double rel_tol = 1e-10;
     int max_iter = 1000;
     unsigned spin_limit = 1u << 23;
+    int warm = 0;                        // first solve of a step starts from the last step's solution
     int grid = 0, device = 0;
     int64_t n = 0, ns = 0;
     void *mem = nullptr;
@@ -2014,6 +2015,7 @@ struct dolinc_implicit {
     double *off = nullptr, *diag = nullptr, *bscale = nullptr;
     double *vec[9] = {};                 // x r rh p0 p1 v0 v1 s t
     double *R = nullptr, *Rn = nullptr, *un = nullptr;
+    double *xw = nullptr;                // the first solve's solution, kept between steps
     double *part = nullptr;
     double *scal = nullptr;              // ctrl block: scalars (256 B), then barrier words and status (512 B)
     double *life = nullptr;              // [2] iterations and solves since creation (not reset per step)
@@ -2069,7 +2071,7 @@ dolinc_status dolinc_implicit_create(dolinc_mesh *m, const dolinc_scheme *s, dou
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t n8 = al(8 * (size_t)std::max<int64_t>(imp->n, 1)), s8 = al(8 * (size_t)std::max<int64_t>(imp->ns, 1));
     const size_t s4 = al(4 * (size_t)std::max<int64_t>(imp->ns, 1)), pb = al(16 * (size_t)imp->grid);
-    const size_t total = s4 + s8 + 14 * n8 + pb + kImpCtrl + 256;
+    const size_t total = s4 + s8 + 15 * n8 + pb + kImpCtrl + 256;
     cudaError_t e = cudaMalloc(&imp->mem, total);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -2086,6 +2088,7 @@ dolinc_status dolinc_implicit_create(dolinc_mesh *m, const dolinc_scheme *s, dou
     imp->R = reinterpret_cast<double *>(take(n8));
     imp->Rn = reinterpret_cast<double *>(take(n8));
     imp->un = reinterpret_cast<double *>(take(n8));
+    imp->xw = reinterpret_cast<double *>(take(n8));
     imp->part = reinterpret_cast<double *>(take(pb));
     imp->scal = reinterpret_cast<double *>(take(kImpCtrl));
     imp->bar = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(imp->scal) + 256);
@@ -2105,14 +2108,23 @@ dolinc_status dolinc_implicit_create(dolinc_mesh *m, const dolinc_scheme *s, dou
 
 void dolinc_implicit_destroy(dolinc_implicit *imp) { delete imp; }
 
-dolinc_status dolinc_implicit_set_solver(dolinc_implicit *imp, double rel_tol, int max_iter, unsigned spin_limit)
+dolinc_status dolinc_implicit_set_solver(dolinc_implicit *imp, double rel_tol, int max_iter, unsigned spin_limit,
+                                         int warm_start)
 {
     if (!imp) return fail(DOLINC_ERR_INVALID_ARG, "null solver");
     if (!(rel_tol >= 0.0) || !std::isfinite(rel_tol)) return fail(DOLINC_ERR_INVALID_ARG, "rel_tol must be >= 0");
     if (max_iter < 1) return fail(DOLINC_ERR_INVALID_ARG, "max_iter must be >= 1");
+    if (warm_start != 0 && warm_start != 1) return fail(DOLINC_ERR_INVALID_ARG, "warm_start must be 0 or 1");
+    int cur = 0;
+    CU(cudaGetDevice(&cur));
+    CU(cudaSetDevice(imp->device));
+    CU(cudaDeviceSynchronize());
+    CU(cudaMemset(imp->xw, 0, 8 * (size_t)imp->n));     // the next warm start begins from 0
+    CU(cudaSetDevice(cur));
     imp->rel_tol = rel_tol;
     imp->max_iter = max_iter;
     imp->spin_limit = spin_limit;
+    imp->warm = warm_start;
     return DOLINC_OK;
 }
 
@@ -2158,6 +2170,10 @@ dolinc_status dolinc_implicit_step(dolinc_implicit *imp, double *u, int n_outer,
         a.R = Rk;
         a.Rn = k == 0 ? nullptr : imp->Rn;
         a.un = k == 0 ? nullptr : imp->un;
+        // warm start: the step's first solve from the last step's first solution; the
+        // outer corrections start from 0
+        a.warm = (imp->warm && k == 0) ? 1 : 0;
+        a.x = a.warm ? imp->xw : imp->vec[0];
         cudaError_t e = cudaSuccess;
         timed(m, DOLINC_KERNEL_SOLVE, cs, [&] { e = launch_imp_solve(a, imp->grid, cs); });
         if (e != cudaSuccess) {

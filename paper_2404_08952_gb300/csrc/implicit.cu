@@ -19,6 +19,8 @@
 //                 most spin_limit times; one that gives up sets status bit 1 and an
 //                 abort word that ends the solve in every block.  The launch is
 //                 cooperative, so all blocks are resident and the waits end.
+//                 Warm start: x starts from the previous solve's solution kept in x
+//                 (r = b - A x, one extra product in the set-up phase); else from 0.
 //                 Vectors written inside the launch are read with ld.global.cg (L2),
 //                 never through the incoherent L1.  40 registers: 6 blocks of 256
 //                 threads per SM.
@@ -179,28 +181,38 @@ __global__ void __launch_bounds__(IMP_BLOCK, 6) k_imp_solve(ImpSolve a)
     const int t0 = blockIdx.x * IMP_BLOCK + threadIdx.x;
     double *sc = a.scal;
 
-    // b = bscale * rhs; x = 0; r = rh = b; p = v = 0 (so the first p is r)
-    double bb = 0.0;
+    // b = bscale * rhs; x = 0 (or the previous solution x0: warm start); r = rh = b - A x0;
+    // p = v = 0 (so the first p is r).  x0 is only read here, so r needs no barrier.
+    double bb = 0.0, rr = 0.0;
     for (int c = t0; c < n; c += nth) {
         double rhs = a.R[c];
         if (a.Rn) rhs = (a.un[c] - a.u[c]) * a.inv_dt + a.theta * rhs + (1.0 - a.theta) * a.Rn[c];
         const double b = a.bscale[c] * rhs;
-        a.x[c] = 0.0;
-        a.r[c] = b;
-        a.rh[c] = b;
+        double r0 = b;
+        if (a.warm) {
+            double ax = a.x[c];
+            const int s0 = __ldg(a.row + c), s1 = __ldg(a.row + c + 1);
+            for (int s = s0; s < s1; ++s) ax = fma(__ldg(a.off + s), a.x[__ldg(a.nbr + s)], ax);
+            r0 = b - ax;
+        }
+        a.r[c] = r0;
+        a.rh[c] = r0;
         a.p[0][c] = 0.0;
         a.v[0][c] = 0.0;
         bb = fma(b, b, bb);
+        rr = fma(r0, r0, rr);
     }
-    bool ok = reduce_barrier(a, bb, 0.0, [&](double s0, double) {
-        stcg(sc + SC_RHO, s0);
+    if (!a.warm)
+        for (int c = t0; c < n; c += nth) a.x[c] = 0.0;
+    bool ok = reduce_barrier(a, bb, rr, [&](double s0, double s1) {
+        stcg(sc + SC_RHO, s1);
         stcg(sc + SC_BB, s0);
-        stcg(sc + SC_RR, s0);
+        stcg(sc + SC_RR, s1);
         stcg(sc + SC_BETA, 0.0);
         stcg(sc + SC_OMEGA, 0.0);
         stcg(sc + SC_SOLVES, ldcg(sc + SC_SOLVES) + 1.0);
         stcg(a.life + 1, ldcg(a.life + 1) + 1.0);
-        stcg(sc + SC_DONE, (s0 == 0.0) ? 1.0 : 0.0);
+        stcg(sc + SC_DONE, (s1 <= a.tol2 * s0) ? 1.0 : 0.0);
     });
 
     for (int it = 0; ok && ldcg(sc + SC_DONE) == 0.0; ++it) {

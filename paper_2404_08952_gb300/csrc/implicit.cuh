@@ -36,6 +36,7 @@ struct ImpSolve {
     unsigned *bar;               // [0] arrivals, [32] generation, [64] abort
     unsigned *status;            // bit 1 barrier wait gave up, bit 2 breakdown, bit 3 not converged
     double tol2;                 // (relative tolerance)^2 on ||b - A x||^2 / ||b||^2
+    int warm;                    // 1: start from the solution already in x (else from 0)
     int max_iter;
     unsigned spin_limit;
 };

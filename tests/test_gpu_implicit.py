@@ -281,3 +281,34 @@ def test_rejections():
     with pytest.raises(dg.DolincError) as e:
         dg.Implicit(Mb, sd, 0.1)
     assert e.value.status == 3
+
+
+@pytest.mark.parametrize("name", ["tet", "hexprism"])
+def test_warm_started_steps_equal_the_oracle(name):
+    """Warm start (the step's first solve from the last step's solution): every step
+    equals the oracle's step from the same state, and after the first step the solves
+    take fewer iterations than cold ones."""
+    m, O = mesh(name)
+    adv = MESHES[name][1]
+    M = dg.Mesh(m)
+    sd, so = schemes(3, 1, adv)
+    dt = cfl_dt(O, adv, 3.0)
+    ws = dg.workspace(M, sd)
+    its = {}
+    for warm in (False, True):
+        S = dg.Implicit(M, sd, dt, 1.0)
+        S.set_solver(rel_tol=1e-13, warm_start=warm)
+        u = field(m, 1, seed=6)
+        ud = to_dev(M, u)
+        its[warm] = []
+        for _ in range(4):
+            S.step(ud, ws)
+            info = S.info()
+            assert info["converged"], info
+            its[warm].append(info["iterations"])
+            got = M.from_lib(ud.cpu().numpy())
+            want = O.semi_implicit_step(u, so, dt, 1.0)
+            assert np.abs(got - want).max() <= 1e-10 * np.abs(want - u).max()
+            u = got
+    assert its[True][0] == its[False][0]
+    assert sum(its[True][1:]) < sum(its[False][1:]), its
