@@ -1232,7 +1232,7 @@ def main():
     ap.add_argument("--stab-time", type=float, default=0.4, help="euler3d_tet64 stability runs: end time")
     ap.add_argument("--imp-dt-factor", type=float, default=16.0, help="semi-implicit dt / explicit dt")
     ap.add_argument("--imp-time", type=float, default=0.1, help="semi-implicit accuracy runs: end time")
-    ap.add_argument("--imp-tol", type=float, default=1e-8, help="semi-implicit solver relative tolerance")
+    ap.add_argument("--imp-tol", type=float, default=1e-6, help="semi-implicit solver relative tolerance")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

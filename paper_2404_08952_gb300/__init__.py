@@ -36,6 +36,7 @@ ABI_SYMBOLS = (
     "dolinc_mesh_part_sizes", "dolinc_part_step_begin", "dolinc_part_step_continue",
     "dolinc_mesh_set_skew_correction", "dolinc_implicit_create", "dolinc_implicit_destroy",
     "dolinc_implicit_set_solver", "dolinc_implicit_step", "dolinc_implicit_info", "dolinc_implicit_rows",
+    "dolinc_implicit_set_layout", "dolinc_implicit_layout",
     "dolinc_last_error",
 )
 KERNEL_KINDS = ("pack", "diff1", "diff2", "diff3", "diff4", "stage", "faces", "diff_pair", "solve")
@@ -114,6 +115,7 @@ def load(path=LIB_PATH):
             "dolinc_implicit_create": [P, P, D, D, P], "dolinc_implicit_destroy": [P],
             "dolinc_implicit_set_solver": [P, D, I, C.c_uint, I], "dolinc_implicit_step": [P, P, I, P, S, P],
             "dolinc_implicit_info": [P, P], "dolinc_implicit_rows": [P, P, P, P, P],
+            "dolinc_implicit_set_layout": [P, I], "dolinc_implicit_layout": [P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -598,6 +600,14 @@ class Implicit:
     def set_solver(self, rel_tol=1e-10, max_iter=1000, spin_limit=1 << 23, warm_start=False):
         _check(load().dolinc_implicit_set_solver(self.handle, float(rel_tol), int(max_iter), int(spin_limit),
                                                  1 if warm_start else 0))
+
+    def set_layout(self, ell):
+        """Row layout: ELL width 4 / 6 / 8, or 0 (per face slot)."""
+        _check(load().dolinc_implicit_set_layout(self.handle, int(ell)))
+
+    @property
+    def layout(self):
+        return int(load().dolinc_implicit_layout(self.handle))
 
     def step(self, u, ws, n_outer=1, stream=None):
         _check(load().dolinc_implicit_step(self.handle, _ptr(u), int(n_outer), _ptr(ws), ws.numel(),

@@ -2009,8 +2009,11 @@ struct dolinc_implicit {
     unsigned spin_limit = 1u << 23;
     int warm = 0;                        // first solve of a step starts from the last step's solution
     int grid = 0, device = 0;
-    int64_t n = 0, ns = 0;
+    int ell = 0;                         // ELL width of the rows (0: per slot)
+    int64_t n = 0, ns = 0, ne = 0;       // cells, slots, row entries
+    int sms = 0;
     void *mem = nullptr;
+    void *rows = nullptr;                // nbr and off (their own allocation: the layout can change)
     int32_t *nbr = nullptr;
     double *off = nullptr, *diag = nullptr, *bscale = nullptr;
     double *vec[9] = {};                 // x r rh p0 p1 v0 v1 s t
@@ -2023,17 +2026,52 @@ struct dolinc_implicit {
     cudaStream_t last = nullptr;
     ~dolinc_implicit()
     {
-        if (!mem) return;
+        if (!mem && !rows) return;
         int cur = 0;
         cudaGetDevice(&cur);
         cudaSetDevice(device);
-        cudaFree(mem);
+        if (mem) cudaFree(mem);
+        if (rows) cudaFree(rows);
         cudaSetDevice(cur);
     }
 };
 
 namespace {
 constexpr size_t kImpCtrl = 768;     // scalars 256 B + barrier words [0], [32], [64] and status [96]
+constexpr int kImpMaxBlocksPerSm = 8;
+
+// (Re)builds the rows in layout ell (ELL width, 0 = per slot) and sizes the grid for it:
+// waits for the device, frees the old rows, assembles, waits again.
+dolinc_status imp_build_rows(dolinc_implicit *imp, int ell)
+{
+    const dolinc_mesh *m = imp->m;
+    CU(cudaDeviceSynchronize());
+    if (imp->rows) {
+        cudaFree(imp->rows);
+        imp->rows = nullptr;
+    }
+    imp->ell = ell;
+    imp->ne = ell ? (int64_t)ell * imp->n : imp->ns;
+    const size_t e4 = (4 * (size_t)std::max<int64_t>(imp->ne, 1) + 255) / 256 * 256;
+    cudaError_t e = cudaMalloc(&imp->rows, e4 + 8 * (size_t)std::max<int64_t>(imp->ne, 1));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        imp->rows = nullptr;
+        return fail(DOLINC_ERR_OOM, std::string("implicit solver rows: ") + cudaGetErrorString(e));
+    }
+    imp->nbr = static_cast<int32_t *>(imp->rows);
+    imp->off = reinterpret_cast<double *>(static_cast<char *>(imp->rows) + e4);
+    const int64_t need = (imp->n + IMP_BLOCK - 1) / IMP_BLOCK;
+    const int bps = std::min(std::max(imp_solve_blocks_per_sm(ell), 1), kImpMaxBlocksPerSm);
+    imp->grid = (int)std::max<int64_t>(1, std::min(need, (int64_t)imp->sms * bps));
+    const dolinc_scheme *s = &imp->s;
+    launch_imp_assemble(m->d, needed_order(*s), s->k, s->r, s->adv[0], s->adv[1], s->adv[2], imp->dt, imp->theta, ell,
+                        imp->nbr, imp->off, imp->diag, imp->bscale, nullptr);
+    dolinc_status st = launch_check();
+    if (st) return st;
+    CU(cudaDeviceSynchronize());
+    return DOLINC_OK;
+}
 }
 
 extern "C" {
@@ -2063,15 +2101,11 @@ dolinc_status dolinc_implicit_create(dolinc_mesh *m, const dolinc_scheme *s, dou
     int cur = 0;
     CU(cudaGetDevice(&cur));
     CU(cudaSetDevice(m->device));
-    int sms = 0;
-    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
-    const int64_t need = (imp->n + IMP_BLOCK - 1) / IMP_BLOCK;
-    const int64_t cap = (int64_t)sms * (int64_t)std::max(imp_solve_blocks_per_sm(), 1);
-    imp->grid = (int)std::max<int64_t>(1, std::min(need, cap));
+    CU(cudaDeviceGetAttribute(&imp->sms, cudaDevAttrMultiProcessorCount, m->device));
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t n8 = al(8 * (size_t)std::max<int64_t>(imp->n, 1)), s8 = al(8 * (size_t)std::max<int64_t>(imp->ns, 1));
-    const size_t s4 = al(4 * (size_t)std::max<int64_t>(imp->ns, 1)), pb = al(16 * (size_t)imp->grid);
-    const size_t total = s4 + s8 + 15 * n8 + pb + kImpCtrl + 256;
+    const size_t n8 = al(8 * (size_t)std::max<int64_t>(imp->n, 1));
+    const size_t pb = al(16 * (size_t)imp->sms * kImpMaxBlocksPerSm);
+    const size_t total = 15 * n8 + pb + kImpCtrl + 256;
     cudaError_t e = cudaMalloc(&imp->mem, total);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -2080,8 +2114,6 @@ dolinc_status dolinc_implicit_create(dolinc_mesh *m, const dolinc_scheme *s, dou
     }
     char *q = static_cast<char *>(imp->mem);
     auto take = [&](size_t b) { char *r = q; q += b; return r; };
-    imp->nbr = reinterpret_cast<int32_t *>(take(s4));
-    imp->off = reinterpret_cast<double *>(take(s8));
     imp->diag = reinterpret_cast<double *>(take(n8));
     imp->bscale = reinterpret_cast<double *>(take(n8));
     for (auto &v : imp->vec) v = reinterpret_cast<double *>(take(n8));
@@ -2094,17 +2126,29 @@ dolinc_status dolinc_implicit_create(dolinc_mesh *m, const dolinc_scheme *s, dou
     imp->bar = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(imp->scal) + 256);
     imp->life = reinterpret_cast<double *>(take(256));
     CU(cudaMemset(imp->mem, 0, total));
-    launch_imp_assemble(m->d, needed_order(*s), s->k, s->r, s->adv[0], s->adv[1], s->adv[2], dt, theta, imp->nbr,
-                        imp->off, imp->diag, imp->bscale, nullptr);
-    if ((st = launch_check())) {
+    if ((st = imp_build_rows(imp.get(), imp_ell_width(m->d.max_slots)))) {
         cudaSetDevice(cur);
         return st;
     }
-    CU(cudaDeviceSynchronize());
     CU(cudaSetDevice(cur));
     *out = imp.release();
     return DOLINC_OK;
 }
+
+dolinc_status dolinc_implicit_set_layout(dolinc_implicit *imp, int ell)
+{
+    if (!imp) return fail(DOLINC_ERR_INVALID_ARG, "null solver");
+    if (!(ell == 0 || ((ell == 4 || ell == 6 || ell == 8) && ell >= imp->m->d.max_slots)))
+        return fail(DOLINC_ERR_INVALID_ARG, "layout must be 0 (per slot) or an ELL width 4, 6 or 8 covering every cell");
+    int cur = 0;
+    CU(cudaGetDevice(&cur));
+    CU(cudaSetDevice(imp->device));
+    dolinc_status st = imp_build_rows(imp, ell);
+    CU(cudaSetDevice(cur));
+    return st;
+}
+
+int dolinc_implicit_layout(const dolinc_implicit *imp) { return imp ? imp->ell : -1; }
 
 void dolinc_implicit_destroy(dolinc_implicit *imp) { delete imp; }
 
@@ -2175,7 +2219,7 @@ dolinc_status dolinc_implicit_step(dolinc_implicit *imp, double *u, int n_outer,
         a.warm = (imp->warm && k == 0) ? 1 : 0;
         a.x = a.warm ? imp->xw : imp->vec[0];
         cudaError_t e = cudaSuccess;
-        timed(m, DOLINC_KERNEL_SOLVE, cs, [&] { e = launch_imp_solve(a, imp->grid, cs); });
+        timed(m, DOLINC_KERNEL_SOLVE, cs, [&] { e = launch_imp_solve(a, imp->ell, imp->grid, cs); });
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(DOLINC_ERR_CUDA, std::string("cooperative launch: ") + cudaGetErrorString(e));
@@ -2212,11 +2256,17 @@ dolinc_status dolinc_implicit_rows(const dolinc_implicit *imp, int32_t *row_offs
     const dolinc_mesh *m = imp->m;
     CU(cudaDeviceSynchronize());
     std::memcpy(row_offsets, m->h.off.data(), sizeof(int32_t) * (size_t)(imp->n + 1));
-    CU(cudaMemcpy(nbr, imp->nbr, 4 * (size_t)imp->ns, cudaMemcpyDeviceToHost));
-    CU(cudaMemcpy(off, imp->off, 8 * (size_t)imp->ns, cudaMemcpyDeviceToHost));
+    std::vector<int32_t> nb(imp->ne);
+    std::vector<double> of(imp->ne);
+    CU(cudaMemcpy(nb.data(), imp->nbr, 4 * (size_t)imp->ne, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(of.data(), imp->off, 8 * (size_t)imp->ne, cudaMemcpyDeviceToHost));
     CU(cudaMemcpy(diag, imp->diag, 8 * (size_t)imp->n, cudaMemcpyDeviceToHost));
     for (int64_t c = 0; c < imp->n; ++c)
-        for (int32_t k = row_offsets[c]; k < row_offsets[c + 1]; ++k) off[k] *= diag[c];
+        for (int32_t k = row_offsets[c]; k < row_offsets[c + 1]; ++k) {
+            const int64_t e = imp->ell ? (int64_t)(k - row_offsets[c]) * imp->n + c : k;
+            nbr[k] = nb[e];
+            off[k] = of[e] * diag[c];
+        }
     return DOLINC_OK;
 }
 

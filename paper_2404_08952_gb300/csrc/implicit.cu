@@ -22,8 +22,9 @@
 //                 Warm start: x starts from the previous solve's solution kept in x
 //                 (r = b - A x, one extra product in the set-up phase); else from 0.
 //                 Vectors written inside the launch are read with ld.global.cg (L2),
-//                 never through the incoherent L1.  40 registers: 6 blocks of 256
-//                 threads per SM.
+//                 never through the incoherent L1.  Rows in ELL form (width 4, 6 or
+//                 8, padded with zero weights) when the mesh's cells have at most 8
+//                 faces, else the slot ranges.
 #include "common.cuh"
 #include "implicit.cuh"
 
@@ -32,14 +33,17 @@ namespace dol {
 // ----------------------------------------------------------------------------- assembly
 template <int NS>
 __global__ void __launch_bounds__(256) k_imp_assemble(DevMesh m, int k, int r, double ax, double ay, double az,
-                                                      double inv_dt, double theta, int32_t *nbr, double *off,
+                                                      double inv_dt, double theta, int ell, int32_t *nbr, double *off,
                                                       double *diag, double *bscale)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= m.n_cells) return;
+    const long long n = m.n_cells;
     const double V = 1.0 / m.cellk64[4ll * c + 3];
     double dsum = 0.0;
     const int s0 = m.off[c], s1 = m.off[c + 1];
+    // entry of slot s: ELL position (s - s0) n + c, or the slot itself (CSR)
+    auto at = [&](int s) { return ell ? (long long)(s - s0) * n + c : (long long)s; };
     for (int s = s0; s < s1; ++s) {
         const int2 sw = m.slot2[s];
         const unsigned word = (unsigned)sw.y;
@@ -49,10 +53,10 @@ __global__ void __launch_bounds__(256) k_imp_assemble(DevMesh m, int k, int r, d
         const double *fr = m.face64 + 8ll * f;
         // a.S of the face in its internal owner -> neighbour orientation
         const double an = ax * fr[4] + ay * fr[5] + (m.dim == 3 ? az * fr[6] : 0.0);
-        nbr[s] = sw.x;
+        nbr[at(s)] = sw.x;
         if (bnd) {            // zero-gradient face: the flux of the cell's own value
             dsum += theta * an;
-            off[s] = 0.0;
+            off[at(s)] = 0.0;
             continue;
         }
         // weights of the owner's (cP) and the neighbour's (cN) averages in the upwind value
@@ -69,30 +73,35 @@ __global__ void __launch_bounds__(256) k_imp_assemble(DevMesh m, int k, int r, d
         // the flux an (cP u_P + cN u_N) leaves the owner and enters the neighbour
         if (side == 0) {
             dsum += theta * an * cP;
-            off[s] = theta * an * cN;
+            off[at(s)] = theta * an * cN;
         } else {
             dsum -= theta * an * cN;
-            off[s] = -theta * an * cP;
+            off[at(s)] = -theta * an * cP;
         }
     }
     const double D = V * inv_dt + dsum;
     const double iD = 1.0 / D;
-    for (int s = s0; s < s1; ++s) off[s] *= iD;
+    for (int s = s0; s < s1; ++s) off[at(s)] *= iD;
+    for (int q = s1 - s0; q < ell; ++q) {      // ELL padding: the cell itself, weight 0
+        nbr[(long long)q * n + c] = c;
+        off[(long long)q * n + c] = 0.0;
+    }
     diag[c] = D;
     bscale[c] = V * iD;
 }
 
 void launch_imp_assemble(const DevMesh &m, int ns, int k, int r, double ax, double ay, double az, double dt,
-                         double theta, int32_t *nbr, double *off, double *diag, double *bscale, cudaStream_t s)
+                         double theta, int ell, int32_t *nbr, double *off, double *diag, double *bscale,
+                         cudaStream_t s)
 {
     const int grid = (m.n_cells + 255) / 256;
     if (grid == 0) return;
     const double idt = 1.0 / dt;
     switch (ns) {
-    case 1: k_imp_assemble<1><<<grid, 256, 0, s>>>(m, k, r, ax, ay, az, idt, theta, nbr, off, diag, bscale); break;
-    case 2: k_imp_assemble<2><<<grid, 256, 0, s>>>(m, k, r, ax, ay, az, idt, theta, nbr, off, diag, bscale); break;
-    case 3: k_imp_assemble<3><<<grid, 256, 0, s>>>(m, k, r, ax, ay, az, idt, theta, nbr, off, diag, bscale); break;
-    default: k_imp_assemble<4><<<grid, 256, 0, s>>>(m, k, r, ax, ay, az, idt, theta, nbr, off, diag, bscale); break;
+    case 1: k_imp_assemble<1><<<grid, 256, 0, s>>>(m, k, r, ax, ay, az, idt, theta, ell, nbr, off, diag, bscale); break;
+    case 2: k_imp_assemble<2><<<grid, 256, 0, s>>>(m, k, r, ax, ay, az, idt, theta, ell, nbr, off, diag, bscale); break;
+    case 3: k_imp_assemble<3><<<grid, 256, 0, s>>>(m, k, r, ax, ay, az, idt, theta, ell, nbr, off, diag, bscale); break;
+    default: k_imp_assemble<4><<<grid, 256, 0, s>>>(m, k, r, ax, ay, az, idt, theta, ell, nbr, off, diag, bscale); break;
     }
 }
 
@@ -174,7 +183,31 @@ __device__ __forceinline__ bool reduce_barrier(const ImpSolve &a, double v0, dou
     return ok;
 }
 
-__global__ void __launch_bounds__(IMP_BLOCK, 6) k_imp_solve(ImpSolve a)
+// a.off . f(neighbour) over the row of cell c, added to acc: ELL rows of W entries
+// (entry q of cell c at q n + c: a warp's loads are contiguous and independent), or the
+// cell's slot range (W = 0).
+template <int W, class F>
+__device__ __forceinline__ double row_sum(const ImpSolve &a, int c, double acc, F f)
+{
+    if constexpr (W > 0) {
+        int j[W];
+        double o[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            j[q] = __ldg(a.nbr + (long long)q * a.n + c);
+            o[q] = __ldg(a.off + (long long)q * a.n + c);
+        }
+#pragma unroll
+        for (int q = 0; q < W; ++q) acc = fma(o[q], f(j[q]), acc);
+    } else {
+        const int s0 = __ldg(a.row + c), s1 = __ldg(a.row + c + 1);
+        for (int s = s0; s < s1; ++s) acc = fma(__ldg(a.off + s), f(__ldg(a.nbr + s)), acc);
+    }
+    return acc;
+}
+
+template <int W>
+__global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
 {
     const int n = a.n;
     const int nth = gridDim.x * IMP_BLOCK;
@@ -189,12 +222,7 @@ __global__ void __launch_bounds__(IMP_BLOCK, 6) k_imp_solve(ImpSolve a)
         if (a.Rn) rhs = (a.un[c] - a.u[c]) * a.inv_dt + a.theta * rhs + (1.0 - a.theta) * a.Rn[c];
         const double b = a.bscale[c] * rhs;
         double r0 = b;
-        if (a.warm) {
-            double ax = a.x[c];
-            const int s0 = __ldg(a.row + c), s1 = __ldg(a.row + c + 1);
-            for (int s = s0; s < s1; ++s) ax = fma(__ldg(a.off + s), a.x[__ldg(a.nbr + s)], ax);
-            r0 = b - ax;
-        }
+        if (a.warm) r0 = b - row_sum<W>(a, c, a.x[c], [&](int j) { return a.x[j]; });
         a.r[c] = r0;
         a.rh[c] = r0;
         a.p[0][c] = 0.0;
@@ -224,13 +252,9 @@ __global__ void __launch_bounds__(IMP_BLOCK, 6) k_imp_solve(ImpSolve a)
             double dot = 0.0;
             for (int c = t0; c < n; c += nth) {
                 const double pc = fma(beta, ldcg(pold + c) - om * ldcg(vold + c), ldcg(a.r + c));
-                double acc = pc;
-                const int s0 = __ldg(a.row + c), s1 = __ldg(a.row + c + 1);
-                for (int s = s0; s < s1; ++s) {
-                    const int j = __ldg(a.nbr + s);
-                    const double pj = fma(beta, ldcg(pold + j) - om * ldcg(vold + j), ldcg(a.r + j));
-                    acc = fma(__ldg(a.off + s), pj, acc);
-                }
+                const double acc = row_sum<W>(a, c, pc, [&](int j) {
+                    return fma(beta, ldcg(pold + j) - om * ldcg(vold + j), ldcg(a.r + j));
+                });
                 pnew[c] = pc;
                 vnew[c] = acc;
                 dot = fma(ldcg(a.rh + c), acc, dot);
@@ -253,12 +277,7 @@ __global__ void __launch_bounds__(IMP_BLOCK, 6) k_imp_solve(ImpSolve a)
             double ts = 0.0, tt = 0.0;
             for (int c = t0; c < n; c += nth) {
                 const double scv = fma(-al, ldcg(vnew + c), ldcg(a.r + c));
-                double acc = scv;
-                const int s0 = __ldg(a.row + c), s1 = __ldg(a.row + c + 1);
-                for (int s = s0; s < s1; ++s) {
-                    const int j = __ldg(a.nbr + s);
-                    acc = fma(__ldg(a.off + s), fma(-al, ldcg(vnew + j), ldcg(a.r + j)), acc);
-                }
+                const double acc = row_sum<W>(a, c, scv, [&](int j) { return fma(-al, ldcg(vnew + j), ldcg(a.r + j)); });
                 a.s[c] = scv;
                 a.t[c] = acc;
                 ts = fma(acc, scv, ts);
@@ -306,7 +325,7 @@ __global__ void __launch_bounds__(IMP_BLOCK, 6) k_imp_solve(ImpSolve a)
     for (int c = t0; c < n; c += nth) a.u[c] += ldcg(a.x + c);
 }
 
-cudaError_t launch_imp_solve(const ImpSolve &a, int grid, cudaStream_t s)
+template <int W> cudaError_t launch_w(const ImpSolve &a, int grid, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -317,14 +336,36 @@ cudaError_t launch_imp_solve(const ImpSolve &a, int grid, cudaStream_t s)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_imp_solve, a);
+    return cudaLaunchKernelEx(&cfg, k_imp_solve<W>, a);
 }
 
-int imp_solve_blocks_per_sm()
+template <int W> int blocks_w()
 {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_imp_solve, IMP_BLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_imp_solve<W>, IMP_BLOCK, 0);
     return n;
+}
+
+int imp_ell_width(int max_slots) { return max_slots <= 4 ? 4 : max_slots <= 6 ? 6 : max_slots <= 8 ? 8 : 0; }
+
+cudaError_t launch_imp_solve(const ImpSolve &a, int ell, int grid, cudaStream_t s)
+{
+    switch (ell) {
+    case 4: return launch_w<4>(a, grid, s);
+    case 6: return launch_w<6>(a, grid, s);
+    case 8: return launch_w<8>(a, grid, s);
+    default: return launch_w<0>(a, grid, s);
+    }
+}
+
+int imp_solve_blocks_per_sm(int ell)
+{
+    switch (ell) {
+    case 4: return blocks_w<4>();
+    case 6: return blocks_w<6>();
+    case 8: return blocks_w<8>();
+    default: return blocks_w<0>();
+    }
 }
 
 }  // namespace dol

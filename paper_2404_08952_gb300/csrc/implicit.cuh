@@ -19,9 +19,9 @@ namespace dol {
 // Arguments of the persistent BiCGSTAB launch.
 struct ImpSolve {
     int n;                       // cells
-    const int32_t *row;          // [n+1] slot ranges (the mesh's)
-    const int32_t *nbr;          // [n_slots] neighbour cell of each slot
-    const double *off;           // [n_slots] scaled off-diagonal coefficient
+    const int32_t *row;          // [n+1] slot ranges (the mesh's; rows without an ELL width)
+    const int32_t *nbr;          // neighbour cell of each entry: ELL [W][n], else [n_slots]
+    const double *off;           // its scaled off-diagonal coefficient, same layout
     const double *bscale;        // [n] V_c / D_c
     // right-hand side b_c = bscale_c * rhs_c:
     //   first solve of a step  rhs = R(u)
@@ -45,13 +45,17 @@ struct ImpSolve {
 // the rest describe the last solve.
 enum { SC_RHO = 0, SC_ALPHA, SC_OMEGA, SC_BETA, SC_BB, SC_RR, SC_DONE, SC_ITERS, SC_SOLVES, SC_COUNT };
 
-cudaError_t launch_imp_solve(const ImpSolve &a, int grid, cudaStream_t s);
-int imp_solve_blocks_per_sm();
+// ELL width of the rows for cells of at most max_slots faces (4, 6, 8; 0: slot ranges)
+int imp_ell_width(int max_slots);
+cudaError_t launch_imp_solve(const ImpSolve &a, int ell, int grid, cudaStream_t s);
+int imp_solve_blocks_per_sm(int ell);
 constexpr int IMP_BLOCK = 256;
 
-// Rows of (V/dt + theta K): nbr, unscaled off[s], diag, then off /= diag and bscale.
-// ns: the scheme's needed differential order (sizes the weight arrays).
+// Rows of (V/dt + theta K): nbr, off (scaled by 1/diag), diag and bscale, in ELL form of
+// width ell (padding: the cell itself with weight 0) or per slot (ell = 0).  ns: the
+// scheme's needed differential order (sizes the weight arrays).
 void launch_imp_assemble(const DevMesh &m, int ns, int k, int r, double ax, double ay, double az, double dt,
-                         double theta, int32_t *nbr, double *off, double *diag, double *bscale, cudaStream_t s);
+                         double theta, int ell, int32_t *nbr, double *off, double *diag, double *bscale,
+                         cudaStream_t s);
 
 }  // namespace dol
