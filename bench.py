@@ -959,9 +959,10 @@ def run_implicit(args):
     dt_exp = w["dt"]
     dt = args.imp_dt_factor * dt_exp
     h = 1.0 / size
-    forms = [("fp32", 3, 1.0, 1, False), ("fp32", 3, 1.0, 1, True), ("fp64", 3, 1.0, 1, False),
-             ("fp32", 3, 0.5, 1, False), ("fp32", 3, 0.5, 1, True), ("fp32", 3, 0.5, 2, False),
-             ("fp32", 5, 1.0, 1, False), ("fp32", 5, 0.5, 2, False)]
+    # (precision, scheme order, theta, outer iterations, warm start, row layout: None = default ELL, 0 = per slot)
+    forms = [("fp32", 3, 0.5, 1, True, None), ("fp32", 3, 0.5, 1, False, None), ("fp32", 3, 0.5, 1, True, 0),
+             ("fp32", 3, 1.0, 1, True, None), ("fp64", 3, 0.5, 1, True, None), ("fp32", 3, 0.5, 2, True, None),
+             ("fp32", 5, 0.5, 2, True, None), ("fp32", 5, 1.0, 1, True, None)]
 
     exact = np.asarray(exact, dtype=np.float64).reshape(-1)
 
@@ -980,11 +981,13 @@ def run_implicit(args):
         return e0.elapsed_time(e1)
 
     out = {}
-    for prec, order, theta, n_outer, warm in forms:
+    for prec, order, theta, n_outer, warm, layout in forms:
         k, r = synth.STENCIL_OF_ORDER[order]
         sch = dg.Scheme(precision=prec, **dict(w["scheme"], k=k, r=r, n_diff=order - 1))
         ws = dg.workspace(M, sch)
         S = dg.Implicit(M, sch, dt, theta)
+        if layout is not None:
+            S.set_layout(layout)
         S.set_solver(rel_tol=args.imp_tol, max_iter=500, warm_start=warm)
         u = torch.from_numpy(M.to_lib(w["u0"])).cuda()
         for _ in range(args.warmup):
@@ -1004,6 +1007,8 @@ def run_implicit(args):
         # accuracy to T: the implicit steps, dt rounded to divide T
         nI = int(np.ceil(T / dt - 1e-9))
         S2 = dg.Implicit(M, sch, T / nI, theta)
+        if layout is not None:
+            S2.set_layout(layout)
         S2.set_solver(rel_tol=args.imp_tol, max_iter=500, warm_start=warm)
         u = torch.from_numpy(M.to_lib(w["u0"])).cuda()
         conv = True
@@ -1016,10 +1021,12 @@ def run_implicit(args):
         u = torch.from_numpy(M.to_lib(w["u0"])).cuda()
         S2.set_solver(rel_tol=args.imp_tol, max_iter=500, warm_start=warm)
         ms_T = timed_steps(lambda: S2.step(u, ws, n_outer), nI)
-        name = "%s_order%d_theta%g_outer%d%s" % (prec, order, theta, n_outer, "_warm" if warm else "")
+        name = "%s_order%d_theta%g_outer%d%s%s" % (prec, order, theta, n_outer, "_warm" if warm else "",
+                                                   "_slots" if layout == 0 else "")
         out[name] = {
             "value": cells * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
             "iterations_per_solve": iters / max(solves, 1), "solves": solves, "launches": int(sum(kn)),
+            "row_layout": S.layout,
             "kernel_ms_share": {KINDS[i]: round(kms[i] / sum(kms), 4) for i in range(len(KINDS)) if kn[i]},
             "solve_roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                                "frac": round(gbs / peak, 4), "alg_bytes_per_cell_iteration":
@@ -1041,17 +1048,21 @@ def run_implicit(args):
         msE = timed_steps(lambda: dg.dolinc_rk_steps(M, sch, T / nE, nE, u, ws), 1)
         expl["%s_order%d_rk3" % (prec, order)] = {"steps": nE, "dt": T / nE, "ms": round(msE, 3), "l2": l2(u)}
         del ws, u
-    main = out["fp32_order3_theta1_outer1"]
+    head = "fp32_order3_theta0.5_outer1_warm"
+    main = out[head]
     line = {"metric": "cell-updates/s per semi-implicit step (residual + linear solve)", "value": main["value"],
             "unit": "cell-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 residual, f64 solve", "data": "synthetic",
             "config": {"workload": "adv3d_hexprism_implicit", "lattice": size, "cells": cells,
-                       "headline": "fp32_order3_theta1_outer1", "flux": "upwind", "adv": list(w["scheme"]["adv"]),
+                       "headline": head, "flux": "upwind", "adv": list(w["scheme"]["adv"]),
                        "jitter": 0.2, "dt": dt, "dt_explicit": dt_exp, "cfl_sum": float(np.abs(a).sum() * dt / h),
                        "rel_tol": args.imp_tol, "time": T, "quad": args.hp_quad, "peak_GBs": peak,
                        "peak_source": peak_src, "l2_flush": "inputs larger than L2 (vectors and rows > 300 MB)"},
             "roofline": main["solve_roofline"], "gpu_launches": main["launches"],
+            "vs_explicit_rk3": {"t": T, "semi_implicit_ms": main["to_time"]["ms"], "semi_implicit_l2": main["to_time"]["l2"],
+                                "rk3_ms": expl["fp32_order3_rk3"]["ms"], "rk3_l2": expl["fp32_order3_rk3"]["l2"],
+                                "speedup": round(expl["fp32_order3_rk3"]["ms"] / main["to_time"]["ms"], 3)},
             "forms": out, "explicit_rk3": expl, "host_input_seconds": round(t_host, 1),
             "seconds_total": time.perf_counter() - t_all}
     print(json.dumps(line), flush=True)
