@@ -1050,6 +1050,18 @@ def run_implicit(args):
         del ws, u
     head = "fp32_order3_theta0.5_outer1_warm"
     main = out[head]
+    cpu = None
+    if not args.no_oracle:      # the oracle's step (sparse LU) on a bounded sample of the workload
+        import oracle
+        ws_ = synth.workload("adv3d_hexprism", order=3, size=24, q=2)
+        O = oracle.Oracle(ws_["mesh"], parallel=True)
+        so = oracle.Scheme(k=3, r=1, n_diff=2, flux="upwind", nv=1, adv=tuple(a))
+        t0 = time.perf_counter()
+        O.semi_implicit_step(ws_["u0"], so, args.imp_dt_factor * ws_["dt"], 0.5)
+        tc = time.perf_counter() - t0
+        cpu = {"value": O.n_cells / tc, "unit": "cell-updates/s", "cores": oracle.threads(), "kind": "oracle",
+               "sample": "one Crank-Nicolson semi-implicit step (explicit residual + direct sparse LU solve) on "
+                         "the 24^3 hex/prism lattice (%d cells), %.1f s" % (O.n_cells, tc)}
     line = {"metric": "cell-updates/s per semi-implicit step (residual + linear solve)", "value": main["value"],
             "unit": "cell-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1063,7 +1075,7 @@ def run_implicit(args):
             "vs_explicit_rk3": {"t": T, "semi_implicit_ms": main["to_time"]["ms"], "semi_implicit_l2": main["to_time"]["l2"],
                                 "rk3_ms": expl["fp32_order3_rk3"]["ms"], "rk3_l2": expl["fp32_order3_rk3"]["l2"],
                                 "speedup": round(expl["fp32_order3_rk3"]["ms"] / main["to_time"]["ms"], 3)},
-            "forms": out, "explicit_rk3": expl, "host_input_seconds": round(t_host, 1),
+            "cpu_baseline": cpu, "forms": out, "explicit_rk3": expl, "host_input_seconds": round(t_host, 1),
             "seconds_total": time.perf_counter() - t_all}
     print(json.dumps(line), flush=True)
 
