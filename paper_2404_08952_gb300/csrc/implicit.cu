@@ -13,8 +13,6 @@
 //                      neighbours; v = A p;                   sum rh.v
 //                   B  s = r - alpha v likewise; t = A s;     sum t.s, t.t
 //                   C  x += alpha p + omega s; r = s - omega t;   sum rh.r, r.r
-//                 r, p, v and rh of a cell live in one 32-byte record (double-buffered
-//                 by iteration), so a neighbour costs one 256-bit load in A and in B.
 //                 The block that arrives last at a barrier sums the per-block partials
 //                 in block order (the result does not depend on arrival order),
 //                 computes the next scalars and releases the grid.  A wait polls at
@@ -134,32 +132,6 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double (*sh)[IM
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ void stcg(double *p, double v) { __stcg(p, v); }
 
-// One iterate record {r, p, v, rh} (32 bytes, 32-byte aligned) read through L2 with a
-// single 256-bit load; written with a single 256-bit store.  Both are ordered with the
-// other memory operations of the thread (the records change between phases).
-__device__ __forceinline__ ImpRec ldrec(const ImpRec *p)
-{
-    unsigned w[8];
-    asm volatile("ld.global.cg.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
-                 : "l"(p)
-                 : "memory");
-    ImpRec q;
-    q.r = __hiloint2double((int)w[1], (int)w[0]);
-    q.p = __hiloint2double((int)w[3], (int)w[2]);
-    q.v = __hiloint2double((int)w[5], (int)w[4]);
-    q.rh = __hiloint2double((int)w[7], (int)w[6]);
-    return q;
-}
-
-__device__ __forceinline__ void strec(ImpRec *p, double r, double pp, double v, double rh)
-{
-    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p),
-                 "r"(__double2loint(r)), "r"(__double2hiint(r)), "r"(__double2loint(pp)), "r"(__double2hiint(pp)),
-                 "r"(__double2loint(v)), "r"(__double2hiint(v)), "r"(__double2loint(rh)), "r"(__double2hiint(rh))
-                 : "memory");
-}
-
 // Grid barrier that reduces (v0, v1) over all threads of the grid.  The last block to
 // arrive sums the per-block partials in block order and calls fin(sum0, sum1) in its
 // thread 0 (fin writes the next scalars) before the others are released.  Returns
@@ -225,11 +197,8 @@ __device__ __forceinline__ double row_sum(const ImpSolve &a, int c, double acc, 
             j[q] = __ldg(a.nbr + (long long)q * a.n + c);
             o[q] = __ldg(a.off + (long long)q * a.n + c);
         }
-        double fv[W];
 #pragma unroll
-        for (int q = 0; q < W; ++q) fv[q] = f(j[q]);
-#pragma unroll
-        for (int q = 0; q < W; ++q) acc = fma(o[q], fv[q], acc);
+        for (int q = 0; q < W; ++q) acc = fma(o[q], f(j[q]), acc);
     } else {
         const int s0 = __ldg(a.row + c), s1 = __ldg(a.row + c + 1);
         for (int s = s0; s < s1; ++s) acc = fma(__ldg(a.off + s), f(__ldg(a.nbr + s)), acc);
@@ -254,7 +223,10 @@ __global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
         const double b = a.bscale[c] * rhs;
         double r0 = b;
         if (a.warm) r0 = b - row_sum<W>(a, c, a.x[c], [&](int j) { return a.x[j]; });
-        strec(a.B[0] + c, r0, 0.0, 0.0, r0);
+        a.r[c] = r0;
+        a.rh[c] = r0;
+        a.p[0][c] = 0.0;
+        a.v[0][c] = 0.0;
         bb = fma(b, b, bb);
         rr = fma(r0, r0, rr);
     }
@@ -272,23 +244,20 @@ __global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
     });
 
     for (int it = 0; ok && ldcg(sc + SC_DONE) == 0.0; ++it) {
-        // records of the previous iterate (r, p, v) and of this one (r, p, v written in A;
-        // r replaced by the next residual in C)
-        const ImpRec *Bo = a.B[it & 1];
-        ImpRec *Bn = a.B[(it + 1) & 1];
+        const double *pold = a.p[it & 1], *vold = a.v[it & 1];
+        double *pnew = a.p[(it + 1) & 1], *vnew = a.v[(it + 1) & 1];
         // A: p = r + beta (p - omega v); v = A p
         {
             const double beta = ldcg(sc + SC_BETA), om = ldcg(sc + SC_OMEGA);
             double dot = 0.0;
             for (int c = t0; c < n; c += nth) {
-                const ImpRec q = ldrec(Bo + c);
-                const double pc = fma(beta, q.p - om * q.v, q.r);
+                const double pc = fma(beta, ldcg(pold + c) - om * ldcg(vold + c), ldcg(a.r + c));
                 const double acc = row_sum<W>(a, c, pc, [&](int j) {
-                    const ImpRec e = ldrec(Bo + j);
-                    return fma(beta, e.p - om * e.v, e.r);
+                    return fma(beta, ldcg(pold + j) - om * ldcg(vold + j), ldcg(a.r + j));
                 });
-                strec(Bn + c, q.r, pc, acc, q.rh);
-                dot = fma(q.rh, acc, dot);
+                pnew[c] = pc;
+                vnew[c] = acc;
+                dot = fma(ldcg(a.rh + c), acc, dot);
             }
             ok = reduce_barrier(a, dot, 0.0, [&](double rv, double) {
                 const double rho = ldcg(sc + SC_RHO);
@@ -307,12 +276,8 @@ __global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
             const double al = ldcg(sc + SC_ALPHA);
             double ts = 0.0, tt = 0.0;
             for (int c = t0; c < n; c += nth) {
-                const ImpRec q = ldrec(Bn + c);
-                const double scv = fma(-al, q.v, q.r);
-                const double acc = row_sum<W>(a, c, scv, [&](int j) {
-                    const ImpRec e = ldrec(Bn + j);
-                    return fma(-al, e.v, e.r);
-                });
+                const double scv = fma(-al, ldcg(vnew + c), ldcg(a.r + c));
+                const double acc = row_sum<W>(a, c, scv, [&](int j) { return fma(-al, ldcg(vnew + j), ldcg(a.r + j)); });
                 a.s[c] = scv;
                 a.t[c] = acc;
                 ts = fma(acc, scv, ts);
@@ -323,17 +288,16 @@ __global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
             });
             if (!ok) break;
         }
-        // C: x += alpha p + omega s; r = s - omega t (into the record)
+        // C: x += alpha p + omega s; r = s - omega t
         {
             const double al = ldcg(sc + SC_ALPHA), om = ldcg(sc + SC_OMEGA);
             double rr0 = 0.0, rr = 0.0;
             for (int c = t0; c < n; c += nth) {
-                const ImpRec q = ldrec(Bn + c);
                 const double sv = ldcg(a.s + c);
-                a.x[c] = fma(om, sv, fma(al, q.p, ldcg(a.x + c)));
+                a.x[c] = fma(om, sv, fma(al, ldcg(pnew + c), ldcg(a.x + c)));
                 const double rv = fma(-om, ldcg(a.t + c), sv);
-                stcg(&Bn[c].r, rv);
-                rr0 = fma(q.rh, rv, rr0);
+                a.r[c] = rv;
+                rr0 = fma(ldcg(a.rh + c), rv, rr0);
                 rr = fma(rv, rv, rr);
             }
             ok = reduce_barrier(a, rr0, rr, [&](double rho1, double rr1) {

@@ -16,11 +16,6 @@
 
 namespace dol {
 
-// BiCGSTAB iterate of one cell: residual r, direction p, v = A p, shadow residual rh.
-struct alignas(32) ImpRec {
-    double r, p, v, rh;
-};
-
 // Arguments of the persistent BiCGSTAB launch.
 struct ImpSolve {
     int n;                       // cells
@@ -34,8 +29,7 @@ struct ImpSolve {
     const double *R, *Rn, *un;   // Rn, un null on the first solve
     double inv_dt, theta;
     double *u;                   // iterate, u += delta at the end
-    double *x, *s, *t;           // [n] each
-    ImpRec *B[2];                // [n] each, 32-byte aligned: iterate records, by iteration parity
+    double *x, *r, *rh, *p[2], *v[2], *s, *t;   // [n] each
     double *part;                // [grid][2] per-block partial sums
     double *scal;                // solver scalars, SC_* layout
     double *life;                // [2] iterations and solves since the solver was created
