@@ -959,8 +959,9 @@ def run_implicit(args):
     dt_exp = w["dt"]
     dt = args.imp_dt_factor * dt_exp
     h = 1.0 / size
-    # (precision, scheme order, theta, outer iterations, warm start, row layout: None = default ELL, 0 = per slot)
-    forms = [("fp32", 3, 0.5, 1, True, None), ("fp32", 3, 0.5, 1, False, None), ("fp32", 3, 0.5, 1, True, 0),
+    # (precision, scheme order, theta, outer iterations, warm start, row layout: None = default per slot,
+    #  6 = ELL of width 6)
+    forms = [("fp32", 3, 0.5, 1, True, None), ("fp32", 3, 0.5, 1, False, None), ("fp32", 3, 0.5, 1, True, 6),
              ("fp32", 3, 1.0, 1, True, None), ("fp64", 3, 0.5, 1, True, None), ("fp32", 3, 0.5, 2, True, None),
              ("fp32", 5, 0.5, 2, True, None), ("fp32", 5, 1.0, 1, True, None)]
 
@@ -1022,7 +1023,7 @@ def run_implicit(args):
         S2.set_solver(rel_tol=args.imp_tol, max_iter=500, warm_start=warm)
         ms_T = timed_steps(lambda: S2.step(u, ws, n_outer), nI)
         name = "%s_order%d_theta%g_outer%d%s%s" % (prec, order, theta, n_outer, "_warm" if warm else "",
-                                                   "_slots" if layout == 0 else "")
+                                                   "_ell%d" % layout if layout else "")
         out[name] = {
             "value": cells * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
             "iterations_per_solve": iters / max(solves, 1), "solves": solves, "launches": int(sum(kn)),

@@ -2126,7 +2126,7 @@ dolinc_status dolinc_implicit_create(dolinc_mesh *m, const dolinc_scheme *s, dou
     imp->bar = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(imp->scal) + 256);
     imp->life = reinterpret_cast<double *>(take(256));
     CU(cudaMemset(imp->mem, 0, total));
-    if ((st = imp_build_rows(imp.get(), imp_ell_width(m->d.max_slots)))) {
+    if ((st = imp_build_rows(imp.get(), 0))) {       // per-slot rows (measured faster than ELL)
         cudaSetDevice(cur);
         return st;
     }

@@ -22,9 +22,10 @@
 //                 Warm start: x starts from the previous solve's solution kept in x
 //                 (r = b - A x, one extra product in the set-up phase); else from 0.
 //                 Vectors written inside the launch are read with ld.global.cg (L2),
-//                 never through the incoherent L1.  Rows in ELL form (width 4, 6 or
-//                 8, padded with zero weights) when the mesh's cells have at most 8
-//                 faces, else the slot ranges.
+//                 never through the incoherent L1.  Rows per face slot (the default:
+//                 a thread's consecutive slot entries share L1 sectors) or in ELL form
+//                 (width 4, 6 or 8, padded with zero weights: coalesced row loads, no
+//                 reuse; measured 9% slower on the hex/prism mesh).
 #include "common.cuh"
 #include "implicit.cuh"
 
