@@ -917,14 +917,14 @@ def run_hexprism(args):
 
 def solve_alg_bytes(M, iterations, solves):
     """Algorithmic bytes of the semi-implicit solve launches: per cell and BiCGSTAB
-    iteration the phases' FP64 vectors (A: r, p, v, rh read, p, v written; B: r, v read,
-    s, t written; C: x, p, s, t, rh read, x, r written) and the scaled rows read in A
-    and B (per slot an 8 B coefficient and a 4 B neighbour, per cell a 4 B offset); per
-    solve the set-up (R and the row scale read; x, r, rh, p, v written) and the final
-    u += x (x, u read, u written).  Neighbour re-reads are not counted."""
+    iteration the two phases' FP64 vectors (A: s, t, p, v, x, rh read, x, r, p, v
+    written; B: r, v, rh read, s, t written) and the scaled rows read in both (per slot
+    an 8 B coefficient and a 4 B neighbour, per cell a 4 B offset); per solve the
+    set-up (R and the row scale read; s, t, rh, p, v, x written) and the final u += x
+    (x, u read, u written).  Neighbour re-reads are not counted."""
     nc, ns = M.n_cells, M.n_slots
-    per_it = nc * 8 * (6 + 4 + 7) + 2 * (ns * 12 + nc * 4)
-    per_solve = nc * 8 * (2 + 5) + nc * 8 * 3
+    per_it = nc * 8 * (10 + 5) + 2 * (ns * 12 + nc * 4)
+    per_solve = nc * 8 * (2 + 6) + nc * 8 * 3
     return iterations * per_it + solves * per_solve
 
 

@@ -2104,7 +2104,7 @@ dolinc_status dolinc_implicit_create(dolinc_mesh *m, const dolinc_scheme *s, dou
     CU(cudaDeviceGetAttribute(&imp->sms, cudaDevAttrMultiProcessorCount, m->device));
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t n8 = al(8 * (size_t)std::max<int64_t>(imp->n, 1));
-    const size_t pb = al(16 * (size_t)imp->sms * kImpMaxBlocksPerSm);
+    const size_t pb = al(8 * IMP_NRED * (size_t)imp->sms * kImpMaxBlocksPerSm);
     const size_t total = 15 * n8 + pb + kImpCtrl + 256;
     cudaError_t e = cudaMalloc(&imp->mem, total);
     if (e != cudaSuccess) {

@@ -7,12 +7,15 @@
 //                 stage kernels use), summed into the diagonal or stored against the
 //                 neighbour; then every row is scaled by its diagonal.
 // k_imp_solve     BiCGSTAB on the scaled rows, all iterations in one launch.  Each
-//                 iteration is three grid-stride phases separated by a grid barrier
+//                 iteration is two grid-stride phases, each ended by a grid barrier
 //                 that also reduces the phase's dot products:
-//                   A  p = r + beta (p - omega v) on the fly for the cell and its
-//                      neighbours; v = A p;                   sum rh.v
-//                   B  s = r - alpha v likewise; t = A s;     sum t.s, t.t
-//                   C  x += alpha p + omega s; r = s - omega t;   sum rh.r, r.r
+//                   A  the last iteration's x += alpha p + omega s and r = s - omega t;
+//                      p = r + beta (p - omega v), the neighbours' r and p formed on
+//                      the fly from their s, t, p, v; v = A p;     sums rh.v, r.r
+//                   B  s = r - alpha v likewise; t = A s;  sums t.s, t.t, rh.s, rh.t
+//                 omega = t.s / t.t and the next rh.r = rh.s - omega rh.t come from
+//                 B's sums, so no third pass updates x and r; the convergence test
+//                 uses the true r.r of the following phase A.
 //                 The block that arrives last at a barrier sums the per-block partials
 //                 in block order (the result does not depend on arrival order),
 //                 computes the next scalars and releases the grid.  A wait polls at
@@ -107,24 +110,25 @@ void launch_imp_assemble(const DevMesh &m, int ns, int k, int r, double ax, doub
 }
 
 // -------------------------------------------------------------------------------- solve
-// Sum over the block of two values, in a fixed order; the result is in thread 0.
-__device__ __forceinline__ void block_sum2(double &a, double &b, double (*sh)[IMP_BLOCK / 32])
+// Sum over the block of N values, in a fixed order; the results are in thread 0.
+template <int N>
+__device__ __forceinline__ void block_sum(double (&v)[N], double (*sh)[IMP_BLOCK / 32])
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-    }
+    for (int k = 0; k < N; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) { sh[0][w] = a; sh[1][w] = b; }
+    if (l == 0)
+#pragma unroll
+        for (int k = 0; k < N; ++k) sh[k][w] = v[k];
     __syncthreads();
     if (w == 0) {
-        a = l < IMP_BLOCK / 32 ? sh[0][l] : 0.0;
-        b = l < IMP_BLOCK / 32 ? sh[1][l] : 0.0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_down_sync(0xffffffffu, a, o);
-            b += __shfl_down_sync(0xffffffffu, b, o);
+        for (int k = 0; k < N; ++k) {
+            v[k] = l < IMP_BLOCK / 32 ? sh[k][l] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
         }
     }
     __syncthreads();
@@ -133,21 +137,22 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double (*sh)[IM
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ void stcg(double *p, double v) { __stcg(p, v); }
 
-// Grid barrier that reduces (v0, v1) over all threads of the grid.  The last block to
-// arrive sums the per-block partials in block order and calls fin(sum0, sum1) in its
-// thread 0 (fin writes the next scalars) before the others are released.  Returns
-// false when the solve was aborted (a wait gave up here or in an earlier barrier).
-template <class Fin>
-__device__ __forceinline__ bool reduce_barrier(const ImpSolve &a, double v0, double v1, Fin fin)
+// Grid barrier that reduces v[0..N) over all threads of the grid.  The last block to
+// arrive sums the per-block partials in block order and calls fin(sums) in its thread
+// 0 (fin writes the next scalars) before the others are released.  Returns false when
+// the solve was aborted (a wait gave up here or in an earlier barrier).
+template <int N, class Fin>
+__device__ __forceinline__ bool reduce_barrier(const ImpSolve &a, double (&v)[N], Fin fin)
 {
-    __shared__ double sh[2][IMP_BLOCK / 32];
+    static_assert(N <= IMP_NRED, "partials hold IMP_NRED values per block");
+    __shared__ double sh[N][IMP_BLOCK / 32];
     __shared__ int last, ok;
-    block_sum2(v0, v1, sh);
+    block_sum<N>(v, sh);
     volatile unsigned *gen = a.bar + 32, *abort = a.bar + 64;
     unsigned g = 0;
     if (threadIdx.x == 0) {
-        a.part[2 * blockIdx.x] = v0;
-        a.part[2 * blockIdx.x + 1] = v1;
+#pragma unroll
+        for (int k = 0; k < N; ++k) a.part[IMP_NRED * blockIdx.x + k] = v[k];
         g = *gen;
         __threadfence();
         last = atomicAdd(a.bar, 1u) == gridDim.x - 1;
@@ -155,14 +160,15 @@ __device__ __forceinline__ bool reduce_barrier(const ImpSolve &a, double v0, dou
     __syncthreads();
     if (last) {
         __threadfence();
-        double t0 = 0.0, t1 = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += IMP_BLOCK) {
-            t0 += ldcg(a.part + 2 * b);
-            t1 += ldcg(a.part + 2 * b + 1);
-        }
-        block_sum2(t0, t1, sh);
+        double t[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) t[k] = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += IMP_BLOCK)
+#pragma unroll
+            for (int k = 0; k < N; ++k) t[k] += ldcg(a.part + IMP_NRED * b + k);
+        block_sum<N>(t, sh);
         if (threadIdx.x == 0) {
-            fin(t0, t1);
+            fin(t);
             atomicExch(a.bar, 0u);
             __threadfence();
             atomicAdd(const_cast<unsigned *>(gen), 1u);
@@ -214,111 +220,115 @@ __global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
     const int nth = gridDim.x * IMP_BLOCK;
     const int t0 = blockIdx.x * IMP_BLOCK + threadIdx.x;
     double *sc = a.scal;
+    bool ok;
 
-    // b = bscale * rhs; x = 0 (or the previous solution x0: warm start); r = rh = b - A x0;
-    // p = v = 0 (so the first p is r).  x0 is only read here, so r needs no barrier.
-    double bb = 0.0, rr = 0.0;
-    for (int c = t0; c < n; c += nth) {
-        double rhs = a.R[c];
-        if (a.Rn) rhs = (a.un[c] - a.u[c]) * a.inv_dt + a.theta * rhs + (1.0 - a.theta) * a.Rn[c];
-        const double b = a.bscale[c] * rhs;
-        double r0 = b;
-        if (a.warm) r0 = b - row_sum<W>(a, c, a.x[c], [&](int j) { return a.x[j]; });
-        a.r[c] = r0;
-        a.rh[c] = r0;
-        a.p[0][c] = 0.0;
-        a.v[0][c] = 0.0;
-        bb = fma(b, b, bb);
-        rr = fma(r0, r0, rr);
+    // Set-up: b = bscale * rhs; x = 0, or the kept solution (warm start; read only
+    // here); r0 = b - A x.  s = r0, t = 0, p = v = 0 and alpha = omega = beta = 0, so
+    // that the first phase A forms r = r0 and p = r0 and leaves x as it is.
+    {
+        double red[2] = {0.0, 0.0};
+        for (int c = t0; c < n; c += nth) {
+            double rhs = a.R[c];
+            if (a.Rn) rhs = (a.un[c] - a.u[c]) * a.inv_dt + a.theta * rhs + (1.0 - a.theta) * a.Rn[c];
+            const double b = a.bscale[c] * rhs;
+            double r0 = b;
+            if (a.warm) r0 = b - row_sum<W>(a, c, a.x[c], [&](int j) { return a.x[j]; });
+            a.s[c] = r0;
+            a.t[c] = 0.0;
+            a.rh[c] = r0;
+            a.p[0][c] = 0.0;
+            a.v[0][c] = 0.0;
+            red[0] = fma(b, b, red[0]);
+            red[1] = fma(r0, r0, red[1]);
+        }
+        if (!a.warm)
+            for (int c = t0; c < n; c += nth) a.x[c] = 0.0;
+        ok = reduce_barrier(a, red, [&](const double *t) {
+            stcg(sc + SC_RHO, t[1]);
+            stcg(sc + SC_BB, t[0]);
+            stcg(sc + SC_RR, t[1]);
+            stcg(sc + SC_ALPHA, 0.0);
+            stcg(sc + SC_BETA, 0.0);
+            stcg(sc + SC_OMEGA, 0.0);
+            stcg(sc + SC_BRK, 0.0);
+            stcg(sc + SC_SOLVES, ldcg(sc + SC_SOLVES) + 1.0);
+            stcg(a.life + 1, ldcg(a.life + 1) + 1.0);
+            stcg(sc + SC_DONE, (t[1] <= a.tol2 * t[0]) ? 1.0 : 0.0);
+        });
     }
-    if (!a.warm)
-        for (int c = t0; c < n; c += nth) a.x[c] = 0.0;
-    bool ok = reduce_barrier(a, bb, rr, [&](double s0, double s1) {
-        stcg(sc + SC_RHO, s1);
-        stcg(sc + SC_BB, s0);
-        stcg(sc + SC_RR, s1);
-        stcg(sc + SC_BETA, 0.0);
-        stcg(sc + SC_OMEGA, 0.0);
-        stcg(sc + SC_SOLVES, ldcg(sc + SC_SOLVES) + 1.0);
-        stcg(a.life + 1, ldcg(a.life + 1) + 1.0);
-        stcg(sc + SC_DONE, (s1 <= a.tol2 * s0) ? 1.0 : 0.0);
-    });
 
     for (int it = 0; ok && ldcg(sc + SC_DONE) == 0.0; ++it) {
         const double *pold = a.p[it & 1], *vold = a.v[it & 1];
         double *pnew = a.p[(it + 1) & 1], *vnew = a.v[(it + 1) & 1];
-        // A: p = r + beta (p - omega v); v = A p
+        // A: the last iteration's updates x += alpha p + omega s and r = s - omega t;
+        //    then p = r + beta (p - omega v) and v = A p, the neighbours' r and p formed
+        //    on the fly;  sums rh.v, r.r (the true recursive residual)
         {
-            const double beta = ldcg(sc + SC_BETA), om = ldcg(sc + SC_OMEGA);
-            double dot = 0.0;
+            const double al = ldcg(sc + SC_ALPHA), om = ldcg(sc + SC_OMEGA), beta = ldcg(sc + SC_BETA);
+            double red[2] = {0.0, 0.0};
             for (int c = t0; c < n; c += nth) {
-                const double pc = fma(beta, ldcg(pold + c) - om * ldcg(vold + c), ldcg(a.r + c));
+                const double sv = ldcg(a.s + c);
+                const double rc = fma(-om, ldcg(a.t + c), sv);
+                const double po = ldcg(pold + c);
+                a.x[c] = fma(om, sv, fma(al, po, ldcg(a.x + c)));
+                const double pc = fma(beta, po - om * ldcg(vold + c), rc);
                 const double acc = row_sum<W>(a, c, pc, [&](int j) {
-                    return fma(beta, ldcg(pold + j) - om * ldcg(vold + j), ldcg(a.r + j));
+                    return fma(beta, ldcg(pold + j) - om * ldcg(vold + j), fma(-om, ldcg(a.t + j), ldcg(a.s + j)));
                 });
+                a.r[c] = rc;
                 pnew[c] = pc;
                 vnew[c] = acc;
-                dot = fma(ldcg(a.rh + c), acc, dot);
+                red[0] = fma(ldcg(a.rh + c), acc, red[0]);
+                red[1] = fma(rc, rc, red[1]);
             }
-            ok = reduce_barrier(a, dot, 0.0, [&](double rv, double) {
-                const double rho = ldcg(sc + SC_RHO);
-                if (rv == 0.0 || !isfinite(rv)) {
+            ok = reduce_barrier(a, red, [&](const double *t) {
+                const double rv = t[0], rr = t[1];
+                stcg(sc + SC_RR, rr);
+                if (rr <= a.tol2 * ldcg(sc + SC_BB)) {
+                    stcg(sc + SC_DONE, 1.0);
+                } else if (ldcg(sc + SC_BRK) != 0.0 || rv == 0.0 || !isfinite(rv) || !isfinite(rr)) {
                     atomicOr(a.status, 4u);
                     stcg(sc + SC_DONE, 1.0);
-                    stcg(sc + SC_ALPHA, 0.0);
+                } else if (it >= a.max_iter) {
+                    atomicOr(a.status, 8u);
+                    stcg(sc + SC_DONE, 1.0);
                 } else {
-                    stcg(sc + SC_ALPHA, rho / rv);
+                    stcg(sc + SC_ALPHA, ldcg(sc + SC_RHO) / rv);
                 }
             });
             if (!ok || ldcg(sc + SC_DONE) != 0.0) break;
         }
-        // B: s = r - alpha v; t = A s
+        // B: s = r - alpha v; t = A s, the neighbours' s on the fly;  sums t.s, t.t,
+        //    rh.s, rh.t, which give omega = t.s / t.t and the next rh.r = rh.s - omega rh.t
         {
             const double al = ldcg(sc + SC_ALPHA);
-            double ts = 0.0, tt = 0.0;
+            double red[4] = {0.0, 0.0, 0.0, 0.0};
             for (int c = t0; c < n; c += nth) {
                 const double scv = fma(-al, ldcg(vnew + c), ldcg(a.r + c));
                 const double acc = row_sum<W>(a, c, scv, [&](int j) { return fma(-al, ldcg(vnew + j), ldcg(a.r + j)); });
                 a.s[c] = scv;
                 a.t[c] = acc;
-                ts = fma(acc, scv, ts);
-                tt = fma(acc, acc, tt);
+                const double rh = ldcg(a.rh + c);
+                red[0] = fma(acc, scv, red[0]);
+                red[1] = fma(acc, acc, red[1]);
+                red[2] = fma(rh, scv, red[2]);
+                red[3] = fma(rh, acc, red[3]);
             }
-            ok = reduce_barrier(a, ts, tt, [&](double sts, double stt) {
-                stcg(sc + SC_OMEGA, stt > 0.0 ? sts / stt : 0.0);
-            });
-            if (!ok) break;
-        }
-        // C: x += alpha p + omega s; r = s - omega t
-        {
-            const double al = ldcg(sc + SC_ALPHA), om = ldcg(sc + SC_OMEGA);
-            double rr0 = 0.0, rr = 0.0;
-            for (int c = t0; c < n; c += nth) {
-                const double sv = ldcg(a.s + c);
-                a.x[c] = fma(om, sv, fma(al, ldcg(pnew + c), ldcg(a.x + c)));
-                const double rv = fma(-om, ldcg(a.t + c), sv);
-                a.r[c] = rv;
-                rr0 = fma(ldcg(a.rh + c), rv, rr0);
-                rr = fma(rv, rv, rr);
-            }
-            ok = reduce_barrier(a, rr0, rr, [&](double rho1, double rr1) {
-                stcg(sc + SC_RR, rr1);
+            ok = reduce_barrier(a, red, [&](const double *t) {
                 stcg(sc + SC_ITERS, ldcg(sc + SC_ITERS) + 1.0);
                 stcg(a.life, ldcg(a.life) + 1.0);
-                const double om = ldcg(sc + SC_OMEGA);
-                if (rr1 <= a.tol2 * ldcg(sc + SC_BB)) {
-                    stcg(sc + SC_DONE, 1.0);
-                } else if (om == 0.0 || rho1 == 0.0 || !isfinite(rr1)) {
-                    atomicOr(a.status, 4u);
-                    stcg(sc + SC_DONE, 1.0);
-                } else if (it + 1 >= a.max_iter) {
-                    atomicOr(a.status, 8u);
-                    stcg(sc + SC_DONE, 1.0);
+                const double om = t[1] > 0.0 ? t[0] / t[1] : 0.0;     // t = 0: s = 0, the next r is 0
+                const double rho1 = t[2] - om * t[3];
+                stcg(sc + SC_OMEGA, om);
+                if (t[1] > 0.0 && (om == 0.0 || rho1 == 0.0 || !isfinite(rho1))) {
+                    stcg(sc + SC_BRK, 1.0);      // breakdown: stop after the next phase A's updates
+                    stcg(sc + SC_BETA, 0.0);
                 } else {
-                    stcg(sc + SC_BETA, (rho1 / ldcg(sc + SC_RHO)) * (ldcg(sc + SC_ALPHA) / om));
-                    stcg(sc + SC_RHO, rho1);
+                    stcg(sc + SC_BETA, om != 0.0 ? (rho1 / ldcg(sc + SC_RHO)) * (ldcg(sc + SC_ALPHA) / om) : 0.0);
                 }
+                stcg(sc + SC_RHO, rho1);
             });
+            if (!ok) break;
         }
     }
     if (!ok) return;

@@ -30,7 +30,7 @@ struct ImpSolve {
     double inv_dt, theta;
     double *u;                   // iterate, u += delta at the end
     double *x, *r, *rh, *p[2], *v[2], *s, *t;   // [n] each
-    double *part;                // [grid][2] per-block partial sums
+    double *part;                // [grid][IMP_NRED] per-block partial sums
     double *scal;                // solver scalars, SC_* layout
     double *life;                // [2] iterations and solves since the solver was created
     unsigned *bar;               // [0] arrivals, [32] generation, [64] abort
@@ -43,13 +43,14 @@ struct ImpSolve {
 
 // Layout of ImpSolve::scal.  Iteration counts accumulate over the solves of a step;
 // the rest describe the last solve.
-enum { SC_RHO = 0, SC_ALPHA, SC_OMEGA, SC_BETA, SC_BB, SC_RR, SC_DONE, SC_ITERS, SC_SOLVES, SC_COUNT };
+enum { SC_RHO = 0, SC_ALPHA, SC_OMEGA, SC_BETA, SC_BB, SC_RR, SC_DONE, SC_ITERS, SC_SOLVES, SC_BRK, SC_COUNT };
 
 // ELL width of the rows for cells of at most max_slots faces (4, 6, 8; 0: slot ranges)
 int imp_ell_width(int max_slots);
 cudaError_t launch_imp_solve(const ImpSolve &a, int ell, int grid, cudaStream_t s);
 int imp_solve_blocks_per_sm(int ell);
 constexpr int IMP_BLOCK = 256;
+constexpr int IMP_NRED = 4;      // values a grid barrier reduces at most (partials per block)
 
 // Rows of (V/dt + theta K): nbr, off (scaled by 1/diag), diag and bscale, in ELL form of
 // width ell (padding: the cell itself with weight 0) or per slot (ell = 0).  ns: the
