@@ -7,15 +7,16 @@
 //                 stage kernels use), summed into the diagonal or stored against the
 //                 neighbour; then every row is scaled by its diagonal.
 // k_imp_solve     BiCGSTAB on the scaled rows, all iterations in one launch.  Each
-//                 iteration is two grid-stride phases, each ended by a grid barrier
+//                 iteration is three grid-stride phases, each ended by a grid barrier
 //                 that also reduces the phase's dot products:
-//                   A  the last iteration's x += alpha p + omega s and r = s - omega t;
-//                      p = r + beta (p - omega v), the neighbours' r and p formed on
-//                      the fly from their s, t, p, v; v = A p;     sums rh.v, r.r
-//                   B  s = r - alpha v likewise; t = A s;  sums t.s, t.t, rh.s, rh.t
-//                 omega = t.s / t.t and the next rh.r = rh.s - omega rh.t come from
-//                 B's sums, so no third pass updates x and r; the convergence test
-//                 uses the true r.r of the following phase A.
+//                   A  v = A p (the neighbours' p gathered);           sum rh.v
+//                   B  s = r - alpha v, t = A s (the neighbours' s formed from their
+//                      r and v);                      sums t.s, t.t, rh.s, rh.t
+//                   C  x += alpha p + omega s; r = s - omega t;
+//                      p = r + beta (p - omega v), own values only;   sum r.r
+//                 omega = t.s / t.t, the next rh.r = rh.s - omega rh.t and beta come
+//                 from B's sums, so C can update p without another barrier, and a
+//                 neighbour is gathered three times per iteration (p; r, v).
 //                 The block that arrives last at a barrier sums the per-block partials
 //                 in block order (the result does not depend on arrival order),
 //                 computes the next scalars and releases the grid.  A wait polls at
@@ -141,10 +142,15 @@ __device__ __forceinline__ void stcg(double *p, double v) { __stcg(p, v); }
 // arrive sums the per-block partials in block order and calls fin(sums) in its thread
 // 0 (fin writes the next scalars) before the others are released.  Returns false when
 // the solve was aborted (a wait gave up here or in an earlier barrier).
+template <int N> struct Red {
+    double v[N];
+};
+
 template <int N, class Fin>
-__device__ __forceinline__ bool reduce_barrier(const ImpSolve &a, double (&v)[N], Fin fin)
+__device__ __forceinline__ bool reduce_barrier(const ImpSolve &a, Red<N> r, Fin fin)
 {
     static_assert(N <= IMP_NRED, "partials hold IMP_NRED values per block");
+    double (&v)[N] = r.v;
     __shared__ double sh[N][IMP_BLOCK / 32];
     __shared__ int last, ok;
     block_sum<N>(v, sh);
@@ -208,6 +214,7 @@ __device__ __forceinline__ double row_sum(const ImpSolve &a, int c, double acc, 
         for (int q = 0; q < W; ++q) acc = fma(o[q], f(j[q]), acc);
     } else {
         const int s0 = __ldg(a.row + c), s1 = __ldg(a.row + c + 1);
+#pragma unroll 2
         for (int s = s0; s < s1; ++s) acc = fma(__ldg(a.off + s), f(__ldg(a.nbr + s)), acc);
     }
     return acc;
@@ -220,26 +227,24 @@ __global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
     const int nth = gridDim.x * IMP_BLOCK;
     const int t0 = blockIdx.x * IMP_BLOCK + threadIdx.x;
     double *sc = a.scal;
+    double *p = a.p[0], *v = a.v[0];
     bool ok;
 
     // Set-up: b = bscale * rhs; x = 0, or the kept solution (warm start; read only
-    // here); r0 = b - A x.  s = r0, t = 0, p = v = 0 and alpha = omega = beta = 0, so
-    // that the first phase A forms r = r0 and p = r0 and leaves x as it is.
+    // here); r = rh = p = b - A x.
     {
-        double red[2] = {0.0, 0.0};
+        Red<2> red{{0.0, 0.0}};
         for (int c = t0; c < n; c += nth) {
             double rhs = a.R[c];
             if (a.Rn) rhs = (a.un[c] - a.u[c]) * a.inv_dt + a.theta * rhs + (1.0 - a.theta) * a.Rn[c];
             const double b = a.bscale[c] * rhs;
             double r0 = b;
             if (a.warm) r0 = b - row_sum<W>(a, c, a.x[c], [&](int j) { return a.x[j]; });
-            a.s[c] = r0;
-            a.t[c] = 0.0;
+            a.r[c] = r0;
             a.rh[c] = r0;
-            a.p[0][c] = 0.0;
-            a.v[0][c] = 0.0;
-            red[0] = fma(b, b, red[0]);
-            red[1] = fma(r0, r0, red[1]);
+            p[c] = r0;
+            red.v[0] = fma(b, b, red.v[0]);
+            red.v[1] = fma(r0, r0, red.v[1]);
         }
         if (!a.warm)
             for (int c = t0; c < n; c += nth) a.x[c] = 0.0;
@@ -247,9 +252,6 @@ __global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
             stcg(sc + SC_RHO, t[1]);
             stcg(sc + SC_BB, t[0]);
             stcg(sc + SC_RR, t[1]);
-            stcg(sc + SC_ALPHA, 0.0);
-            stcg(sc + SC_BETA, 0.0);
-            stcg(sc + SC_OMEGA, 0.0);
             stcg(sc + SC_BRK, 0.0);
             stcg(sc + SC_SOLVES, ldcg(sc + SC_SOLVES) + 1.0);
             stcg(a.life + 1, ldcg(a.life + 1) + 1.0);
@@ -258,61 +260,40 @@ __global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
     }
 
     for (int it = 0; ok && ldcg(sc + SC_DONE) == 0.0; ++it) {
-        const double *pold = a.p[it & 1], *vold = a.v[it & 1];
-        double *pnew = a.p[(it + 1) & 1], *vnew = a.v[(it + 1) & 1];
-        // A: the last iteration's updates x += alpha p + omega s and r = s - omega t;
-        //    then p = r + beta (p - omega v) and v = A p, the neighbours' r and p formed
-        //    on the fly;  sums rh.v, r.r (the true recursive residual)
+        // A: v = A p (the neighbours' p gathered);  sum rh.v
         {
-            const double al = ldcg(sc + SC_ALPHA), om = ldcg(sc + SC_OMEGA), beta = ldcg(sc + SC_BETA);
-            double red[2] = {0.0, 0.0};
+            Red<1> red{{0.0}};
             for (int c = t0; c < n; c += nth) {
-                const double sv = ldcg(a.s + c);
-                const double rc = fma(-om, ldcg(a.t + c), sv);
-                const double po = ldcg(pold + c);
-                a.x[c] = fma(om, sv, fma(al, po, ldcg(a.x + c)));
-                const double pc = fma(beta, po - om * ldcg(vold + c), rc);
-                const double acc = row_sum<W>(a, c, pc, [&](int j) {
-                    return fma(beta, ldcg(pold + j) - om * ldcg(vold + j), fma(-om, ldcg(a.t + j), ldcg(a.s + j)));
-                });
-                a.r[c] = rc;
-                pnew[c] = pc;
-                vnew[c] = acc;
-                red[0] = fma(ldcg(a.rh + c), acc, red[0]);
-                red[1] = fma(rc, rc, red[1]);
+                const double acc = row_sum<W>(a, c, ldcg(p + c), [&](int j) { return ldcg(p + j); });
+                v[c] = acc;
+                red.v[0] = fma(ldcg(a.rh + c), acc, red.v[0]);
             }
             ok = reduce_barrier(a, red, [&](const double *t) {
-                const double rv = t[0], rr = t[1];
-                stcg(sc + SC_RR, rr);
-                if (rr <= a.tol2 * ldcg(sc + SC_BB)) {
-                    stcg(sc + SC_DONE, 1.0);
-                } else if (ldcg(sc + SC_BRK) != 0.0 || rv == 0.0 || !isfinite(rv) || !isfinite(rr)) {
+                if (t[0] == 0.0 || !isfinite(t[0])) {
                     atomicOr(a.status, 4u);
                     stcg(sc + SC_DONE, 1.0);
-                } else if (it >= a.max_iter) {
-                    atomicOr(a.status, 8u);
-                    stcg(sc + SC_DONE, 1.0);
                 } else {
-                    stcg(sc + SC_ALPHA, ldcg(sc + SC_RHO) / rv);
+                    stcg(sc + SC_ALPHA, ldcg(sc + SC_RHO) / t[0]);
                 }
             });
             if (!ok || ldcg(sc + SC_DONE) != 0.0) break;
         }
-        // B: s = r - alpha v; t = A s, the neighbours' s on the fly;  sums t.s, t.t,
-        //    rh.s, rh.t, which give omega = t.s / t.t and the next rh.r = rh.s - omega rh.t
+        // B: s = r - alpha v; t = A s, the neighbours' s formed from their r and v;
+        //    sums t.s, t.t, rh.s, rh.t: omega = t.s / t.t, the next rh.r = rh.s - omega
+        //    rh.t, and beta, all known before the updates of phase C
         {
             const double al = ldcg(sc + SC_ALPHA);
-            double red[4] = {0.0, 0.0, 0.0, 0.0};
+            Red<4> red{{0.0, 0.0, 0.0, 0.0}};
             for (int c = t0; c < n; c += nth) {
-                const double scv = fma(-al, ldcg(vnew + c), ldcg(a.r + c));
-                const double acc = row_sum<W>(a, c, scv, [&](int j) { return fma(-al, ldcg(vnew + j), ldcg(a.r + j)); });
+                const double scv = fma(-al, ldcg(v + c), ldcg(a.r + c));
+                const double acc = row_sum<W>(a, c, scv, [&](int j) { return fma(-al, ldcg(v + j), ldcg(a.r + j)); });
                 a.s[c] = scv;
                 a.t[c] = acc;
                 const double rh = ldcg(a.rh + c);
-                red[0] = fma(acc, scv, red[0]);
-                red[1] = fma(acc, acc, red[1]);
-                red[2] = fma(rh, scv, red[2]);
-                red[3] = fma(rh, acc, red[3]);
+                red.v[0] = fma(acc, scv, red.v[0]);
+                red.v[1] = fma(acc, acc, red.v[1]);
+                red.v[2] = fma(rh, scv, red.v[2]);
+                red.v[3] = fma(rh, acc, red.v[3]);
             }
             ok = reduce_barrier(a, red, [&](const double *t) {
                 stcg(sc + SC_ITERS, ldcg(sc + SC_ITERS) + 1.0);
@@ -321,7 +302,7 @@ __global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
                 const double rho1 = t[2] - om * t[3];
                 stcg(sc + SC_OMEGA, om);
                 if (t[1] > 0.0 && (om == 0.0 || rho1 == 0.0 || !isfinite(rho1))) {
-                    stcg(sc + SC_BRK, 1.0);      // breakdown: stop after the next phase A's updates
+                    stcg(sc + SC_BRK, 1.0);      // breakdown: stop after phase C's updates
                     stcg(sc + SC_BETA, 0.0);
                 } else {
                     stcg(sc + SC_BETA, om != 0.0 ? (rho1 / ldcg(sc + SC_RHO)) * (ldcg(sc + SC_ALPHA) / om) : 0.0);
@@ -329,6 +310,32 @@ __global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
                 stcg(sc + SC_RHO, rho1);
             });
             if (!ok) break;
+        }
+        // C: x += alpha p + omega s; r = s - omega t; p = r + beta (p - omega v), all
+        //    of the cell's own values;  sum r.r (the true recursive residual)
+        {
+            const double al = ldcg(sc + SC_ALPHA), om = ldcg(sc + SC_OMEGA), beta = ldcg(sc + SC_BETA);
+            Red<1> red{{0.0}};
+            for (int c = t0; c < n; c += nth) {
+                const double sv = ldcg(a.s + c), pc = ldcg(p + c);
+                a.x[c] = fma(om, sv, fma(al, pc, ldcg(a.x + c)));
+                const double rv = fma(-om, ldcg(a.t + c), sv);
+                a.r[c] = rv;
+                p[c] = fma(beta, pc - om * ldcg(v + c), rv);
+                red.v[0] = fma(rv, rv, red.v[0]);
+            }
+            ok = reduce_barrier(a, red, [&](const double *t) {
+                stcg(sc + SC_RR, t[0]);
+                if (t[0] <= a.tol2 * ldcg(sc + SC_BB)) {
+                    stcg(sc + SC_DONE, 1.0);
+                } else if (ldcg(sc + SC_BRK) != 0.0 || !isfinite(t[0])) {
+                    atomicOr(a.status, 4u);
+                    stcg(sc + SC_DONE, 1.0);
+                } else if (it + 1 >= a.max_iter) {
+                    atomicOr(a.status, 8u);
+                    stcg(sc + SC_DONE, 1.0);
+                }
+            });
         }
     }
     if (!ok) return;
