@@ -917,14 +917,14 @@ def run_hexprism(args):
 
 def solve_alg_bytes(M, iterations, solves):
     """Algorithmic bytes of the semi-implicit solve launches: per cell and BiCGSTAB
-    iteration the two phases' FP64 vectors (A: s, t, p, v, x, rh read, x, r, p, v
-    written; B: r, v, rh read, s, t written) and the scaled rows read in both (per slot
-    an 8 B coefficient and a 4 B neighbour, per cell a 4 B offset); per solve the
-    set-up (R and the row scale read; s, t, rh, p, v, x written) and the final u += x
-    (x, u read, u written).  Neighbour re-reads are not counted."""
+    iteration the three phases' FP64 vectors (A: p, rh read, v written; B: r, v, rh
+    read, s, t written; C: s, p, x, t, v read, x, r, p written) and the scaled rows
+    read in A and B (per slot an 8 B coefficient and a 4 B neighbour, per cell a 4 B
+    offset); per solve the set-up (R and the row scale read; r, rh, p, x written) and
+    the final u += x (x, u read, u written).  Neighbour re-reads are not counted."""
     nc, ns = M.n_cells, M.n_slots
-    per_it = nc * 8 * (10 + 5) + 2 * (ns * 12 + nc * 4)
-    per_solve = nc * 8 * (2 + 6) + nc * 8 * 3
+    per_it = nc * 8 * (3 + 5 + 8) + 2 * (ns * 12 + nc * 4)
+    per_solve = nc * 8 * (2 + 4) + nc * 8 * 3
     return iterations * per_it + solves * per_solve
 
 

@@ -69,14 +69,14 @@ def test_stage_orders_follow_the_stencil_and_limiter():
     assert bench.stage_orders(s(k=9, r=4, n_diff=4)) == 4
 
 
-@pytest.mark.parametrize("nfc,per_it", [(3, 200), (4, 224), (16 / 3, 256)])
+@pytest.mark.parametrize("nfc,per_it", [(3, 208), (4, 232), (16 / 3, 264)])
 def test_solve_bytes(nfc, per_it):
-    """Semi-implicit solve, per cell: an iteration reads or writes 15 FP64 vectors
-    (120 B) and the scaled rows twice, 2 (12 nfc + 4) B (triangles 120 + 80 = 200,
-    tetrahedra 120 + 104 = 224, hex/prism 120 + 136 = 256); a solve adds 88 B of
+    """Semi-implicit solve, per cell: an iteration reads or writes 16 FP64 vectors
+    (128 B) and the scaled rows twice, 2 (12 nfc + 4) B (triangles 128 + 80 = 208,
+    tetrahedra 128 + 104 = 232, hex/prism 128 + 136 = 264); a solve adds 72 B of
     set-up and final update."""
     n = 3000
     M = SimpleNamespace(n_cells=n, n_slots=nfc * n)
     assert bench.solve_alg_bytes(M, 1, 0) / n == pytest.approx(per_it)
-    assert bench.solve_alg_bytes(M, 0, 1) / n == pytest.approx(88)
-    assert bench.solve_alg_bytes(M, 7, 2) / n == pytest.approx(7 * per_it + 176)
+    assert bench.solve_alg_bytes(M, 0, 1) / n == pytest.approx(72)
+    assert bench.solve_alg_bytes(M, 7, 2) / n == pytest.approx(7 * per_it + 144)
