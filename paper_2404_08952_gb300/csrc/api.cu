@@ -2016,8 +2016,7 @@ struct dolinc_implicit {
     void *rows = nullptr;                // nbr and off (their own allocation: the layout can change)
     int32_t *nbr = nullptr;
     double *off = nullptr, *diag = nullptr, *bscale = nullptr;
-    double *vec[5] = {};                 // x rh p s t
-    double2 *rv = nullptr;               // (r, v) pairs
+    double *vec[9] = {};                 // x r rh p0 p1 v0 v1 s t
     double *R = nullptr, *Rn = nullptr, *un = nullptr;
     double *xw = nullptr;                // the first solve's solution, kept between steps
     double *part = nullptr;
@@ -2106,7 +2105,7 @@ dolinc_status dolinc_implicit_create(dolinc_mesh *m, const dolinc_scheme *s, dou
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t n8 = al(8 * (size_t)std::max<int64_t>(imp->n, 1));
     const size_t pb = al(8 * IMP_NRED * (size_t)imp->sms * kImpMaxBlocksPerSm);
-    const size_t total = 13 * n8 + pb + kImpCtrl + 256;    // 5 vectors, the pairs (2), 6 more
+    const size_t total = 15 * n8 + pb + kImpCtrl + 256;
     cudaError_t e = cudaMalloc(&imp->mem, total);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -2118,7 +2117,6 @@ dolinc_status dolinc_implicit_create(dolinc_mesh *m, const dolinc_scheme *s, dou
     imp->diag = reinterpret_cast<double *>(take(n8));
     imp->bscale = reinterpret_cast<double *>(take(n8));
     for (auto &v : imp->vec) v = reinterpret_cast<double *>(take(n8));
-    imp->rv = reinterpret_cast<double2 *>(take(2 * n8));
     imp->R = reinterpret_cast<double *>(take(n8));
     imp->Rn = reinterpret_cast<double *>(take(n8));
     imp->un = reinterpret_cast<double *>(take(n8));
@@ -2193,11 +2191,14 @@ dolinc_status dolinc_implicit_step(dolinc_implicit *imp, double *u, int n_outer,
     a.theta = imp->theta;
     a.u = u;
     a.x = imp->vec[0];
-    a.rh = imp->vec[1];
-    a.p = imp->vec[2];
-    a.s = imp->vec[3];
-    a.t = imp->vec[4];
-    a.rv = imp->rv;
+    a.r = imp->vec[1];
+    a.rh = imp->vec[2];
+    a.p[0] = imp->vec[3];
+    a.p[1] = imp->vec[4];
+    a.v[0] = imp->vec[5];
+    a.v[1] = imp->vec[6];
+    a.s = imp->vec[7];
+    a.t = imp->vec[8];
     a.part = imp->part;
     a.scal = imp->scal;
     a.life = imp->life;

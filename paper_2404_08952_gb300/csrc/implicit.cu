@@ -227,8 +227,7 @@ __global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
     const int nth = gridDim.x * IMP_BLOCK;
     const int t0 = blockIdx.x * IMP_BLOCK + threadIdx.x;
     double *sc = a.scal;
-    double *p = a.p;
-    double2 *rv = a.rv;       // (r, v) of each cell: phase B gathers both with one 16-byte load
+    double *p = a.p[0], *v = a.v[0];
     bool ok;
 
     // Set-up: b = bscale * rhs; x = 0, or the kept solution (warm start; read only
@@ -241,7 +240,7 @@ __global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
             const double b = a.bscale[c] * rhs;
             double r0 = b;
             if (a.warm) r0 = b - row_sum<W>(a, c, a.x[c], [&](int j) { return a.x[j]; });
-            stcg(&rv[c].x, r0);
+            a.r[c] = r0;
             a.rh[c] = r0;
             p[c] = r0;
             red.v[0] = fma(b, b, red.v[0]);
@@ -266,7 +265,7 @@ __global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
             Red<1> red{{0.0}};
             for (int c = t0; c < n; c += nth) {
                 const double acc = row_sum<W>(a, c, ldcg(p + c), [&](int j) { return ldcg(p + j); });
-                stcg(&rv[c].y, acc);
+                v[c] = acc;
                 red.v[0] = fma(ldcg(a.rh + c), acc, red.v[0]);
             }
             ok = reduce_barrier(a, red, [&](const double *t) {
@@ -286,12 +285,8 @@ __global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
             const double al = ldcg(sc + SC_ALPHA);
             Red<4> red{{0.0, 0.0, 0.0, 0.0}};
             for (int c = t0; c < n; c += nth) {
-                const double2 q = __ldcg(rv + c);
-                const double scv = fma(-al, q.y, q.x);
-                const double acc = row_sum<W>(a, c, scv, [&](int j) {
-                    const double2 e = __ldcg(rv + j);
-                    return fma(-al, e.y, e.x);
-                });
+                const double scv = fma(-al, ldcg(v + c), ldcg(a.r + c));
+                const double acc = row_sum<W>(a, c, scv, [&](int j) { return fma(-al, ldcg(v + j), ldcg(a.r + j)); });
                 a.s[c] = scv;
                 a.t[c] = acc;
                 const double rh = ldcg(a.rh + c);
@@ -324,11 +319,10 @@ __global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
             for (int c = t0; c < n; c += nth) {
                 const double sv = ldcg(a.s + c), pc = ldcg(p + c);
                 a.x[c] = fma(om, sv, fma(al, pc, ldcg(a.x + c)));
-                const double rnew = fma(-om, ldcg(a.t + c), sv);
-                const double vc = ldcg(&rv[c].y);
-                stcg(&rv[c].x, rnew);
-                p[c] = fma(beta, pc - om * vc, rnew);
-                red.v[0] = fma(rnew, rnew, red.v[0]);
+                const double rv = fma(-om, ldcg(a.t + c), sv);
+                a.r[c] = rv;
+                p[c] = fma(beta, pc - om * ldcg(v + c), rv);
+                red.v[0] = fma(rv, rv, red.v[0]);
             }
             ok = reduce_barrier(a, red, [&](const double *t) {
                 stcg(sc + SC_RR, t[0]);

@@ -29,8 +29,7 @@ struct ImpSolve {
     const double *R, *Rn, *un;   // Rn, un null on the first solve
     double inv_dt, theta;
     double *u;                   // iterate, u += delta at the end
-    double *x, *rh, *p, *s, *t;  // [n] each
-    double2 *rv;                 // [n] (r, v) pairs, 16-byte aligned
+    double *x, *r, *rh, *p[2], *v[2], *s, *t;   // [n] each
     double *part;                // [grid][IMP_NRED] per-block partial sums
     double *scal;                // solver scalars, SC_* layout
     double *life;                // [2] iterations and solves since the solver was created
