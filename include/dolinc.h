@@ -577,8 +577,11 @@ dolinc_status dolinc_implicit_set_solver(dolinc_implicit *solver, double rel_tol
 /* Layout of the rows the solve reads: an ELL width (4, 6 or 8, at least the mesh's
  * largest number of faces per cell; entry q of cell c at q n_cells + c, padded with the
  * cell itself at weight 0) or 0 (per face slot, the default).  Both give the same
- * rows; the per-cell sums keep their order.  Re-assembles the rows and waits for the device.  INVALID_ARG
- * otherwise.  dolinc_implicit_layout returns the current layout (-1 for NULL). */
+ * rows; the per-cell sums keep their order.  Re-assembles the rows and waits for the
+ * device.  INVALID_ARG for another width; OOM when the new rows do not fit, after which
+ * the solver has no rows and dolinc_implicit_step / _rows return INVALID_ARG until a
+ * dolinc_implicit_set_layout succeeds.  dolinc_implicit_layout returns the current
+ * layout (-1 for NULL). */
 dolinc_status dolinc_implicit_set_layout(dolinc_implicit *solver, int ell);
 int dolinc_implicit_layout(const dolinc_implicit *solver);
 

@@ -2177,6 +2177,7 @@ dolinc_status dolinc_implicit_step(dolinc_implicit *imp, double *u, int n_outer,
 {
     if (!imp || !u) return fail(DOLINC_ERR_INVALID_ARG, "null solver or field");
     if (n_outer < 1) return fail(DOLINC_ERR_INVALID_ARG, "n_outer must be >= 1");
+    if (!imp->rows) return fail(DOLINC_ERR_INVALID_ARG, "the solver has no rows (a failed dolinc_implicit_set_layout)");
     dolinc_mesh *m = imp->m;
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     CU(cudaMemsetAsync(imp->scal, 0, kImpCtrl, cs));
@@ -2253,6 +2254,7 @@ dolinc_status dolinc_implicit_rows(const dolinc_implicit *imp, int32_t *row_offs
                                    double *diag)
 {
     if (!imp || !row_offsets || !nbr || !off || !diag) return fail(DOLINC_ERR_INVALID_ARG, "null argument");
+    if (!imp->rows) return fail(DOLINC_ERR_INVALID_ARG, "the solver has no rows (a failed dolinc_implicit_set_layout)");
     const dolinc_mesh *m = imp->m;
     CU(cudaDeviceSynchronize());
     std::memcpy(row_offsets, m->h.off.data(), sizeof(int32_t) * (size_t)(imp->n + 1));
