@@ -171,8 +171,8 @@ def test_outer_iterations_reach_the_full_theta_scheme():
 
 
 def test_usr3_weight_part_is_dissipative_and_csr4_is_not():
-    """The paper's remark that the DOLINC split contributes to the stability of the
-    implicit matrix, measured: on jittered triangles and tetrahedra every eigenvalue of
+    """Sec 2.4 remarks that the DOLINC split helps the implicit matrix; measured: on
+    jittered triangles and tetrahedra every eigenvalue of
     V^-1 K has a non-negative real part for USR3 (its w_s favours the upwind cell), so
     V/dt + theta K is definite at any dt; CSR4's central weights give eigenvalues with
     negative real parts, so its matrix turns indefinite above some Courant number."""
