@@ -961,9 +961,10 @@ def run_implicit(args):
     h = 1.0 / size
     # (precision, scheme order, theta, outer iterations, warm start, row layout: None = default per slot,
     #  6 = ELL of width 6)
-    forms = [("fp32", 3, 0.5, 1, True, None), ("fp32", 3, 0.5, 1, False, None), ("fp32", 3, 0.5, 1, True, 6),
-             ("fp32", 3, 1.0, 1, True, None), ("fp64", 3, 0.5, 1, True, None), ("fp32", 3, 0.5, 2, True, None),
-             ("fp32", 5, 0.5, 2, True, None), ("fp32", 5, 1.0, 1, True, None)]
+    # warm start: 0 from zero, 1 from the last step's solution, 2 extrapolated from the last two
+    forms = [("fp32", 3, 0.5, 1, 2, None), ("fp32", 3, 0.5, 1, 1, None), ("fp32", 3, 0.5, 1, 0, None),
+             ("fp32", 3, 0.5, 1, 2, 6), ("fp32", 3, 1.0, 1, 2, None), ("fp64", 3, 0.5, 1, 2, None),
+             ("fp32", 3, 0.5, 2, 2, None), ("fp32", 5, 0.5, 2, 2, None), ("fp32", 5, 1.0, 1, 2, None)]
 
     exact = np.asarray(exact, dtype=np.float64).reshape(-1)
 
@@ -1022,7 +1023,7 @@ def run_implicit(args):
         u = torch.from_numpy(M.to_lib(w["u0"])).cuda()
         S2.set_solver(rel_tol=args.imp_tol, max_iter=500, warm_start=warm)
         ms_T = timed_steps(lambda: S2.step(u, ws, n_outer), nI)
-        name = "%s_order%d_theta%g_outer%d%s%s" % (prec, order, theta, n_outer, "_warm" if warm else "",
+        name = "%s_order%d_theta%g_outer%d%s%s" % (prec, order, theta, n_outer, ("", "_warm", "_extrap")[warm],
                                                    "_ell%d" % layout if layout else "")
         out[name] = {
             "value": cells * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
@@ -1049,7 +1050,7 @@ def run_implicit(args):
         msE = timed_steps(lambda: dg.dolinc_rk_steps(M, sch, T / nE, nE, u, ws), 1)
         expl["%s_order%d_rk3" % (prec, order)] = {"steps": nE, "dt": T / nE, "ms": round(msE, 3), "l2": l2(u)}
         del ws, u
-    head = "fp32_order3_theta0.5_outer1_warm"
+    head = "fp32_order3_theta0.5_outer1_extrap"
     main = out[head]
     cpu = None
     if not args.no_oracle:      # the oracle's step (sparse LU) on a bounded sample of the workload

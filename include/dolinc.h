@@ -567,10 +567,11 @@ void dolinc_implicit_destroy(dolinc_implicit *solver);
 
 /* Solver settings: relative tolerance (default 1e-10), iterations per solve (default
  * 1000), the polls a grid-barrier wait makes before it gives up (default 2^23), and
- * warm_start (default 0): 1 starts the first solve of each step from the previous
- * step's first solution instead of 0 (the outer corrections start from 0).  The call
- * waits for the device and resets the kept solution to 0.  INVALID_ARG for
- * rel_tol < 0, max_iter < 1 or warm_start not 0/1. */
+ * warm_start (default 0): the initial guess of each step's first solve is 0, the
+ * previous step's first solution (1), or its linear extrapolation from the last two
+ * steps, 2 x(n-1) - x(n-2) (2; the previous solution while only one is kept); the
+ * outer corrections start from 0.  The call waits for the device and forgets the kept
+ * solutions.  INVALID_ARG for rel_tol < 0, max_iter < 1 or warm_start outside 0..2. */
 dolinc_status dolinc_implicit_set_solver(dolinc_implicit *solver, double rel_tol, int max_iter,
                                          unsigned spin_limit, int warm_start);
 

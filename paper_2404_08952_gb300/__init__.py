@@ -599,7 +599,7 @@ class Implicit:
 
     def set_solver(self, rel_tol=1e-10, max_iter=1000, spin_limit=1 << 23, warm_start=False):
         _check(load().dolinc_implicit_set_solver(self.handle, float(rel_tol), int(max_iter), int(spin_limit),
-                                                 1 if warm_start else 0))
+                                                 int(warm_start)))
 
     def set_layout(self, ell):
         """Row layout: ELL width 4 / 6 / 8, or 0 (per face slot)."""

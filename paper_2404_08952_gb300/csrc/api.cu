@@ -2007,7 +2007,7 @@ struct dolinc_implicit {
     double rel_tol = 1e-10;
     int max_iter = 1000;
     unsigned spin_limit = 1u << 23;
-    int warm = 0;                        // first solve of a step starts from the last step's solution
+    int warm = 0;                        // initial guess of a step's first solve: 0, 1 previous, 2 extrapolated
     int grid = 0, device = 0;
     int ell = 0;                         // ELL width of the rows (0: per slot)
     int64_t n = 0, ns = 0, ne = 0;       // cells, slots, row entries
@@ -2018,7 +2018,8 @@ struct dolinc_implicit {
     double *off = nullptr, *diag = nullptr, *bscale = nullptr;
     double *vec[9] = {};                 // x r rh p0 p1 v0 v1 s t
     double *R = nullptr, *Rn = nullptr, *un = nullptr;
-    double *xw = nullptr;                // the first solve's solution, kept between steps
+    double *xw[3] = {};                  // the steps' first solutions, rotated between steps
+    int xw_last = 0, xw_have = 0;        // buffer of the last step's solution; solutions kept (0..2)
     double *part = nullptr;
     double *scal = nullptr;              // ctrl block: scalars (256 B), then barrier words and status (512 B)
     double *life = nullptr;              // [2] iterations and solves since creation (not reset per step)
@@ -2105,7 +2106,7 @@ dolinc_status dolinc_implicit_create(dolinc_mesh *m, const dolinc_scheme *s, dou
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t n8 = al(8 * (size_t)std::max<int64_t>(imp->n, 1));
     const size_t pb = al(8 * IMP_NRED * (size_t)imp->sms * kImpMaxBlocksPerSm);
-    const size_t total = 15 * n8 + pb + kImpCtrl + 256;
+    const size_t total = 17 * n8 + pb + kImpCtrl + 256;
     cudaError_t e = cudaMalloc(&imp->mem, total);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -2120,7 +2121,7 @@ dolinc_status dolinc_implicit_create(dolinc_mesh *m, const dolinc_scheme *s, dou
     imp->R = reinterpret_cast<double *>(take(n8));
     imp->Rn = reinterpret_cast<double *>(take(n8));
     imp->un = reinterpret_cast<double *>(take(n8));
-    imp->xw = reinterpret_cast<double *>(take(n8));
+    for (auto &w : imp->xw) w = reinterpret_cast<double *>(take(n8));
     imp->part = reinterpret_cast<double *>(take(pb));
     imp->scal = reinterpret_cast<double *>(take(kImpCtrl));
     imp->bar = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(imp->scal) + 256);
@@ -2158,12 +2159,12 @@ dolinc_status dolinc_implicit_set_solver(dolinc_implicit *imp, double rel_tol, i
     if (!imp) return fail(DOLINC_ERR_INVALID_ARG, "null solver");
     if (!(rel_tol >= 0.0) || !std::isfinite(rel_tol)) return fail(DOLINC_ERR_INVALID_ARG, "rel_tol must be >= 0");
     if (max_iter < 1) return fail(DOLINC_ERR_INVALID_ARG, "max_iter must be >= 1");
-    if (warm_start != 0 && warm_start != 1) return fail(DOLINC_ERR_INVALID_ARG, "warm_start must be 0 or 1");
+    if (warm_start < 0 || warm_start > 2) return fail(DOLINC_ERR_INVALID_ARG, "warm_start must be 0, 1 or 2");
     int cur = 0;
     CU(cudaGetDevice(&cur));
     CU(cudaSetDevice(imp->device));
     CU(cudaDeviceSynchronize());
-    CU(cudaMemset(imp->xw, 0, 8 * (size_t)imp->n));     // the next warm start begins from 0
+    imp->xw_have = 0;                                   // the next warm start begins from 0
     CU(cudaSetDevice(cur));
     imp->rel_tol = rel_tol;
     imp->max_iter = max_iter;
@@ -2215,15 +2216,23 @@ dolinc_status dolinc_implicit_step(dolinc_implicit *imp, double *u, int n_outer,
         a.R = Rk;
         a.Rn = k == 0 ? nullptr : imp->Rn;
         a.un = k == 0 ? nullptr : imp->un;
-        // warm start: the step's first solve from the last step's first solution; the
+        // warm start of the step's first solve from the last steps' first solutions (the
+        // solution goes to the third buffer, which then becomes the last); the
         // outer corrections start from 0
-        a.warm = (imp->warm && k == 0) ? 1 : 0;
-        a.x = a.warm ? imp->xw : imp->vec[0];
+        const bool first = imp->warm && k == 0;
+        a.warm = first ? std::min(imp->warm, imp->xw_have) : 0;
+        a.x1 = imp->xw[imp->xw_last];
+        a.x2 = imp->xw[(imp->xw_last + 2) % 3];
+        a.x = first ? imp->xw[(imp->xw_last + 1) % 3] : imp->vec[0];
         cudaError_t e = cudaSuccess;
         timed(m, DOLINC_KERNEL_SOLVE, cs, [&] { e = launch_imp_solve(a, imp->ell, imp->grid, cs); });
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(DOLINC_ERR_CUDA, std::string("cooperative launch: ") + cudaGetErrorString(e));
+        }
+        if (first) {
+            imp->xw_last = (imp->xw_last + 1) % 3;
+            imp->xw_have = std::min(imp->xw_have + 1, 2);
         }
     }
     imp->last = cs;

@@ -23,8 +23,9 @@
 //                 most spin_limit times; one that gives up sets status bit 1 and an
 //                 abort word that ends the solve in every block.  The launch is
 //                 cooperative, so all blocks are resident and the waits end.
-//                 Warm start: x starts from the previous solve's solution kept in x
-//                 (r = b - A x, one extra product in the set-up phase); else from 0.
+//                 Warm start: x starts from the previous step's solution, or from the
+//                 linear extrapolation of the last two (r = b - A x0, one extra
+//                 product in the set-up phase); else from 0.
 //                 Vectors written inside the launch are read with ld.global.cg (L2),
 //                 never through the incoherent L1.  Rows per face slot (the default:
 //                 a thread's consecutive slot entries share L1 sectors) or in ELL form
@@ -230,24 +231,28 @@ __global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
     double *p = a.p[0], *v = a.v[0];
     bool ok;
 
-    // Set-up: b = bscale * rhs; x = 0, or the kept solution (warm start; read only
-    // here); r = rh = p = b - A x.
+    // Set-up: b = bscale * rhs; the initial guess x0 = 0, the previous step's solution
+    // x1 (warm 1), or 2 x1 - x2 (warm 2: linear extrapolation from the last two steps),
+    // formed for the neighbours on the fly and written to x; r = rh = p = b - A x0.
     {
         Red<2> red{{0.0, 0.0}};
         for (int c = t0; c < n; c += nth) {
             double rhs = a.R[c];
             if (a.Rn) rhs = (a.un[c] - a.u[c]) * a.inv_dt + a.theta * rhs + (1.0 - a.theta) * a.Rn[c];
             const double b = a.bscale[c] * rhs;
-            double r0 = b;
-            if (a.warm) r0 = b - row_sum<W>(a, c, a.x[c], [&](int j) { return a.x[j]; });
+            double r0 = b, x0 = 0.0;
+            if (a.warm) {
+                auto guess = [&](int j) { return a.warm == 2 ? fma(2.0, a.x1[j], -a.x2[j]) : a.x1[j]; };
+                x0 = guess(c);
+                r0 = b - row_sum<W>(a, c, x0, guess);
+            }
+            a.x[c] = x0;
             a.r[c] = r0;
             a.rh[c] = r0;
             p[c] = r0;
             red.v[0] = fma(b, b, red.v[0]);
             red.v[1] = fma(r0, r0, red.v[1]);
         }
-        if (!a.warm)
-            for (int c = t0; c < n; c += nth) a.x[c] = 0.0;
         ok = reduce_barrier(a, red, [&](const double *t) {
             stcg(sc + SC_RHO, t[1]);
             stcg(sc + SC_BB, t[0]);

@@ -36,7 +36,8 @@ struct ImpSolve {
     unsigned *bar;               // [0] arrivals, [32] generation, [64] abort
     unsigned *status;            // bit 1 barrier wait gave up, bit 2 breakdown, bit 3 not converged
     double tol2;                 // (relative tolerance)^2 on ||b - A x||^2 / ||b||^2
-    int warm;                    // 1: start from the solution already in x (else from 0)
+    int warm;                    // initial guess: 0 zero, 1 x1, 2 2 x1 - x2
+    const double *x1, *x2;       // the previous steps' solutions (warm >= 1, warm = 2)
     int max_iter;
     unsigned spin_limit;
 };

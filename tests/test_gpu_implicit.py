@@ -285,34 +285,40 @@ def test_rejections():
 
 @pytest.mark.parametrize("name", ["tet", "hexprism"])
 def test_warm_started_steps_equal_the_oracle(name):
-    """Warm start (the step's first solve from the last step's solution): every step
-    equals the oracle's step from the same state; the first step, which starts from 0
-    either way, takes the cold start's iterations.  (Whether later steps need fewer
-    iterations depends on how far the increment moves in a step, so it is measured by
-    the benchmark, not asserted here.)"""
+    """Warm start (the step's first solve from the last step's solution, 1, or from its
+    linear extrapolation from the last two steps, 2): every step equals the oracle's
+    step from the same state; the first step starts from 0 in every mode, and the
+    second uses the one kept solution in modes 1 and 2 alike.  (Whether later steps
+    need fewer iterations depends on how the increment moves between steps, so it is
+    measured by the benchmark, not asserted here.)"""
     m, O = mesh(name)
     adv = MESHES[name][1]
     M = dg.Mesh(m)
     sd, so = schemes(3, 1, adv)
     dt = cfl_dt(O, adv, 3.0)
     ws = dg.workspace(M, sd)
-    its = {}
-    for warm in (False, True):
+    its, res = {}, {}
+    for warm in (0, 1, 2):
         S = dg.Implicit(M, sd, dt, 1.0)
         S.set_solver(rel_tol=1e-13, warm_start=warm)
         u = field(m, 1, seed=6)
         ud = to_dev(M, u)
-        its[warm] = []
+        its[warm], res[warm] = [], []
         for _ in range(4):
             S.step(ud, ws)
             info = S.info()
             assert info["converged"], info
             its[warm].append(info["iterations"])
             got = M.from_lib(ud.cpu().numpy())
+            res[warm].append(got)
             want = O.semi_implicit_step(u, so, dt, 1.0)
             assert np.abs(got - want).max() <= 1e-10 * np.abs(want - u).max()
             u = got
-    assert its[True][0] == its[False][0]
+    assert its[1][0] == its[0][0] == its[2][0]
+    assert its[2][1] == its[1][1] and np.array_equal(res[2][1], res[1][1])
+    with pytest.raises(dg.DolincError) as e:
+        S.set_solver(warm_start=3)
+    assert e.value.status == 1
 
 
 @pytest.mark.parametrize("name,narrowest", [("tri", 4), ("tet", 4), ("hexprism", 6)])
