@@ -962,9 +962,12 @@ def run_implicit(args):
     # (precision, scheme order, theta, outer iterations, warm start, row layout: None = default per slot,
     #  6 = ELL of width 6)
     # warm start: 0 from zero, 1 from the last step's solution, 2 extrapolated from the last two
-    forms = [("fp32", 3, 0.5, 1, 2, None), ("fp32", 3, 0.5, 1, 1, None), ("fp32", 3, 0.5, 1, 0, None),
-             ("fp32", 3, 0.5, 1, 2, 6), ("fp32", 3, 1.0, 1, 2, None), ("fp64", 3, 0.5, 1, 2, None),
-             ("fp32", 3, 0.5, 2, 2, None), ("fp32", 5, 0.5, 2, 2, None), ("fp32", 5, 1.0, 1, 2, None)]
+    # (Crank-Nicolson damps no mode, so its increments' high-frequency parts alternate and
+    # extrapolation does not pay there; backward Euler's do not)
+    forms = [("fp32", 3, 0.5, 1, 1, None), ("fp32", 3, 0.5, 1, 0, None), ("fp32", 3, 0.5, 1, 2, None),
+             ("fp32", 3, 0.5, 1, 1, 6), ("fp32", 3, 1.0, 1, 2, None), ("fp32", 3, 1.0, 1, 1, None),
+             ("fp64", 3, 0.5, 1, 1, None), ("fp32", 3, 0.5, 2, 1, None), ("fp32", 5, 0.5, 2, 1, None),
+             ("fp32", 5, 1.0, 1, 2, None)]
 
     exact = np.asarray(exact, dtype=np.float64).reshape(-1)
 
@@ -1050,7 +1053,7 @@ def run_implicit(args):
         msE = timed_steps(lambda: dg.dolinc_rk_steps(M, sch, T / nE, nE, u, ws), 1)
         expl["%s_order%d_rk3" % (prec, order)] = {"steps": nE, "dt": T / nE, "ms": round(msE, 3), "l2": l2(u)}
         del ws, u
-    head = "fp32_order3_theta0.5_outer1_extrap"
+    head = "fp32_order3_theta0.5_outer1_warm"
     main = out[head]
     cpu = None
     if not args.no_oracle:      # the oracle's step (sparse LU) on a bounded sample of the workload
