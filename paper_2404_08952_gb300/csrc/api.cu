@@ -2016,7 +2016,7 @@ struct dolinc_implicit {
     void *rows = nullptr;                // nbr and off (their own allocation: the layout can change)
     int32_t *nbr = nullptr;
     double *off = nullptr, *diag = nullptr, *bscale = nullptr;
-    double *vec[9] = {};                 // x r rh p0 p1 v0 v1 s t
+    double *vec[7] = {};                 // x r rh p v s t
     double *R = nullptr, *Rn = nullptr, *un = nullptr;
     double *xw[3] = {};                  // the steps' first solutions, rotated between steps
     int xw_last = 0, xw_have = 0;        // buffer of the last step's solution; solutions kept (0..2)
@@ -2106,7 +2106,7 @@ dolinc_status dolinc_implicit_create(dolinc_mesh *m, const dolinc_scheme *s, dou
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t n8 = al(8 * (size_t)std::max<int64_t>(imp->n, 1));
     const size_t pb = al(8 * IMP_NRED * (size_t)imp->sms * kImpMaxBlocksPerSm);
-    const size_t total = 17 * n8 + pb + kImpCtrl + 256;
+    const size_t total = 15 * n8 + pb + kImpCtrl + 256;    // 7 vectors, diag, bscale, R, Rn, un, 3 kept solutions
     cudaError_t e = cudaMalloc(&imp->mem, total);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -2195,12 +2195,10 @@ dolinc_status dolinc_implicit_step(dolinc_implicit *imp, double *u, int n_outer,
     a.x = imp->vec[0];
     a.r = imp->vec[1];
     a.rh = imp->vec[2];
-    a.p[0] = imp->vec[3];
-    a.p[1] = imp->vec[4];
-    a.v[0] = imp->vec[5];
-    a.v[1] = imp->vec[6];
-    a.s = imp->vec[7];
-    a.t = imp->vec[8];
+    a.p = imp->vec[3];
+    a.v = imp->vec[4];
+    a.s = imp->vec[5];
+    a.t = imp->vec[6];
     a.part = imp->part;
     a.scal = imp->scal;
     a.life = imp->life;

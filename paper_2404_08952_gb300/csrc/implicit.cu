@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(IMP_BLOCK) k_imp_solve(ImpSolve a)
     const int nth = gridDim.x * IMP_BLOCK;
     const int t0 = blockIdx.x * IMP_BLOCK + threadIdx.x;
     double *sc = a.scal;
-    double *p = a.p[0], *v = a.v[0];
+    double *p = a.p, *v = a.v;
     bool ok;
 
     // Set-up: b = bscale * rhs; the initial guess x0 = 0, the previous step's solution

@@ -29,7 +29,7 @@ struct ImpSolve {
     const double *R, *Rn, *un;   // Rn, un null on the first solve
     double inv_dt, theta;
     double *u;                   // iterate, u += delta at the end
-    double *x, *r, *rh, *p[2], *v[2], *s, *t;   // [n] each
+    double *x, *r, *rh, *p, *v, *s, *t;   // [n] each
     double *part;                // [grid][IMP_NRED] per-block partial sums
     double *scal;                // solver scalars, SC_* layout
     double *life;                // [2] iterations and solves since the solver was created
