@@ -30,7 +30,7 @@
 //                 never through the incoherent L1.  Rows per face slot (the default:
 //                 a thread's consecutive slot entries share L1 sectors) or in ELL form
 //                 (width 4, 6 or 8, padded with zero weights: coalesced row loads, no
-//                 reuse; measured 9% slower on the hex/prism mesh).
+//                 reuse; measured no faster on the hex/prism mesh).
 #include "common.cuh"
 #include "implicit.cuh"
 
