@@ -322,6 +322,9 @@ def run_dolinc(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    summaries = rank == 0 and not args.no_variants and args.workload == "euler3d_tet64" and world == 1
+    # host inputs of the semi-implicit summary: forked workers, before CUDA starts
+    imp_inputs = _implicit_inputs(args, 100, 2) if summaries else None
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -494,9 +497,10 @@ def run_dolinc(args):
         line["variants"] = variants
     if stability:
         line["stability"] = stability
-    if rank == 0 and not args.no_variants and args.workload == "euler3d_tet64" and world == 1:
+    if summaries:
         line["indicator"] = _indicator_summary(args)
         line["batch"] = _batch_summary(args)
+        line["semi_implicit"] = _implicit_summary(args, imp_inputs)
     line["finite_after_steps"] = main["finite"]
     if "fp64" in results and args.precision != "fp64":
         f = results["fp64"]
@@ -943,7 +947,21 @@ def solve_alg_bytes(M, iterations, solves):
     return iterations * per_it + solves * per_solve
 
 
-def run_implicit(args):
+def _implicit_inputs(args, size, q):
+    """Host inputs of the semi-implicit workload (mesh, initial and exact cell averages
+    at t = imp_time), computed by forked workers: call before CUDA is initialised."""
+    import synth
+    from synth import fields
+    t0 = time.perf_counter()
+    workers = max(1, min(16, os.cpu_count() or 1))
+    w = synth.workload("adv3d_hexprism", order=3, size=size, q=q, workers=workers)
+    a = np.asarray(w["scheme"]["adv"], dtype=np.float64)
+    c = tuple(0.5 + a[k] * args.imp_time for k in range(3))
+    exact = fields.cell_average(w["mesh"], lambda p: fields.gaussian3d(p, centre=c), q=q, workers=workers)
+    return dict(w=w, exact=exact, size=size, q=q, seconds=time.perf_counter() - t0)
+
+
+def run_implicit(args, emit=True, forms=None, inputs=None, rk3_orders=(3, 5)):
     """Semi-implicit DOLINC steps (Sec 2.4: the weight part of every face value at the
     new level, c_r explicit) of the Gaussian pulse on the mixed hex/prism mesh.
 
@@ -951,18 +969,17 @@ def run_implicit(args):
     launch) at dt = imp_dt_factor times the explicit step, for backward Euler and
     Crank-Nicolson (one and two outer iterations), FP32 and FP64 residuals, orders 3
     and 5; the solve kernel's roofline; and, to t = imp_time, the L2 error against the
-    exact translated pulse beside SSP-RK3 at the explicit step, with each run's time."""
+    exact translated pulse beside SSP-RK3 at the explicit step, with each run's time.
+    emit=False returns the line instead of printing it; forms and inputs restrict the
+    forms and supply precomputed host inputs (_implicit_inputs)."""
     import synth
-    from synth import fields
     t_all = time.perf_counter()
-    workers = max(1, min(16, os.cpu_count() or 1))
-    size = args.size or 140
-    w = synth.workload("adv3d_hexprism", order=3, size=size, q=args.hp_quad, workers=workers)
+    if inputs is None:
+        inputs = _implicit_inputs(args, args.size or 140, args.hp_quad)
+    w, exact, size = inputs["w"], inputs["exact"], inputs["size"]
     a = np.asarray(w["scheme"]["adv"], dtype=np.float64)
     T = args.imp_time
-    c = tuple(0.5 + a[k] * T for k in range(3))
-    exact = fields.cell_average(w["mesh"], lambda p: fields.gaussian3d(p, centre=c), q=args.hp_quad, workers=workers)
-    t_host = time.perf_counter() - t_all
+    t_host = inputs["seconds"]
     import torch
     import paper_2404_08952_gb300 as dg
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -979,7 +996,7 @@ def run_implicit(args):
     # warm start: 0 from zero, 1 from the last step's solution, 2 extrapolated from the last two
     # (Crank-Nicolson damps no mode, so its increments' high-frequency parts alternate and
     # extrapolation does not pay there; backward Euler's do not)
-    forms = [("fp32", 3, 0.5, 1, 1, None), ("fp32", 3, 0.5, 1, 0, None), ("fp32", 3, 0.5, 1, 2, None),
+    forms = forms or [("fp32", 3, 0.5, 1, 1, None), ("fp32", 3, 0.5, 1, 0, None), ("fp32", 3, 0.5, 1, 2, None),
              ("fp32", 3, 0.5, 1, 1, 6), ("fp32", 3, 1.0, 1, 2, None), ("fp32", 3, 1.0, 1, 1, None),
              ("fp64", 3, 0.5, 1, 1, None), ("fp32", 3, 0.5, 2, 1, None), ("fp32", 5, 0.5, 2, 1, None),
              ("fp32", 5, 1.0, 1, 2, None)]
@@ -1056,7 +1073,7 @@ def run_implicit(args):
         del ws, S, S2, u
     # SSP-RK3 at the explicit step to the same time
     expl = {}
-    for prec, order in (("fp32", 3), ("fp32", 5)):
+    for prec, order in (("fp32", o) for o in rk3_orders):
         k, r = synth.STENCIL_OF_ORDER[order]
         sch = dg.Scheme(precision=prec, **dict(w["scheme"], k=k, r=r, n_diff=order - 1))
         ws = dg.workspace(M, sch)
@@ -1089,7 +1106,7 @@ def run_implicit(args):
             "config": {"workload": "adv3d_hexprism_implicit", "lattice": size, "cells": cells,
                        "headline": head, "flux": "upwind", "adv": list(w["scheme"]["adv"]),
                        "jitter": 0.2, "dt": dt, "dt_explicit": dt_exp, "cfl_sum": float(np.abs(a).sum() * dt / h),
-                       "rel_tol": args.imp_tol, "time": T, "quad": args.hp_quad, "peak_GBs": peak,
+                       "rel_tol": args.imp_tol, "time": T, "quad": inputs["q"], "peak_GBs": peak,
                        "peak_source": peak_src, "l2_flush": "inputs larger than L2 (vectors and rows > 300 MB)"},
             "roofline": main["solve_roofline"], "gpu_launches": main["launches"],
             "vs_explicit_rk3": {"t": T, "semi_implicit_ms": main["to_time"]["ms"], "semi_implicit_l2": main["to_time"]["l2"],
@@ -1097,7 +1114,23 @@ def run_implicit(args):
                                 "speedup": round(expl["fp32_order3_rk3"]["ms"] / main["to_time"]["ms"], 3)},
             "cpu_baseline": cpu, "forms": out, "explicit_rk3": expl, "host_input_seconds": round(t_host, 1),
             "seconds_total": time.perf_counter() - t_all}
+    if not emit:
+        return line
     print(json.dumps(line), flush=True)
+
+
+def _implicit_summary(args, inputs):
+    """The semi-implicit variant inside the default run, on a reduced mesh (the 100^3
+    hex/prism lattice, 1.5M cells; inputs built before CUDA starts): Crank-Nicolson from
+    the previous solution and backward Euler from the extrapolated one, each to t =
+    imp_time beside SSP-RK3 USR3 at the explicit step."""
+    a = argparse.Namespace(**vars(args))
+    a.steps, a.warmup, a.no_oracle, a.size = 10, 3, True, inputs["size"]
+    line = run_implicit(a, emit=False, inputs=inputs, rk3_orders=(3,),
+                        forms=[("fp32", 3, 0.5, 1, 1, None), ("fp32", 3, 1.0, 1, 2, None)])
+    keep = ("metric", "value", "unit", "ms_per_step", "config", "roofline", "vs_explicit_rk3", "forms",
+            "explicit_rk3", "host_input_seconds", "seconds_total")
+    return {k: line[k] for k in keep}
 
 
 def bl_mesh(growth, h0=0.002, ymax=0.3, nx=12, nz=3, x0=0.5, x1=1.0, dz=0.01):
